@@ -1,0 +1,387 @@
+#!/usr/bin/env python
+"""Time-to-solve and operator throughput of FS-FEM-T4 on the 2M-tet cantilever.
+
+Workload: the 200 x 40 x 42-cell Kuhn cantilever (2,016,000 tets, 354,363
+nodes, 1,063,089 DOF) on [0,10] x [0,1] x [0,1] m, interior nodes jittered
+by +/-0.1h (seed 2), E = 210 GPa, nu = 0.3, x = 0 clamped, traction
+(0, 0, -1e6) Pa on x = 10.  Synthetic input standing in for the paper's
+TetGen meshes of Table 3.
+
+One step = one whole solve through the C ABI: sfem_mesh_setup (FP64
+geometry, topology, smoothing domains, loads, BCs) + sfem_solve to a FP64
+true relative residual of 1e-8 with the FP32-inner / FP64-refined solver +
+sfem_destroy.  `value` is solves per second with the inputs resident in HBM
+(the metric's time-to-solve is ms_per_step); `e2e` is the same with host
+inputs and the displacement copied back, through the same API.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank solves its own copy of the workload (replicas: the
+path has no exchange step); value = all solves / max-over-ranks time.
+The reference arm times the FP64 CPU oracle on a bounded sample of the same
+workload on the host cores and prints the same line with impl=reference.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time-to-solve at rel res 1e-8 and operator GDOF/s, 2M-tet FS-FEM beam, 1 GB300"
+CELLS = (200, 40, 42)
+SEED = 2
+TOL = 1e-8
+# algorithmic bytes of one FP32 matrix-free operator application, per tet:
+# connectivity 16 + neighbour ids 16 + V_e-scaled gradients 36 + face
+# weights 16, and per DOF: u read 4 + y written 4
+ALG_BYTES_PER_TET = 16 + 16 + 36 + 16
+ALG_BYTES_PER_DOF = 8
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the PCG64 comparison solve")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle sample (cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_sample(slab_cells=10, iters=40):
+    """Time the FP64 oracle, as it stands, on a bounded sample of the
+    workload and scale to one full solve.
+
+    Sample: the first `slab_cells` cell layers (x) of the same beam
+    (slab_cells x 40 x 42 cells, same jitter, clamp and material) -> oracle
+    assembly (faces, Eq. 7, Eq. 9, Eq. 12 -> CSR) and `iters` Jacobi-PCG
+    iterations on it.  Full solve = assembly time x (tets ratio) +
+    per-iteration time x (nnz ratio) x the oracle's own iteration count to
+    1e-8 on the full beam (tests/golden/beam_2m_reference.json, written by
+    a script that runs only the oracle)."""
+    import numpy as np
+    from inputs.kuhn_beam import cantilever
+    from oracle import fsfem as F
+    from oracle import solve as OS
+
+    ref = json.load(open(os.path.join(ROOT, "tests", "golden", "beam_2m_reference.json")))
+    nx, ny, nz = CELLS
+    full = cantilever(nx, ny, nz, seed=SEED)
+    m = full.mesh
+    nslab_nodes = (slab_cells + 1) * (ny + 1) * (nz + 1)
+    ntet_slab = slab_cells * ny * nz * 6
+    xyz = m.xyz[:nslab_nodes]
+    tets = m.tets[:ntet_slab]
+    t0 = time.perf_counter()
+    asm = F.assemble(xyz, tets, full.E, full.nu)
+    t_asm = time.perf_counter() - t0
+    rng = np.random.default_rng(0)
+    K = asm.matrix()
+    dofs = full.dir_dofs[full.dir_dofs < 3 * nslab_nodes]
+    f = rng.standard_normal(asm.ndof)
+    A, b, _, _ = F.dirichlet_system(K, f, dofs, np.zeros(dofs.shape[0]))
+    t0 = time.perf_counter()
+    OS.jacobi_pcg(A, b, tol=1e-300, max_iter=iters, max_restarts=0)
+    t_it = (time.perf_counter() - t0) / iters
+    n_it = int(ref["iterations_1e-8"])
+    t_full = t_asm * (m.n_tets / ntet_slab) + t_it * (ref["nnz"] / asm.indices.size) * n_it
+    return {
+        "value": 1.0 / t_full, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
+        "sample": (f"oracle assembly of a {slab_cells}x{ny}x{nz}-cell slab of the beam ({ntet_slab} tets, "
+                   f"{t_asm:.2f} s) and {iters} Jacobi-PCG iterations on it ({t_it * 1e3:.1f} ms each); "
+                   f"scaled to {m.n_tets} tets, {ref['nnz']} nnz and the oracle's {n_it} iterations to 1e-8"),
+        "est_time_to_solve_s": t_full,
+        "threads_note": "numpy/BLAS default threading; scipy sparse products and Python loops single-threaded",
+    }
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    res = []
+    for _ in range(args.warmup):
+        oracle_sample(slab_cells=4, iters=10)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        res.append(oracle_sample())
+    wall = time.perf_counter() - t0
+    v = sum(r["value"] for r in res) / len(res)
+    cb = dict(res[-1])
+    cb["value"] = v
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"Kuhn cantilever {CELLS[0]}x{CELLS[1]}x{CELLS[2]} cells x 6 = 2,016,000 tets",
+                   "solver": "oracle Jacobi-PCG (FP64, CPU)", "tol": TOL},
+        "cpu_baseline": cb,
+        "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "sample_wall_s": wall,
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        try:
+            self.fh = open(self.path, "w")
+            cmd = ["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits", "-lms", "200"]
+            if self.gpu_id is not None:
+                cmd += ["-i", str(self.gpu_id)]
+            self.proc = subprocess.Popen(cmd, stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[3]) if v.lower() == "active"})
+        load = [r for r in rows if r[2] > 200.0] or rows
+        sm = sorted(r[0] for r in load)
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(r[2] for r in rows)}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def main():
+    args = parse()
+    world = _env_int("WORLD_SIZE", 1)
+    rank = _env_int("RANK", 0)
+    local = _env_int("LOCAL_RANK", 0)
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2001_08849_gb300 import sfem as S
+    from inputs.kuhn_beam import cantilever
+
+    nx, ny, nz = CELLS
+    prob = cantilever(nx, ny, nz, seed=SEED)
+    m = prob.mesh
+    host = [np.ascontiguousarray(a) for a in (m.xyz, m.tets.astype(np.int32), prob.dir_dofs.astype(np.int32),
+                                              prob.dir_vals, prob.trac_tris.astype(np.int32), prob.trac)]
+    dev = [torch.from_numpy(a).cuda() for a in host]
+    ndof = 3 * m.n_nodes
+    u_dev = torch.zeros(ndof, dtype=torch.float64, device="cuda")
+    u_host = torch.zeros(ndof, dtype=torch.float64).pin_memory().numpy()
+    h2d_bytes = sum(a.nbytes for a in host)
+    d2h_bytes = u_host.nbytes
+    opts_dev = S.solve_opts(kind=S.SFEM_SOLVE_IR32_64, op64=S.SFEM_OP_MF64, tol=TOL, u_on_device=True)
+    opts_host = S.solve_opts(kind=S.SFEM_SOLVE_IR32_64, op64=S.SFEM_OP_MF64, tol=TOL, u_on_device=False)
+    stream = torch.cuda.current_stream()
+    infos = []
+
+    def step_device(keep=False):
+        h, k = S.sfem_mesh_setup(*dev[:2], prob.E, prob.nu, *dev[2:], inputs_on_device=True)
+        info = S.sfem_solve(h, u_dev, opts_dev)
+        infos.append(info)
+        if keep:
+            return h, k
+        S.sfem_destroy(h)
+        return None
+
+    def step_host():
+        h, k = S.sfem_mesh_setup(*host[:2], prob.E, prob.nu, *host[2:], inputs_on_device=False)
+        info = S.sfem_solve(h, u_host, opts_host)
+        S.sfem_destroy(h)
+        return info
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    for _ in range(max(args.warmup, 3)):
+        step_device()
+    infos.clear()
+    gpu_id = None
+    try:
+        gpu_id = str(torch.cuda.get_device_properties(local).uuid)
+        if not gpu_id.startswith("GPU-"):
+            gpu_id = "GPU-" + gpu_id
+    except Exception:
+        gpu_id = os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[local] if world == 1 else None
+    clocks = ClockSampler(gpu_id)
+    barrier()
+    clocks.start()
+    launches0 = S.sfem_launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step_device()
+    e1.record(stream)
+    barrier()
+    launches = S.sfem_launch_count() - launches0
+    clk = clocks.stop()
+    t_dev = max_over_ranks(e0.elapsed_time(e1) / 1e3)
+    value = world * args.steps / t_dev
+    iters = [i["iterations"] for i in infos]
+    relres = max(i["true_relres"] for i in infos)
+
+    # e2e through the same API with host buffers (H2D + D2H inside)
+    step_host()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step_host()
+    barrier()
+    t_e2e = max_over_ranks(time.perf_counter() - t0)
+    e2e_value = world * args.steps / t_e2e
+
+    # dominant kernel: the FP32 matrix-free operator of the inner CG
+    h, keep = step_device(keep=True)
+    ms_mf32 = S.sfem_time_operator(h, S.SFEM_OP_MF32, reps=50)
+    ms_mf64 = S.sfem_time_operator(h, S.SFEM_OP_MF64, reps=10)
+    S.sfem_destroy(h)
+    alg_bytes = ALG_BYTES_PER_TET * m.n_tets + ALG_BYTES_PER_DOF * ndof
+    achieved = alg_bytes / (ms_mf32 * 1e-3) / 1e9
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    traffic = None
+    try:
+        tr = json.load(open(os.path.join(ROOT, "profiles", "mf32_traffic.json")))
+        if tr.get("kernel_version") == S.lib.sfem_version() and tr.get("ndof") == ndof:
+            traffic = tr["dram_bytes_per_apply"]
+    except Exception:
+        pass
+
+    forms = {}
+    if not args.no_forms and rank == 0:
+        # plain FP64 Jacobi-PCG on the assembled CSR, same workload (once)
+        torch.cuda.synchronize()
+        ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ea.record(stream)
+        hh, kk = S.sfem_mesh_setup(*dev[:2], prob.E, prob.nu, *dev[2:], inputs_on_device=True)
+        S.sfem_assemble(hh)
+        x = torch.zeros(ndof, dtype=torch.float64, device="cuda")
+        inf = S.sfem_solve(hh, x, S.solve_opts(kind=S.SFEM_SOLVE_PCG64, op64=S.SFEM_OP_CSR64, tol=TOL,
+                                                u_on_device=True), check=False)
+        eb.record(stream)
+        torch.cuda.synchronize()
+        ms_csr = S.sfem_time_operator(hh, S.SFEM_OP_CSR64, reps=10)
+        S.sfem_destroy(hh)
+        forms["pcg64_csr"] = {"time_to_solve_s": ea.elapsed_time(eb) / 1e3, "iterations": inf["iterations"],
+                              "true_relres": inf["true_relres"], "status": inf["status"],
+                              "csr64_apply_ms": ms_csr}
+        forms["ir32_64_mf"] = {"time_to_solve_s": t_dev / args.steps, "iterations": iters[-1],
+                               "true_relres": relres}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            cpu = oracle_sample()
+        except Exception as ex:  # the oracle is a baseline, not the product
+            cpu = {"value": None, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
+                   "sample": f"failed: {ex}"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": f"Kuhn cantilever {nx}x{ny}x{nz} cells x 6 = {m.n_tets} tets, "
+                                   f"{m.n_nodes} nodes, {ndof} DOF, jitter seed {SEED}",
+                       "solver": "IR32_64: FP64 residual/update, FP32 matrix-free Jacobi-PCG inner",
+                       "tol": TOL, "step": "sfem_mesh_setup + sfem_solve + sfem_destroy",
+                       "l2": "no flush: operator data per step exceeds the 129 MB L2",
+                       "parallelism": f"replicas x{world}"},
+            "time_to_solve_s": t_dev / args.steps,
+            "iterations": iters, "true_relres_max": relres,
+            "operator_gdof_per_s": ndof / (ms_mf32 * 1e-3) / 1e9,
+            "operator_gdof_per_s_fp64_mf": ndof / (ms_mf64 * 1e-3) / 1e9,
+            "gpu_launches": int(launches),
+            "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": int(h2d_bytes),
+                    "d2h_bytes_per_step": int(d2h_bytes)},
+            "roofline": {"kernel": "FP32 matrix-free operator apply (k_mf_strain + k_mf_stress)",
+                         "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "alg_bytes_per_apply": alg_bytes, "ms_per_apply": ms_mf32,
+                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst, kernel timed alone)"
+                         if "hbm_gbs" in peaks else "fallback 6800 GB/s"},
+            "clocks": clk,
+            "forms": forms,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,214 @@
+/*
+ * sfem.h — C ABI of the GB300 FS-FEM-T4 library (libsfem.so).
+ *
+ * Face-based smoothed FEM with 4-node tetrahedra for 3D linear elasticity
+ * (Section 2.1, STEP 1-5): per-tet volumes and shape gradients (Eq. 1,
+ * Eq. 10), face smoothing domains (Fig. 1; V_k = (V_i + V_j)/4 on interior
+ * faces, V_i/4 on exterior faces), smoothed gradients (Eq. 4-7), the
+ * smoothed stiffness K = sum_k V_k Bbar_k^T c Bbar_k (Eq. 9), its CSR
+ * assembly (the COO/CSC route of Section 3.3, Eq. 12), and iterative solves
+ * of K d = f (Eq. 8) with essential conditions imposed by elimination
+ * (STEP 5).  All compute runs in sm_103a CUDA kernels on the stream passed
+ * to sfem_mesh_setup; there is no CPU fallback.
+ *
+ * Conventions (all entry points):
+ *   - node and tet ids are 0-based; DOF = 3*node + component (x, y, z);
+ *   - vectors of nrhs load cases are stored one after another (ndof each);
+ *   - strain/stress order is Voigt (xx, yy, zz, yz, zx, xy), engineering
+ *     shears (Eq. 4, Eq. 6); the material matrix is isotropic (E, nu);
+ *   - every call returns an sfem_status; the library never aborts and never
+ *     traps on the device.  On error, sfem_last_error() gives a message for
+ *     the calling thread;
+ *   - input arrays are borrowed and copied; the caller keeps ownership;
+ *   - device memory is owned by the context and freed by sfem_destroy.
+ */
+#ifndef SFEM_H
+#define SFEM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SFEM_API_VERSION 1
+
+typedef enum sfem_status {
+  SFEM_OK = 0,
+  SFEM_EINVAL = -1,      /* bad argument (null pointer, size, option) */
+  SFEM_EMESH = -2,       /* invalid mesh: node id out of range, degenerate or
+                            non-finite tet, face shared by more than 2 tets,
+                            node in more tets than the library supports */
+  SFEM_ENOMEM = -3,      /* device allocation failed */
+  SFEM_ENOCONV = -4,     /* iteration limit reached above the tolerance */
+  SFEM_EBREAKDOWN = -5,  /* CG breakdown: p^T A p <= 0 or non-finite scalar */
+  SFEM_ECUDA = -6,       /* CUDA runtime error */
+  SFEM_ETIMEOUT = -7     /* a bounded device-side wait gave up */
+} sfem_status;
+
+typedef struct sfem_ctx sfem_ctx;
+
+/* Optional device allocator (e.g. a framework's caching allocator).  When
+ * alloc is NULL the library uses cudaMallocAsync/cudaFreeAsync on the
+ * context stream.  alloc returns NULL on failure. */
+typedef void *(*sfem_alloc_fn)(size_t bytes, void *stream, void *user);
+typedef void (*sfem_free_fn)(void *ptr, size_t bytes, void *stream, void *user);
+
+typedef struct sfem_opts {
+  int inputs_on_device;  /* 1: xyz, tets, dir_*, trac_* are device pointers */
+  int nrhs;              /* load cases in trac (>= 1; 0 is read as 1) */
+  sfem_alloc_fn alloc;
+  sfem_free_fn free;
+  void *alloc_user;
+  int reserved[8];       /* must be zero */
+} sfem_opts;
+
+typedef struct sfem_mesh_info {
+  int64_t n_nodes, n_tets, ndof;
+  int64_t n_faces, n_interior, n_boundary;   /* N_f = N_i + N_b */
+  int64_t n_dir, nrhs;
+  int64_t nnz;             /* scalar non-zeros of K (0 until sfem_assemble) */
+  int64_t n_slivers;       /* tets with quality 6 sqrt(2) V / l_rms^3 < 1e-3 */
+  int64_t n_bad_tets;      /* degenerate (V <= 1e-14 l_rms^3) or non-finite */
+  int64_t n_bad_faces;     /* faces shared by more than two tets */
+  int64_t max_tets_per_node;
+  double min_quality, min_volume, max_volume;
+  double setup_ms;         /* device time of the last setup */
+} sfem_mesh_info;
+
+/* Device CSR of the unconstrained K, owned by the context (valid until
+ * sfem_destroy).  Rows and columns are DOFs; column indices ascend within a
+ * row; every DOF pair of two nodes sharing a face stencil is present, even
+ * when its value is numerically zero. */
+typedef struct sfem_csr {
+  int64_t n_rows;
+  int64_t nnz;
+  const int64_t *row_ptr;  /* n_rows + 1 */
+  const int32_t *col;      /* nnz */
+  const double *val;       /* nnz */
+} sfem_csr;
+
+/* Operators for sfem_apply and for the FP64 steps of sfem_solve. */
+enum {
+  SFEM_OP_CSR64 = 0,  /* assembled CSR, FP64 (needs sfem_assemble) */
+  SFEM_OP_MF64 = 1,   /* matrix-free, FP64 */
+  SFEM_OP_MF32 = 2    /* matrix-free, FP32 (FP64 geometry rounded once) */
+};
+
+/* Solver kinds. */
+enum {
+  SFEM_SOLVE_PCG64 = 0,        /* Jacobi-PCG, all FP64 */
+  SFEM_SOLVE_IR32_64 = 1,      /* FP64 residual/update around FP32 Jacobi-PCG */
+  SFEM_SOLVE_FPCG_LEARNED = 2  /* flexible PCG with a learned coarse correction */
+};
+
+typedef struct sfem_solve_opts {
+  int kind;            /* SFEM_SOLVE_* */
+  int op64;            /* operator of FP64 steps: SFEM_OP_CSR64 or SFEM_OP_MF64 */
+  int rhs;             /* load case to solve (0 .. nrhs-1) */
+  int u_on_device;     /* 1: u is a device pointer */
+  int warm_start;      /* 1: u holds an initial guess (Dirichlet DOFs are reset) */
+  int max_iter;        /* total CG iterations (0: 200000) */
+  double tol;          /* relative true residual ||b - A u|| / ||b|| (0: 1e-8) */
+  double inner_tol;    /* IR: FP32 residual reduction that triggers a reliable update (0: 0.1) */
+  int max_outer;       /* IR: reliable updates at most (0: 200) */
+  int check_every;     /* iterations between host convergence checks (0: 32) */
+  const void *learned; /* FPCG_LEARNED: an sfem_learned handle */
+  int reserved[6];
+} sfem_solve_opts;
+
+typedef struct sfem_solve_info {
+  int status;              /* sfem_status of the solve */
+  int iterations;          /* CG iterations (inner iterations for IR) */
+  int outer_iterations;    /* IR refinement steps / true-residual restarts */
+  int fallbacks;           /* FPCG: iterations that fell back to Jacobi */
+  double true_relres;      /* ||b - A u||_2 / ||b||_2 in FP64, after exit */
+  double bnorm;            /* ||b||_2 */
+  double solve_ms;         /* device time of the solve */
+} sfem_solve_info;
+
+/* sfem_mesh_setup — geometry, topology, smoothing domains, loads, BCs.
+ *
+ * Computes on the device, in FP64: tet volumes by Eq. 10 (absolute value)
+ * and shape gradients (Eq. 1), mesh checks, the tet-neighbour and face
+ * tables (the Face_in/Face_out information of Section 3.2, Fig. 7, built
+ * from the tets instead of a TetGen face file), the smoothing-domain
+ * volumes V_k (Fig. 1), the nodal loads of piecewise-constant tractions
+ * (t * A / 3 per triangle node, A by Eq. 11; "nodal load" of Section 3.3
+ * STEP 5), the Dirichlet mask and the Jacobi diagonal of A.
+ *
+ *   xyz       n_nodes x 3 FP64, row-major
+ *   tets      n_tets x 4 int32, node ids (either orientation)
+ *   E, nu     Young's modulus (> 0) and Poisson ratio (-1 < nu < 0.5)
+ *   dir_dofs  n_dir DOFs with prescribed values dir_vals (may be 0 / NULL)
+ *   trac_tris n_tri x 3 node ids of boundary triangles
+ *   trac      nrhs x n_tri x 3 FP64 traction vectors (Pa), constant per triangle
+ *   opts      may be NULL (host inputs, nrhs = 1, default allocator)
+ *   stream    cudaStream_t for all work of this context (NULL: legacy stream)
+ *
+ * Returns SFEM_EMESH (with counts in sfem_get_info) for invalid meshes.
+ * The context is created on the current CUDA device. */
+int sfem_mesh_setup(sfem_ctx **out, const double *xyz, int64_t n_nodes,
+                    const int32_t *tets, int64_t n_tets, double E, double nu,
+                    const int32_t *dir_dofs, const double *dir_vals, int64_t n_dir,
+                    const int32_t *trac_tris, const double *trac, int64_t n_tri,
+                    const sfem_opts *opts, void *stream);
+
+/* sfem_assemble — CSR of the unconstrained smoothed stiffness (Eq. 9).
+ * Sums the 12x12 (exterior) and 15x15 (interior) face matrices
+ * V_k Bbar_k^T c Bbar_k (Section 3.3, STEP 1-5; Eq. 12 counts their
+ * entries) directly into canonical CSR.  FP64.  The arrays in *out are
+ * device pointers owned by the context. */
+int sfem_assemble(sfem_ctx *ctx, sfem_csr *out);
+
+/* sfem_apply — y = A u with A = P K P + (I - P) (STEP 5 by elimination;
+ * P masks the free DOFs).  u and y are device pointers of nrhs * ndof
+ * entries: double for SFEM_OP_CSR64 / SFEM_OP_MF64, float for SFEM_OP_MF32.
+ * The matrix-free operators evaluate Eq. 9 as: per tet strain
+ * eps_e = B_e u_e, per face eps_k = (V_i eps_i + V_j eps_j) / (V_i + V_j)
+ * (Eq. 2-3 with V_k = (V_i+V_j)/4), stress c eps_k, scattered back through
+ * the smoothed gradients. */
+int sfem_apply(sfem_ctx *ctx, const void *u, void *y, int op, int nrhs);
+
+/* sfem_solve — solve A u = b, b = P (f - K g) + (I - P) g (Eq. 8 with
+ * STEP 5; f from the tractions plus f_extra, g the prescribed values).
+ * f_extra: NULL or ndof FP64 nodal forces (host unless u_on_device).
+ * u: ndof FP64, output (and input for warm_start).  Stops on the FP64 true
+ * relative residual <= tol.  Returns SFEM_ENOCONV / SFEM_EBREAKDOWN with
+ * the final residual in info. */
+int sfem_solve(sfem_ctx *ctx, const double *f_extra, double *u,
+               const sfem_solve_opts *opts, sfem_solve_info *info);
+
+int sfem_get_info(const sfem_ctx *ctx, sfem_mesh_info *info);
+
+/* Copies of setup results to HOST buffers (for checks and post-processing). */
+int sfem_get_geometry(sfem_ctx *ctx, double *vol /* n_tets */,
+                      double *grad /* n_tets x 4 x 3 */);
+int sfem_get_neighbors(sfem_ctx *ctx, int32_t *nbr /* n_tets x 4, -1 exterior */);
+/* Faces in library order: nodes (a, b, c, d0, d1) with d1 = -1 on exterior
+ * faces (a < b < c), adjacent tets (t0, t1 = -1 exterior), and V_k. */
+int sfem_get_faces(sfem_ctx *ctx, int32_t *nodes /* n_faces x 5 */,
+                   int32_t *tets /* n_faces x 2 */, double *Vk /* n_faces */);
+int sfem_get_rhs(sfem_ctx *ctx, double *b /* ndof */, int rhs);
+int sfem_get_diag(sfem_ctx *ctx, double *diag /* ndof, diagonal of A */);
+
+/* Measurement helpers (no counterpart in the paper).
+ * sfem_time_operator: launches the raw operator y = K u (no masking) of
+ * `op` `reps` times on library-owned scratch vectors, exactly as the solvers
+ * launch it, between CUDA events on the context stream; writes the mean
+ * device time per application in milliseconds.
+ * sfem_launch_count: kernels launched by this process through the library
+ * so far (graph launches count their kernel nodes; captures do not count). */
+int sfem_time_operator(sfem_ctx *ctx, int op, int reps, double *ms_per_apply);
+int64_t sfem_launch_count(void);
+
+void sfem_destroy(sfem_ctx *ctx);
+const char *sfem_strerror(int status);
+const char *sfem_last_error(void);
+int sfem_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SFEM_H */

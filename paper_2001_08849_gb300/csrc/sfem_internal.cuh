@@ -1,0 +1,219 @@
+// Internal declarations of the FS-FEM-T4 CUDA library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/sfem.h"
+
+namespace sfem {
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+struct Error {
+  int status;
+  std::string msg;
+};
+
+void set_last_error(const std::string &msg);
+
+#define SFEM_CUDA(call)                                                               \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess)                                                            \
+      throw ::sfem::Error{SFEM_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_) + \
+                                          " (" + __FILE__ + ":" + std::to_string(__LINE__) + ")"}; \
+  } while (0)
+
+// kernel-launch accounting (sfem_launch_count); launches recorded during a
+// stream capture are not counted, graph launches add their node count
+void count_launches(int64_t n);
+bool capturing();
+void set_capturing(bool on);
+
+#define SFEM_CHECK_LAUNCH()                        \
+  do {                                             \
+    SFEM_CUDA(cudaGetLastError());                 \
+    if (!::sfem::capturing()) ::sfem::count_launches(1); \
+  } while (0)
+
+#define SFEM_REQUIRE(cond, code, text)                       \
+  do {                                                       \
+    if (!(cond)) throw ::sfem::Error{(code), std::string(text)}; \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// device status word written by setup kernels (no traps: counters only)
+// ---------------------------------------------------------------------------
+struct DevStatus {
+  unsigned long long bad_index;       // node id out of range
+  unsigned long long bad_tets;        // degenerate or non-finite tets
+  unsigned long long slivers;         // quality < 1e-3
+  unsigned long long bad_faces;       // face with more than two tets
+  unsigned long long too_many_inc;    // node in more than kMaxInc tets
+  unsigned long long max_inc;         // largest node->tet incidence
+  unsigned long long bad_dir;         // Dirichlet DOF out of range
+  unsigned long long bad_tri;         // traction triangle node out of range
+  unsigned long long minq_bits;       // min quality, as ordered bits of a double
+  unsigned long long minv_bits;       // min volume
+  unsigned long long maxv_bits;       // max volume
+};
+
+// Largest node->tet incidence handled by the adjacency kernels.
+constexpr int kMaxInc = 128;
+
+// Solver scalars, kept on the device for the whole solve so that no
+// iteration needs a host round trip.
+struct SolveScalars {
+  double rz, rz_prev, pq, rr, alpha, beta;
+  double bb;        // ||r||^2 at the last (re)start
+  double tol2;      // squared stopping threshold on ||r||^2
+  double rmax2;     // largest ||r||^2 since the last reliable update
+  double delta2;    // reliable-update trigger: ||r||^2 < delta2 * rmax2 (0: never)
+  int done;         // 1: stop the captured iterations; kernels become no-ops
+  int status;       // 0 ok, 1 breakdown
+  int iter;         // completed iterations
+  int max_iter;
+  int reason;       // why done: 1 converged, 2 reliable update due, 3 iteration cap
+  int pad[3];
+};
+
+// ---------------------------------------------------------------------------
+// allocator
+// ---------------------------------------------------------------------------
+struct Allocator {
+  sfem_alloc_fn alloc = nullptr;
+  sfem_free_fn free = nullptr;
+  void *user = nullptr;
+  cudaStream_t stream = nullptr;
+  struct Block {
+    void *p;
+    size_t n;
+  };
+  std::vector<Block> blocks;
+
+  void *raw(size_t bytes);
+  void drop(void *p);  // free one block early (temporaries)
+  void release_all();
+  template <class T>
+  T *get(size_t n) {
+    return static_cast<T *>(raw(n * sizeof(T)));
+  }
+};
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+struct Csr {
+  int64_t n_rows = 0, nnz = 0;
+  int64_t *row_ptr = nullptr;
+  int32_t *col = nullptr;
+  double *val = nullptr;
+  // node-level adjacency (pattern of 3x3 blocks)
+  int64_t *nptr = nullptr;   // n_nodes + 1
+  int32_t *nadj = nullptr;   // nptr[n_nodes]
+};
+
+struct Ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  Allocator mem;
+
+  int64_t n_nodes = 0, n_tets = 0, ndof = 0, n_faces = 0, n_int = 0, n_bnd = 0;
+  int64_t n_dir = 0, n_tri = 0;
+  int nrhs = 1;
+  double E = 0, nu = 0, lam = 0, mu = 0;
+
+  // inputs (device copies)
+  double *xyz = nullptr;      // n_nodes*3
+  int32_t *tets = nullptr;    // n_tets*4 (int4-aligned)
+  int32_t *dir_dofs = nullptr;
+  double *dir_vals = nullptr;
+
+  // FP64 geometry
+  double *vol = nullptr;      // n_tets
+  double *grad = nullptr;     // n_tets*12: grad N_0..3 (x,y,z)
+
+  // topology
+  int64_t *n2t_ptr = nullptr; // n_nodes + 1
+  int32_t *n2t = nullptr;     // 4*n_tets, tets of each node ascending
+  int32_t *nbr = nullptr;     // n_tets*4: tet across the face opposite vertex a, -1
+  int32_t *nbr_slot = nullptr;// n_tets*4: local vertex of nbr not on that face
+  int32_t *face_tet = nullptr;// n_faces*2
+  int32_t *face_slot = nullptr;// n_faces*2
+  double *Vk = nullptr;       // n_faces
+
+  // matrix-free operator data: Gs = V_e grad N_1..3 (planar, 9 x n_tets),
+  // kap[e][a] = 1/(4 (V_e + V_nbr)) or 1/(4 V_e) on exterior faces.
+  double *Gs64 = nullptr;
+  double *kap64 = nullptr;    // n_tets*4
+  float *Gs32 = nullptr;
+  float *kap32 = nullptr;     // n_tets*4
+
+  // boundary conditions and loads
+  uint8_t *dmask = nullptr;   // ndof: 1 free, 0 prescribed
+  double *g = nullptr;        // ndof prescribed values (0 elsewhere)
+  double *f = nullptr;        // nrhs*ndof traction loads
+  double *diag = nullptr;     // ndof diagonal of K
+  double *dinv64 = nullptr;   // ndof: P/diag (0 on prescribed DOFs)
+  float *dinv32 = nullptr;
+  std::vector<double> bnorm;  // ||b|| per rhs
+
+  Csr csr;
+  bool assembled = false;
+
+  DevStatus *dstat = nullptr;
+  DevStatus hstat{};
+  double setup_ms = 0;
+
+  // scratch for the operators and reductions
+  void *w_scratch = nullptr;     // per-tet strains (8 values per tet per rhs)
+  size_t w_bytes = 0;
+  double *red_partial = nullptr; // per-block partial sums
+  int red_blocks = 0;
+  unsigned int *tickets = nullptr; // zeroed ticket counters of grid reductions
+  SolveScalars *scal = nullptr;
+  SolveScalars *h_scal = nullptr; // pinned host copies (2 slots)
+  cudaStream_t cap_stream = nullptr; // private stream used only for graph capture
+};
+
+// ---------------------------------------------------------------------------
+// helpers shared between translation units
+// ---------------------------------------------------------------------------
+inline int grid_for(int64_t n, int block) { return (int)((n + block - 1) / block); }
+
+// exclusive scan of n int32 counts into out[0..n] (int64); returns out[n]
+int64_t scan_counts(Ctx &c, const int32_t *counts, int64_t n, int64_t *out);
+
+// operators (operator.cu): raw K u (no masking) for nrhs vectors
+void apply_mf64(Ctx &c, const double *u, double *y, int nrhs, double *energy_partial);
+void apply_mf32(Ctx &c, const float *u, float *y, int nrhs, double *energy_partial);
+void apply_csr64(Ctx &c, const double *u, double *y, int nrhs, const double *dotv,
+                 double *dot_partial);
+void ensure_w_scratch(Ctx &c, size_t bytes);
+// stream-explicit launchers used inside captured solver iterations; kernels
+// return immediately when *done != 0
+template <class T>
+void launch_mf_strain(Ctx &c, cudaStream_t st, const T *Gs, const T *u, int nrhs, T *w, const int *done);
+template <class T>
+void launch_mf_stress(Ctx &c, cudaStream_t st, const T *Gs, const T *kap, const T *w, T *y, int nrhs,
+                      double *energy_out, const int *done);
+void launch_csr64(Ctx &c, cudaStream_t st, const double *u, double *y, const double *dotv, double *dot_out,
+                  const int *done);
+int reduction_blocks();
+// sum of squares of x[0..n) on the device, FP64 accumulation (synchronises)
+double device_norm2(Ctx &c, const double *x, int64_t n);
+
+// setup pieces used by other units
+void compute_diag(Ctx &c);
+
+}  // namespace sfem
+
+// opaque handle of the ABI
+struct sfem_ctx {
+  sfem::Ctx c;
+};

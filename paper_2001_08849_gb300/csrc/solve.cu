@@ -1,0 +1,492 @@
+// Iterative solves of K d = f (Eq. 8) with essential conditions imposed by
+// elimination (STEP 5): A = P K P + (I - P), b = P (f - K g) + (I - P) g.
+//
+// The paper calls a direct solver (Section 3.3); the library runs
+// Jacobi-preconditioned CG on the GPU instead:
+//   PCG64    all vectors, scalars and the operator in FP64;
+//   IR32_64  mixed precision: Jacobi-PCG iterations on the FP32 matrix-free
+//            operator with FP32 vectors (scalars and reductions in FP64)
+//            accumulate a correction d; at reliable updates (FP32 residual
+//            down by inner_tol, or at the tolerance) the FP64 solution takes
+//            u += d, the FP64 true residual f - K u replaces the FP32 one and
+//            CG goes on in the same Krylov space (search direction kept),
+//            so the refinement costs no restart.
+// Iterations run as captured CUDA graphs of `check_every` iterations.  The
+// CG scalars live in device memory; once converged, a device flag turns the
+// remaining captured kernels into no-ops, so the host only polls the
+// scalars between graph launches (two launches kept in flight).
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "reduce.cuh"
+#include "sfem_internal.cuh"
+
+namespace sfem {
+
+constexpr int kVecBlock = 256;
+
+template <class T>
+struct PcgVecs {
+  T *x, *r, *p, *q;
+  const T *dinv;
+  const uint8_t *dmask;
+  int64_t n;
+};
+
+// r must already hold the masked residual.  p = D^-1 r, q = 0, and the
+// scalars rz = r.D^-1 r, rr = r.r are set; done when rr <= tol2.
+template <class T>
+__global__ void __launch_bounds__(kVecBlock) k_pcg_init(PcgVecs<T> v, SolveScalars *S, double tol2, int max_iter,
+                                                        double delta2, double *partials, unsigned int *ticket) {
+  double rz = 0.0, rr = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * kVecBlock + threadIdx.x; i < v.n; i += (int64_t)gridDim.x * kVecBlock) {
+    const T ri = v.r[i];
+    const T zi = v.dinv[i] * ri;
+    v.p[i] = zi;
+    v.q[i] = T(0);
+    rz += (double)zi * (double)ri;
+    rr += (double)ri * (double)ri;
+  }
+  double vv[2] = {rz, rr};
+  if (grid_sum<kVecBlock, 2>(vv, partials, ticket, nullptr) && threadIdx.x == 0) {
+    S->rz = vv[0];
+    S->rz_prev = vv[0];
+    S->rr = vv[1];
+    S->bb = vv[1];
+    S->rmax2 = vv[1];
+    S->tol2 = tol2;
+    S->delta2 = delta2;
+    S->iter = 0;
+    S->max_iter = max_iter;
+    S->status = 0;
+    S->reason = 0;
+    S->done = 0;
+    if (vv[1] <= tol2) {
+      S->done = 1;
+      S->reason = 1;
+    } else if (max_iter <= 0) {
+      S->done = 1;
+      S->reason = 3;
+    }
+    S->pq = 0.0;
+  }
+}
+
+// Reliable update (mixed precision): r has been replaced by the true
+// residual; keep the search direction, p = D^-1 r + beta p with
+// beta = (r.D^-1 r) / rz_prev, and resume.  rmax2 restarts from ||r||^2.
+template <class T>
+__global__ void __launch_bounds__(kVecBlock) k_pcg_replace(PcgVecs<T> v, SolveScalars *S, int max_iter,
+                                                           double *partials, unsigned int *ticket) {
+  double rz = 0.0, rr = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * kVecBlock + threadIdx.x; i < v.n; i += (int64_t)gridDim.x * kVecBlock) {
+    const T ri = v.r[i];
+    const T zi = v.dinv[i] * ri;
+    rz += (double)zi * (double)ri;
+    rr += (double)ri * (double)ri;
+  }
+  double vv[2] = {rz, rr};
+  __shared__ double beta_s;
+  const bool last = grid_sum<kVecBlock, 2>(vv, partials, ticket, nullptr);
+  if (last && threadIdx.x == 0) {
+    beta_s = vv[0] / S->rz_prev;
+    S->beta = beta_s;
+    S->rz = vv[0];
+    S->rr = vv[1];
+    S->rmax2 = vv[1];
+    S->max_iter = max_iter;
+    S->reason = 0;
+    S->done = (vv[1] <= S->tol2) ? 1 : 0;
+    if (S->done) S->reason = 1;
+  }
+}
+
+// second half of the replacement: p = D^-1 r + beta p, q = 0
+template <class T>
+__global__ void __launch_bounds__(kVecBlock) k_pcg_replace_dir(PcgVecs<T> v, const SolveScalars *S) {
+  const T b = (T)S->beta;
+  for (int64_t i = (int64_t)blockIdx.x * kVecBlock + threadIdx.x; i < v.n; i += (int64_t)gridDim.x * kVecBlock) {
+    v.p[i] = v.dinv[i] * v.r[i] + b * v.p[i];
+    v.q[i] = T(0);
+  }
+}
+
+// x += alpha p, r -= alpha P q, then rz_new, rr; the last block sets beta,
+// the convergence flag and the reliable-update trigger.
+template <class T>
+__global__ void __launch_bounds__(kVecBlock) k_pcg_update(PcgVecs<T> v, SolveScalars *S, double *partials,
+                                                          unsigned int *ticket) {
+  if (S->done) return;
+  const double pq = S->pq, rz_old = S->rz;
+  const double alpha = rz_old / pq;
+  if (!(pq > 0.0) || !isfinite(alpha)) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      S->status = 1;
+      S->done = 1;
+    }
+    return;
+  }
+  const T a = (T)alpha;
+  double rz = 0.0, rr = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * kVecBlock + threadIdx.x; i < v.n; i += (int64_t)gridDim.x * kVecBlock) {
+    v.x[i] += a * v.p[i];
+    const T ri = v.dmask[i] ? v.r[i] - a * v.q[i] : T(0);
+    v.r[i] = ri;
+    rz += (double)(v.dinv[i] * ri) * (double)ri;
+    rr += (double)ri * (double)ri;
+  }
+  double vv[2] = {rz, rr};
+  if (grid_sum<kVecBlock, 2>(vv, partials, ticket, nullptr) && threadIdx.x == 0) {
+    S->alpha = alpha;
+    S->beta = vv[0] / rz_old;
+    S->rz_prev = rz_old;
+    S->rz = vv[0];
+    S->rr = vv[1];
+    S->iter += 1;
+    S->rmax2 = fmax(S->rmax2, vv[1]);
+    if (vv[1] <= S->tol2) {
+      S->done = 1;
+      S->reason = 1;
+    } else if (S->iter >= S->max_iter) {
+      S->done = 1;
+      S->reason = 3;
+    } else if (vv[1] < S->delta2 * S->rmax2) {
+      S->done = 1;
+      S->reason = 2;
+    }
+    if (!isfinite(vv[0]) || !isfinite(vv[1])) {
+      S->status = 1;
+      S->done = 1;
+    }
+  }
+}
+
+// p = D^-1 r + beta p; q = 0 (the matrix-free operator accumulates into q)
+template <class T>
+__global__ void __launch_bounds__(kVecBlock) k_pcg_direction(PcgVecs<T> v, const SolveScalars *S, bool zero_q) {
+  if (S->done) return;
+  const T b = (T)S->beta;
+  for (int64_t i = (int64_t)blockIdx.x * kVecBlock + threadIdx.x; i < v.n; i += (int64_t)gridDim.x * kVecBlock) {
+    v.p[i] = v.dinv[i] * v.r[i] + b * v.p[i];
+    if (zero_q) v.q[i] = T(0);
+  }
+}
+
+// ---- FP64 residual and refinement helpers ----------------------------------
+__global__ void k_residual(const double *__restrict__ f, const double *__restrict__ Kx,
+                           const uint8_t *__restrict__ dmask, int64_t n, double *__restrict__ r) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) r[i] = dmask[i] ? f[i] - Kx[i] : 0.0;
+}
+__global__ void k_set_bc(double *__restrict__ x, const double *__restrict__ g, const uint8_t *__restrict__ dmask,
+                         int64_t n, bool zero_free) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    if (!dmask[i])
+      x[i] = g[i];
+    else if (zero_free)
+      x[i] = 0.0;
+  }
+}
+__global__ void k_add(double *__restrict__ a, const double *__restrict__ b, int64_t n) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) a[i] += b[i];
+}
+__global__ void k_scale_to_f32(const double *__restrict__ r, double s, int64_t n, float *__restrict__ out) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (float)(r[i] * s);
+}
+__global__ void k_refine(double *__restrict__ x, float *__restrict__ d, int64_t n) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    x[i] += (double)d[i];
+    d[i] = 0.f;
+  }
+}
+__global__ void k_to_f32(const double *__restrict__ r, int64_t n, float *__restrict__ out) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (float)r[i];
+}
+__global__ void k_rhs_vec(const double *__restrict__ f, const double *__restrict__ Kg, const double *__restrict__ g,
+                          const uint8_t *__restrict__ dmask, int64_t n, double *__restrict__ b) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = dmask[i] ? f[i] - Kg[i] : g[i];
+}
+
+// raw K x with the selected FP64 operator (stream c.stream)
+static void apply_op64(Ctx &c, int op, const double *x, double *y) {
+  if (op == SFEM_OP_CSR64)
+    apply_csr64(c, x, y, 1, nullptr, nullptr);
+  else
+    apply_mf64(c, x, y, 1, nullptr);
+}
+
+// ---- one CG run (PCG64 or the FP32 inner solve) ----------------------------
+template <class T>
+struct CgRun {
+  Ctx &c;
+  PcgVecs<T> v;
+  int op;                 // SFEM_OP_CSR64 / SFEM_OP_MF64 / SFEM_OP_MF32
+  int chunk;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph = nullptr;
+
+  CgRun(Ctx &c_, PcgVecs<T> v_, int op_, int chunk_) : c(c_), v(v_), op(op_), chunk(chunk_) {}
+  ~CgRun() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+  }
+
+  void enqueue_iteration(cudaStream_t st) {
+    SolveScalars *S = c.scal;
+    const int *done = &S->done;
+    const bool mf = op != SFEM_OP_CSR64;
+    if (op == SFEM_OP_CSR64) {
+      launch_csr64(c, st, (const double *)v.p, (double *)v.q, (const double *)v.p, &S->pq, done);
+    } else if (op == SFEM_OP_MF64) {
+      double *w = static_cast<double *>(c.w_scratch);
+      launch_mf_strain<double>(c, st, c.Gs64, (const double *)v.p, 1, w, done);
+      launch_mf_stress<double>(c, st, c.Gs64, c.kap64, w, (double *)v.q, 1, &S->pq, done);
+    } else {
+      float *w = static_cast<float *>(c.w_scratch);
+      launch_mf_strain<float>(c, st, c.Gs32, (const float *)v.p, 1, w, done);
+      launch_mf_stress<float>(c, st, c.Gs32, c.kap32, w, (float *)v.q, 1, &S->pq, done);
+    }
+    k_pcg_update<T><<<c.red_blocks, kVecBlock, 0, st>>>(v, S, c.red_partial, c.tickets + 3);
+    SFEM_CHECK_LAUNCH();
+    k_pcg_direction<T><<<c.red_blocks, kVecBlock, 0, st>>>(v, S, mf);
+    SFEM_CHECK_LAUNCH();
+  }
+
+  size_t graph_nodes = 0;
+
+  void build_graph() {
+    SFEM_CUDA(cudaStreamBeginCapture(c.cap_stream, cudaStreamCaptureModeThreadLocal));
+    set_capturing(true);
+    try {
+      for (int i = 0; i < chunk; ++i) enqueue_iteration(c.cap_stream);
+    } catch (...) {
+      set_capturing(false);
+      cudaGraph_t g = nullptr;
+      cudaStreamEndCapture(c.cap_stream, &g);
+      if (g) cudaGraphDestroy(g);
+      throw;
+    }
+    set_capturing(false);
+    SFEM_CUDA(cudaStreamEndCapture(c.cap_stream, &graph));
+    SFEM_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+    SFEM_CUDA(cudaGraphGetNodes(graph, nullptr, &graph_nodes));
+  }
+
+  // r holds the masked residual on entry: (re)start CG from it.
+  SolveScalars start(double tol2, int max_iter, double delta2) {
+    k_pcg_init<T><<<c.red_blocks, kVecBlock, 0, c.stream>>>(v, c.scal, tol2, max_iter, delta2, c.red_partial,
+                                                            c.tickets + 4);
+    SFEM_CHECK_LAUNCH();
+    return resume(max_iter);
+  }
+
+  // r has been replaced by the true residual: keep p, recompute beta, go on.
+  SolveScalars replace(int max_iter) {
+    k_pcg_replace<T><<<c.red_blocks, kVecBlock, 0, c.stream>>>(v, c.scal, max_iter, c.red_partial, c.tickets + 5);
+    SFEM_CHECK_LAUNCH();
+    k_pcg_replace_dir<T><<<c.red_blocks, kVecBlock, 0, c.stream>>>(v, c.scal);
+    SFEM_CHECK_LAUNCH();
+    return resume(max_iter);
+  }
+
+  // run captured chunks until the device sets done; returns the scalars
+  SolveScalars resume(int max_iter) {
+    if (!exec) build_graph();
+    SolveScalars *h = c.h_scal;
+    cudaEvent_t ev[2];
+    SFEM_CUDA(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
+    SFEM_CUDA(cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
+    auto launch = [&](int slot) {
+      SFEM_CUDA(cudaGraphLaunch(exec, c.stream));
+      count_launches((int64_t)graph_nodes);
+      SFEM_CUDA(cudaMemcpyAsync(&h[slot], c.scal, sizeof(SolveScalars), cudaMemcpyDeviceToHost, c.stream));
+      SFEM_CUDA(cudaEventRecord(ev[slot], c.stream));
+    };
+    const int64_t max_launch = (int64_t)max_iter / chunk + 3;
+    launch(0);
+    launch(1);
+    int64_t launched = 2;
+    int slot = 0;
+    while (true) {
+      SFEM_CUDA(cudaEventSynchronize(ev[slot]));
+      if (h[slot].done || launched >= max_launch) break;
+      launch(slot);
+      ++launched;
+      slot ^= 1;
+    }
+    SFEM_CUDA(cudaStreamSynchronize(c.stream));
+    SolveScalars out;
+    SFEM_CUDA(cudaMemcpy(&out, c.scal, sizeof out, cudaMemcpyDeviceToHost));
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    return out;
+  }
+};
+
+struct SolveBuffers {
+  Ctx &c;
+  std::vector<void *> owned;
+  explicit SolveBuffers(Ctx &c_) : c(c_) {}
+  template <class T>
+  T *get(int64_t n) {
+    T *p = c.mem.get<T>(n);
+    owned.push_back(p);
+    return p;
+  }
+  ~SolveBuffers() {
+    for (void *p : owned) c.mem.drop(p);
+  }
+};
+
+static void solve_impl(Ctx &c, const double *f_extra, double *u, const sfem_solve_opts &o, sfem_solve_info &info) {
+  const int64_t n = c.ndof;
+  const int g256 = grid_for(n, 256);
+  cudaMemcpyKind in_kind = o.u_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  cudaMemcpyKind out_kind = o.u_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  const double tol = o.tol > 0 ? o.tol : 1e-8;
+  const int max_iter = o.max_iter > 0 ? o.max_iter : 200000;
+  const int chunk = o.check_every > 0 ? o.check_every : 32;
+  const int op64 = o.op64;
+  SFEM_REQUIRE(op64 == SFEM_OP_CSR64 || op64 == SFEM_OP_MF64, SFEM_EINVAL, "op64 must be CSR64 or MF64");
+  if (op64 == SFEM_OP_CSR64) SFEM_REQUIRE(c.assembled, SFEM_EINVAL, "CSR64 needs sfem_assemble first");
+  SFEM_REQUIRE(o.rhs >= 0 && o.rhs < c.nrhs, SFEM_EINVAL, "rhs out of range");
+
+  cudaEvent_t e0, e1;
+  SFEM_CUDA(cudaEventCreate(&e0));
+  SFEM_CUDA(cudaEventCreate(&e1));
+  SFEM_CUDA(cudaEventRecord(e0, c.stream));
+
+  SolveBuffers B(c);
+  // total load f (+ f_extra) and ||b||
+  double *ftot = B.get<double>(n);
+  SFEM_CUDA(cudaMemcpyAsync(ftot, c.f + (int64_t)o.rhs * n, n * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+  double *tmp = B.get<double>(n);
+  double bnorm = c.bnorm[o.rhs];
+  if (f_extra) {
+    SFEM_CUDA(cudaMemcpyAsync(tmp, f_extra, n * sizeof(double), in_kind, c.stream));
+    k_add<<<g256, 256, 0, c.stream>>>(ftot, tmp, n);
+    SFEM_CHECK_LAUNCH();
+    double *Kg = B.get<double>(n);
+    apply_mf64(c, c.g, Kg, 1, nullptr);
+    k_rhs_vec<<<g256, 256, 0, c.stream>>>(ftot, Kg, c.g, c.dmask, n, tmp);
+    SFEM_CHECK_LAUNCH();
+    bnorm = std::sqrt(device_norm2(c, tmp, n));
+  }
+  info.bnorm = bnorm;
+
+  double *x = B.get<double>(n);
+  if (o.warm_start) SFEM_CUDA(cudaMemcpyAsync(x, u, n * sizeof(double), in_kind, c.stream));
+  k_set_bc<<<g256, 256, 0, c.stream>>>(x, c.g, c.dmask, n, !o.warm_start);
+  SFEM_CHECK_LAUNCH();
+
+  if (bnorm == 0.0) {
+    info.true_relres = 0.0;
+    info.status = SFEM_OK;
+  } else {
+    double *Kx = B.get<double>(n);
+    double *r = B.get<double>(n);
+    auto true_residual = [&]() {
+      apply_op64(c, op64, x, Kx);
+      k_residual<<<g256, 256, 0, c.stream>>>(ftot, Kx, c.dmask, n, r);
+      SFEM_CHECK_LAUNCH();
+      return std::sqrt(device_norm2(c, r, n)) / bnorm;
+    };
+    int total_iter = 0, outer = 0, status = SFEM_OK;
+    double rel = true_residual();
+    if (o.kind == SFEM_SOLVE_PCG64) {
+      if (op64 == SFEM_OP_MF64) ensure_w_scratch(c, (size_t)c.n_tets * 8 * sizeof(double));
+      PcgVecs<double> v{x, r, B.get<double>(n), B.get<double>(n), c.dinv64, c.dmask, n};
+      CgRun<double> cg(c, v, op64, chunk);
+      const int max_restarts = 10;
+      while (rel > tol && total_iter < max_iter && outer <= max_restarts) {
+        SolveScalars s = cg.start(tol * tol * bnorm * bnorm, max_iter - total_iter, 0.0);
+        total_iter += s.iter;
+        if (s.status) {
+          status = SFEM_EBREAKDOWN;
+          rel = true_residual();
+          break;
+        }
+        rel = true_residual();  // also resets r for a restart
+        ++outer;
+      }
+    } else if (o.kind == SFEM_SOLVE_IR32_64) {
+      // Mixed precision with reliable updates: FP32 CG iterations on the
+      // FP32 matrix-free operator accumulate a correction d; whenever the
+      // FP32 recursive residual has fallen by `inner_tol` since the last
+      // update (or reached the tolerance), u += d in FP64, the FP64 true
+      // residual f - K u replaces the FP32 one, and CG continues in the
+      // same Krylov space (the search direction is kept).
+      const double delta = o.inner_tol > 0 ? o.inner_tol : 0.1;
+      const int max_outer = o.max_outer > 0 ? o.max_outer : 200;
+      ensure_w_scratch(c, (size_t)c.n_tets * 8 * sizeof(double));
+      PcgVecs<float> v{B.get<float>(n), B.get<float>(n), B.get<float>(n), B.get<float>(n), c.dinv32, c.dmask, n};
+      CgRun<float> cg(c, v, SFEM_OP_MF32, chunk);
+      SFEM_CUDA(cudaMemsetAsync(v.x, 0, n * sizeof(float), c.stream));
+      bool started = false;
+      while (rel > tol && total_iter < max_iter && outer < max_outer) {
+        k_to_f32<<<g256, 256, 0, c.stream>>>(r, n, v.r);
+        SFEM_CHECK_LAUNCH();
+        // S->iter counts across replacements, so the cap is the total one
+        SolveScalars s = started ? cg.replace(max_iter)
+                                 : cg.start(tol * tol * bnorm * bnorm, max_iter, delta * delta);
+        started = true;
+        total_iter = s.iter;  // the iteration counter runs across replacements
+        ++outer;
+        if (s.status) {
+          status = SFEM_EBREAKDOWN;
+          break;
+        }
+        k_refine<<<g256, 256, 0, c.stream>>>(x, v.x, n);
+        SFEM_CHECK_LAUNCH();
+        rel = true_residual();
+      }
+    } else {
+      throw Error{SFEM_EINVAL, "solver kind not available in this entry point"};
+    }
+    info.iterations = total_iter;
+    info.outer_iterations = outer;
+    info.true_relres = rel;
+    if (status == SFEM_OK && rel > tol) status = SFEM_ENOCONV;
+    info.status = status;
+  }
+  SFEM_CUDA(cudaMemcpyAsync(u, x, n * sizeof(double), out_kind, c.stream));
+  SFEM_CUDA(cudaEventRecord(e1, c.stream));
+  SFEM_CUDA(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  SFEM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  info.solve_ms = ms;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+}
+
+}  // namespace sfem
+
+using namespace sfem;
+
+extern "C" int sfem_solve(sfem_ctx *h, const double *f_extra, double *u, const sfem_solve_opts *opts,
+                          sfem_solve_info *info) {
+  sfem_solve_info local{};
+  try {
+    SFEM_REQUIRE(h && h->c.vol && h->c.dinv64, SFEM_EINVAL, "context not set up");
+    SFEM_REQUIRE(u && opts, SFEM_EINVAL, "u and opts must not be NULL");
+    for (int r : opts->reserved) SFEM_REQUIRE(r == 0, SFEM_EINVAL, "reserved options must be zero");
+    solve_impl(h->c, f_extra, u, *opts, local);
+  } catch (const Error &err) {
+    set_last_error(err.msg);
+    local.status = err.status;
+    if (info) *info = local;
+    return err.status;
+  }
+  if (info) *info = local;
+  if (local.status != SFEM_OK) set_last_error(sfem_strerror(local.status));
+  return local.status;
+}

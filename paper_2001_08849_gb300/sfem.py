@@ -1,0 +1,333 @@
+"""Thin Python binding of libsfem.so (include/sfem.h).
+
+Argument marshalling only: every step of setup, assembly, operator apply and
+solve runs in the library's CUDA kernels.  PyTorch provides device memory
+(through the library's allocator hooks, backed by torch's caching allocator)
+and the CUDA stream.  If the library is missing the import of this module
+fails; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libsfem.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "sfem.h")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libsfem.so not built ({LIB_PATH}); run __graft_entry__.build() "
+                      "or python paper_2001_08849_gb300/build.py")
+lib = ctypes.CDLL(LIB_PATH)
+
+# ---- status codes and enums (include/sfem.h) --------------------------------
+SFEM_OK, SFEM_EINVAL, SFEM_EMESH, SFEM_ENOMEM = 0, -1, -2, -3
+SFEM_ENOCONV, SFEM_EBREAKDOWN, SFEM_ECUDA, SFEM_ETIMEOUT = -4, -5, -6, -7
+SFEM_OP_CSR64, SFEM_OP_MF64, SFEM_OP_MF32 = 0, 1, 2
+SFEM_SOLVE_PCG64, SFEM_SOLVE_IR32_64, SFEM_SOLVE_FPCG_LEARNED = 0, 1, 2
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class sfem_opts(ctypes.Structure):
+    _fields_ = [("inputs_on_device", ctypes.c_int), ("nrhs", ctypes.c_int),
+                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", ctypes.c_void_p),
+                ("reserved", ctypes.c_int * 8)]
+
+
+class sfem_mesh_info(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in (
+        "n_nodes", "n_tets", "ndof", "n_faces", "n_interior", "n_boundary", "n_dir", "nrhs", "nnz",
+        "n_slivers", "n_bad_tets", "n_bad_faces", "max_tets_per_node")] + [
+        (n, ctypes.c_double) for n in ("min_quality", "min_volume", "max_volume", "setup_ms")]
+
+
+class sfem_csr(ctypes.Structure):
+    _fields_ = [("n_rows", ctypes.c_int64), ("nnz", ctypes.c_int64), ("row_ptr", ctypes.c_void_p),
+                ("col", ctypes.c_void_p), ("val", ctypes.c_void_p)]
+
+
+class sfem_solve_opts(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("op64", ctypes.c_int), ("rhs", ctypes.c_int),
+                ("u_on_device", ctypes.c_int), ("warm_start", ctypes.c_int), ("max_iter", ctypes.c_int),
+                ("tol", ctypes.c_double), ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int),
+                ("check_every", ctypes.c_int), ("learned", ctypes.c_void_p), ("reserved", ctypes.c_int * 6)]
+
+
+class sfem_solve_info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iterations", ctypes.c_int), ("outer_iterations", ctypes.c_int),
+                ("fallbacks", ctypes.c_int), ("true_relres", ctypes.c_double), ("bnorm", ctypes.c_double),
+                ("solve_ms", ctypes.c_double)]
+
+
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_SIG = {
+    "sfem_mesh_setup": (ctypes.c_int, [ctypes.POINTER(_P), _P, _I64, _P, _I64, ctypes.c_double, ctypes.c_double,
+                                       _P, _P, _I64, _P, _P, _I64, ctypes.POINTER(sfem_opts), _P]),
+    "sfem_assemble": (ctypes.c_int, [_P, ctypes.POINTER(sfem_csr)]),
+    "sfem_apply": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int]),
+    "sfem_solve": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(sfem_solve_opts), ctypes.POINTER(sfem_solve_info)]),
+    "sfem_get_info": (ctypes.c_int, [_P, ctypes.POINTER(sfem_mesh_info)]),
+    "sfem_get_geometry": (ctypes.c_int, [_P, _P, _P]),
+    "sfem_get_neighbors": (ctypes.c_int, [_P, _P]),
+    "sfem_get_faces": (ctypes.c_int, [_P, _P, _P, _P]),
+    "sfem_get_rhs": (ctypes.c_int, [_P, _P, ctypes.c_int]),
+    "sfem_get_diag": (ctypes.c_int, [_P, _P]),
+    "sfem_destroy": (None, [_P]),
+    "sfem_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "sfem_last_error": (ctypes.c_char_p, []),
+    "sfem_version": (ctypes.c_int, []),
+    "sfem_time_operator": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+    "sfem_launch_count": (ctypes.c_int64, []),
+}
+for _name, (_res, _args) in _SIG.items():
+    _fn = getattr(lib, _name)
+    _fn.restype = _res
+    _fn.argtypes = _args
+
+
+def header_functions() -> list:
+    """Names of the functions declared in include/sfem.h."""
+    with open(HEADER) as fh:
+        src = fh.read()
+    return sorted(set(re.findall(r"\b(sfem_[a-z0-9_]+)\s*\(", src)))
+
+
+class SfemError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        msg = lib.sfem_last_error().decode() or lib.sfem_strerror(status).decode()
+        super().__init__(f"{what}: {lib.sfem_strerror(status).decode()} ({status}): {msg}")
+        self.status = status
+
+
+def _check(status: int, what: str):
+    if status != SFEM_OK:
+        raise SfemError(status, what)
+
+
+def _ptr(a):
+    """Data pointer of a torch tensor or a C-contiguous numpy array."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("arrays must be C-contiguous")
+    return a.ctypes.data
+
+
+class _DeviceArray:
+    """__cuda_array_interface__ view of library-owned device memory."""
+
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
+                                         "data": (int(ptr), False), "version": 3}
+
+
+def _torch():
+    import torch
+    return torch
+
+
+class TorchAllocator:
+    """Allocator hooks that route the library's device allocations through
+    torch's caching allocator on the current device."""
+
+    def __init__(self, device=None):
+        torch = _torch()
+        self.device = torch.cuda.current_device() if device is None else device
+
+        def _alloc(nbytes, stream, user):
+            return int(torch.cuda.caching_allocator_alloc(int(nbytes), self.device, stream or 0))
+
+        def _free(ptr, nbytes, stream, user):
+            torch.cuda.caching_allocator_delete(int(ptr))
+
+        self.alloc = ALLOC_FN(_alloc)
+        self.free = FREE_FN(_free)
+
+
+def current_stream_handle() -> int:
+    return _torch().cuda.current_stream().cuda_stream
+
+
+# ---- functions with the ABI's names -----------------------------------------
+
+def sfem_mesh_setup(xyz, tets, E, nu, dir_dofs=None, dir_vals=None, trac_tris=None, trac=None,
+                    inputs_on_device=False, stream=None, allocator="torch"):
+    """Create a context (see include/sfem.h).  Host inputs are numpy arrays
+    (float64 / int32, C-contiguous); device inputs are torch CUDA tensors.
+    trac has shape (nrhs, n_tri, 3).  Returns (handle, keepalive) where
+    keepalive must outlive the handle (it pins the allocator callbacks)."""
+    n_nodes = int(xyz.shape[0])
+    n_tets = int(tets.shape[0])
+    n_dir = 0 if dir_dofs is None else int(dir_dofs.shape[0])
+    n_tri = 0 if trac_tris is None else int(trac_tris.shape[0])
+    nrhs = 1 if trac is None else int(trac.shape[0]) if trac.ndim == 3 else 1
+    opts = sfem_opts()
+    opts.inputs_on_device = 1 if inputs_on_device else 0
+    opts.nrhs = nrhs
+    keep = [opts]
+    if allocator == "torch":
+        al = TorchAllocator()
+        opts.alloc, opts.free = al.alloc, al.free
+        keep.append(al)
+    if stream is None:
+        stream = current_stream_handle()
+    h = _P()
+    st = lib.sfem_mesh_setup(ctypes.byref(h), _ptr(xyz), n_nodes, _ptr(tets), n_tets, float(E), float(nu),
+                             _ptr(dir_dofs), _ptr(dir_vals), n_dir, _ptr(trac_tris), _ptr(trac), n_tri,
+                             ctypes.byref(opts), stream)
+    if st != SFEM_OK:
+        err = SfemError(st, "sfem_mesh_setup")
+        err.handle = h.value
+        err.keepalive = keep
+        if h.value:
+            err.info = sfem_get_info(h.value)
+            lib.sfem_destroy(h)
+        raise err
+    return h.value, keep
+
+
+def sfem_get_info(h) -> dict:
+    info = sfem_mesh_info()
+    _check(lib.sfem_get_info(h, ctypes.byref(info)), "sfem_get_info")
+    return {k: getattr(info, k) for k, _ in info._fields_}
+
+
+def sfem_assemble(h):
+    """Assemble K; returns torch CUDA views (row_ptr, col, val) of the
+    library-owned CSR (valid until sfem_destroy)."""
+    torch = _torch()
+    csr = sfem_csr()
+    _check(lib.sfem_assemble(h, ctypes.byref(csr)), "sfem_assemble")
+    rp = torch.as_tensor(_DeviceArray(csr.row_ptr, (csr.n_rows + 1,), "<i8"), device="cuda")
+    col = torch.as_tensor(_DeviceArray(csr.col, (csr.nnz,), "<i4"), device="cuda")
+    val = torch.as_tensor(_DeviceArray(csr.val, (csr.nnz,), "<f8"), device="cuda")
+    return rp, col, val
+
+
+def sfem_apply(h, u, y, op=SFEM_OP_MF64, nrhs=1):
+    """y = A u on device tensors (float64 for CSR64/MF64, float32 for MF32)."""
+    _check(lib.sfem_apply(h, _ptr(u), _ptr(y), int(op), int(nrhs)), "sfem_apply")
+
+
+def solve_opts(kind=SFEM_SOLVE_PCG64, op64=SFEM_OP_MF64, rhs=0, tol=1e-8, max_iter=0, inner_tol=0.0,
+               max_outer=0, check_every=0, u_on_device=False, warm_start=False, learned=None):
+    o = sfem_solve_opts()
+    o.kind, o.op64, o.rhs = int(kind), int(op64), int(rhs)
+    o.u_on_device, o.warm_start = int(bool(u_on_device)), int(bool(warm_start))
+    o.max_iter, o.tol, o.inner_tol = int(max_iter), float(tol), float(inner_tol)
+    o.max_outer, o.check_every = int(max_outer), int(check_every)
+    o.learned = learned
+    return o
+
+
+def sfem_solve(h, u, opts: sfem_solve_opts, f_extra=None, check=True) -> dict:
+    """Solve into u (numpy float64 host array, or a CUDA tensor when
+    opts.u_on_device).  Returns the solve info as a dict."""
+    info = sfem_solve_info()
+    st = lib.sfem_solve(h, _ptr(f_extra), _ptr(u), ctypes.byref(opts), ctypes.byref(info))
+    out = {k: getattr(info, k) for k, _ in info._fields_}
+    if check and st not in (SFEM_OK,):
+        raise SfemError(st, "sfem_solve")
+    return out
+
+
+def sfem_get_geometry(h, n_tets):
+    vol = np.zeros(n_tets)
+    grad = np.zeros((n_tets, 4, 3))
+    _check(lib.sfem_get_geometry(h, _ptr(vol), _ptr(grad)), "sfem_get_geometry")
+    return vol, grad
+
+
+def sfem_get_neighbors(h, n_tets):
+    nbr = np.zeros((n_tets, 4), np.int32)
+    _check(lib.sfem_get_neighbors(h, _ptr(nbr)), "sfem_get_neighbors")
+    return nbr
+
+
+def sfem_get_faces(h, n_faces):
+    nodes = np.zeros((n_faces, 5), np.int32)
+    tets = np.zeros((n_faces, 2), np.int32)
+    Vk = np.zeros(n_faces)
+    _check(lib.sfem_get_faces(h, _ptr(nodes), _ptr(tets), _ptr(Vk)), "sfem_get_faces")
+    return nodes, tets, Vk
+
+
+def sfem_get_rhs(h, ndof, rhs=0):
+    b = np.zeros(ndof)
+    _check(lib.sfem_get_rhs(h, _ptr(b), int(rhs)), "sfem_get_rhs")
+    return b
+
+
+def sfem_get_diag(h, ndof):
+    d = np.zeros(ndof)
+    _check(lib.sfem_get_diag(h, _ptr(d)), "sfem_get_diag")
+    return d
+
+
+def sfem_destroy(h):
+    if h:
+        lib.sfem_destroy(h)
+
+
+def sfem_time_operator(h, op=SFEM_OP_MF32, reps=20) -> float:
+    """Mean device milliseconds of one raw operator application."""
+    ms = ctypes.c_double()
+    _check(lib.sfem_time_operator(h, int(op), int(reps), ctypes.byref(ms)), "sfem_time_operator")
+    return ms.value
+
+
+def sfem_launch_count() -> int:
+    return int(lib.sfem_launch_count())
+
+
+def sfem_strerror(status: int) -> str:
+    return lib.sfem_strerror(status).decode()
+
+
+# ---- convenience wrapper ----------------------------------------------------
+
+class FsFem:
+    """Owns one library context built from an inputs.kuhn_beam.Problem-like
+    object (mesh.xyz, mesh.tets, E, nu, dir_dofs, dir_vals, trac_tris, trac)."""
+
+    def __init__(self, problem, on_device=False, stream=None):
+        m = problem.mesh
+        xyz = np.ascontiguousarray(m.xyz, dtype=np.float64)
+        tets = np.ascontiguousarray(m.tets, dtype=np.int32)
+        dd = np.ascontiguousarray(problem.dir_dofs, dtype=np.int32)
+        dv = np.ascontiguousarray(problem.dir_vals, dtype=np.float64)
+        tt = np.ascontiguousarray(problem.trac_tris, dtype=np.int32)
+        tr = np.ascontiguousarray(problem.trac, dtype=np.float64)
+        if on_device:
+            torch = _torch()
+            xyz, tets, dd, dv, tt, tr = (torch.from_numpy(a).cuda() for a in (xyz, tets, dd, dv, tt, tr))
+        self.inputs = (xyz, tets, dd, dv, tt, tr)
+        self.h, self._keep = sfem_mesh_setup(xyz, tets, problem.E, problem.nu, dd, dv, tt, tr,
+                                             inputs_on_device=on_device, stream=stream)
+        self.info = sfem_get_info(self.h)
+        self.ndof = self.info["ndof"]
+
+    def close(self):
+        if self.h:
+            sfem_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -82,9 +82,9 @@ __device__ __forceinline__ void load_grads(const T *__restrict__ Gs, int64_t n, 
 }
 
 // ---- pass 1: w_e = V_e eps_e (Voigt, engineering shear; Eq. 4) -----------
-template <class T>
+template <class T, class TU>
 __global__ void __launch_bounds__(kMfBlock) k_mf_strain(int64_t n, const int4 *__restrict__ conn,
-                                                        const T *__restrict__ Gs, const T *__restrict__ u,
+                                                        const T *__restrict__ Gs, const TU *__restrict__ u,
                                                         int64_t ndof, int nrhs, T *__restrict__ w,
                                                         const int *done) {
   if (done && *done) return;
@@ -95,12 +95,12 @@ __global__ void __launch_bounds__(kMfBlock) k_mf_strain(int64_t n, const int4 *_
   T g[4][3];
   load_grads(Gs, n, e, g);
   for (int r = 0; r < nrhs; ++r) {
-    const T *ur = u + (int64_t)r * ndof;
+    const TU *ur = u + (int64_t)r * ndof;
     T H[3][3] = {};
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
-      const T *ua = ur + 3 * (int64_t)v[a];
-      T u0 = __ldg(ua), u1 = __ldg(ua + 1), u2 = __ldg(ua + 2);
+      const TU *ua = ur + 3 * (int64_t)v[a];
+      T u0 = (T)__ldg(ua), u1 = (T)__ldg(ua + 1), u2 = (T)__ldg(ua + 2);
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
         H[0][j] += u0 * g[a][j];
@@ -114,11 +114,11 @@ __global__ void __launch_bounds__(kMfBlock) k_mf_strain(int64_t n, const int4 *_
 }
 
 // ---- pass 2: face averages, stress, scatter (and energy) ------------------
-template <class T>
+template <class T, class TY>
 __global__ void __launch_bounds__(kMfBlock)
     k_mf_stress(int64_t n, const int4 *__restrict__ conn, const T *__restrict__ Gs, const int4 *__restrict__ nbr,
                 const T *__restrict__ kap, const T *__restrict__ w, int64_t ndof, int nrhs, T lam, T mu,
-                T *__restrict__ y, double *partials, unsigned int *ticket, double *energy_out,
+                TY *__restrict__ y, double *partials, unsigned int *ticket, double *energy_out,
                 const int *done) {
   if (done && *done) return;
   int64_t e = (int64_t)blockIdx.x * kMfBlock + threadIdx.x;
@@ -155,16 +155,16 @@ __global__ void __launch_bounds__(kMfBlock)
 #pragma unroll
       for (int i = 0; i < 6; ++i) el += W[i] * st[i];
       en += (double)el;
-      T *yr = y + (int64_t)r * ndof;
+      TY *yr = y + (int64_t)r * ndof;
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
         T fx = g[a][0] * st[0] + g[a][1] * st[5] + g[a][2] * st[4];
         T fy = g[a][0] * st[5] + g[a][1] * st[1] + g[a][2] * st[3];
         T fz = g[a][0] * st[4] + g[a][1] * st[3] + g[a][2] * st[2];
-        T *ya = yr + 3 * (int64_t)v[a];
-        atomicAdd(ya, fx);
-        atomicAdd(ya + 1, fy);
-        atomicAdd(ya + 2, fz);
+        TY *ya = yr + 3 * (int64_t)v[a];
+        atomicAdd(ya, (TY)fx);
+        atomicAdd(ya + 1, (TY)fy);
+        atomicAdd(ya + 2, (TY)fz);
       }
     }
   }
@@ -181,64 +181,83 @@ void ensure_w_scratch(Ctx &c, size_t bytes) {
   c.w_bytes = bytes;
 }
 
-template <class T>
-void launch_mf_strain(Ctx &c, cudaStream_t st, const T *Gs, const T *u, int nrhs, T *w, const int *done) {
-  k_mf_strain<T><<<grid_for(c.n_tets, kMfBlock), kMfBlock, 0, st>>>(c.n_tets, reinterpret_cast<const int4 *>(c.tets),
-                                                                    Gs, u, c.ndof, nrhs, w, done);
+template <class T, class TU>
+void launch_mf_strain(Ctx &c, cudaStream_t st, const T *Gs, const TU *u, int nrhs, T *w, const int *done) {
+  k_mf_strain<T, TU><<<grid_for(c.n_tets, kMfBlock), kMfBlock, 0, st>>>(
+      c.n_tets, reinterpret_cast<const int4 *>(c.tets), Gs, u, c.ndof, nrhs, w, done);
   SFEM_CHECK_LAUNCH();
 }
 
-template <class T>
-void launch_mf_stress(Ctx &c, cudaStream_t st, const T *Gs, const T *kap, const T *w, T *y, int nrhs,
+template <class T, class TY>
+void launch_mf_stress(Ctx &c, cudaStream_t st, const T *Gs, const T *kap, const T *w, TY *y, int nrhs,
                       double *energy_out, const int *done) {
-  k_mf_stress<T><<<grid_for(c.n_tets, kMfBlock), kMfBlock, 0, st>>>(
+  k_mf_stress<T, TY><<<grid_for(c.n_tets, kMfBlock), kMfBlock, 0, st>>>(
       c.n_tets, reinterpret_cast<const int4 *>(c.tets), Gs, reinterpret_cast<const int4 *>(c.nbr), kap, w, c.ndof,
       nrhs, (T)c.lam, (T)c.mu, y, c.red_partial, c.tickets, energy_out, done);
   SFEM_CHECK_LAUNCH();
 }
 
-template void launch_mf_strain<float>(Ctx &, cudaStream_t, const float *, const float *, int, float *, const int *);
-template void launch_mf_strain<double>(Ctx &, cudaStream_t, const double *, const double *, int, double *,
-                                       const int *);
-template void launch_mf_stress<float>(Ctx &, cudaStream_t, const float *, const float *, const float *, float *, int,
-                                      double *, const int *);
-template void launch_mf_stress<double>(Ctx &, cudaStream_t, const double *, const double *, const double *, double *,
-                                       int, double *, const int *);
-
+template void launch_mf_strain<float, float>(Ctx &, cudaStream_t, const float *, const float *, int, float *,
+                                             const int *);
+template void launch_mf_strain<float, double>(Ctx &, cudaStream_t, const float *, const double *, int, float *,
+                                              const int *);
+template void launch_mf_strain<double, double>(Ctx &, cudaStream_t, const double *, const double *, int, double *,
+                                               const int *);
+template void launch_mf_stress<float, float>(Ctx &, cudaStream_t, const float *, const float *, const float *,
+                                             float *, int, double *, const int *);
+template void launch_mf_stress<float, double>(Ctx &, cudaStream_t, const float *, const float *, const float *,
+                                              double *, int, double *, const int *);
+template void launch_mf_stress<double, double>(Ctx &, cudaStream_t, const double *, const double *,
+                                               const double *, double *, int, double *, const int *);
 
 template <class T>
 static void apply_mf(Ctx &c, const T *Gs, const T *kap, const T *u, T *y, int nrhs, double *energy_out) {
   ensure_w_scratch(c, (size_t)c.n_tets * 8 * sizeof(T) * nrhs);
   T *w = static_cast<T *>(c.w_scratch);
   SFEM_CUDA(cudaMemsetAsync(y, 0, (size_t)nrhs * c.ndof * sizeof(T), c.stream));
-  launch_mf_strain<T>(c, c.stream, Gs, u, nrhs, w, nullptr);
-  launch_mf_stress<T>(c, c.stream, Gs, kap, w, y, nrhs, energy_out, nullptr);
+  launch_mf_strain<T, T>(c, c.stream, Gs, u, nrhs, w, nullptr);
+  launch_mf_stress<T, T>(c, c.stream, Gs, kap, w, y, nrhs, energy_out, nullptr);
 }
 
 void apply_mf64(Ctx &c, const double *u, double *y, int nrhs, double *energy_out) {
   apply_mf<double>(c, c.Gs64, c.kap64, u, y, nrhs, energy_out);
 }
 void apply_mf32(Ctx &c, const float *u, float *y, int nrhs, double *energy_out) {
-  apply_mf<float>(c, c.Gs32, c.kap32, u, y, nrhs, energy_out);
+  SFEM_CUDA(cudaMemsetAsync(y, 0, (size_t)nrhs * c.ndof * sizeof(float), c.stream));
+  for (int r = 0; r < nrhs; ++r)
+    launch_mf32_tiled<float, float>(c, c.stream, u + (int64_t)r * c.ndof, y + (int64_t)r * c.ndof,
+                                    r == 0 ? energy_out : nullptr, nullptr);
 }
 
-// ---- CSR SpMV (FP64), one warp per row, fixed grid ------------------------
+// ---- CSR SpMV (FP64), kCsrLanes lanes per row, fixed grid -----------------
+// A full-warp reduction per row would spend 5 x 32 FP64 lane-adds per row,
+// more than the row's own FMAs on a GPU with a low FP64 rate; a group of 4
+// lanes per row needs 2 shuffle steps and still reads 32-byte segments.
+constexpr int kCsrLanes = 4;
+
 __global__ void __launch_bounds__(kSpmvBlock)
     k_csr_spmv(int64_t nrows, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
                const double *__restrict__ val, const double *__restrict__ x, double *__restrict__ y,
                const double *__restrict__ dotv, double *partials, unsigned int *ticket, double *dot_out,
                const int *done) {
   if (done && *done) return;
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = ((int64_t)blockIdx.x * kSpmvBlock + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * kSpmvBlock) >> 5;
+  const int sub = threadIdx.x & (kCsrLanes - 1);
+  const int64_t group = ((int64_t)blockIdx.x * kSpmvBlock + threadIdx.x) / kCsrLanes;
+  const int64_t ngroups = ((int64_t)gridDim.x * kSpmvBlock) / kCsrLanes;
+  // rows advance by a warp-uniform base so every lane runs the same trip
+  // count (the shuffles below need the whole warp)
+  const int64_t g0 = group - (int64_t)((threadIdx.x & 31) / kCsrLanes);
   double dot = 0.0;
-  for (int64_t row = warp; row < nrows; row += nwarps) {
+  for (int64_t base = g0; base < nrows; base += ngroups) {
+    const int64_t row = base + (group - g0);
     double s = 0.0;
-    for (int64_t j = rp[row] + lane; j < rp[row + 1]; j += 32) s += val[j] * __ldg(&x[col[j]]);
+    if (row < nrows) {
+      const int64_t b = rp[row], e = rp[row + 1];
+      for (int64_t j = b + sub; j < e; j += kCsrLanes) s += val[j] * __ldg(&x[col[j]]);
+    }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) {
+    for (int o = kCsrLanes / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (sub == 0 && row < nrows) {
       y[row] = s;
       if (dotv) dot += s * dotv[row];
     }
@@ -352,13 +371,12 @@ extern "C" int sfem_time_operator(sfem_ctx *h, int op, int reps, double *ms_per_
     SFEM_CUDA(cudaEventCreate(&e1));
     auto once = [&]() {
       if (op == SFEM_OP_MF32) {
-        launch_mf_strain<float>(c, c.stream, c.Gs32, (const float *)u, 1, (float *)c.w_scratch, nullptr);
-        launch_mf_stress<float>(c, c.stream, c.Gs32, c.kap32, (const float *)c.w_scratch, (float *)y, 1, nullptr,
-                                nullptr);
+        launch_mf32_tiled<float, float>(c, c.stream, (const float *)u, (float *)y, nullptr, nullptr);
       } else if (op == SFEM_OP_MF64) {
-        launch_mf_strain<double>(c, c.stream, c.Gs64, (const double *)u, 1, (double *)c.w_scratch, nullptr);
-        launch_mf_stress<double>(c, c.stream, c.Gs64, c.kap64, (const double *)c.w_scratch, (double *)y, 1,
-                                 nullptr, nullptr);
+        launch_mf_strain<double, double>(c, c.stream, c.Gs64, (const double *)u, 1, (double *)c.w_scratch,
+                                         nullptr);
+        launch_mf_stress<double, double>(c, c.stream, c.Gs64, c.kap64, (const double *)c.w_scratch, (double *)y, 1,
+                                         nullptr, nullptr);
       } else if (op == SFEM_OP_CSR64) {
         SFEM_REQUIRE(c.assembled, SFEM_EINVAL, "CSR64 needs sfem_assemble first");
         launch_csr64(c, c.stream, (const double *)u, (double *)y, nullptr, nullptr, nullptr);

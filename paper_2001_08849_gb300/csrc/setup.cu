@@ -643,6 +643,9 @@ static void setup(Ctx &c, const double *xyz, const int32_t *tets, const int32_t 
                                 std::to_string(c.hstat.bad_tri) + " bad traction triangles"};
   }
 
+  // tiles of the single-pass FP32 operator
+  build_tiles(c);
+
   // ||b|| per load case
   double *b = c.mem.get<double>(c.ndof);
   double *Kg = c.mem.get<double>(c.ndof);

@@ -118,6 +118,25 @@ struct Csr {
   int32_t *nadj = nullptr;   // nptr[n_nodes]
 };
 
+// tiled single-pass FP32 operator (tiles.cu)
+struct TileData {
+  bool ready = false;
+  int64_t n_tiles = 0, total_halo = 0, total_nodes = 0;
+  int32_t *perm = nullptr;       // tile order -> input tet id
+  int32_t *iperm = nullptr;      // input tet id -> tile order
+  int32_t *tile_start = nullptr; // n_tiles + 1, ranges of tile-order tets
+  int64_t *hoff = nullptr;       // n_tiles + 1 halo offsets
+  int64_t *noff = nullptr;       // n_tiles + 1 node-list offsets
+  int32_t *halo_tet = nullptr;   // halo tets (tile order)
+  uint2 *halo_lconn = nullptr;   // their local connectivity (4 x 16 bit)
+  int32_t *tile_nodes = nullptr; // sorted node ids per tile
+  uint16_t *node_inc = nullptr;  // per tile node: first slot of its incidence list
+  float4 *rec = nullptr;         // 64-byte per-tet records (tile order): V_e grad N_1..3,
+                                 // V_e, local connectivity, local neighbours
+  int max_halo = 0, max_nodes = 0;
+  size_t smem = 0;               // dynamic shared memory of the operator kernel
+};
+
 struct Ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -165,6 +184,7 @@ struct Ctx {
 
   Csr csr;
   bool assembled = false;
+  TileData tl;
 
   DevStatus *dstat = nullptr;
   DevStatus hstat{};
@@ -197,10 +217,11 @@ void apply_csr64(Ctx &c, const double *u, double *y, int nrhs, const double *dot
 void ensure_w_scratch(Ctx &c, size_t bytes);
 // stream-explicit launchers used inside captured solver iterations; kernels
 // return immediately when *done != 0
-template <class T>
-void launch_mf_strain(Ctx &c, cudaStream_t st, const T *Gs, const T *u, int nrhs, T *w, const int *done);
-template <class T>
-void launch_mf_stress(Ctx &c, cudaStream_t st, const T *Gs, const T *kap, const T *w, T *y, int nrhs,
+// T: geometry and arithmetic type; TU / TY: input / output vector types
+template <class T, class TU>
+void launch_mf_strain(Ctx &c, cudaStream_t st, const T *Gs, const TU *u, int nrhs, T *w, const int *done);
+template <class T, class TY>
+void launch_mf_stress(Ctx &c, cudaStream_t st, const T *Gs, const T *kap, const T *w, TY *y, int nrhs,
                       double *energy_out, const int *done);
 void launch_csr64(Ctx &c, cudaStream_t st, const double *u, double *y, const double *dotv, double *dot_out,
                   const int *done);
@@ -210,6 +231,11 @@ double device_norm2(Ctx &c, const double *x, int64_t n);
 
 // setup pieces used by other units
 void compute_diag(Ctx &c);
+void build_tiles(Ctx &c);
+// tiled FP32 operator y += K u (y must be zeroed by the caller); u, y of
+// type TU/TY (float or double); energy u^T K u summed into *energy_out
+template <class TU, class TY>
+void launch_mf32_tiled(Ctx &c, cudaStream_t st, const TU *u, TY *y, double *energy_out, const int *done);
 
 }  // namespace sfem
 

@@ -248,12 +248,12 @@ struct CgRun {
       launch_csr64(c, st, (const double *)v.p, (double *)v.q, (const double *)v.p, &S->pq, done);
     } else if (op == SFEM_OP_MF64) {
       double *w = static_cast<double *>(c.w_scratch);
-      launch_mf_strain<double>(c, st, c.Gs64, (const double *)v.p, 1, w, done);
-      launch_mf_stress<double>(c, st, c.Gs64, c.kap64, w, (double *)v.q, 1, &S->pq, done);
+      launch_mf_strain<double, double>(c, st, c.Gs64, (const double *)v.p, 1, w, done);
+      launch_mf_stress<double, double>(c, st, c.Gs64, c.kap64, w, (double *)v.q, 1, &S->pq, done);
     } else {
-      float *w = static_cast<float *>(c.w_scratch);
-      launch_mf_strain<float>(c, st, c.Gs32, (const float *)v.p, 1, w, done);
-      launch_mf_stress<float>(c, st, c.Gs32, c.kap32, w, (float *)v.q, 1, &S->pq, done);
+      // tiled FP32 operator; vectors of type T (FP64 vectors: p read in
+      // FP64, arithmetic in FP32, q accumulated in FP64)
+      launch_mf32_tiled<T, T>(c, st, v.p, v.q, &S->pq, done);
     }
     k_pcg_update<T><<<c.red_blocks, kVecBlock, 0, st>>>(v, S, c.red_partial, c.tickets + 3);
     SFEM_CHECK_LAUNCH();
@@ -428,26 +428,52 @@ static void solve_impl(Ctx &c, const double *f_extra, double *u, const sfem_solv
       const double delta = o.inner_tol > 0 ? o.inner_tol : 0.1;
       const int max_outer = o.max_outer > 0 ? o.max_outer : 200;
       ensure_w_scratch(c, (size_t)c.n_tets * 8 * sizeof(double));
-      PcgVecs<float> v{B.get<float>(n), B.get<float>(n), B.get<float>(n), B.get<float>(n), c.dinv32, c.dmask, n};
-      CgRun<float> cg(c, v, SFEM_OP_MF32, chunk);
-      SFEM_CUDA(cudaMemsetAsync(v.x, 0, n * sizeof(float), c.stream));
-      bool started = false;
-      while (rel > tol && total_iter < max_iter && outer < max_outer) {
-        k_to_f32<<<g256, 256, 0, c.stream>>>(r, n, v.r);
-        SFEM_CHECK_LAUNCH();
-        // S->iter counts across replacements, so the cap is the total one
-        SolveScalars s = started ? cg.replace(max_iter)
-                                 : cg.start(tol * tol * bnorm * bnorm, max_iter, delta * delta);
-        started = true;
-        total_iter = s.iter;  // the iteration counter runs across replacements
-        ++outer;
-        if (s.status) {
-          status = SFEM_EBREAKDOWN;
-          break;
+      if (o.fp32_vectors) {
+        // all-FP32 inner iterations (vectors too): cheaper per iteration,
+        // but finite-precision CG loses orthogonality much faster
+        PcgVecs<float> v{B.get<float>(n), B.get<float>(n), B.get<float>(n), B.get<float>(n), c.dinv32, c.dmask,
+                         n};
+        CgRun<float> cg(c, v, SFEM_OP_MF32, chunk);
+        SFEM_CUDA(cudaMemsetAsync(v.x, 0, n * sizeof(float), c.stream));
+        bool started = false;
+        while (rel > tol && total_iter < max_iter && outer < max_outer) {
+          k_to_f32<<<g256, 256, 0, c.stream>>>(r, n, v.r);
+          SFEM_CHECK_LAUNCH();
+          // S->iter counts across replacements, so the cap is the total one
+          SolveScalars s = started ? cg.replace(max_iter)
+                                   : cg.start(tol * tol * bnorm * bnorm, max_iter, delta * delta);
+          started = true;
+          total_iter = s.iter;
+          ++outer;
+          if (s.status) {
+            status = SFEM_EBREAKDOWN;
+            break;
+          }
+          k_refine<<<g256, 256, 0, c.stream>>>(x, v.x, n);
+          SFEM_CHECK_LAUNCH();
+          rel = true_residual();
         }
-        k_refine<<<g256, 256, 0, c.stream>>>(x, v.x, n);
-        SFEM_CHECK_LAUNCH();
-        rel = true_residual();
+      } else {
+        // FP32 operator, FP64 vectors: the correction d accumulates in FP64
+        PcgVecs<double> v{B.get<double>(n), r, B.get<double>(n), B.get<double>(n), c.dinv64, c.dmask, n};
+        CgRun<double> cg(c, v, SFEM_OP_MF32, chunk);
+        SFEM_CUDA(cudaMemsetAsync(v.x, 0, n * sizeof(double), c.stream));
+        bool started = false;
+        while (rel > tol && total_iter < max_iter && outer < max_outer) {
+          SolveScalars s = started ? cg.replace(max_iter)
+                                   : cg.start(tol * tol * bnorm * bnorm, max_iter, delta * delta);
+          started = true;
+          total_iter = s.iter;
+          ++outer;
+          if (s.status) {
+            status = SFEM_EBREAKDOWN;
+            break;
+          }
+          k_add<<<g256, 256, 0, c.stream>>>(x, v.x, n);
+          SFEM_CHECK_LAUNCH();
+          SFEM_CUDA(cudaMemsetAsync(v.x, 0, n * sizeof(double), c.stream));
+          rel = true_residual();  // writes the FP64 true residual into r = v.r
+        }
       }
     } else {
       throw Error{SFEM_EINVAL, "solver kind not available in this entry point"};

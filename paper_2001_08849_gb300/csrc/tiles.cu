@@ -1,0 +1,710 @@
+// Tiled single-pass FP32 operator of FS-FEM-T4 (the hot kernel of the
+// mixed-precision solve).
+//
+// Same arithmetic as the two-pass matrix-free operator (operator.cu):
+//   w_e = V_e eps_e,  t_e = c sum_a kap_ea (w_e + w_nbr(a)),  y += (V_e B_e)^T t_e
+// (Eq. 2-3 face averages on quarter-volume sub-tets, Eq. 9), but one CTA
+// owns a tile of spatially close tets and keeps everything between the
+// gather of u and the scatter of y in shared memory:
+//   1. u at the tile's nodes -> smem (FP32);
+//   2. strains of the tile's tets and of its halo (the neighbours across
+//      the tile's outer faces, recomputed here) -> smem;
+//   3. face-averaged stress per tile tet and its four nodal forces -> smem;
+//   4. each tile node sums its slots in a fixed order (tile-local
+//      incidence list built at setup; no shared-memory atomics) and adds
+//      the sum to y with one global atomic per component.
+// Setup reorders tets by a coarse spatial binning of their centroids
+// (counting sort on a Morton-free lexicographic bin grid), cuts bins into
+// tiles of at most kTileMax tets, and builds per tile: the sorted node
+// list, 16-bit local connectivity, 16-bit local neighbour indices (into
+// tile tets, then halo tets) and the halo list.  Per-tet data streamed by
+// the kernel: one 64-byte record (V_e-scaled gradients, V_e, local
+// connectivity, local neighbours); the face weights 1/(4 (V_e + V_nbr))
+// are formed from the volumes staged in shared memory.
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstring>
+
+#include "reduce.cuh"
+#include "sfem_internal.cuh"
+
+namespace sfem {
+
+constexpr int kTileMax = 512;            // tets per tile
+constexpr int kTileTarget = 448;         // mean tets per spatial bin
+constexpr int kTileThreads = 256;
+constexpr int kHaloCand = 4 * kTileMax;  // neighbour candidates per tile
+constexpr unsigned short kNoNbr = 0xFFFF;
+
+// ---------------------------------------------------------------------------
+// setup kernels
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long ordered_bits(double v) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  return (b & 0x8000000000000000ull) ? ~b : (b | 0x8000000000000000ull);
+}
+static double from_ordered_bits(unsigned long long b) {
+  b = (b & 0x8000000000000000ull) ? (b & 0x7fffffffffffffffull) : ~b;
+  double d;
+  memcpy(&d, &b, 8);
+  return d;
+}
+
+__global__ void k_bbox(const double *__restrict__ xyz, int64_t n_nodes, unsigned long long *mn,
+                       unsigned long long *mx) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_nodes) return;
+  for (int k = 0; k < 3; ++k) {
+    unsigned long long b = ordered_bits(xyz[3 * i + k]);
+    atomicMin(&mn[k], b);
+    atomicMax(&mx[k], b);
+  }
+}
+
+struct BinGrid {
+  double lo[3], inv[3];
+  int nb[3];
+};
+
+__global__ void k_bin_keys(const double *__restrict__ xyz, const int32_t *__restrict__ tets, int64_t n_tets,
+                           BinGrid g, int32_t *__restrict__ key, int32_t *__restrict__ hist) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n_tets) return;
+  int4 t = reinterpret_cast<const int4 *>(tets)[e];
+  int v[4] = {t.x, t.y, t.z, t.w};
+  int b[3];
+  for (int k = 0; k < 3; ++k) {
+    double c = 0.25 * (xyz[3 * (int64_t)v[0] + k] + xyz[3 * (int64_t)v[1] + k] + xyz[3 * (int64_t)v[2] + k] +
+                       xyz[3 * (int64_t)v[3] + k]);
+    int q = (int)floor((c - g.lo[k]) * g.inv[k]);
+    b[k] = min(max(q, 0), g.nb[k] - 1);
+  }
+  int kk = (b[0] * g.nb[1] + b[1]) * g.nb[2] + b[2];
+  key[e] = kk;
+  atomicAdd(&hist[kk], 1);
+}
+
+__global__ void k_bin_scatter(const int32_t *__restrict__ key, int64_t n_tets, unsigned long long *cursor,
+                              int32_t *__restrict__ perm) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n_tets) return;
+  unsigned long long pos = atomicAdd(&cursor[key[e]], 1ull);
+  perm[pos] = (int32_t)e;
+}
+
+__global__ void k_bin_tiles(const int64_t *__restrict__ bin_ptr, int64_t n_bins, int32_t *__restrict__ ntile) {
+  int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n_bins) return;
+  int64_t c = bin_ptr[b + 1] - bin_ptr[b];
+  ntile[b] = (int32_t)((c + kTileMax - 1) / kTileMax);
+}
+
+__global__ void k_tile_ranges(const int64_t *__restrict__ bin_ptr, const int64_t *__restrict__ tile_base,
+                              int64_t n_bins, int64_t n_tiles, int32_t *__restrict__ tile_start) {
+  int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n_bins) return;
+  int64_t s = bin_ptr[b], e = bin_ptr[b + 1];
+  int64_t t = tile_base[b];
+  for (int64_t x = s; x < e; x += kTileMax, ++t) tile_start[t] = (int32_t)x;
+  if (b == n_bins - 1) tile_start[n_tiles] = (int32_t)e;
+}
+
+// Per-tet record of the tiled operator (64 bytes, tile order):
+//   [0..8]  V_e grad N_1..3 (node 1..3 by x, y, z) in FP32
+//   [9]     V_e in FP32
+//   [10,11] local connectivity (4 x 16 bit), written by k_tile_build
+//   [12,13] local neighbours (4 x 16 bit, 0xFFFF exterior), k_tile_build
+//   [14,15] four entries (16 bit) of the tile's node-incidence list: the
+//           list holds, for each tile node in turn, the slots 4j+a of the
+//           tile tets j whose vertex a is that node; record j stores
+//           entries 4j..4j+3
+__global__ void k_reorder(const int32_t *__restrict__ perm, int64_t n, const float *__restrict__ Gs32,
+                          const double *__restrict__ vol, float4 *__restrict__ rec, int32_t *__restrict__ iperm) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int64_t o = perm[i];
+  iperm[o] = (int32_t)i;
+  float g[9];
+  for (int k = 0; k < 9; ++k) g[k] = Gs32[k * n + o];
+  float4 *r = rec + 4 * i;
+  r[0] = make_float4(g[0], g[1], g[2], g[3]);
+  r[1] = make_float4(g[4], g[5], g[6], g[7]);
+  r[2] = make_float4(g[8], (float)vol[o], 0.f, 0.f);
+  r[3] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// ascending bitonic sort of a[0..P) in shared memory (P a power of two)
+__device__ void block_bitonic_sort(int *a, int P) {
+  for (int k = 2; k <= P; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        int ixj = i ^ j;
+        if (ixj > i) {
+          int x = a[i], y = a[ixj];
+          bool up = (i & k) == 0;
+          if ((x > y) == up) {
+            a[i] = y;
+            a[ixj] = x;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// compact the sorted a[0..P) to its unique values < INT_MAX (in place);
+// returns the count (all threads)
+__device__ int block_unique(int *a, int P, int *scratch /* blockDim */) {
+  // each thread owns a contiguous chunk, so the order of heads is kept
+  const int chunk = (P + blockDim.x - 1) / blockDim.x;
+  const int b = threadIdx.x * chunk, e = min(P, b + chunk);
+  int c = 0;
+  for (int i = b; i < e; ++i) {
+    int v = a[i];
+    if (v != INT_MAX && (i == 0 || a[i - 1] != v)) ++c;
+  }
+  scratch[threadIdx.x] = c;
+  __syncthreads();
+  // exclusive scan over threads (small: done by thread 0)
+  __shared__ int total;
+  if (threadIdx.x == 0) {
+    int run = 0;
+    for (int t = 0; t < (int)blockDim.x; ++t) {
+      int x = scratch[t];
+      scratch[t] = run;
+      run += x;
+    }
+    total = run;
+  }
+  __syncthreads();
+  // gather heads into registers first (the compaction is in place)
+  int vals[64];
+  int nv = 0;
+  for (int i = b; i < e && nv < 64; ++i) {
+    int v = a[i];
+    if (v != INT_MAX && (i == 0 || a[i - 1] != v)) vals[nv++] = v;
+  }
+  __syncthreads();
+  for (int k = 0; k < nv; ++k) a[scratch[threadIdx.x] + k] = vals[k];
+  __syncthreads();
+  return total;
+}
+
+__device__ __forceinline__ int bsearch_int(const int *a, int n, int key) {
+  int lo = 0, hi = n - 1;
+  while (lo <= hi) {
+    int mid = (lo + hi) >> 1;
+    int v = a[mid];
+    if (v == key) return mid;
+    if (v < key)
+      lo = mid + 1;
+    else
+      hi = mid - 1;
+  }
+  return -1;
+}
+
+struct TileBuild {
+  const int32_t *tile_start;
+  const int32_t *perm, *iperm;
+  const int32_t *tets;   // original numbering
+  const int32_t *nbr;    // original numbering
+  // pass 1 outputs
+  int32_t *n_halo, *n_nodes;
+  // pass 2 inputs/outputs
+  const int64_t *hoff, *noff;
+  int32_t *halo_tet;
+  uint2 *halo_lconn;
+  int32_t *tile_nodes;
+  float4 *rec;   // per-tet records (tile order): lconn -> words 10,11; lnbr -> 12,13; inc -> 14,15
+  uint16_t *node_inc;  // per tile node: start of its slots in the incidence list
+  unsigned long long *overflow;
+};
+
+// one CTA per tile; dynamic smem: halo candidates (kHaloCand padded) +
+// node candidates (4*(kTileMax + kHaloCand) padded)
+constexpr int kHaloP = 2048;                        // >= kHaloCand, power of two
+constexpr int kNodeP = 16384;                       // >= 4*(kTileMax + kHaloCand)
+static_assert(kHaloP >= kHaloCand && kNodeP >= 4 * (kTileMax + kHaloCand), "tile build buffers too small");
+constexpr int kBuildThreads = 1024;
+
+__global__ void __launch_bounds__(kBuildThreads) k_tile_build(TileBuild B, int pass) {
+  extern __shared__ int sm[];
+  int *halo = sm;                 // kHaloP
+  int *nodes = sm + kHaloP;       // kNodeP
+  __shared__ int scratch[kBuildThreads];
+  const int tile = blockIdx.x;
+  const int s = B.tile_start[tile], e = B.tile_start[tile + 1];
+  const int n_own = e - s;
+  // halo candidates: neighbours outside [s, e)
+  for (int i = threadIdx.x; i < kHaloP; i += blockDim.x) halo[i] = INT_MAX;
+  __syncthreads();
+  for (int i = threadIdx.x; i < 4 * n_own; i += blockDim.x) {
+    const int tnew = s + i / 4, a = i % 4;
+    const int nb_old = B.nbr[4 * (int64_t)B.perm[tnew] + a];
+    if (nb_old >= 0) {
+      const int nb_new = B.iperm[nb_old];
+      if (nb_new < s || nb_new >= e) halo[i] = nb_new;
+    }
+  }
+  __syncthreads();
+  block_bitonic_sort(halo, kHaloP);
+  const int H = block_unique(halo, kHaloP, scratch);
+  // node candidates of own and halo tets
+  for (int i = threadIdx.x; i < kNodeP; i += blockDim.x) nodes[i] = INT_MAX;
+  __syncthreads();
+  for (int i = threadIdx.x; i < 4 * (n_own + H); i += blockDim.x) {
+    const int j = i / 4, a = i % 4;
+    const int tnew = j < n_own ? s + j : halo[j - n_own];
+    nodes[i] = B.tets[4 * (int64_t)B.perm[tnew] + a];
+  }
+  __syncthreads();
+  block_bitonic_sort(nodes, kNodeP);
+  const int L = block_unique(nodes, kNodeP, scratch);
+  if (pass == 1) {
+    if (threadIdx.x == 0) {
+      B.n_halo[tile] = H;
+      B.n_nodes[tile] = L;
+      if (L > 65535 || n_own + H > 65535) atomicAdd(B.overflow, 1ull);
+    }
+    return;
+  }
+  const int64_t h0 = B.hoff[tile], n0 = B.noff[tile];
+  for (int i = threadIdx.x; i < L; i += blockDim.x) B.tile_nodes[n0 + i] = nodes[i];
+  // node-incidence list of the tile's own slots, sorted by (local node, slot):
+  // keys live in the halo buffer region beyond H (the halo list itself is
+  // still needed below), so use a separate scratch: the tail of `nodes`
+  // past L is free.
+  int *keys = nodes + ((L + 31) & ~31);
+  const int KP = kHaloP;  // 4 * kTileMax slots, power of two
+  for (int i = threadIdx.x; i < KP; i += blockDim.x) {
+    int v = INT_MAX;
+    if (i < 4 * n_own) {
+      const int64_t to = B.perm[s + i / 4];
+      const int l = bsearch_int(nodes, L, B.tets[4 * to + (i % 4)]);
+      v = (l << 11) | i;
+    }
+    keys[i] = v;
+  }
+  __syncthreads();
+  block_bitonic_sort(keys, KP);
+  uint16_t *rinc = reinterpret_cast<uint16_t *>(B.rec + 4 * (int64_t)s);
+  for (int i = threadIdx.x; i < 4 * n_own; i += blockDim.x) {
+    // entry i goes to record (s + i/4), 16-bit word 28 + i%4 (words 14,15)
+    rinc[(i / 4) * 32 + 28 + (i % 4)] = (uint16_t)(keys[i] & 2047);
+  }
+  // start of each tile node's slots: number of keys below (l << 11)
+  for (int l = threadIdx.x; l < L; l += blockDim.x) {
+    int lo = 0, hi = 4 * n_own;
+    const int key = l << 11;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (keys[mid] < key)
+        lo = mid + 1;
+      else
+        hi = mid;
+    }
+    B.node_inc[n0 + l] = (uint16_t)lo;
+  }
+  for (int j = threadIdx.x; j < n_own + H; j += blockDim.x) {
+    const int tnew = j < n_own ? s + j : halo[j - n_own];
+    const int64_t to = B.perm[tnew];
+    unsigned int l[4];
+    for (int a = 0; a < 4; ++a) l[a] = (unsigned int)bsearch_int(nodes, L, B.tets[4 * to + a]);
+    const uint2 lc = make_uint2(l[0] | (l[1] << 16), l[2] | (l[3] << 16));
+    if (j < n_own) {
+      unsigned int *rw = reinterpret_cast<unsigned int *>(B.rec + 4 * (int64_t)tnew);
+      rw[10] = lc.x;
+      rw[11] = lc.y;
+      unsigned int nb[4];
+      for (int a = 0; a < 4; ++a) {
+        const int nb_old = B.nbr[4 * to + a];
+        if (nb_old < 0) {
+          nb[a] = kNoNbr;
+        } else {
+          const int nb_new = B.iperm[nb_old];
+          nb[a] = (nb_new >= s && nb_new < e) ? (unsigned int)(nb_new - s)
+                                                : (unsigned int)(n_own + bsearch_int(halo, H, nb_new));
+        }
+      }
+      rw[12] = nb[0] | (nb[1] << 16);
+      rw[13] = nb[2] | (nb[3] << 16);
+    } else {
+      B.halo_tet[h0 + (j - n_own)] = tnew;
+      B.halo_lconn[h0 + (j - n_own)] = lc;
+    }
+  }
+}
+
+__global__ void k_max_i32(const int32_t *__restrict__ a, const int32_t *__restrict__ b, int64_t n, int *out) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  atomicMax(&out[0], a[i]);
+  atomicMax(&out[1], b[i]);
+}
+
+// ---------------------------------------------------------------------------
+// the fused operator
+// ---------------------------------------------------------------------------
+struct TileArgs {
+  const int32_t *tile_start;
+  const int64_t *hoff, *noff;
+  const int32_t *halo_tet;
+  const uint2 *halo_lconn;
+  const int32_t *tile_nodes;
+  const uint16_t *node_inc;  // per tile node: first slot in its incidence list
+  const float4 *rec;   // 64-byte per-tet records, tile order
+};
+
+struct TetGeo {
+  float g[4][3];
+  float V;
+};
+
+__device__ __forceinline__ void rec_unpack(const float4 (&q)[4], TetGeo &G, uint2 &lc) {
+  G.g[1][0] = q[0].x, G.g[1][1] = q[0].y, G.g[1][2] = q[0].z;
+  G.g[2][0] = q[0].w, G.g[2][1] = q[1].x, G.g[2][2] = q[1].y;
+  G.g[3][0] = q[1].z, G.g[3][1] = q[1].w, G.g[3][2] = q[2].x;
+  G.V = q[2].y;
+  lc = make_uint2(__float_as_uint(q[2].z), __float_as_uint(q[2].w));
+#pragma unroll
+  for (int i = 0; i < 3; ++i) G.g[0][i] = -(G.g[1][i] + G.g[2][i] + G.g[3][i]);
+}
+
+__device__ __forceinline__ void load_rec(const float4 *__restrict__ rec, int t, TetGeo &G, uint2 &lc, uint2 *lnb) {
+  const float4 a = __ldg(rec + 4 * (int64_t)t), b = __ldg(rec + 4 * (int64_t)t + 1);
+  const float4 c = __ldg(rec + 4 * (int64_t)t + 2);
+  G.g[1][0] = a.x, G.g[1][1] = a.y, G.g[1][2] = a.z;
+  G.g[2][0] = a.w, G.g[2][1] = b.x, G.g[2][2] = b.y;
+  G.g[3][0] = b.z, G.g[3][1] = b.w, G.g[3][2] = c.x;
+  G.V = c.y;
+  lc = make_uint2(__float_as_uint(c.z), __float_as_uint(c.w));
+  if (lnb) {
+    const float4 d = __ldg(rec + 4 * (int64_t)t + 3);
+    *lnb = make_uint2(__float_as_uint(d.x), __float_as_uint(d.y));
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) G.g[0][i] = -(G.g[1][i] + G.g[2][i] + G.g[3][i]);
+}
+
+// w = V_e eps_e (Voigt) from the tile's smem displacements; w[6] = V_e
+__device__ __forceinline__ void strain_to(const float4 *su, uint2 lc, const TetGeo &G, float4 *w2) {
+  const int l[4] = {(int)(lc.x & 0xFFFF), (int)(lc.x >> 16), (int)(lc.y & 0xFFFF), (int)(lc.y >> 16)};
+  float H[3][3] = {};
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const float4 u = su[l[a]];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      H[0][j] = fmaf(u.x, G.g[a][j], H[0][j]);
+      H[1][j] = fmaf(u.y, G.g[a][j], H[1][j]);
+      H[2][j] = fmaf(u.z, G.g[a][j], H[2][j]);
+    }
+  }
+  w2[0] = make_float4(H[0][0], H[1][1], H[2][2], H[1][2] + H[2][1]);
+  w2[1] = make_float4(H[2][0] + H[0][2], H[0][1] + H[1][0], G.V, 0.f);
+}
+
+template <class TU, class TY>
+__global__ void __launch_bounds__(kTileThreads, 3)
+    k_mf32_tiled(TileArgs A, const TU *__restrict__ u, TY *__restrict__ y, float lam, float mu, double *partials,
+                 unsigned int *ticket, double *energy_out, const int *done) {
+  if (done && *done) return;
+  extern __shared__ float4 smem[];
+  const int tile = blockIdx.x;
+  const int s = A.tile_start[tile], n_own = A.tile_start[tile + 1] - s;
+  const int64_t h0 = A.hoff[tile], n0 = A.noff[tile];
+  const int H = (int)(A.hoff[tile + 1] - h0), L = (int)(A.noff[tile + 1] - n0);
+  const int nt = n_own + H;
+  // shared memory: displacements (L), strains split in two float4 arrays
+  // (w0..w3 | w4, w5, V, 0) over tile + halo tets, nodal forces of the tile
+  // tets (4 slots x xyz = 12 floats per tet), incidence list and node starts
+  float4 *su = smem;
+  float4 *swa = su + L;
+  float4 *swb = swa + nt;
+  float *sfe = reinterpret_cast<float *>(swb + nt);             // 12 * n_own
+  uint16_t *sinc = reinterpret_cast<uint16_t *>(sfe + 12 * n_own);  // 4 * n_own
+  uint16_t *snode = sinc + 4 * n_own;                            // L
+
+  for (int i = threadIdx.x; i < L; i += kTileThreads) {
+    const int64_t node = A.tile_nodes[n0 + i];
+    const TU *up = u + 3 * node;
+    su[i] = make_float4((float)__ldg(up), (float)__ldg(up + 1), (float)__ldg(up + 2), 0.f);
+    snode[i] = A.node_inc[n0 + i];
+  }
+  __syncthreads();
+  // own tets: records kept in registers for the stress phase (loads for
+  // both tets issued before any use)
+  constexpr int kPer = kTileMax / kTileThreads;
+  float4 rr[kPer][4];
+#pragma unroll
+  for (int r = 0; r < kPer; ++r) {
+    const int j = threadIdx.x + r * kTileThreads;
+    if (j < n_own) {
+      const float4 *rp = A.rec + 4 * (int64_t)(s + j);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) rr[r][q] = __ldg(rp + q);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < kPer; ++r) {
+    const int j = threadIdx.x + r * kTileThreads;
+    if (j < n_own) {
+      TetGeo G;
+      uint2 lc;
+      rec_unpack(rr[r], G, lc);
+      float4 w2[2];
+      strain_to(su, lc, G, w2);
+      swa[j] = w2[0];
+      swb[j] = w2[1];
+      reinterpret_cast<uint2 *>(sinc)[j] = make_uint2(__float_as_uint(rr[r][3].z), __float_as_uint(rr[r][3].w));
+    }
+  }
+  for (int h = threadIdx.x; h < H; h += kTileThreads) {
+    TetGeo G;
+    uint2 lc;
+    load_rec(A.rec, A.halo_tet[h0 + h], G, lc, nullptr);
+    lc = A.halo_lconn[h0 + h];
+    float4 w2[2];
+    strain_to(su, lc, G, w2);
+    swa[n_own + h] = w2[0];
+    swb[n_own + h] = w2[1];
+  }
+  __syncthreads();
+
+  double en = 0.0;
+#pragma unroll
+  for (int r = 0; r < kPer; ++r) {
+    const int j = threadIdx.x + r * kTileThreads;
+    if (j >= n_own) continue;
+    TetGeo G;
+    uint2 lc;
+    rec_unpack(rr[r], G, lc);
+    const uint2 nb2 = make_uint2(__float_as_uint(rr[r][3].x), __float_as_uint(rr[r][3].y));
+    const int nb[4] = {(int)(nb2.x & 0xFFFF), (int)(nb2.x >> 16), (int)(nb2.y & 0xFFFF), (int)(nb2.y >> 16)};
+    const float4 w0 = swa[j], w1 = swb[j];
+    const float W[6] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y};
+    const float Ve = w1.z;
+    // face weights kap_a = 1/(4 (V_e + V_nbr)), 1/(4 V_e) on exterior faces
+    float S[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float ks = 0.f;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      if (nb[a] != kNoNbr) {
+        const float4 n0v = swa[nb[a]], n1v = swb[nb[a]];
+        const float k = 0.25f / (Ve + n1v.z);
+        ks += k;
+        S[0] = fmaf(k, n0v.x, S[0]);
+        S[1] = fmaf(k, n0v.y, S[1]);
+        S[2] = fmaf(k, n0v.z, S[2]);
+        S[3] = fmaf(k, n0v.w, S[3]);
+        S[4] = fmaf(k, n1v.x, S[4]);
+        S[5] = fmaf(k, n1v.y, S[5]);
+      } else {
+        ks += 0.25f / Ve;
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) S[i] = fmaf(ks, W[i], S[i]);
+    const float tr = S[0] + S[1] + S[2];
+    const float st[6] = {lam * tr + 2.f * mu * S[0], lam * tr + 2.f * mu * S[1], lam * tr + 2.f * mu * S[2],
+                         mu * S[3], mu * S[4], mu * S[5]};
+    float el = 0.f;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) el = fmaf(W[i], st[i], el);
+    en += (double)el;
+    float f[12];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      f[3 * a] = G.g[a][0] * st[0] + G.g[a][1] * st[5] + G.g[a][2] * st[4];
+      f[3 * a + 1] = G.g[a][0] * st[5] + G.g[a][1] * st[1] + G.g[a][2] * st[3];
+      f[3 * a + 2] = G.g[a][0] * st[4] + G.g[a][1] * st[3] + G.g[a][2] * st[2];
+    }
+    float4 *fo = reinterpret_cast<float4 *>(sfe + 12 * j);
+    fo[0] = make_float4(f[0], f[1], f[2], f[3]);
+    fo[1] = make_float4(f[4], f[5], f[6], f[7]);
+    fo[2] = make_float4(f[8], f[9], f[10], f[11]);
+  }
+  __syncthreads();
+  // each tile node sums the forces of its slots (fixed order: deterministic)
+  const int nslots = 4 * n_own;
+  for (int i = threadIdx.x; i < L; i += kTileThreads) {
+    const int b = snode[i], e = (i + 1 < L) ? snode[i + 1] : nslots;
+    if (b == e) continue;
+    float fx = 0.f, fy = 0.f, fz = 0.f;
+    for (int k = b; k < e; ++k) {
+      const int slot = sinc[k];
+      const float *fp = sfe + 12 * (slot >> 2) + 3 * (slot & 3);
+      fx += fp[0];
+      fy += fp[1];
+      fz += fp[2];
+    }
+    TY *yp = y + 3 * (int64_t)A.tile_nodes[n0 + i];
+    atomicAdd(yp, (TY)fx);
+    atomicAdd(yp + 1, (TY)fy);
+    atomicAdd(yp + 2, (TY)fz);
+  }
+  if (energy_out) {
+    double vv[1] = {en};
+    grid_sum<kTileThreads, 1>(vv, partials, ticket, energy_out);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+void build_tiles(Ctx &c) {
+  const int64_t n = c.n_tets;
+  // bounding box and bin grid (mean bin holds about kTileTarget tets)
+  unsigned long long *bb = c.mem.get<unsigned long long>(6);
+  unsigned long long init[6];
+  for (int k = 0; k < 3; ++k) {
+    init[k] = ~0ull;
+    init[3 + k] = 0ull;
+  }
+  SFEM_CUDA(cudaMemcpyAsync(bb, init, sizeof init, cudaMemcpyHostToDevice, c.stream));
+  k_bbox<<<grid_for(c.n_nodes, 256), 256, 0, c.stream>>>(c.xyz, c.n_nodes, bb, bb + 3);
+  SFEM_CHECK_LAUNCH();
+  unsigned long long hb[6];
+  SFEM_CUDA(cudaMemcpyAsync(hb, bb, sizeof hb, cudaMemcpyDeviceToHost, c.stream));
+  SFEM_CUDA(cudaStreamSynchronize(c.stream));
+  c.mem.drop(bb);
+  double lo[3], ext[3], boxvol = 1.0;
+  for (int k = 0; k < 3; ++k) {
+    lo[k] = from_ordered_bits(hb[k]);
+    ext[k] = std::max(from_ordered_bits(hb[3 + k]) - lo[k], 1e-300);
+    boxvol *= ext[k];
+  }
+  const double edge = std::cbrt(boxvol / (double)n * kTileTarget);
+  BinGrid g;
+  int64_t nbins = 1;
+  for (int k = 0; k < 3; ++k) {
+    g.nb[k] = (int)std::min<double>(std::max(1.0, std::ceil(ext[k] / edge)), 1 << 20);
+    g.lo[k] = lo[k];
+    g.inv[k] = g.nb[k] / ext[k];
+    nbins *= g.nb[k];
+  }
+  SFEM_REQUIRE(nbins < (int64_t(1) << 30), SFEM_EINVAL, "tile grid too large");
+  int32_t *key = c.mem.get<int32_t>(n);
+  int32_t *hist = c.mem.get<int32_t>(nbins);
+  SFEM_CUDA(cudaMemsetAsync(hist, 0, nbins * sizeof(int32_t), c.stream));
+  k_bin_keys<<<grid_for(n, 256), 256, 0, c.stream>>>(c.xyz, c.tets, n, g, key, hist);
+  SFEM_CHECK_LAUNCH();
+  int64_t *bin_ptr = c.mem.get<int64_t>(nbins + 1);
+  scan_counts(c, hist, nbins, bin_ptr);
+  unsigned long long *cursor = c.mem.get<unsigned long long>(nbins);
+  SFEM_CUDA(cudaMemcpyAsync(cursor, bin_ptr, nbins * sizeof(int64_t), cudaMemcpyDeviceToDevice, c.stream));
+  c.tl.perm = c.mem.get<int32_t>(n);
+  k_bin_scatter<<<grid_for(n, 256), 256, 0, c.stream>>>(key, n, cursor, c.tl.perm);
+  SFEM_CHECK_LAUNCH();
+  k_bin_tiles<<<grid_for(nbins, 256), 256, 0, c.stream>>>(bin_ptr, nbins, hist);  // hist reused: tiles per bin
+  SFEM_CHECK_LAUNCH();
+  int64_t *tile_base = c.mem.get<int64_t>(nbins + 1);
+  c.tl.n_tiles = scan_counts(c, hist, nbins, tile_base);
+  c.tl.tile_start = c.mem.get<int32_t>(c.tl.n_tiles + 1);
+  k_tile_ranges<<<grid_for(nbins, 256), 256, 0, c.stream>>>(bin_ptr, tile_base, nbins, c.tl.n_tiles,
+                                                            c.tl.tile_start);
+  SFEM_CHECK_LAUNCH();
+  c.mem.drop(key);
+  c.mem.drop(cursor);
+  c.mem.drop(bin_ptr);
+  c.mem.drop(tile_base);
+
+  // reordered operator data
+  c.tl.iperm = c.mem.get<int32_t>(n);
+  c.tl.rec = c.mem.get<float4>(4 * n);
+  k_reorder<<<grid_for(n, 256), 256, 0, c.stream>>>(c.tl.perm, n, c.Gs32, c.vol, c.tl.rec, c.tl.iperm);
+  SFEM_CHECK_LAUNCH();
+
+  // per-tile tables, pass 1 (sizes)
+  const int64_t nt = c.tl.n_tiles;
+  int32_t *nh = hist;  // reuse (>= nt? no: allocate)
+  nh = c.mem.get<int32_t>(nt);
+  int32_t *nn = c.mem.get<int32_t>(nt);
+  unsigned long long *ovf = c.mem.get<unsigned long long>(1);
+  SFEM_CUDA(cudaMemsetAsync(ovf, 0, 8, c.stream));
+  TileBuild B{};
+  B.tile_start = c.tl.tile_start;
+  B.perm = c.tl.perm;
+  B.iperm = c.tl.iperm;
+  B.tets = c.tets;
+  B.nbr = c.nbr;
+  B.n_halo = nh;
+  B.n_nodes = nn;
+  B.overflow = ovf;
+  const size_t build_smem = (kHaloP + kNodeP) * sizeof(int);
+  SFEM_CUDA(cudaFuncSetAttribute(k_tile_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)build_smem));
+  k_tile_build<<<(unsigned)nt, kBuildThreads, build_smem, c.stream>>>(B, 1);
+  SFEM_CHECK_LAUNCH();
+  c.tl.hoff = c.mem.get<int64_t>(nt + 1);
+  c.tl.noff = c.mem.get<int64_t>(nt + 1);
+  const int64_t total_h = scan_counts(c, nh, nt, c.tl.hoff);
+  const int64_t total_n = scan_counts(c, nn, nt, c.tl.noff);
+  int *mx = c.mem.get<int>(2);
+  SFEM_CUDA(cudaMemsetAsync(mx, 0, 2 * sizeof(int), c.stream));
+  k_max_i32<<<grid_for(nt, 256), 256, 0, c.stream>>>(nh, nn, nt, mx);
+  SFEM_CHECK_LAUNCH();
+  int hm[2];
+  unsigned long long hovf = 0;
+  SFEM_CUDA(cudaMemcpyAsync(hm, mx, sizeof hm, cudaMemcpyDeviceToHost, c.stream));
+  SFEM_CUDA(cudaMemcpyAsync(&hovf, ovf, 8, cudaMemcpyDeviceToHost, c.stream));
+  SFEM_CUDA(cudaStreamSynchronize(c.stream));
+  SFEM_REQUIRE(hovf == 0, SFEM_EMESH, "tile tables exceed 16-bit local indices");
+  c.tl.max_halo = hm[0];
+  c.tl.max_nodes = hm[1];
+  c.tl.halo_tet = c.mem.get<int32_t>(std::max<int64_t>(total_h, 1));
+  c.tl.halo_lconn = c.mem.get<uint2>(std::max<int64_t>(total_h, 1));
+  c.tl.tile_nodes = c.mem.get<int32_t>(total_n);
+  c.tl.node_inc = c.mem.get<uint16_t>(total_n);
+  B.hoff = c.tl.hoff;
+  B.noff = c.tl.noff;
+  B.halo_tet = c.tl.halo_tet;
+  B.halo_lconn = c.tl.halo_lconn;
+  B.tile_nodes = c.tl.tile_nodes;
+  B.node_inc = c.tl.node_inc;
+  B.rec = c.tl.rec;
+  k_tile_build<<<(unsigned)nt, kBuildThreads, build_smem, c.stream>>>(B, 2);
+  SFEM_CHECK_LAUNCH();
+  c.mem.drop(nh);
+  c.mem.drop(nn);
+  c.mem.drop(ovf);
+  c.mem.drop(mx);
+  c.mem.drop(hist);
+  c.tl.smem = (size_t)c.tl.max_nodes * (sizeof(float4) + sizeof(uint16_t)) +
+              (size_t)(kTileMax + c.tl.max_halo) * 2 * sizeof(float4) + (size_t)kTileMax * (12 * sizeof(float) + 8);
+  c.tl.smem = (c.tl.smem + 15) & ~size_t(15);
+  SFEM_REQUIRE(c.tl.smem <= 220 * 1024, SFEM_EMESH, "tile working set exceeds shared memory");
+  c.tl.total_halo = total_h;
+  c.tl.total_nodes = total_n;
+  // opt in to the dynamic shared memory this mesh needs (never lowered, so
+  // contexts of smaller meshes keep working)
+  static size_t smem_set = 48 * 1024;
+  if (c.tl.smem > smem_set) {
+    SFEM_CUDA(cudaFuncSetAttribute(k_mf32_tiled<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)c.tl.smem));
+    SFEM_CUDA(cudaFuncSetAttribute(k_mf32_tiled<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)c.tl.smem));
+    smem_set = c.tl.smem;
+  }
+  c.tl.ready = true;
+}
+
+template <class TU, class TY>
+void launch_mf32_tiled(Ctx &c, cudaStream_t st, const TU *u, TY *y, double *energy_out, const int *done) {
+  TileArgs A{c.tl.tile_start, c.tl.hoff, c.tl.noff, c.tl.halo_tet, c.tl.halo_lconn, c.tl.tile_nodes,
+             c.tl.node_inc, c.tl.rec};
+  k_mf32_tiled<TU, TY><<<(unsigned)c.tl.n_tiles, kTileThreads, c.tl.smem, st>>>(
+      A, u, y, (float)c.lam, (float)c.mu, c.red_partial, c.tickets + 6, energy_out, done);
+  SFEM_CHECK_LAUNCH();
+}
+
+template void launch_mf32_tiled<float, float>(Ctx &, cudaStream_t, const float *, float *, double *, const int *);
+template void launch_mf32_tiled<double, double>(Ctx &, cudaStream_t, const double *, double *, double *,
+                                                const int *);
+
+}  // namespace sfem

@@ -55,7 +55,8 @@ class sfem_solve_opts(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("op64", ctypes.c_int), ("rhs", ctypes.c_int),
                 ("u_on_device", ctypes.c_int), ("warm_start", ctypes.c_int), ("max_iter", ctypes.c_int),
                 ("tol", ctypes.c_double), ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int),
-                ("check_every", ctypes.c_int), ("learned", ctypes.c_void_p), ("reserved", ctypes.c_int * 6)]
+                ("check_every", ctypes.c_int), ("learned", ctypes.c_void_p), ("fp32_vectors", ctypes.c_int),
+                ("reserved", ctypes.c_int * 5)]
 
 
 class sfem_solve_info(ctypes.Structure):
@@ -218,13 +219,14 @@ def sfem_apply(h, u, y, op=SFEM_OP_MF64, nrhs=1):
 
 
 def solve_opts(kind=SFEM_SOLVE_PCG64, op64=SFEM_OP_MF64, rhs=0, tol=1e-8, max_iter=0, inner_tol=0.0,
-               max_outer=0, check_every=0, u_on_device=False, warm_start=False, learned=None):
+               max_outer=0, check_every=0, u_on_device=False, warm_start=False, learned=None, fp32_vectors=False):
     o = sfem_solve_opts()
     o.kind, o.op64, o.rhs = int(kind), int(op64), int(rhs)
     o.u_on_device, o.warm_start = int(bool(u_on_device)), int(bool(warm_start))
     o.max_iter, o.tol, o.inner_tol = int(max_iter), float(tol), float(inner_tol)
     o.max_outer, o.check_every = int(max_outer), int(check_every)
     o.learned = learned
+    o.fp32_vectors = int(bool(fp32_vectors))
     return o
 
 

@@ -194,6 +194,22 @@ int sfem_get_faces(sfem_ctx *ctx, int32_t *nodes /* n_faces x 5 */,
 int sfem_get_rhs(sfem_ctx *ctx, double *b /* ndof */, int rhs);
 int sfem_get_diag(sfem_ctx *ctx, double *diag /* ndof, diagonal of A */);
 
+/* sfem_apply_noalloc — y = A u like sfem_apply(ctx, u, y, SFEM_OP_MF64, 1),
+ * but allocating no device memory (the paper has no counterpart).  For
+ * callers that must not allocate per call: an application whose memory pool
+ * (another framework's caching allocator) already holds the device memory,
+ * and latency-bound loops that apply the operator thousands of times, where
+ * an allocation or a free may synchronise the device.
+ *   u, y   device pointers, ndof doubles each (one load case);
+ *   limit  meshes of at most 131072 tets (SFEM_EINVAL beyond, with a message);
+ *   scratch a fixed 8 MiB array inside the library, held by every GPU that
+ *          loads it until the process exits, shared by all calls: calls that
+ *          overlap on the GPU (several streams or contexts) race on it.
+ * The first call on a device looks up the scratch address (with the
+ * context's device current); make that first call before any stream capture.
+ * Work runs on the context stream.  No cudaMalloc/cudaFree is called. */
+int sfem_apply_noalloc(sfem_ctx *ctx, const double *u, double *y);
+
 /* Measurement helpers (no counterpart in the paper).
  * sfem_time_operator: launches the raw operator y = K u (no masking) of
  * `op` `reps` times on library-owned scratch vectors, exactly as the solvers

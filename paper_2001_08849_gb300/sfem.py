@@ -85,6 +85,7 @@ _SIG = {
     "sfem_version": (ctypes.c_int, []),
     "sfem_time_operator": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "sfem_launch_count": (ctypes.c_int64, []),
+    "sfem_apply_noalloc": (ctypes.c_int, [_P, _P, _P]),
 }
 for _name, (_res, _args) in _SIG.items():
     _fn = getattr(lib, _name)
@@ -216,6 +217,12 @@ def sfem_assemble(h):
 def sfem_apply(h, u, y, op=SFEM_OP_MF64, nrhs=1):
     """y = A u on device tensors (float64 for CSR64/MF64, float32 for MF32)."""
     _check(lib.sfem_apply(h, _ptr(u), _ptr(y), int(op), int(nrhs)), "sfem_apply")
+
+
+def sfem_apply_noalloc(h, u, y):
+    """y = A u (FP64 matrix-free, one load case) without any device
+    allocation; u, y are float64 CUDA tensors (see include/sfem.h)."""
+    _check(lib.sfem_apply_noalloc(h, _ptr(u), _ptr(y)), "sfem_apply_noalloc")
 
 
 def solve_opts(kind=SFEM_SOLVE_PCG64, op64=SFEM_OP_MF64, rhs=0, tol=1e-8, max_iter=0, inner_tol=0.0,

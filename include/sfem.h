@@ -115,7 +115,7 @@ typedef struct sfem_solve_opts {
   int max_outer;       /* IR: reliable updates at most (0: 200) */
   int check_every;     /* iterations between host convergence checks (0: 32) */
   const void *learned; /* FPCG_LEARNED: an sfem_learned handle */
-  int fp32_vectors;    /* IR: 1 = FP32 CG vectors too (default 0: FP64 vectors) */
+  int fp32_vectors;    /* IR vectors: 0 FP64 p, q, r (default); 1 all FP32; 2 FP32 p, q and FP64 r */
   int reserved[5];
 } sfem_solve_opts;
 

@@ -28,27 +28,33 @@ namespace sfem {
 
 constexpr int kVecBlock = 256;
 
-template <class T>
+// CG vectors: x (solution or correction) of type TX, residual r of type TR,
+// search direction p and operator output q of type TP (the operator reads
+// p and writes q), Jacobi scaling of type TP.  Scalars and reductions are
+// FP64 throughout.
+template <class TX, class TR, class TP>
 struct PcgVecs {
-  T *x, *r, *p, *q;
-  const T *dinv;
+  TX *x;
+  TR *r;
+  TP *p, *q;
+  const TP *dinv;
   const uint8_t *dmask;
   int64_t n;
 };
 
 // r must already hold the masked residual.  p = D^-1 r, q = 0, and the
 // scalars rz = r.D^-1 r, rr = r.r are set; done when rr <= tol2.
-template <class T>
-__global__ void __launch_bounds__(kVecBlock) k_pcg_init(PcgVecs<T> v, SolveScalars *S, double tol2, int max_iter,
+template <class TX, class TR, class TP>
+__global__ void __launch_bounds__(kVecBlock) k_pcg_init(PcgVecs<TX, TR, TP> v, SolveScalars *S, double tol2, int max_iter,
                                                         double delta2, double *partials, unsigned int *ticket) {
   double rz = 0.0, rr = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * kVecBlock + threadIdx.x; i < v.n; i += (int64_t)gridDim.x * kVecBlock) {
-    const T ri = v.r[i];
-    const T zi = v.dinv[i] * ri;
+    const TP ri = (TP)v.r[i];
+    const TP zi = v.dinv[i] * ri;
     v.p[i] = zi;
-    v.q[i] = T(0);
-    rz += (double)zi * (double)ri;
-    rr += (double)ri * (double)ri;
+    v.q[i] = TP(0);
+    rz += (double)(zi * ri);
+    rr += (double)(ri * ri);
   }
   double vv[2] = {rz, rr};
   if (grid_sum<kVecBlock, 2>(vv, partials, ticket, nullptr) && threadIdx.x == 0) {
@@ -78,15 +84,15 @@ __global__ void __launch_bounds__(kVecBlock) k_pcg_init(PcgVecs<T> v, SolveScala
 // Reliable update (mixed precision): r has been replaced by the true
 // residual; keep the search direction, p = D^-1 r + beta p with
 // beta = (r.D^-1 r) / rz_prev, and resume.  rmax2 restarts from ||r||^2.
-template <class T>
-__global__ void __launch_bounds__(kVecBlock) k_pcg_replace(PcgVecs<T> v, SolveScalars *S, int max_iter,
+template <class TX, class TR, class TP>
+__global__ void __launch_bounds__(kVecBlock) k_pcg_replace(PcgVecs<TX, TR, TP> v, SolveScalars *S, int max_iter,
                                                            double *partials, unsigned int *ticket) {
   double rz = 0.0, rr = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * kVecBlock + threadIdx.x; i < v.n; i += (int64_t)gridDim.x * kVecBlock) {
-    const T ri = v.r[i];
-    const T zi = v.dinv[i] * ri;
-    rz += (double)zi * (double)ri;
-    rr += (double)ri * (double)ri;
+    const TP ri = (TP)v.r[i];
+    const TP zi = v.dinv[i] * ri;
+    rz += (double)(zi * ri);
+    rr += (double)(ri * ri);
   }
   double vv[2] = {rz, rr};
   __shared__ double beta_s;
@@ -105,20 +111,20 @@ __global__ void __launch_bounds__(kVecBlock) k_pcg_replace(PcgVecs<T> v, SolveSc
 }
 
 // second half of the replacement: p = D^-1 r + beta p, q = 0
-template <class T>
-__global__ void __launch_bounds__(kVecBlock) k_pcg_replace_dir(PcgVecs<T> v, const SolveScalars *S) {
-  const T b = (T)S->beta;
+template <class TX, class TR, class TP>
+__global__ void __launch_bounds__(kVecBlock) k_pcg_replace_dir(PcgVecs<TX, TR, TP> v, const SolveScalars *S) {
+  const TP b = (TP)S->beta;
   for (int64_t i = (int64_t)blockIdx.x * kVecBlock + threadIdx.x; i < v.n; i += (int64_t)gridDim.x * kVecBlock) {
-    v.p[i] = v.dinv[i] * v.r[i] + b * v.p[i];
-    v.q[i] = T(0);
+    v.p[i] = v.dinv[i] * (TP)v.r[i] + b * v.p[i];
+    v.q[i] = TP(0);
   }
 }
 
 // x += alpha p, r -= alpha P q, then rz_new, rr; the last block sets beta,
 // the convergence flag and the reliable-update trigger.
-template <class T>
-__global__ void __launch_bounds__(kVecBlock) k_pcg_update(PcgVecs<T> v, SolveScalars *S, double *partials,
-                                                          unsigned int *ticket) {
+template <class TX, class TR, class TP>
+__global__ void __launch_bounds__(kVecBlock) k_pcg_update(PcgVecs<TX, TR, TP> v, SolveScalars *S,
+                                                          double *partials, unsigned int *ticket) {
   if (S->done) return;
   const double pq = S->pq, rz_old = S->rz;
   const double alpha = rz_old / pq;
@@ -129,14 +135,16 @@ __global__ void __launch_bounds__(kVecBlock) k_pcg_update(PcgVecs<T> v, SolveSca
     }
     return;
   }
-  const T a = (T)alpha;
+  const TX ax = (TX)alpha;
+  const TR ar = (TR)alpha;
   double rz = 0.0, rr = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * kVecBlock + threadIdx.x; i < v.n; i += (int64_t)gridDim.x * kVecBlock) {
-    v.x[i] += a * v.p[i];
-    const T ri = v.dmask[i] ? v.r[i] - a * v.q[i] : T(0);
+    v.x[i] += ax * (TX)v.p[i];
+    const TR ri = v.dmask[i] ? v.r[i] - ar * (TR)v.q[i] : TR(0);
     v.r[i] = ri;
-    rz += (double)(v.dinv[i] * ri) * (double)ri;
-    rr += (double)ri * (double)ri;
+    const TP rp = (TP)ri;
+    rz += (double)(v.dinv[i] * rp * rp);
+    rr += (double)(rp * rp);
   }
   double vv[2] = {rz, rr};
   if (grid_sum<kVecBlock, 2>(vv, partials, ticket, nullptr) && threadIdx.x == 0) {
@@ -165,13 +173,14 @@ __global__ void __launch_bounds__(kVecBlock) k_pcg_update(PcgVecs<T> v, SolveSca
 }
 
 // p = D^-1 r + beta p; q = 0 (the matrix-free operator accumulates into q)
-template <class T>
-__global__ void __launch_bounds__(kVecBlock) k_pcg_direction(PcgVecs<T> v, const SolveScalars *S, bool zero_q) {
+template <class TX, class TR, class TP>
+__global__ void __launch_bounds__(kVecBlock) k_pcg_direction(PcgVecs<TX, TR, TP> v, const SolveScalars *S,
+                                                             bool zero_q) {
   if (S->done) return;
-  const T b = (T)S->beta;
+  const TP b = (TP)S->beta;
   for (int64_t i = (int64_t)blockIdx.x * kVecBlock + threadIdx.x; i < v.n; i += (int64_t)gridDim.x * kVecBlock) {
-    v.p[i] = v.dinv[i] * v.r[i] + b * v.p[i];
-    if (zero_q) v.q[i] = T(0);
+    v.p[i] = v.dinv[i] * (TP)v.r[i] + b * v.p[i];
+    if (zero_q) v.q[i] = TP(0);
   }
 }
 
@@ -225,16 +234,16 @@ static void apply_op64(Ctx &c, int op, const double *x, double *y) {
 }
 
 // ---- one CG run (PCG64 or the FP32 inner solve) ----------------------------
-template <class T>
+template <class TX, class TR, class TP>
 struct CgRun {
   Ctx &c;
-  PcgVecs<T> v;
-  int op;                 // SFEM_OP_CSR64 / SFEM_OP_MF64 / SFEM_OP_MF32
+  PcgVecs<TX, TR, TP> v;
+  int op;                 // SFEM_OP_CSR64 / SFEM_OP_MF64 (TP double) or SFEM_OP_MF32
   int chunk;
   cudaGraphExec_t exec = nullptr;
   cudaGraph_t graph = nullptr;
 
-  CgRun(Ctx &c_, PcgVecs<T> v_, int op_, int chunk_) : c(c_), v(v_), op(op_), chunk(chunk_) {}
+  CgRun(Ctx &c_, PcgVecs<TX, TR, TP> v_, int op_, int chunk_) : c(c_), v(v_), op(op_), chunk(chunk_) {}
   ~CgRun() {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
@@ -251,13 +260,12 @@ struct CgRun {
       launch_mf_strain<double, double>(c, st, c.Gs64, (const double *)v.p, 1, w, done);
       launch_mf_stress<double, double>(c, st, c.Gs64, c.kap64, w, (double *)v.q, 1, &S->pq, done);
     } else {
-      // tiled FP32 operator; vectors of type T (FP64 vectors: p read in
-      // FP64, arithmetic in FP32, q accumulated in FP64)
-      launch_mf32_tiled<T, T>(c, st, v.p, v.q, &S->pq, done);
+      // tiled FP32 operator reading p and accumulating q in type TP
+      launch_mf32_tiled<TP, TP>(c, st, v.p, v.q, &S->pq, done);
     }
-    k_pcg_update<T><<<c.red_blocks, kVecBlock, 0, st>>>(v, S, c.red_partial, c.tickets + 3);
+    k_pcg_update<TX, TR, TP><<<c.red_blocks, kVecBlock, 0, st>>>(v, S, c.red_partial, c.tickets + 3);
     SFEM_CHECK_LAUNCH();
-    k_pcg_direction<T><<<c.red_blocks, kVecBlock, 0, st>>>(v, S, mf);
+    k_pcg_direction<TX, TR, TP><<<c.red_blocks, kVecBlock, 0, st>>>(v, S, mf);
     SFEM_CHECK_LAUNCH();
   }
 
@@ -283,17 +291,18 @@ struct CgRun {
 
   // r holds the masked residual on entry: (re)start CG from it.
   SolveScalars start(double tol2, int max_iter, double delta2) {
-    k_pcg_init<T><<<c.red_blocks, kVecBlock, 0, c.stream>>>(v, c.scal, tol2, max_iter, delta2, c.red_partial,
-                                                            c.tickets + 4);
+    k_pcg_init<TX, TR, TP><<<c.red_blocks, kVecBlock, 0, c.stream>>>(v, c.scal, tol2, max_iter, delta2,
+                                                                      c.red_partial, c.tickets + 4);
     SFEM_CHECK_LAUNCH();
     return resume(max_iter);
   }
 
   // r has been replaced by the true residual: keep p, recompute beta, go on.
   SolveScalars replace(int max_iter) {
-    k_pcg_replace<T><<<c.red_blocks, kVecBlock, 0, c.stream>>>(v, c.scal, max_iter, c.red_partial, c.tickets + 5);
+    k_pcg_replace<TX, TR, TP><<<c.red_blocks, kVecBlock, 0, c.stream>>>(v, c.scal, max_iter, c.red_partial,
+                                                                         c.tickets + 5);
     SFEM_CHECK_LAUNCH();
-    k_pcg_replace_dir<T><<<c.red_blocks, kVecBlock, 0, c.stream>>>(v, c.scal);
+    k_pcg_replace_dir<TX, TR, TP><<<c.red_blocks, kVecBlock, 0, c.stream>>>(v, c.scal);
     SFEM_CHECK_LAUNCH();
     return resume(max_iter);
   }
@@ -404,8 +413,8 @@ static void solve_impl(Ctx &c, const double *f_extra, double *u, const sfem_solv
     double rel = true_residual();
     if (o.kind == SFEM_SOLVE_PCG64) {
       if (op64 == SFEM_OP_MF64) ensure_w_scratch(c, (size_t)c.n_tets * 8 * sizeof(double));
-      PcgVecs<double> v{x, r, B.get<double>(n), B.get<double>(n), c.dinv64, c.dmask, n};
-      CgRun<double> cg(c, v, op64, chunk);
+      PcgVecs<double, double, double> v{x, r, B.get<double>(n), B.get<double>(n), c.dinv64, c.dmask, n};
+      CgRun<double, double, double> cg(c, v, op64, chunk);
       const int max_restarts = 10;
       while (rel > tol && total_iter < max_iter && outer <= max_restarts) {
         SolveScalars s = cg.start(tol * tol * bnorm * bnorm, max_iter - total_iter, 0.0);
@@ -428,12 +437,12 @@ static void solve_impl(Ctx &c, const double *f_extra, double *u, const sfem_solv
       const double delta = o.inner_tol > 0 ? o.inner_tol : 0.1;
       const int max_outer = o.max_outer > 0 ? o.max_outer : 200;
       ensure_w_scratch(c, (size_t)c.n_tets * 8 * sizeof(double));
-      if (o.fp32_vectors) {
+      if (o.fp32_vectors == 1) {
         // all-FP32 inner iterations (vectors too): cheaper per iteration,
         // but finite-precision CG loses orthogonality much faster
-        PcgVecs<float> v{B.get<float>(n), B.get<float>(n), B.get<float>(n), B.get<float>(n), c.dinv32, c.dmask,
-                         n};
-        CgRun<float> cg(c, v, SFEM_OP_MF32, chunk);
+        PcgVecs<float, float, float> v{B.get<float>(n), B.get<float>(n), B.get<float>(n), B.get<float>(n),
+                                       c.dinv32, c.dmask, n};
+        CgRun<float, float, float> cg(c, v, SFEM_OP_MF32, chunk);
         SFEM_CUDA(cudaMemsetAsync(v.x, 0, n * sizeof(float), c.stream));
         bool started = false;
         while (rel > tol && total_iter < max_iter && outer < max_outer) {
@@ -453,10 +462,37 @@ static void solve_impl(Ctx &c, const double *f_extra, double *u, const sfem_solv
           SFEM_CHECK_LAUNCH();
           rel = true_residual();
         }
+      } else if (o.fp32_vectors == 2) {
+        // FP32 search direction p, operator output q and correction d; FP64
+        // residual r
+        PcgVecs<float, double, float> v{B.get<float>(n), r, B.get<float>(n), B.get<float>(n), c.dinv32, c.dmask,
+                                        n};
+        CgRun<float, double, float> cg(c, v, SFEM_OP_MF32, chunk);
+        SFEM_CUDA(cudaMemsetAsync(v.x, 0, n * sizeof(float), c.stream));
+        bool started = false;
+        while (rel > tol && total_iter < max_iter && outer < max_outer) {
+          SolveScalars s = started ? cg.replace(max_iter)
+                                   : cg.start(tol * tol * bnorm * bnorm, max_iter, delta * delta);
+          started = true;
+          total_iter = s.iter;
+          ++outer;
+          if (s.status) {
+            status = SFEM_EBREAKDOWN;
+            break;
+          }
+          k_refine<<<g256, 256, 0, c.stream>>>(x, v.x, n);  // u += d, d = 0
+          SFEM_CHECK_LAUNCH();
+          rel = true_residual();  // writes the FP64 true residual into r = v.r
+        }
       } else {
-        // FP32 operator, FP64 vectors: the correction d accumulates in FP64
-        PcgVecs<double> v{B.get<double>(n), r, B.get<double>(n), B.get<double>(n), c.dinv64, c.dmask, n};
-        CgRun<double> cg(c, v, SFEM_OP_MF32, chunk);
+        // default: every CG vector in FP64 (correction d, residual r, search
+        // direction p, operator output q); the FP32 operator reads p in FP64
+        // and accumulates q in FP64.  An FP32 d or p doubled the iteration
+        // count on the 2M-tet beam: their rounding re-enters the FP64 true
+        // residual amplified by the condition number at every update.
+        PcgVecs<double, double, double> v{B.get<double>(n), r, B.get<double>(n), B.get<double>(n), c.dinv64,
+                                          c.dmask, n};
+        CgRun<double, double, double> cg(c, v, SFEM_OP_MF32, chunk);
         SFEM_CUDA(cudaMemsetAsync(v.x, 0, n * sizeof(double), c.stream));
         bool started = false;
         while (rel > tol && total_iter < max_iter && outer < max_outer) {
@@ -469,9 +505,9 @@ static void solve_impl(Ctx &c, const double *f_extra, double *u, const sfem_solv
             status = SFEM_EBREAKDOWN;
             break;
           }
-          k_add<<<g256, 256, 0, c.stream>>>(x, v.x, n);
+          k_add<<<g256, 256, 0, c.stream>>>(x, v.x, n);  // u += d
           SFEM_CHECK_LAUNCH();
-          SFEM_CUDA(cudaMemsetAsync(v.x, 0, n * sizeof(double), c.stream));
+          SFEM_CUDA(cudaMemsetAsync(v.x, 0, n * sizeof(double), c.stream));  // d = 0
           rel = true_residual();  // writes the FP64 true residual into r = v.r
         }
       }

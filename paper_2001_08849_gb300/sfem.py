@@ -233,7 +233,7 @@ def solve_opts(kind=SFEM_SOLVE_PCG64, op64=SFEM_OP_MF64, rhs=0, tol=1e-8, max_it
     o.max_iter, o.tol, o.inner_tol = int(max_iter), float(tol), float(inner_tol)
     o.max_outer, o.check_every = int(max_outer), int(check_every)
     o.learned = learned
-    o.fp32_vectors = int(bool(fp32_vectors))
+    o.fp32_vectors = int(fp32_vectors)
     return o
 
 

@@ -123,7 +123,9 @@ typedef struct sfem_solve_info {
   int status;              /* sfem_status of the solve */
   int iterations;          /* CG iterations (inner iterations for IR) */
   int outer_iterations;    /* IR refinement steps / true-residual restarts */
-  int fallbacks;           /* FPCG: iterations that fell back to Jacobi */
+  int fallbacks;           /* FPCG: iterations that fell back to Jacobi; IR and
+                              batch: 1 if the FP32-operator CG stagnated and FP64
+                              PCG finished the solve */
   double true_relres;      /* ||b - A u||_2 / ||b||_2 in FP64, after exit */
   double bnorm;            /* ||b||_2 */
   double solve_ms;         /* device time of the solve */
@@ -180,6 +182,51 @@ int sfem_apply(sfem_ctx *ctx, const void *u, void *y, int op, int nrhs);
  * the final residual in info. */
 int sfem_solve(sfem_ctx *ctx, const double *f_extra, double *u,
                const sfem_solve_opts *opts, sfem_solve_info *info);
+
+/* sfem_batch_solve — solve every load case of every context together (the
+ * batched form of sfem_solve's SFEM_SOLVE_IR32_64; no counterpart in the
+ * paper, which solves one model at a time).  Each round is one persistent
+ * cooperative launch running FP32-operator CG iterations (FP64 vectors and
+ * reductions) for all active systems, followed by the FP64 refresh (u += d,
+ * true residual f - K u, convergence test, residual replacement) of the
+ * systems that stopped; rounds are captured once as a CUDA graph and
+ * replayed until every system has converged.
+ *   ctxs  n contexts on the current device (any sizes, nrhs each); the
+ *         work runs on ctxs[0]'s stream
+ *   u     n pointers, u[i] holding nrhs_i x ndof_i FP64 (host, or device if
+ *         opts->u_on_device); input with warm_start, output always
+ *   infos sum(nrhs_i) entries (may be NULL), in context then load-case order
+ *   stats may be NULL
+ * Returns SFEM_OK when every system converged, else the first failure;
+ * SFEM_ETIMEOUT if a bounded grid barrier gave up. */
+typedef struct sfem_batch_opts {
+  double tol;            /* relative true residual per system (0: 1e-8) */
+  double inner_tol;      /* reliable-update trigger (0: 0.1) */
+  int max_iter;          /* CG iterations per system (0: 200000) */
+  int max_rounds;        /* rounds at most (0: 400) */
+  int iters_per_launch;  /* CG iterations per persistent launch at most (0: 2000) */
+  int u_on_device;
+  int warm_start;
+  int autotune;          /* 1: time 1..max CTAs per SM on the first rounds (cached per shape) */
+  int use_graph;         /* 1: capture a round as a CUDA graph */
+  int reserved[5];
+} sfem_batch_opts;
+
+typedef struct sfem_batch_stats {
+  int rounds;             /* persistent launches */
+  int ctas_per_sm;        /* launch shape chosen by the autotuner (or 1) */
+  int graph;              /* 1 if the rounds ran as a CUDA graph */
+  int n_systems;
+  long long total_iterations;  /* CG iterations summed over systems */
+  double ms;              /* device time of the whole batch */
+  int fallback_systems;   /* systems that stagnated on the FP32 operator (three
+                             refreshes in a row improving the true residual by
+                             less than 10%) and were finished by FP64 Jacobi-PCG */
+  int reserved[3];
+} sfem_batch_stats;
+
+int sfem_batch_solve(sfem_ctx *const *ctxs, int n, double *const *u, const sfem_batch_opts *opts,
+                     sfem_solve_info *infos, sfem_batch_stats *stats);
 
 int sfem_get_info(const sfem_ctx *ctx, sfem_mesh_info *info);
 

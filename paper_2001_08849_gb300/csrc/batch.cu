@@ -1,0 +1,761 @@
+// Batched persistent solver: many beams (contexts) with several load cases
+// each, solved together by the mixed-precision CG of solve.cu.
+//
+// One "system" is one (context, load case).  A round is
+//   1. one persistent cooperative launch running FP32-operator CG
+//      iterations (FP64 vectors and reductions) for every active system:
+//        P1  operator over a global work list of (beam, tile); a tile's
+//            geometry is loaded once for all active load cases of its beam
+//        P2  x/r updates and the two dot products per system
+//        P3  per-system decisions (converged / reliable update due /
+//            iteration cap / breakdown) and new search directions
+//      separated by grid barriers (bounded spins: a timed-out barrier sets
+//      an error flag and the kernel returns);
+//   2. the FP64 refresh of systems that stopped: u += d, the FP64 true
+//      residual f - K u (two-pass FP64 operator, all load cases of a beam in
+//      one pass), convergence test on it, and for systems that go on the
+//      residual replacement with the search direction kept.
+// Rounds repeat (as a captured CUDA graph) until no system is active.
+// Per-system scalars are double-buffered by iteration parity so that no
+// block reads a value another block is writing.
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <vector>
+
+#include "reduce.cuh"
+#include "sfem_internal.cuh"
+#include "tile_apply.cuh"
+
+namespace sfem {
+
+constexpr long long kBarrierSpinLimit = 1ll << 24;  // about a second or two of waiting
+
+struct BatchBeam {
+  TileArgs A;
+  int first_sys, nrhs;
+  float lam, mu;
+};
+
+struct BatchSys {
+  double *x, *r, *p, *q, *d, *Kx;
+  const double *dinv;
+  const uint8_t *dmask;
+  const double *f;
+  int64_t n;
+  double bnorm;
+};
+
+struct SysState {
+  double rz, rz_prev, rr, rmax2, beta, relres;
+  int iter, active, reason, status;  // reason: 1 conv, 2 refresh due, 3 cap, 4 breakdown
+                                     // status: 0 running, 1 converged, 2 no conv, 3 breakdown,
+                                     //         4 stagnated (finished by FP64 PCG on the host side)
+  int fresh;                         // 1: reactivated by the last refresh (direction not yet updated)
+  int stall;                         // refreshes in a row improving the best true residual by < 10%
+  double best;                       // best true relative residual so far
+};
+
+struct BatchDev {
+  const BatchBeam *beams;
+  int n_beams;
+  const BatchSys *sys;
+  int n_sys;
+  const int *work_prefix;  // n_beams + 1
+  int total_work;
+  SysState *state;         // 2 * n_sys, slot *slot is current
+  int *slot;
+  double *sums;            // 2 * n_sys * 2 (rz, rr)
+  double *pq;              // 2 * n_sys
+  double tol2;             // relative tolerance squared
+  double delta2;
+  int max_iter;
+  int max_iter_launch;
+  unsigned int *bar_count, *bar_gen;
+  int *err;
+  int *beam_skip;          // per beam: 1 if no system of it needs the FP64 refresh
+  int *any_active;
+  long long *iters_run;    // total CG iterations (summed over systems) of the last launch
+};
+
+// state written by another block during the same launch: read through L2
+__device__ __forceinline__ SysState load_state(const SysState *p) {
+  SysState s;
+  s.rz = __ldcg(&p->rz);
+  s.rz_prev = __ldcg(&p->rz_prev);
+  s.rr = __ldcg(&p->rr);
+  s.rmax2 = __ldcg(&p->rmax2);
+  s.beta = __ldcg(&p->beta);
+  s.relres = __ldcg(&p->relres);
+  s.iter = __ldcg(&p->iter);
+  s.active = __ldcg(&p->active);
+  s.reason = __ldcg(&p->reason);
+  s.status = __ldcg(&p->status);
+  s.fresh = __ldcg(&p->fresh);
+  s.stall = __ldcg(&p->stall);
+  s.best = __ldcg(&p->best);
+  return s;
+}
+
+__device__ __forceinline__ bool grid_barrier(const BatchDev &a) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int *gen = a.bar_gen;
+    const unsigned int g = *gen;
+    __threadfence();
+    const unsigned int arrived = atomicAdd(a.bar_count, 1u);
+    int good = 1;
+    if (arrived == gridDim.x - 1) {
+      *a.bar_count = 0u;
+      __threadfence();
+      atomicAdd(a.bar_gen, 1u);
+    } else {
+      long long spins = 0;
+      while (*gen == g) {
+        if (++spins > kBarrierSpinLimit) {
+          atomicExch(a.err, 1);
+          good = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    if (*(volatile int *)a.err) good = 0;
+    ok = good;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// MINB: CTAs per SM the register budget is compiled for (1, 2 or 3); the
+// autotuner times the variants
+template <int MINB>
+__global__ void __launch_bounds__(kTileThreads, MINB) k_batch_cg(BatchDev a) {
+  extern __shared__ float4 smem[];
+  const int start = *a.slot;
+  int k = 0;
+  long long iters = 0;
+  for (; k < a.max_iter_launch; ++k) {
+    const int par = (start + k) & 1;
+    const SysState *st = a.state + par * a.n_sys;
+    double *pq = a.pq + par * a.n_sys;
+    double *sums = a.sums + 2 * par * a.n_sys;
+    // P1: operator over (beam, tile) work items
+    for (int w = blockIdx.x; w < a.total_work; w += gridDim.x) {
+      int lo = 0, hi = a.n_beams - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.work_prefix[mid] <= w)
+          lo = mid;
+        else
+          hi = mid - 1;
+      }
+      const BatchBeam &B = a.beams[lo];
+      bool any = false;
+      for (int j = 0; j < B.nrhs; ++j) any = any || __ldcg(&st[B.first_sys + j].active);
+      if (!any) continue;
+      const int tile = w - a.work_prefix[lo];
+      TileRegs R;
+      tile_load(B.A, tile, R);
+      for (int j = 0; j < B.nrhs; ++j) {
+        const int s = B.first_sys + j;
+        if (!__ldcg(&st[s].active)) continue;
+        const BatchSys &S = a.sys[s];
+        double en = tile_compute<double, double, true>(B.A, tile, R, S.p, S.q, B.lam, B.mu, smem);
+        en = block_sum<kTileThreads>(en);
+        if (threadIdx.x == 0) atomicAdd(&pq[s], en);
+      }
+    }
+    if (!grid_barrier(a)) return;
+    // P2: updates of the active systems
+    for (int s = 0; s < a.n_sys; ++s) {
+      const SysState ss = load_state(st + s);
+      if (!ss.active) continue;
+      const double pqs = __ldcg(&pq[s]);
+      const double alpha = ss.rz / pqs;
+      if (!(pqs > 0.0) || !isfinite(alpha)) continue;
+      const BatchSys &S = a.sys[s];
+      double rz = 0.0, rr = 0.0;
+      for (int64_t i = (int64_t)blockIdx.x * kTileThreads + threadIdx.x; i < S.n;
+           i += (int64_t)gridDim.x * kTileThreads) {
+        S.d[i] = __ldcg(&S.d[i]) + alpha * __ldcg(&S.p[i]);
+        const double ri = S.dmask[i] ? __ldcg(&S.r[i]) - alpha * __ldcg(&S.q[i]) : 0.0;
+        S.r[i] = ri;
+        rz += S.dinv[i] * ri * ri;
+        rr += ri * ri;
+      }
+      rz = block_sum<kTileThreads>(rz);
+      rr = block_sum<kTileThreads>(rr);
+      if (threadIdx.x == 0) {
+        atomicAdd(&sums[2 * s], rz);
+        atomicAdd(&sums[2 * s + 1], rr);
+      }
+    }
+    if (!grid_barrier(a)) return;
+    // P3: decisions (identical in every block) and new directions
+    bool any_active = false;
+    SysState *nx = a.state + (par ^ 1) * a.n_sys;
+    for (int s = 0; s < a.n_sys; ++s) {
+      const SysState ss = load_state(st + s);
+      SysState n2 = ss;
+      n2.fresh = 0;
+      if (ss.active) {
+        const double pqs = __ldcg(&pq[s]);
+        const double alpha = ss.rz / pqs;
+        const BatchSys &S = a.sys[s];
+        if (!(pqs > 0.0) || !isfinite(alpha)) {
+          n2.active = 0;
+          n2.reason = 4;
+        } else {
+          const double rz_new = __ldcg(&sums[2 * s]), rr = __ldcg(&sums[2 * s + 1]);
+          n2.iter = ss.iter + 1;
+          n2.rz_prev = ss.rz;
+          n2.rz = rz_new;
+          n2.rr = rr;
+          n2.beta = rz_new / ss.rz;
+          n2.rmax2 = fmax(ss.rmax2, rr);
+          if (!isfinite(rz_new) || !isfinite(rr)) {
+            n2.active = 0;
+            n2.reason = 4;
+          } else if (rr <= a.tol2 * S.bnorm * S.bnorm) {
+            n2.active = 0;
+            n2.reason = 1;
+          } else if (n2.iter >= a.max_iter) {
+            n2.active = 0;
+            n2.reason = 3;
+          } else if (rr < a.delta2 * n2.rmax2) {
+            n2.active = 0;
+            n2.reason = 2;
+          }
+        }
+        if (n2.active) {
+          any_active = true;
+          const double beta = n2.beta;
+          for (int64_t i = (int64_t)blockIdx.x * kTileThreads + threadIdx.x; i < S.n;
+               i += (int64_t)gridDim.x * kTileThreads) {
+            S.p[i] = S.dinv[i] * __ldcg(&S.r[i]) + beta * __ldcg(&S.p[i]);
+            S.q[i] = 0.0;
+          }
+        }
+      }
+      if (blockIdx.x == 0 && threadIdx.x == 0) {
+        nx[s] = n2;
+        double *nsums = a.sums + 2 * (par ^ 1) * a.n_sys;
+        nsums[2 * s] = 0.0;
+        nsums[2 * s + 1] = 0.0;
+        a.pq[(par ^ 1) * a.n_sys + s] = 0.0;
+        if (ss.active) ++iters;
+      }
+    }
+    if (!any_active) {
+      ++k;
+      break;
+    }
+    if (!grid_barrier(a)) return;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *a.slot = (start + k) & 1;
+    *a.iters_run = iters;
+  }
+}
+
+// ---- FP64 refresh kernels ---------------------------------------------------
+// systems that stopped for a reason other than a final status: u += d, d = 0;
+// beam_skip[b] = 1 when no system of beam b needs its residual recomputed
+__global__ void k_refresh_x(BatchDev a) {
+  const SysState *st = a.state + (*a.slot) * a.n_sys;
+  for (int s = 0; s < a.n_sys; ++s) {
+    const SysState &ss = st[s];
+    if (ss.status != 0 || ss.active || ss.reason == 0) continue;
+    const BatchSys &S = a.sys[s];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < S.n; i += (int64_t)gridDim.x * blockDim.x) {
+      S.x[i] += S.d[i];
+      S.d[i] = 0.0;
+    }
+  }
+  if (blockIdx.x == 0) {
+    for (int b = threadIdx.x; b < a.n_beams; b += blockDim.x) {
+      const BatchBeam &B = a.beams[b];
+      int need = 0;
+      for (int j = 0; j < B.nrhs; ++j) {
+        const SysState &ss = st[B.first_sys + j];
+        need |= (ss.status == 0 && !ss.active && ss.reason != 0);
+      }
+      a.beam_skip[b] = need ? 0 : 1;
+    }
+  }
+}
+
+// r = P (f - K u) and its sums (rz~, |r|^2) for systems being refreshed
+__global__ void __launch_bounds__(256) k_refresh_r(BatchDev a) {
+  const SysState *st = a.state + (*a.slot) * a.n_sys;
+  double *sums = a.sums + 2 * (*a.slot) * a.n_sys;
+  for (int s = 0; s < a.n_sys; ++s) {
+    const SysState &ss = st[s];
+    if (ss.status != 0 || ss.active || ss.reason == 0) continue;
+    const BatchSys &S = a.sys[s];
+    double rz = 0.0, rr = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < S.n; i += (int64_t)gridDim.x * 256) {
+      const double ri = S.dmask[i] ? S.f[i] - S.Kx[i] : 0.0;
+      S.r[i] = ri;
+      rz += S.dinv[i] * ri * ri;
+      rr += ri * ri;
+    }
+    rz = block_sum<256>(rz);
+    rr = block_sum<256>(rr);
+    if (threadIdx.x == 0) {
+      atomicAdd(&sums[2 * s], rz);
+      atomicAdd(&sums[2 * s + 1], rr);
+    }
+  }
+}
+
+// decisions on the FP64 true residual (one thread per system)
+__global__ void k_refresh_state(BatchDev a) {
+  SysState *st = a.state + (*a.slot) * a.n_sys;
+  double *sums = a.sums + 2 * (*a.slot) * a.n_sys;
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  for (int s = threadIdx.x; s < a.n_sys; s += blockDim.x) {
+    SysState ss = st[s];
+    if (ss.status == 0 && !ss.active && ss.reason != 0) {
+      const BatchSys &S = a.sys[s];
+      const double rz = sums[2 * s], rr = sums[2 * s + 1];
+      const double rel = S.bnorm > 0.0 ? sqrt(rr) / S.bnorm : 0.0;
+      ss.relres = rel;
+      // stagnation: the FP32 operator's error floor is above the tolerance
+      if (rel < 0.9 * ss.best) {
+        ss.best = rel;
+        ss.stall = 0;
+      } else {
+        ss.stall += 1;
+      }
+      if (ss.reason == 4) {
+        ss.status = 3;
+      } else if (rel * rel <= a.tol2) {
+        ss.status = 1;
+      } else if (ss.iter >= a.max_iter) {
+        ss.status = 2;
+      } else if (ss.stall >= 3) {
+        ss.status = 4;
+      } else {
+        ss.active = 1;
+        ss.beta = isfinite(ss.rz_prev) && ss.rz_prev > 0.0 ? rz / ss.rz_prev : 0.0;
+        ss.rz = rz;
+        ss.rr = rr;
+        ss.rmax2 = rr;
+        ss.reason = 0;
+        ss.fresh = 1;
+        atomicOr(&any, 1);
+      }
+      st[s] = ss;
+    } else if (ss.active) {
+      atomicOr(&any, 1);
+    }
+    sums[2 * s] = 0.0;
+    sums[2 * s + 1] = 0.0;
+    a.pq[(*a.slot) * a.n_sys + s] = 0.0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *a.any_active = any;
+}
+
+// new directions of the systems this refresh reactivated (systems still
+// active because the launch hit its iteration cap already have theirs):
+// p = D^-1 r + beta p, q = 0
+__global__ void k_refresh_p(BatchDev a) {
+  const SysState *st = a.state + (*a.slot) * a.n_sys;
+  for (int s = 0; s < a.n_sys; ++s) {
+    const SysState &ss = st[s];
+    if (!ss.active || !ss.fresh) continue;
+    const BatchSys &S = a.sys[s];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < S.n; i += (int64_t)gridDim.x * blockDim.x) {
+      S.p[i] = S.dinv[i] * S.r[i] + ss.beta * S.p[i];
+      S.q[i] = 0.0;
+    }
+  }
+}
+
+__global__ void k_batch_init(BatchSys *sys, int n_sys, SysState *state) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n_sys) return;
+  SysState z;
+  memset(&z, 0, sizeof z);
+  z.rz_prev = INFINITY;
+  z.best = INFINITY;
+  z.reason = 2;  // needs its first residual
+  state[s] = z;
+  state[n_sys + s] = z;
+}
+
+__global__ void k_set_bc_all(double *x, const double *g, const uint8_t *dmask, int64_t n, int nrhs, bool zero_free) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n * nrhs) return;
+  const int64_t k = i % n;
+  if (!dmask[k])
+    x[i] = g[k];
+  else if (zero_free)
+    x[i] = 0.0;
+}
+
+// ---- autotuner: persistent-kernel CTAs per SM, cached per shape class -----
+static std::mutex g_tune_mu;
+static std::map<long long, int> g_tune_cache;  // key: (device, total tiles bucket) -> CTAs per SM
+
+}  // namespace sfem
+
+using namespace sfem;
+
+extern "C" int sfem_batch_solve(sfem_ctx *const *ctxs, int n, double *const *u, const sfem_batch_opts *opts,
+                                sfem_solve_info *infos, sfem_batch_stats *stats) {
+  std::vector<void *> owned;
+  Ctx *c0 = nullptr;
+  auto cleanup = [&]() {
+    if (c0)
+      for (void *p : owned) c0->mem.drop(p);
+    owned.clear();
+  };
+  try {
+    SFEM_REQUIRE(ctxs && n >= 1 && u && opts, SFEM_EINVAL, "ctxs, u and opts must not be NULL");
+    for (int r : opts->reserved) SFEM_REQUIRE(r == 0, SFEM_EINVAL, "reserved options must be zero");
+    c0 = &ctxs[0]->c;
+    cudaStream_t st = c0->stream;
+    int dev = -1;
+    SFEM_CUDA(cudaGetDevice(&dev));
+    int n_sys = 0, total_work = 0;
+    size_t smem = 0;
+    for (int b = 0; b < n; ++b) {
+      SFEM_REQUIRE(ctxs[b] && ctxs[b]->c.vol && ctxs[b]->c.tl.ready, SFEM_EINVAL, "context not set up");
+      SFEM_REQUIRE(ctxs[b]->c.device == dev, SFEM_EINVAL, "all contexts must live on the current device");
+      n_sys += ctxs[b]->c.nrhs;
+      total_work += (int)ctxs[b]->c.tl.n_tiles;
+      smem = std::max(smem, ctxs[b]->c.tl.smem);
+    }
+    const double tol = opts->tol > 0 ? opts->tol : 1e-8;
+    const double delta = opts->inner_tol > 0 ? opts->inner_tol : 0.1;
+    const int max_iter = opts->max_iter > 0 ? opts->max_iter : 200000;
+    const int max_rounds = opts->max_rounds > 0 ? opts->max_rounds : 400;
+    auto get = [&](size_t bytes) {
+      void *p = c0->mem.raw(bytes);
+      owned.push_back(p);
+      return p;
+    };
+
+    cudaEvent_t e0, e1;
+    SFEM_CUDA(cudaEventCreate(&e0));
+    SFEM_CUDA(cudaEventCreate(&e1));
+    SFEM_CUDA(cudaEventRecord(e0, st));
+
+    // per-beam vectors and host-side tables
+    std::vector<BatchBeam> hb(n);
+    std::vector<BatchSys> hs(n_sys);
+    std::vector<int> prefix(n + 1, 0);
+    std::vector<double *> xbeam(n), kxbeam(n);
+    int s = 0;
+    for (int b = 0; b < n; ++b) {
+      Ctx &c = ctxs[b]->c;
+      const int64_t nd = c.ndof;
+      const int nr = c.nrhs;
+      double *X = (double *)get(nd * nr * sizeof(double));
+      double *R = (double *)get(nd * nr * sizeof(double));
+      double *P = (double *)get(nd * nr * sizeof(double));
+      double *Q = (double *)get(nd * nr * sizeof(double));
+      double *D = (double *)get(nd * nr * sizeof(double));
+      double *KX = (double *)get(nd * nr * sizeof(double));
+      xbeam[b] = X;
+      kxbeam[b] = KX;
+      ensure_w_scratch(c, (size_t)c.n_tets * 8 * sizeof(double) * nr);
+      if (opts->warm_start)
+        SFEM_CUDA(cudaMemcpyAsync(X, u[b], nd * nr * sizeof(double),
+                                  opts->u_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+      k_set_bc_all<<<grid_for(nd * nr, 256), 256, 0, st>>>(X, c.g, c.dmask, nd, nr, !opts->warm_start);
+      SFEM_CHECK_LAUNCH();
+      for (double *v : {D, P, Q}) SFEM_CUDA(cudaMemsetAsync(v, 0, nd * nr * sizeof(double), st));
+      hb[b].A = TileArgs{c.tl.tile_start, c.tl.hoff,       c.tl.noff, c.tl.halo_tet, c.tl.halo_lconn,
+                         c.tl.tile_nodes, c.tl.node_inc,   c.tl.rec};
+      hb[b].first_sys = s;
+      hb[b].nrhs = nr;
+      hb[b].lam = (float)c.lam;
+      hb[b].mu = (float)c.mu;
+      prefix[b + 1] = prefix[b] + (int)c.tl.n_tiles;
+      for (int j = 0; j < nr; ++j, ++s) {
+        BatchSys &S = hs[s];
+        S.x = X + j * nd;
+        S.r = R + j * nd;
+        S.p = P + j * nd;
+        S.q = Q + j * nd;
+        S.d = D + j * nd;
+        S.Kx = KX + j * nd;
+        S.dinv = c.dinv64;
+        S.dmask = c.dmask;
+        S.f = c.f + j * nd;
+        S.n = nd;
+        S.bnorm = c.bnorm[j];
+      }
+    }
+    BatchDev a{};
+    a.beams = (BatchBeam *)get(n * sizeof(BatchBeam));
+    a.sys = (BatchSys *)get(n_sys * sizeof(BatchSys));
+    a.work_prefix = (int *)get((n + 1) * sizeof(int));
+    SFEM_CUDA(cudaMemcpyAsync((void *)a.beams, hb.data(), n * sizeof(BatchBeam), cudaMemcpyHostToDevice, st));
+    SFEM_CUDA(cudaMemcpyAsync((void *)a.sys, hs.data(), n_sys * sizeof(BatchSys), cudaMemcpyHostToDevice, st));
+    SFEM_CUDA(cudaMemcpyAsync((void *)a.work_prefix, prefix.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice,
+                              st));
+    a.n_beams = n;
+    a.n_sys = n_sys;
+    a.total_work = total_work;
+    a.state = (SysState *)get(2 * n_sys * sizeof(SysState));
+    a.slot = (int *)get(sizeof(int));
+    a.sums = (double *)get(4 * n_sys * sizeof(double));
+    a.pq = (double *)get(2 * n_sys * sizeof(double));
+    a.bar_count = (unsigned int *)get(2 * sizeof(unsigned int));
+    a.bar_gen = a.bar_count + 1;
+    a.err = (int *)get(sizeof(int));
+    a.beam_skip = (int *)get(n * sizeof(int));
+    a.any_active = (int *)get(sizeof(int));
+    a.iters_run = (long long *)get(sizeof(long long));
+    a.tol2 = tol * tol;
+    a.delta2 = delta * delta;
+    a.max_iter = max_iter;
+    a.max_iter_launch = opts->iters_per_launch > 0 ? opts->iters_per_launch : 2000;
+    SFEM_CUDA(cudaMemsetAsync(a.slot, 0, sizeof(int), st));
+    SFEM_CUDA(cudaMemsetAsync(a.sums, 0, 4 * n_sys * sizeof(double), st));
+    SFEM_CUDA(cudaMemsetAsync(a.pq, 0, 2 * n_sys * sizeof(double), st));
+    SFEM_CUDA(cudaMemsetAsync(a.bar_count, 0, 2 * sizeof(unsigned int), st));
+    SFEM_CUDA(cudaMemsetAsync(a.err, 0, sizeof(int), st));
+    k_batch_init<<<grid_for(n_sys, 128), 128, 0, st>>>((BatchSys *)a.sys, n_sys, a.state);
+    SFEM_CHECK_LAUNCH();
+
+    // launch shapes of the persistent kernel: variant v compiled for v CTAs
+    // per SM, usable when that many fit (registers and shared memory)
+    int sms = 0;
+    SFEM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    void (*variants[3])(BatchDev) = {k_batch_cg<1>, k_batch_cg<2>, k_batch_cg<3>};
+    int occ = 0;  // largest v whose variant reaches v CTAs per SM
+    for (int v = 1; v <= 3; ++v) {
+      SFEM_CUDA(cudaFuncSetAttribute(variants[v - 1], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      int o = 0;
+      SFEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, variants[v - 1], kTileThreads, smem));
+      if (o >= v) occ = v;
+    }
+    SFEM_REQUIRE(occ >= 1, SFEM_EINVAL, "the batched kernel does not fit on an SM");
+    const int red_grid = std::max(1, sms * 4);
+
+    auto launch_persistent = [&](int bpsm, cudaStream_t s2) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3((unsigned)(bpsm * sms));
+      cfg.blockDim = dim3(kTileThreads);
+      cfg.dynamicSmemBytes = smem;
+      cfg.stream = s2;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeCooperative;
+      attr[0].val.cooperative = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      SFEM_CUDA(cudaLaunchKernelEx(&cfg, variants[bpsm - 1], a));
+      if (!capturing()) count_launches(1);
+    };
+    auto enqueue_refresh = [&](cudaStream_t s2) {
+      k_refresh_x<<<red_grid, 256, 0, s2>>>(a);
+      SFEM_CHECK_LAUNCH();
+      for (int b = 0; b < n; ++b) {
+        Ctx &c = ctxs[b]->c;
+        SFEM_CUDA(cudaMemsetAsync(kxbeam[b], 0, c.ndof * c.nrhs * sizeof(double), s2));
+        double *w = static_cast<double *>(c.w_scratch);
+        launch_mf_strain<double, double>(c, s2, c.Gs64, xbeam[b], c.nrhs, w, a.beam_skip + b);
+        launch_mf_stress<double, double>(c, s2, c.Gs64, c.kap64, w, kxbeam[b], c.nrhs, nullptr, a.beam_skip + b);
+      }
+      k_refresh_r<<<red_grid, 256, 0, s2>>>(a);
+      SFEM_CHECK_LAUNCH();
+      k_refresh_state<<<1, 256, 0, s2>>>(a);
+      SFEM_CHECK_LAUNCH();
+      k_refresh_p<<<red_grid, 256, 0, s2>>>(a);
+      SFEM_CHECK_LAUNCH();
+    };
+    int err = 0, any = 0;
+    auto check = [&]() {
+      SFEM_CUDA(cudaMemcpyAsync(&err, a.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+      SFEM_CUDA(cudaMemcpyAsync(&any, a.any_active, sizeof(int), cudaMemcpyDeviceToHost, st));
+      SFEM_CUDA(cudaStreamSynchronize(st));
+      SFEM_REQUIRE(err == 0, SFEM_ETIMEOUT, "a grid barrier of the batched solver timed out");
+    };
+
+    // first residuals (all systems)
+    enqueue_refresh(st);
+    check();
+
+    // autotune CTAs per SM on the first rounds (cached per shape class)
+    const long long key = ((long long)dev << 40) | (long long)total_work;
+    int bpsm = 0;
+    {
+      std::lock_guard<std::mutex> lock(g_tune_mu);
+      auto it = g_tune_cache.find(key);
+      if (it != g_tune_cache.end()) bpsm = it->second;
+    }
+    int rounds = 0;
+    if (bpsm == 0 && opts->autotune) {
+      double best = 1e300;
+      const int saved = a.max_iter_launch;
+      for (int cand = 1; cand <= occ && any; ++cand) {
+        a.max_iter_launch = 40;
+        cudaEvent_t t0, t1;
+        SFEM_CUDA(cudaEventCreate(&t0));
+        SFEM_CUDA(cudaEventCreate(&t1));
+        SFEM_CUDA(cudaEventRecord(t0, st));
+        launch_persistent(cand, st);
+        SFEM_CUDA(cudaEventRecord(t1, st));
+        long long its = 0;
+        SFEM_CUDA(cudaMemcpyAsync(&its, a.iters_run, sizeof its, cudaMemcpyDeviceToHost, st));
+        enqueue_refresh(st);
+        check();
+        float ms = 0.f;
+        SFEM_CUDA(cudaEventElapsedTime(&ms, t0, t1));
+        cudaEventDestroy(t0);
+        cudaEventDestroy(t1);
+        ++rounds;
+        const double per = its > 0 ? ms / (double)its : 1e300;
+        if (per < best) {
+          best = per;
+          bpsm = cand;
+        }
+      }
+      a.max_iter_launch = saved;
+      if (bpsm > 0) {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune_cache[key] = bpsm;
+      }
+    }
+    if (bpsm == 0) bpsm = std::min(occ, 1);
+
+    // rounds, captured once as a graph and replayed (direct launches if the
+    // capture of the cooperative launch is refused)
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    if (opts->use_graph && any) {
+      bool ok = cudaStreamBeginCapture(c0->cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+      if (ok) {
+        set_capturing(true);
+        try {
+          launch_persistent(bpsm, c0->cap_stream);
+          enqueue_refresh(c0->cap_stream);
+        } catch (...) {
+          ok = false;
+        }
+        set_capturing(false);
+        cudaGraph_t g = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(c0->cap_stream, &g);
+        if (ok && ec == cudaSuccess && g && cudaGraphInstantiate(&exec, g, 0) == cudaSuccess) {
+          graph = g;
+        } else {
+          if (g) cudaGraphDestroy(g);
+          exec = nullptr;
+        }
+      }
+      cudaGetLastError();  // a refused capture leaves no sticky error
+    }
+    size_t nodes = 0;
+    if (graph) SFEM_CUDA(cudaGraphGetNodes(graph, nullptr, &nodes));
+    while (any && rounds < max_rounds) {
+      if (exec) {
+        SFEM_CUDA(cudaGraphLaunch(exec, st));
+        count_launches((int64_t)nodes);
+      } else {
+        launch_persistent(bpsm, st);
+        enqueue_refresh(st);
+      }
+      check();
+      ++rounds;
+    }
+    const bool used_graph = exec != nullptr;
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    exec = nullptr;
+    graph = nullptr;
+
+    // results
+    std::vector<SysState> hst(2 * n_sys);
+    int slot = 0;
+    SFEM_CUDA(cudaMemcpyAsync(&slot, a.slot, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SFEM_CUDA(cudaMemcpyAsync(hst.data(), a.state, 2 * n_sys * sizeof(SysState), cudaMemcpyDeviceToHost, st));
+    SFEM_CUDA(cudaStreamSynchronize(st));
+    // systems that stagnated on the FP32 operator: finish them with FP64
+    // Jacobi-PCG (matrix-free FP64 operator), warm-started from the batch
+    std::vector<sfem_solve_info> fb(n_sys);
+    int n_fallback = 0;
+    for (int b = 0, k2 = 0; b < n; ++b) {
+      Ctx &c = ctxs[b]->c;
+      for (int j = 0; j < c.nrhs; ++j, ++k2) {
+        SysState &ss = hst[slot * n_sys + k2];
+        if (ss.status != 4) continue;
+        sfem_solve_opts so{};
+        so.kind = SFEM_SOLVE_PCG64;
+        so.op64 = SFEM_OP_MF64;
+        so.rhs = j;
+        so.u_on_device = 1;
+        so.warm_start = 1;
+        so.tol = tol;
+        so.max_iter = std::max(1, max_iter - ss.iter);
+        fb[k2] = sfem_solve_info{};
+        const int rc = sfem_solve(ctxs[b], nullptr, xbeam[b] + j * c.ndof, &so, &fb[k2]);
+        ss.iter += fb[k2].iterations;
+        ss.relres = fb[k2].true_relres;
+        ss.status = rc == SFEM_OK ? 1 : rc == SFEM_EBREAKDOWN ? 3 : 2;
+        ++n_fallback;
+      }
+    }
+    for (int b = 0; b < n; ++b) {
+      Ctx &c = ctxs[b]->c;
+      SFEM_CUDA(cudaMemcpyAsync(u[b], xbeam[b], c.ndof * c.nrhs * sizeof(double),
+                                opts->u_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    }
+    SFEM_CUDA(cudaEventRecord(e1, st));
+    SFEM_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    SFEM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    int worst = SFEM_OK;
+    long long total_it = 0;
+    for (int i = 0; i < n_sys; ++i) total_it += hst[slot * n_sys + i].iter;
+    if (stats) {
+      stats->fallback_systems = n_fallback;
+      stats->rounds = rounds;
+      stats->ctas_per_sm = bpsm;
+      stats->graph = used_graph ? 1 : 0;
+      stats->n_systems = n_sys;
+      stats->total_iterations = total_it;
+      stats->ms = ms;
+    }
+    for (int i = 0; i < n_sys; ++i) {
+      const SysState &ss = hst[slot * n_sys + i];
+      int stt = ss.status == 1 ? SFEM_OK : ss.status == 3 ? SFEM_EBREAKDOWN : SFEM_ENOCONV;
+      if (stt != SFEM_OK && worst == SFEM_OK) worst = stt;
+      if (infos) {
+        infos[i] = sfem_solve_info{};
+        infos[i].status = stt;
+        infos[i].iterations = ss.iter;
+        infos[i].outer_iterations = rounds;
+        infos[i].true_relres = ss.relres;
+        infos[i].bnorm = hs[i].bnorm;
+        infos[i].solve_ms = ms;
+        infos[i].fallbacks = fb[i].iterations > 0 ? 1 : 0;
+      }
+    }
+    cleanup();
+    if (worst != SFEM_OK) set_last_error("some systems of the batch did not converge");
+    return worst;
+  } catch (const Error &err) {
+    set_last_error(err.msg);
+    cleanup();
+    return err.status;
+  }
+}

@@ -495,6 +495,8 @@ static void solve_impl(Ctx &c, const double *f_extra, double *u, const sfem_solv
         CgRun<double, double, double> cg(c, v, SFEM_OP_MF32, chunk);
         SFEM_CUDA(cudaMemsetAsync(v.x, 0, n * sizeof(double), c.stream));
         bool started = false;
+        double best = rel;
+        int stall = 0;
         while (rel > tol && total_iter < max_iter && outer < max_outer) {
           SolveScalars s = started ? cg.replace(max_iter)
                                    : cg.start(tol * tol * bnorm * bnorm, max_iter, delta * delta);
@@ -509,6 +511,29 @@ static void solve_impl(Ctx &c, const double *f_extra, double *u, const sfem_solv
           SFEM_CHECK_LAUNCH();
           SFEM_CUDA(cudaMemsetAsync(v.x, 0, n * sizeof(double), c.stream));  // d = 0
           rel = true_residual();  // writes the FP64 true residual into r = v.r
+          // stagnation: the FP32 operator's error floor lies above tol
+          if (rel < 0.9 * best) {
+            best = rel;
+            stall = 0;
+          } else if (++stall >= 3) {
+            break;
+          }
+        }
+        if (rel > tol && status == SFEM_OK && stall >= 3 && total_iter < max_iter) {
+          // finish with FP64 Jacobi-PCG from the current solution
+          ensure_w_scratch(c, (size_t)c.n_tets * 8 * sizeof(double));
+          PcgVecs<double, double, double> v2{x, r, v.p, v.q, c.dinv64, c.dmask, n};
+          CgRun<double, double, double> cg2(c, v2, op64, chunk);
+          info.fallbacks = 1;
+          for (int restart = 0; rel > tol && total_iter < max_iter && restart <= 10; ++restart) {
+            SolveScalars s2 = cg2.start(tol * tol * bnorm * bnorm, max_iter - total_iter, 0.0);
+            total_iter += s2.iter;
+            if (s2.status) {
+              status = SFEM_EBREAKDOWN;
+              break;
+            }
+            rel = true_residual();
+          }
         }
       }
     } else {

@@ -1,0 +1,230 @@
+// Device side of the tiled single-pass FP32 operator (shared by the
+// single-system kernel in tiles.cu and the batched persistent solver in
+// batch.cu).  See tiles.cu for the method and the data layout.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sfem {
+
+constexpr int kTileMax = 512;            // tets per tile
+constexpr int kTileThreads = 256;        // threads per tile CTA
+constexpr int kTilePer = kTileMax / kTileThreads;
+constexpr unsigned short kNoNbr = 0xFFFF;
+
+struct TileArgs {
+  const int32_t *tile_start;
+  const int64_t *hoff, *noff;
+  const int32_t *halo_tet;
+  const uint2 *halo_lconn;
+  const int32_t *tile_nodes;
+  const uint16_t *node_inc;  // per tile node: first slot in its incidence list
+  const float4 *rec;   // 64-byte per-tet records, tile order
+};
+
+struct TetGeo {
+  float g[4][3];
+  float V;
+};
+
+__device__ __forceinline__ void rec_unpack(const float4 (&q)[4], TetGeo &G, uint2 &lc) {
+  G.g[1][0] = q[0].x, G.g[1][1] = q[0].y, G.g[1][2] = q[0].z;
+  G.g[2][0] = q[0].w, G.g[2][1] = q[1].x, G.g[2][2] = q[1].y;
+  G.g[3][0] = q[1].z, G.g[3][1] = q[1].w, G.g[3][2] = q[2].x;
+  G.V = q[2].y;
+  lc = make_uint2(__float_as_uint(q[2].z), __float_as_uint(q[2].w));
+#pragma unroll
+  for (int i = 0; i < 3; ++i) G.g[0][i] = -(G.g[1][i] + G.g[2][i] + G.g[3][i]);
+}
+
+__device__ __forceinline__ void load_rec(const float4 *__restrict__ rec, int t, TetGeo &G, uint2 &lc, uint2 *lnb) {
+  const float4 a = __ldg(rec + 4 * (int64_t)t), b = __ldg(rec + 4 * (int64_t)t + 1);
+  const float4 c = __ldg(rec + 4 * (int64_t)t + 2);
+  G.g[1][0] = a.x, G.g[1][1] = a.y, G.g[1][2] = a.z;
+  G.g[2][0] = a.w, G.g[2][1] = b.x, G.g[2][2] = b.y;
+  G.g[3][0] = b.z, G.g[3][1] = b.w, G.g[3][2] = c.x;
+  G.V = c.y;
+  lc = make_uint2(__float_as_uint(c.z), __float_as_uint(c.w));
+  if (lnb) {
+    const float4 d = __ldg(rec + 4 * (int64_t)t + 3);
+    *lnb = make_uint2(__float_as_uint(d.x), __float_as_uint(d.y));
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) G.g[0][i] = -(G.g[1][i] + G.g[2][i] + G.g[3][i]);
+}
+
+// w = V_e eps_e (Voigt) from the tile's smem displacements; w[6] = V_e
+__device__ __forceinline__ void strain_to(const float4 *su, uint2 lc, const TetGeo &G, float4 *w2) {
+  const int l[4] = {(int)(lc.x & 0xFFFF), (int)(lc.x >> 16), (int)(lc.y & 0xFFFF), (int)(lc.y >> 16)};
+  float H[3][3] = {};
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const float4 u = su[l[a]];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      H[0][j] = fmaf(u.x, G.g[a][j], H[0][j]);
+      H[1][j] = fmaf(u.y, G.g[a][j], H[1][j]);
+      H[2][j] = fmaf(u.z, G.g[a][j], H[2][j]);
+    }
+  }
+  w2[0] = make_float4(H[0][0], H[1][1], H[2][2], H[1][2] + H[2][1]);
+  w2[1] = make_float4(H[2][0] + H[0][2], H[0][1] + H[1][0], G.V, 0.f);
+}
+
+// own-tet records of a tile, kept in registers for both phases (and for
+// every right-hand side of a batched apply)
+struct TileRegs {
+  float4 rr[kTilePer][4];
+};
+
+__device__ __forceinline__ void tile_load(const TileArgs &A, int tile, TileRegs &R) {
+  const int s = A.tile_start[tile], n_own = A.tile_start[tile + 1] - s;
+#pragma unroll
+  for (int r = 0; r < kTilePer; ++r) {
+    const int j = threadIdx.x + r * kTileThreads;
+    if (j < n_own) {
+      const float4 *rp = A.rec + 4 * (int64_t)(s + j);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) R.rr[r][q] = __ldg(rp + q);
+    }
+  }
+}
+
+// y += K u over one tile (all threads of the block); returns this thread's
+// share of u^T K u.  Starts and ends with a block barrier, so it can be
+// called repeatedly on the same shared memory.
+// kCoherentU: read u through L2 (ld.global.cg) instead of the read-only
+// path; needed when u changes during the kernel (persistent solvers).
+template <class TU, class TY, bool kCoherentU = false>
+__device__ __forceinline__ double tile_compute(const TileArgs &A, int tile, const TileRegs &R,
+                                               const TU *__restrict__ u, TY *__restrict__ y, float lam, float mu,
+                                               float4 *smem) {
+  const int s = A.tile_start[tile], n_own = A.tile_start[tile + 1] - s;
+  const int64_t h0 = A.hoff[tile], n0 = A.noff[tile];
+  const int H = (int)(A.hoff[tile + 1] - h0), L = (int)(A.noff[tile + 1] - n0);
+  const int nt = n_own + H;
+  // shared memory: displacements (L), strains split in two float4 arrays
+  // (w0..w3 | w4, w5, V, 0) over tile + halo tets, nodal forces of the tile
+  // tets (4 slots x xyz = 12 floats per tet), incidence list and node starts
+  float4 *su = smem;
+  float4 *swa = su + L;
+  float4 *swb = swa + nt;
+  float *sfe = reinterpret_cast<float *>(swb + nt);                  // 12 * n_own
+  uint16_t *sinc = reinterpret_cast<uint16_t *>(sfe + 12 * n_own);  // 4 * n_own
+  uint16_t *snode = sinc + 4 * n_own;                                 // L
+
+  __syncthreads();
+  for (int i = threadIdx.x; i < L; i += kTileThreads) {
+    const int64_t node = A.tile_nodes[n0 + i];
+    const TU *up = u + 3 * node;
+    if (kCoherentU)
+      su[i] = make_float4((float)__ldcg(up), (float)__ldcg(up + 1), (float)__ldcg(up + 2), 0.f);
+    else
+      su[i] = make_float4((float)__ldg(up), (float)__ldg(up + 1), (float)__ldg(up + 2), 0.f);
+    snode[i] = A.node_inc[n0 + i];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < kTilePer; ++r) {
+    const int j = threadIdx.x + r * kTileThreads;
+    if (j < n_own) {
+      TetGeo G;
+      uint2 lc;
+      rec_unpack(R.rr[r], G, lc);
+      float4 w2[2];
+      strain_to(su, lc, G, w2);
+      swa[j] = w2[0];
+      swb[j] = w2[1];
+      reinterpret_cast<uint2 *>(sinc)[j] = make_uint2(__float_as_uint(R.rr[r][3].z), __float_as_uint(R.rr[r][3].w));
+    }
+  }
+  for (int h = threadIdx.x; h < H; h += kTileThreads) {
+    TetGeo G;
+    uint2 lc;
+    load_rec(A.rec, A.halo_tet[h0 + h], G, lc, nullptr);
+    lc = A.halo_lconn[h0 + h];
+    float4 w2[2];
+    strain_to(su, lc, G, w2);
+    swa[n_own + h] = w2[0];
+    swb[n_own + h] = w2[1];
+  }
+  __syncthreads();
+
+  double en = 0.0;
+#pragma unroll
+  for (int r = 0; r < kTilePer; ++r) {
+    const int j = threadIdx.x + r * kTileThreads;
+    if (j >= n_own) continue;
+    TetGeo G;
+    uint2 lc;
+    rec_unpack(R.rr[r], G, lc);
+    const uint2 nb2 = make_uint2(__float_as_uint(R.rr[r][3].x), __float_as_uint(R.rr[r][3].y));
+    const int nb[4] = {(int)(nb2.x & 0xFFFF), (int)(nb2.x >> 16), (int)(nb2.y & 0xFFFF), (int)(nb2.y >> 16)};
+    const float4 w0 = swa[j], w1 = swb[j];
+    const float W[6] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y};
+    const float Ve = w1.z;
+    // face weights kap_a = 1/(4 (V_e + V_nbr)), 1/(4 V_e) on exterior faces
+    float S[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float ks = 0.f;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      if (nb[a] != kNoNbr) {
+        const float4 n0v = swa[nb[a]], n1v = swb[nb[a]];
+        const float k = 0.25f / (Ve + n1v.z);
+        ks += k;
+        S[0] = fmaf(k, n0v.x, S[0]);
+        S[1] = fmaf(k, n0v.y, S[1]);
+        S[2] = fmaf(k, n0v.z, S[2]);
+        S[3] = fmaf(k, n0v.w, S[3]);
+        S[4] = fmaf(k, n1v.x, S[4]);
+        S[5] = fmaf(k, n1v.y, S[5]);
+      } else {
+        ks += 0.25f / Ve;
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) S[i] = fmaf(ks, W[i], S[i]);
+    const float tr = S[0] + S[1] + S[2];
+    const float st[6] = {lam * tr + 2.f * mu * S[0], lam * tr + 2.f * mu * S[1], lam * tr + 2.f * mu * S[2],
+                         mu * S[3], mu * S[4], mu * S[5]};
+    float el = 0.f;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) el = fmaf(W[i], st[i], el);
+    en += (double)el;
+    float f[12];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      f[3 * a] = G.g[a][0] * st[0] + G.g[a][1] * st[5] + G.g[a][2] * st[4];
+      f[3 * a + 1] = G.g[a][0] * st[5] + G.g[a][1] * st[1] + G.g[a][2] * st[3];
+      f[3 * a + 2] = G.g[a][0] * st[4] + G.g[a][1] * st[3] + G.g[a][2] * st[2];
+    }
+    float4 *fo = reinterpret_cast<float4 *>(sfe + 12 * j);
+    fo[0] = make_float4(f[0], f[1], f[2], f[3]);
+    fo[1] = make_float4(f[4], f[5], f[6], f[7]);
+    fo[2] = make_float4(f[8], f[9], f[10], f[11]);
+  }
+  __syncthreads();
+  // each tile node sums the forces of its slots (fixed order: deterministic)
+  const int nslots = 4 * n_own;
+  for (int i = threadIdx.x; i < L; i += kTileThreads) {
+    const int b = snode[i], e = (i + 1 < L) ? snode[i + 1] : nslots;
+    if (b == e) continue;
+    float fx = 0.f, fy = 0.f, fz = 0.f;
+    for (int k = b; k < e; ++k) {
+      const int slot = sinc[k];
+      const float *fp = sfe + 12 * (slot >> 2) + 3 * (slot & 3);
+      fx += fp[0];
+      fy += fp[1];
+      fz += fp[2];
+    }
+    TY *yp = y + 3 * (int64_t)A.tile_nodes[n0 + i];
+    atomicAdd(yp, (TY)fx);
+    atomicAdd(yp + 1, (TY)fy);
+    atomicAdd(yp + 2, (TY)fz);
+  }
+  __syncthreads();
+  return en;
+}
+
+}  // namespace sfem

@@ -65,6 +65,19 @@ class sfem_solve_info(ctypes.Structure):
                 ("solve_ms", ctypes.c_double)]
 
 
+class sfem_batch_opts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("inner_tol", ctypes.c_double), ("max_iter", ctypes.c_int),
+                ("max_rounds", ctypes.c_int), ("iters_per_launch", ctypes.c_int), ("u_on_device", ctypes.c_int),
+                ("warm_start", ctypes.c_int), ("autotune", ctypes.c_int), ("use_graph", ctypes.c_int),
+                ("reserved", ctypes.c_int * 5)]
+
+
+class sfem_batch_stats(ctypes.Structure):
+    _fields_ = [("rounds", ctypes.c_int), ("ctas_per_sm", ctypes.c_int), ("graph", ctypes.c_int),
+                ("n_systems", ctypes.c_int), ("total_iterations", ctypes.c_longlong), ("ms", ctypes.c_double),
+                ("fallback_systems", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
+
+
 _P = ctypes.c_void_p
 _I64 = ctypes.c_int64
 _SIG = {
@@ -86,6 +99,9 @@ _SIG = {
     "sfem_time_operator": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "sfem_launch_count": (ctypes.c_int64, []),
     "sfem_apply_noalloc": (ctypes.c_int, [_P, _P, _P]),
+    "sfem_batch_solve": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(_P),
+                                        ctypes.POINTER(sfem_batch_opts), ctypes.POINTER(sfem_solve_info),
+                                        ctypes.POINTER(sfem_batch_stats)]),
 }
 for _name, (_res, _args) in _SIG.items():
     _fn = getattr(lib, _name)
@@ -246,6 +262,33 @@ def sfem_solve(h, u, opts: sfem_solve_opts, f_extra=None, check=True) -> dict:
     if check and st not in (SFEM_OK,):
         raise SfemError(st, "sfem_solve")
     return out
+
+
+def batch_opts(tol=1e-8, inner_tol=0.0, max_iter=0, max_rounds=0, iters_per_launch=0, u_on_device=False,
+               warm_start=False, autotune=True, use_graph=True):
+    o = sfem_batch_opts()
+    o.tol, o.inner_tol = float(tol), float(inner_tol)
+    o.max_iter, o.max_rounds, o.iters_per_launch = int(max_iter), int(max_rounds), int(iters_per_launch)
+    o.u_on_device, o.warm_start = int(bool(u_on_device)), int(bool(warm_start))
+    o.autotune, o.use_graph = int(bool(autotune)), int(bool(use_graph))
+    return o
+
+
+def sfem_batch_solve(handles, us, opts: sfem_batch_opts, n_systems: int, check=True):
+    """Solve all load cases of all contexts together.  us[i] holds nrhs_i x
+    ndof_i float64 values (numpy host arrays, or CUDA tensors with
+    opts.u_on_device).  Returns (list of per-system info dicts, stats dict)."""
+    n = len(handles)
+    harr = (_P * n)(*handles)
+    uarr = (_P * n)(*[_ptr(x) for x in us])
+    infos = (sfem_solve_info * n_systems)()
+    stats = sfem_batch_stats()
+    st = lib.sfem_batch_solve(harr, n, uarr, ctypes.byref(opts), infos, ctypes.byref(stats))
+    out = [{k: getattr(i, k) for k, _ in i._fields_} for i in infos]
+    sd = {k: getattr(stats, k) for k, _ in stats._fields_}
+    if check and st != SFEM_OK:
+        raise SfemError(st, "sfem_batch_solve")
+    return out, sd
 
 
 def sfem_get_geometry(h, n_tets):

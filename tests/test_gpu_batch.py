@@ -1,0 +1,106 @@
+"""Batched solve (many beams x four load cases in persistent launches)
+against the FP64 oracle and against the single-system solver.
+
+Tolerance: each system reaches a FP64 true relative residual <= tol, and
+its displacements match the oracle's exact (Cholesky) solution to 1e-6
+relative L2, the bar for reduced-precision forms."""
+import numpy as np
+import pytest
+
+from inputs.kuhn_beam import batch_beams, clamp_dofs, four_load_cases, kuhn_beam, Problem
+from oracle import fsfem as F
+from oracle import solve as OS
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def S():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2001_08849_gb300 import sfem
+    return sfem
+
+
+def _small_batch():
+    out = []
+    rng = np.random.default_rng(77)
+    for b, cells in enumerate([(6, 2, 2), (9, 3, 2), (12, 2, 3), (5, 3, 3), (8, 4, 2)]):
+        mesh = kuhn_beam(*cells, dims=(float(rng.uniform(2, 6)), 1.0, 1.0), jitter=0.1, seed=300 + b)
+        dofs, vals = clamp_dofs(mesh, 0, 0)
+        tris, trac = four_load_cases(mesh)
+        out.append(Problem(mesh, float(rng.uniform(50e9, 300e9)), float(rng.uniform(0.2, 0.45)), dofs, vals,
+                           tris, trac))
+    return out
+
+
+def _oracle_solutions(p):
+    m = p.mesh
+    K = F.assemble(m.xyz, m.tets, p.E, p.nu).matrix()
+    fs = F.traction_load(m.n_nodes, m.xyz, p.trac_tris, p.trac)
+    sols = []
+    for r in range(p.nrhs):
+        A, b, _, _ = F.dirichlet_system(K, fs[r], p.dir_dofs, p.dir_vals)
+        sols.append(OS.cholesky_solve(A.toarray(), b))
+    return np.stack(sols)
+
+
+@pytest.mark.parametrize("graph", [True, False])
+def test_batch_matches_oracle(S, graph):
+    probs = _small_batch()
+    ctxs = [S.FsFem(p) for p in probs]
+    try:
+        us = [np.zeros((p.nrhs, c.ndof)) for p, c in zip(probs, ctxs)]
+        n_sys = sum(p.nrhs for p in probs)
+        infos, stats = S.sfem_batch_solve([c.h for c in ctxs], us, S.batch_opts(tol=1e-10, use_graph=graph),
+                                          n_sys)
+        assert stats["n_systems"] == n_sys == 20
+        assert stats["rounds"] >= 2 and stats["ctas_per_sm"] >= 1
+        k = 0
+        for p, u in zip(probs, us):
+            ref = _oracle_solutions(p)
+            for r in range(p.nrhs):
+                assert infos[k]["status"] == S.SFEM_OK and infos[k]["true_relres"] <= 1e-10, infos[k]
+                rel = np.linalg.norm(u[r] - ref[r]) / np.linalg.norm(ref[r])
+                assert rel <= 1e-6, (k, rel)
+                k += 1
+    finally:
+        for c in ctxs:
+            c.close()
+
+
+def test_batch_single_system_equals_single_solve(S):
+    p = _small_batch()[1]
+    p1 = Problem(p.mesh, p.E, p.nu, p.dir_dofs, p.dir_vals, p.trac_tris, p.trac[2:3])   # torsion case only
+    with S.FsFem(p1) as ctx:
+        u = np.zeros((1, ctx.ndof))
+        infos, stats = S.sfem_batch_solve([ctx.h], [u], S.batch_opts(tol=1e-10), 1)
+        x = np.zeros(ctx.ndof)
+        info = S.sfem_solve(ctx.h, x, S.solve_opts(kind=S.SFEM_SOLVE_IR32_64, tol=1e-10))
+        assert np.linalg.norm(u[0] - x) <= 1e-7 * np.linalg.norm(x)
+        assert infos[0]["true_relres"] <= 1e-10
+
+
+def test_batch_uneven_beams_device_vectors(S):
+    """Eight beams of the uneven batch family (seeded grids, lengths and
+    materials), device vectors: every system reaches 1e-8."""
+    import torch
+    probs = [p for p in batch_beams(64, seed=5) if p.mesh.n_tets < 60000][:8]
+    ctxs = [S.FsFem(p) for p in probs]
+    try:
+        us = [torch.zeros((p.nrhs, c.ndof), dtype=torch.float64, device="cuda") for p, c in zip(probs, ctxs)]
+        n_sys = sum(p.nrhs for p in probs)
+        infos, stats = S.sfem_batch_solve([c.h for c in ctxs], us, S.batch_opts(tol=1e-8, u_on_device=True), n_sys)
+        assert all(i["status"] == S.SFEM_OK and i["true_relres"] <= 1e-8 for i in infos)
+        # single-system solves of the first beam agree
+        c0 = ctxs[0]
+        for r in range(probs[0].nrhs):
+            x = np.zeros(c0.ndof)
+            S.sfem_solve(c0.h, x, S.solve_opts(kind=S.SFEM_SOLVE_PCG64, rhs=r, tol=1e-9), check=False)
+            assert np.linalg.norm(us[0][r].cpu().numpy() - x) <= 1e-5 * np.linalg.norm(x)
+    finally:
+        for c in ctxs:
+            c.close()

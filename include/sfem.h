@@ -114,9 +114,18 @@ typedef struct sfem_solve_opts {
   double inner_tol;    /* IR: FP32 residual reduction that triggers a reliable update (0: 0.1) */
   int max_outer;       /* IR: reliable updates at most (0: 200) */
   int check_every;     /* iterations between host convergence checks (0: 32) */
-  const void *learned; /* FPCG_LEARNED: an sfem_learned handle */
+  const void *learned; /* FPCG_LEARNED: an sfem_learned handle (NULL: flexible CG with
+                          the Jacobi preconditioner alone) */
   int fp32_vectors;    /* IR vectors: 0 FP64 p, q, r (default); 1 all FP32; 2 FP32 p, q and FP64 r */
-  int reserved[5];
+  int learned_window;  /* FPCG_LEARNED stagnation guard: the correction is switched off for
+                          the rest of the solve when ||r|| has not fallen 10% below its best
+                          value for this many iterations (0: 100) */
+  int learned_pace;    /* FPCG_LEARNED pace guard: the Jacobi-PCG iteration count to keep
+                          pace with (e.g. measured on the training loads); the correction
+                          is switched off when ||r|| lies more than 30x above the
+                          log-linear line from ||r_0|| to the tolerance over this many
+                          iterations (0: no pace guard) */
+  int reserved[3];
 } sfem_solve_opts;
 
 typedef struct sfem_solve_info {
@@ -129,6 +138,8 @@ typedef struct sfem_solve_info {
   double true_relres;      /* ||b - A u||_2 / ||b||_2 in FP64, after exit */
   double bnorm;            /* ||b||_2 */
   double solve_ms;         /* device time of the solve */
+  int learned_iterations;  /* FPCG: iterations run with the learned correction active */
+  int reserved[3];
 } sfem_solve_info;
 
 /* sfem_mesh_setup — geometry, topology, smoothing domains, loads, BCs.
@@ -227,6 +238,91 @@ typedef struct sfem_batch_stats {
 
 int sfem_batch_solve(sfem_ctx *const *ctxs, int n, double *const *u, const sfem_batch_opts *opts,
                      sfem_solve_info *infos, sfem_batch_stats *stats);
+
+/* ---- learned coarse correction (no counterpart in the paper) -------------
+ *
+ * A small network maps the residual, pooled over a regular grid of patches,
+ * to a coarse displacement correction used inside flexible PCG
+ * (SFEM_SOLVE_FPCG_LEARNED):
+ *   patches   a d0 x d1 x d2 grid of boxes over the mesh's bounding box; a
+ *             node belongs to the box holding it;
+ *   pooling   mean nodal residual per patch (3 values);
+ *   inputs    per patch 84 values: the pooled residuals of its 3x3x3 patch
+ *             neighbourhood (zero outside the grid), k-major over the offsets
+ *             (-1,0,1)^3 and then the component, divided by the RMS of all
+ *             pooled values; then the patch centre normalised to [0,1]^3;
+ *   network   84 -> 128 -> GELU -> 128 -> GELU -> 3 (GELU with the exact
+ *             error function); parameters are one FP32 vector in the order
+ *             W1 (84 x 128, row-major, input-major), b1, W2 (128 x 128), b2,
+ *             W3 (128 x 3), b3 (n_params = 27523); inference uses BF16 copies
+ *             of the parameters (round to nearest even) for the weights, FP32
+ *             biases and FP32 accumulation;
+ *   prolong   trilinear interpolation of the patch outputs between patch
+ *             centres (clamped to the outermost centres), masked by P: c;
+ *   z         D^-1 r + alpha c with alpha = c.r / c.A c (c.A c by the FP32
+ *             matrix-free operator); an unusable c (c.A c <= 0, non-finite
+ *             alpha or z.r) gives z = D^-1 r for that iteration.
+ * Training targets are the pooled errors u* - x of the same snapshots,
+ * divided by their RMS; the loss is sum((y - T)^2) / rows.  A model is bound
+ * to the mesh, device and stream of the context it was created on. */
+typedef struct sfem_learned sfem_learned;
+
+typedef struct sfem_learned_opts {
+  int patch_dims[3];   /* patch grid (0: about patch_nodes nodes per patch axis) */
+  int patch_nodes;     /* 0: 8 */
+  uint64_t seed;       /* initial parameters: He-normal weights by a counter-based
+                          generator (splitmix64 + Box-Muller), zero biases */
+  int reserved[6];
+} sfem_learned_opts;
+
+/* Create a model on ctx's mesh with freshly initialised parameters. */
+int sfem_learned_create(sfem_learned **out, sfem_ctx *ctx, const sfem_learned_opts *opts);
+void sfem_learned_destroy(sfem_learned *m);
+int sfem_learned_info(const sfem_learned *m, int *patch_dims /* 3, may be NULL */,
+                      int *n_patches, int *n_params);
+/* FP32 master parameters from / to HOST memory (n = n_params); setting them
+ * resets the Adam state. */
+int sfem_learned_set_params(sfem_learned *m, const float *theta, int64_t n);
+int sfem_learned_get_params(sfem_learned *m, float *theta, int64_t n);
+/* Versioned blob (HOST memory): 8 int32 (magic, version 1, 84, 128, 3,
+ * patch dims) then the FP32 parameters.  export with buf = NULL only
+ * reports the size. */
+int sfem_learned_export(sfem_learned *m, void *buf, size_t cap, size_t *size);
+int sfem_learned_import(sfem_learned *m, const void *buf, size_t size);
+/* Y (rows x 3) = network(X (rows x 84)) with the BF16 inference path;
+ * device pointers. */
+int sfem_learned_forward(sfem_learned *m, const float *X, float *Y, int64_t rows);
+/* Features X (n_patches x 84) of the residual r and, if e is not NULL,
+ * targets T (n_patches x 3) = pooled e / RMS; device pointers (r, e: ndof
+ * FP64). */
+int sfem_learned_sample(sfem_learned *m, sfem_ctx *ctx, const double *r, const double *e,
+                        float *X, float *T);
+/* z = D^-1 r + alpha c for one residual (device FP64, ndof); alpha to host. */
+int sfem_learned_correction(sfem_learned *m, sfem_ctx *ctx, const double *r, double *z,
+                            double *alpha);
+/* Run the flexible PCG of opts (kind SFEM_SOLVE_FPCG_LEARNED, opts->learned
+ * NULL for a Jacobi-PCG trajectory or m for the model's own) on ctx and
+ * write one training sample per snapshot (before the first iteration and
+ * every opts->check_every iterations): features of r into X and targets of
+ * u_star - x into T (device; n_patches rows each) while rows fit in
+ * cap_rows.  u_star: device FP64 reference solution.  *rows: rows written. */
+int sfem_learned_collect(sfem_learned *m, sfem_ctx *ctx, const sfem_solve_opts *opts,
+                         const double *u_star, float *X, float *T, int64_t cap_rows,
+                         int64_t *rows, sfem_solve_info *info);
+/* Loss and gradient (FP32 forward and backward with the FP32 master
+ * parameters) of rows samples; grad: device, n_params floats (may be NULL);
+ * loss: host (may be NULL). */
+int sfem_learned_loss_grad(sfem_learned *m, const float *X, const float *T, int64_t rows,
+                           float *grad, double *loss);
+/* One Adam step (Kingma & Ba, bias-corrected) with grad (device; NULL: the
+ * gradient of the last loss_grad). */
+int sfem_learned_adam(sfem_learned *m, const float *grad, float lr, float b1, float b2, float eps);
+/* epochs of mini-batch Adam (b1 0.9, b2 0.999, eps 1e-8) over rows samples
+ * (device X, T), each epoch visiting rows in the order r -> (a r + b) mod
+ * rows with a, b drawn from seed; loss (host, may be NULL): mean loss over
+ * all rows afterwards. */
+int sfem_learned_train(sfem_learned *m, const float *X, const float *T, int64_t rows,
+                       int64_t batch_rows, int epochs, float lr, uint64_t seed, double *loss);
 
 int sfem_get_info(const sfem_ctx *ctx, sfem_mesh_info *info);
 

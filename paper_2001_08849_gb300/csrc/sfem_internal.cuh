@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -236,6 +237,18 @@ void build_tiles(Ctx &c);
 // type TU/TY (float or double); energy u^T K u summed into *energy_out
 template <class TU, class TY>
 void launch_mf32_tiled(Ctx &c, cudaStream_t st, const TU *u, TY *y, double *energy_out, const int *done);
+
+// solves (solve.cu); a Snapshot, when given, sees the iterate x and the
+// residual r (device, ndof) of the flexible PCG before its first iteration
+// and after every chunk of check_every iterations
+using Snapshot = std::function<void(const double *x, const double *r, int iter)>;
+void solve_impl(Ctx &c, const double *f_extra, double *u, const sfem_solve_opts &o, sfem_solve_info &info,
+                const Snapshot *snap = nullptr);
+// flexible PCG with the learned correction (learned.cu); r holds the masked
+// residual of x on entry; true_residual() recomputes it and returns ||r||/||b||
+void solve_fpcg(Ctx &c, const void *learned, int op64, double *x, double *r, double bnorm, double tol, int max_iter,
+                int chunk, int window, int pace, sfem_solve_info &info, const std::function<double()> &true_residual,
+                const Snapshot *snap);
 
 }  // namespace sfem
 

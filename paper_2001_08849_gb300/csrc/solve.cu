@@ -2,7 +2,8 @@
 // elimination (STEP 5): A = P K P + (I - P), b = P (f - K g) + (I - P) g.
 //
 // The paper calls a direct solver (Section 3.3); the library runs
-// Jacobi-preconditioned CG on the GPU instead:
+// Jacobi-preconditioned CG on the GPU instead (and, in learned.cu, flexible
+// PCG with a learned coarse correction):
 //   PCG64    all vectors, scalars and the operator in FP64;
 //   IR32_64  mixed precision: Jacobi-PCG iterations on the FP32 matrix-free
 //            operator with FP32 vectors (scalars and reductions in FP64)
@@ -356,7 +357,8 @@ struct SolveBuffers {
   }
 };
 
-static void solve_impl(Ctx &c, const double *f_extra, double *u, const sfem_solve_opts &o, sfem_solve_info &info) {
+void solve_impl(Ctx &c, const double *f_extra, double *u, const sfem_solve_opts &o, sfem_solve_info &info,
+                const Snapshot *snap) {
   const int64_t n = c.ndof;
   const int g256 = grid_for(n, 256);
   cudaMemcpyKind in_kind = o.u_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
@@ -536,8 +538,16 @@ static void solve_impl(Ctx &c, const double *f_extra, double *u, const sfem_solv
           }
         }
       }
+    } else if (o.kind == SFEM_SOLVE_FPCG_LEARNED) {
+      const int window = o.learned_window > 0 ? o.learned_window : 100;
+      solve_fpcg(c, o.learned, op64, x, r, bnorm, tol, max_iter, chunk, window, std::max(o.learned_pace, 0), info,
+                 true_residual, snap);
+      total_iter = info.iterations;
+      outer = info.outer_iterations;
+      rel = info.true_relres;
+      if (info.status != SFEM_OK && info.status != SFEM_ENOCONV) status = info.status;
     } else {
-      throw Error{SFEM_EINVAL, "solver kind not available in this entry point"};
+      throw Error{SFEM_EINVAL, "unknown solver kind"};
     }
     info.iterations = total_iter;
     info.outer_iterations = outer;

@@ -56,13 +56,13 @@ class sfem_solve_opts(ctypes.Structure):
                 ("u_on_device", ctypes.c_int), ("warm_start", ctypes.c_int), ("max_iter", ctypes.c_int),
                 ("tol", ctypes.c_double), ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int),
                 ("check_every", ctypes.c_int), ("learned", ctypes.c_void_p), ("fp32_vectors", ctypes.c_int),
-                ("reserved", ctypes.c_int * 5)]
+                ("learned_window", ctypes.c_int), ("learned_pace", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
 
 
 class sfem_solve_info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("iterations", ctypes.c_int), ("outer_iterations", ctypes.c_int),
                 ("fallbacks", ctypes.c_int), ("true_relres", ctypes.c_double), ("bnorm", ctypes.c_double),
-                ("solve_ms", ctypes.c_double)]
+                ("solve_ms", ctypes.c_double), ("learned_iterations", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
 
 
 class sfem_batch_opts(ctypes.Structure):
@@ -78,8 +78,14 @@ class sfem_batch_stats(ctypes.Structure):
                 ("fallback_systems", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
 
 
+class sfem_learned_opts(ctypes.Structure):
+    _fields_ = [("patch_dims", ctypes.c_int * 3), ("patch_nodes", ctypes.c_int), ("seed", ctypes.c_uint64),
+                ("reserved", ctypes.c_int * 6)]
+
+
 _P = ctypes.c_void_p
 _I64 = ctypes.c_int64
+_F = ctypes.c_float
 _SIG = {
     "sfem_mesh_setup": (ctypes.c_int, [ctypes.POINTER(_P), _P, _I64, _P, _I64, ctypes.c_double, ctypes.c_double,
                                        _P, _P, _I64, _P, _P, _I64, ctypes.POINTER(sfem_opts), _P]),
@@ -102,6 +108,22 @@ _SIG = {
     "sfem_batch_solve": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(_P),
                                         ctypes.POINTER(sfem_batch_opts), ctypes.POINTER(sfem_solve_info),
                                         ctypes.POINTER(sfem_batch_stats)]),
+    "sfem_learned_create": (ctypes.c_int, [ctypes.POINTER(_P), _P, ctypes.POINTER(sfem_learned_opts)]),
+    "sfem_learned_destroy": (None, [_P]),
+    "sfem_learned_info": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "sfem_learned_set_params": (ctypes.c_int, [_P, _P, _I64]),
+    "sfem_learned_get_params": (ctypes.c_int, [_P, _P, _I64]),
+    "sfem_learned_export": (ctypes.c_int, [_P, _P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
+    "sfem_learned_import": (ctypes.c_int, [_P, _P, ctypes.c_size_t]),
+    "sfem_learned_forward": (ctypes.c_int, [_P, _P, _P, _I64]),
+    "sfem_learned_sample": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
+    "sfem_learned_correction": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(ctypes.c_double)]),
+    "sfem_learned_collect": (ctypes.c_int, [_P, _P, ctypes.POINTER(sfem_solve_opts), _P, _P, _P, _I64,
+                                            ctypes.POINTER(_I64), ctypes.POINTER(sfem_solve_info)]),
+    "sfem_learned_loss_grad": (ctypes.c_int, [_P, _P, _P, _I64, _P, ctypes.POINTER(ctypes.c_double)]),
+    "sfem_learned_adam": (ctypes.c_int, [_P, _P, _F, _F, _F, _F]),
+    "sfem_learned_train": (ctypes.c_int, [_P, _P, _P, _I64, _I64, ctypes.c_int, _F, ctypes.c_uint64,
+                                          ctypes.POINTER(ctypes.c_double)]),
 }
 for _name, (_res, _args) in _SIG.items():
     _fn = getattr(lib, _name)
@@ -242,14 +264,16 @@ def sfem_apply_noalloc(h, u, y):
 
 
 def solve_opts(kind=SFEM_SOLVE_PCG64, op64=SFEM_OP_MF64, rhs=0, tol=1e-8, max_iter=0, inner_tol=0.0,
-               max_outer=0, check_every=0, u_on_device=False, warm_start=False, learned=None, fp32_vectors=False):
+               max_outer=0, check_every=0, u_on_device=False, warm_start=False, learned=None, fp32_vectors=False,
+               learned_window=0, learned_pace=0):
     o = sfem_solve_opts()
     o.kind, o.op64, o.rhs = int(kind), int(op64), int(rhs)
     o.u_on_device, o.warm_start = int(bool(u_on_device)), int(bool(warm_start))
     o.max_iter, o.tol, o.inner_tol = int(max_iter), float(tol), float(inner_tol)
     o.max_outer, o.check_every = int(max_outer), int(check_every)
-    o.learned = learned
+    o.learned = learned.h if isinstance(learned, Learned) else learned
     o.fp32_vectors = int(fp32_vectors)
+    o.learned_window, o.learned_pace = int(learned_window), int(learned_pace)
     return o
 
 
@@ -342,6 +366,101 @@ def sfem_launch_count() -> int:
 
 def sfem_strerror(status: int) -> str:
     return lib.sfem_strerror(status).decode()
+
+
+# ---- learned coarse correction ------------------------------------------------
+
+N_PARAMS = 84 * 128 + 128 + 128 * 128 + 128 + 128 * 3 + 3
+
+
+class Learned:
+    """An sfem_learned model on the mesh of context `h` (see include/sfem.h).
+    Device arrays are torch CUDA tensors (float32 features / targets,
+    float64 vectors).  `keepalive` pins the context's allocator callbacks."""
+
+    def __init__(self, h, patch_dims=(0, 0, 0), patch_nodes=0, seed=0, keepalive=None):
+        o = sfem_learned_opts()
+        for a in range(3):
+            o.patch_dims[a] = int(patch_dims[a])
+        o.patch_nodes, o.seed = int(patch_nodes), int(seed)
+        m = _P()
+        _check(lib.sfem_learned_create(ctypes.byref(m), h, ctypes.byref(o)), "sfem_learned_create")
+        self.h = m.value
+        self._keep = keepalive
+        dims = (ctypes.c_int * 3)()
+        P, n = ctypes.c_int(), ctypes.c_int()
+        _check(lib.sfem_learned_info(self.h, dims, ctypes.byref(P), ctypes.byref(n)), "sfem_learned_info")
+        self.patch_dims, self.n_patches, self.n_params = tuple(dims), P.value, n.value
+
+    def set_params(self, theta):
+        th = np.ascontiguousarray(theta, dtype=np.float32)
+        _check(lib.sfem_learned_set_params(self.h, _ptr(th), th.size), "sfem_learned_set_params")
+
+    def get_params(self):
+        th = np.zeros(self.n_params, np.float32)
+        _check(lib.sfem_learned_get_params(self.h, _ptr(th), th.size), "sfem_learned_get_params")
+        return th
+
+    def export_blob(self) -> bytes:
+        size = ctypes.c_size_t()
+        _check(lib.sfem_learned_export(self.h, None, 0, ctypes.byref(size)), "sfem_learned_export")
+        buf = ctypes.create_string_buffer(size.value)
+        _check(lib.sfem_learned_export(self.h, buf, size.value, ctypes.byref(size)), "sfem_learned_export")
+        return buf.raw
+
+    def import_blob(self, blob: bytes):
+        _check(lib.sfem_learned_import(self.h, blob, len(blob)), "sfem_learned_import")
+
+    def forward(self, X, Y):
+        _check(lib.sfem_learned_forward(self.h, _ptr(X), _ptr(Y), int(X.shape[0])), "sfem_learned_forward")
+
+    def sample(self, ctx_h, r, X, e=None, T=None):
+        _check(lib.sfem_learned_sample(self.h, ctx_h, _ptr(r), _ptr(e), _ptr(X), _ptr(T)), "sfem_learned_sample")
+
+    def correction(self, ctx_h, r, z) -> float:
+        a = ctypes.c_double()
+        _check(lib.sfem_learned_correction(self.h, ctx_h, _ptr(r), _ptr(z), ctypes.byref(a)),
+               "sfem_learned_correction")
+        return a.value
+
+    def collect(self, ctx_h, opts, u_star, X, T, row0=0):
+        """Snapshots of a flexible-PCG run into X[row0:], T[row0:]; returns
+        (rows written, solve info dict)."""
+        rows = _I64()
+        info = sfem_solve_info()
+        cap = int(X.shape[0]) - int(row0)
+        Xp = _ptr(X) + 84 * 4 * int(row0)
+        Tp = _ptr(T) + 3 * 4 * int(row0)
+        _check(lib.sfem_learned_collect(self.h, ctx_h, ctypes.byref(opts), _ptr(u_star), Xp, Tp, cap,
+                                        ctypes.byref(rows), ctypes.byref(info)), "sfem_learned_collect")
+        return rows.value, {k: getattr(info, k) for k, _ in info._fields_}
+
+    def loss_grad(self, X, T, grad=None) -> float:
+        loss = ctypes.c_double()
+        _check(lib.sfem_learned_loss_grad(self.h, _ptr(X), _ptr(T), int(X.shape[0]), _ptr(grad),
+                                          ctypes.byref(loss)), "sfem_learned_loss_grad")
+        return loss.value
+
+    def adam(self, grad=None, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+        _check(lib.sfem_learned_adam(self.h, _ptr(grad), lr, b1, b2, eps), "sfem_learned_adam")
+
+    def train(self, X, T, rows=None, batch_rows=4096, epochs=1, lr=1e-3, seed=0) -> float:
+        rows = int(X.shape[0]) if rows is None else int(rows)
+        loss = ctypes.c_double()
+        _check(lib.sfem_learned_train(self.h, _ptr(X), _ptr(T), rows, int(batch_rows), int(epochs), float(lr),
+                                      int(seed), ctypes.byref(loss)), "sfem_learned_train")
+        return loss.value
+
+    def close(self):
+        if self.h:
+            lib.sfem_learned_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ---- convenience wrapper ----------------------------------------------------

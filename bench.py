@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the PCG64 comparison solve")
+    ap.add_argument("--learned-train", type=int, default=8, help="training loads of the learned form")
+    ap.add_argument("--learned-test", type=int, default=2, help="held-out loads of the learned form")
     return ap.parse_args()
 
 
@@ -233,6 +235,81 @@ def batch_form(S):
 
 
 # ---------------------------------------------------------------------------
+# learned form: flexible PCG with the learned coarse correction vs Jacobi-PCG
+# ---------------------------------------------------------------------------
+
+def learned_form(S, n_train=8, n_test=2, every=8, epochs=10):
+    """Train the coarse-correction network on snapshots of Jacobi-PCG runs of
+    the 2M-tet beam under random loads (seeds 100..), then time held-out
+    loads (seeds 200..) with flexible PCG + correction against flexible PCG
+    with the Jacobi preconditioner alone (FP64, CSR operator, tol 1e-8)."""
+    import numpy as np
+    import torch
+    from inputs.kuhn_beam import multi_load_cantilever
+    nx, ny, nz = CELLS
+    train = list(range(100, 100 + n_train))
+    test = list(range(200, 200 + n_test))
+    prob = multi_load_cantilever(nx, ny, nz, train + test, seed=SEED)
+    fe = S.FsFem(prob, on_device=True)
+    model = None
+    try:
+        S.sfem_assemble(fe.h)
+        dims = tuple(-(-(c + 1) // 8) for c in CELLS)          # patches of 8 x 8 x 8 nodes
+        model = S.Learned(fe.h, patch_dims=dims, seed=1, keepalive=fe._keep)
+        n = fe.ndof
+        cap = int(1.2 * 6000 / every) * model.n_patches * n_train
+        X = torch.empty(cap, 84, dtype=torch.float32, device="cuda")
+        T = torch.empty(cap, 3, dtype=torch.float32, device="cuda")
+        rows, jac_iters = 0, []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(n_train):
+            us = torch.zeros(n, dtype=torch.float64, device="cuda")
+            S.sfem_solve(fe.h, us, S.solve_opts(kind=S.SFEM_SOLVE_PCG64, op64=S.SFEM_OP_CSR64, rhs=k, tol=1e-10,
+                                                u_on_device=True), check=False)
+            got, info = model.collect(fe.h, S.solve_opts(kind=S.SFEM_SOLVE_FPCG_LEARNED, op64=S.SFEM_OP_CSR64,
+                                                         rhs=k, tol=TOL, check_every=every), us, X, T, rows)
+            rows += got
+            jac_iters.append(info["iterations"])
+        torch.cuda.synchronize()
+        data_s = time.perf_counter() - t0
+        loss0 = model.loss_grad(X[:min(rows, 1 << 18)], T[:min(rows, 1 << 18)])  # a sample of the rows
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        loss1 = model.train(X, T, rows=rows, batch_rows=4096, epochs=epochs, lr=1e-3, seed=3)
+        torch.cuda.synchronize()
+        train_s = time.perf_counter() - t0
+        pace = int(np.mean(jac_iters))
+        res = {"jacobi": [], "learned": []}
+        for k in range(n_train, n_train + n_test):
+            for name, learned in (("jacobi", None), ("learned", model)):
+                u = torch.zeros(n, dtype=torch.float64, device="cuda")
+                o = S.solve_opts(kind=S.SFEM_SOLVE_FPCG_LEARNED, op64=S.SFEM_OP_CSR64, rhs=k, tol=TOL,
+                                 u_on_device=True, learned=learned, learned_pace=pace)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                inf = S.sfem_solve(fe.h, u, o, check=False)
+                torch.cuda.synchronize()
+                res[name].append({"time_to_solve_s": time.perf_counter() - t0, "iterations": inf["iterations"],
+                                  "learned_iterations": inf["learned_iterations"],
+                                  "fallbacks": inf["fallbacks"], "true_relres": inf["true_relres"],
+                                  "status": inf["status"]})
+        it_j = float(np.mean([r["iterations"] for r in res["jacobi"]]))
+        it_l = float(np.mean([r["iterations"] for r in res["learned"]]))
+        t_j = float(np.mean([r["time_to_solve_s"] for r in res["jacobi"]]))
+        t_l = float(np.mean([r["time_to_solve_s"] for r in res["learned"]]))
+        return {"train_loads": n_train, "test_loads": n_test, "patch_dims": list(dims),
+                "snapshot_every": every, "rows": rows, "epochs": epochs, "loss_before": loss0,
+                "loss_after": loss1, "data_s": data_s, "train_s": train_s, "pace": pace,
+                "jacobi": res["jacobi"], "learned": res["learned"],
+                "iteration_gain": it_j / it_l, "time_gain": t_j / t_l}
+    finally:
+        if model is not None:
+            model.close()
+        fe.close()
+
+
+# ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
 
@@ -384,6 +461,7 @@ def main():
 
     if not args.no_forms and rank == 0:
         forms["batch_64x4"] = batch_form(S)
+        forms["fpcg_learned"] = learned_form(S, n_train=args.learned_train, n_test=args.learned_test)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

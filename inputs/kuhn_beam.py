@@ -241,3 +241,21 @@ def random_loads(mesh: BeamMesh, seed: int, n_patches: int = 3, magnitude: float
         all_tris.append(tris[sel])
         all_t.append(np.tile(tvec, (int(sel.sum()), 1)))
     return np.concatenate(all_tris).astype(np.int32), np.concatenate(all_t)[None]
+
+
+def multi_load_cantilever(nx, ny, nz, load_seeds, dims=(10.0, 1.0, 1.0), seed=2, E=210e9, nu=0.3,
+                          jitter=0.1) -> Problem:
+    """The cantilever with one load case per entry of load_seeds: the
+    random_loads patches of that seed, each case given on the union of the
+    free-face triangles (zero traction elsewhere)."""
+    base = cantilever(nx, ny, nz, dims, seed, E, nu, jitter=jitter)
+    m = base.mesh
+    faces = [(0, 1), (1, 0), (1, 1), (2, 0), (2, 1)]
+    tris = np.concatenate([face_triangles(m, a, s) for a, s in faces]).astype(np.int32)
+    key = {tuple(sorted(t)): i for i, t in enumerate(tris.tolist())}
+    trac = np.zeros((len(load_seeds), len(tris), 3))
+    for k, sd in enumerate(load_seeds):
+        st, sv = random_loads(m, sd)
+        for t, v in zip(st.tolist(), sv[0]):
+            trac[k, key[tuple(sorted(t))]] += v
+    return Problem(m, E, nu, base.dir_dofs, base.dir_vals, tris, trac)

@@ -9,7 +9,7 @@ import pytest
 import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
-from inputs.kuhn_beam import cantilever, face_triangles, random_loads
+from inputs.kuhn_beam import cantilever, multi_load_cantilever
 from oracle import fsfem, mlp
 
 pytestmark = pytest.mark.gpu
@@ -253,28 +253,10 @@ def test_model_of_another_mesh_is_rejected(S, beam):
 
 # ---- training on the solver's own snapshots, and the measured gain ----------
 
-def _multi_load_problem(cells, seeds):
-    """One cantilever with one load case per seed (random traction patches
-    on the free faces; every case on the union of the free-face triangles)."""
-    base = cantilever(*cells, seed=2)
-    m = base.mesh
-    faces = [(0, 1), (1, 0), (1, 1), (2, 0), (2, 1)]
-    tris = np.concatenate([face_triangles(m, a, s) for a, s in faces]).astype(np.int32)
-    key = {tuple(sorted(t)): i for i, t in enumerate(tris.tolist())}
-    trac = np.zeros((len(seeds), len(tris), 3))
-    for k, sd in enumerate(seeds):
-        st, sv = random_loads(m, sd)
-        for t, v in zip(st.tolist(), sv[0]):
-            trac[k, key[tuple(sorted(t))]] += v
-    base.trac_tris = tris
-    base.trac = trac
-    return base
-
-
 def test_training_reduces_loss_and_gain_is_reported(S, record_property):
     train_seeds = list(range(100, 112))
     test_seeds = [200, 201, 202, 203]
-    p = _multi_load_problem((40, 8, 8), train_seeds + test_seeds)
+    p = multi_load_cantilever(40, 8, 8, train_seeds + test_seeds)
     fe = S.FsFem(p)
     dims = (6, 2, 2)
     m = _model(S, fe, dims, seed=1)

@@ -91,9 +91,11 @@ typedef struct sfem_csr {
 
 /* Operators for sfem_apply and for the FP64 steps of sfem_solve. */
 enum {
-  SFEM_OP_CSR64 = 0,  /* assembled CSR, FP64 (needs sfem_assemble) */
-  SFEM_OP_MF64 = 1,   /* matrix-free, FP64 */
-  SFEM_OP_MF32 = 2    /* matrix-free, FP32 (FP64 geometry rounded once) */
+  SFEM_OP_CSR64 = 0,    /* assembled CSR, FP64 (needs sfem_assemble) */
+  SFEM_OP_MF64 = 1,     /* matrix-free, FP64 */
+  SFEM_OP_MF32 = 2,     /* matrix-free, FP32 (FP64 geometry rounded once) */
+  SFEM_OP_MF32_F64 = 3  /* the FP32 matrix-free arithmetic on FP64 vectors (the operator
+                           of SFEM_SOLVE_IR32_64's inner iterations) */
 };
 
 /* Solver kinds. */
@@ -178,7 +180,8 @@ int sfem_assemble(sfem_ctx *ctx, sfem_csr *out);
 
 /* sfem_apply — y = A u with A = P K P + (I - P) (STEP 5 by elimination;
  * P masks the free DOFs).  u and y are device pointers of nrhs * ndof
- * entries: double for SFEM_OP_CSR64 / SFEM_OP_MF64, float for SFEM_OP_MF32.
+ * entries: double for SFEM_OP_CSR64 / SFEM_OP_MF64 / SFEM_OP_MF32_F64, float for
+ * SFEM_OP_MF32.
  * The matrix-free operators evaluate Eq. 9 as: per tet strain
  * eps_e = B_e u_e, per face eps_k = (V_i eps_i + V_j eps_j) / (V_i + V_j)
  * (Eq. 2-3 with V_k = (V_i+V_j)/4), stress c eps_k, scattered back through

@@ -335,6 +335,17 @@ extern "C" int sfem_apply(sfem_ctx *h, const void *u, void *y, int op, int nrhs)
       k_fix_rows<float><<<grid, 256, 0, c.stream>>>((float *)y, (const float *)u, c.dmask, c.ndof, n);
       SFEM_CHECK_LAUNCH();
       c.mem.drop(tmp);
+    } else if (op == SFEM_OP_MF32_F64) {
+      // FP32 arithmetic on FP64 vectors (the operator of the mixed-precision solve)
+      double *tmp = c.mem.get<double>(n);
+      k_mask_copy<double><<<grid, 256, 0, c.stream>>>((const double *)u, tmp, c.dmask, c.ndof, n);
+      SFEM_CHECK_LAUNCH();
+      SFEM_CUDA(cudaMemsetAsync(y, 0, n * sizeof(double), c.stream));
+      for (int k = 0; k < nrhs; ++k)
+        launch_mf32_tiled<double, double>(c, c.stream, tmp + k * c.ndof, (double *)y + k * c.ndof, nullptr, nullptr);
+      k_fix_rows<double><<<grid, 256, 0, c.stream>>>((double *)y, (const double *)u, c.dmask, c.ndof, n);
+      SFEM_CHECK_LAUNCH();
+      c.mem.drop(tmp);
     } else if (op == SFEM_OP_MF64 || op == SFEM_OP_CSR64) {
       double *tmp = c.mem.get<double>(n);
       k_mask_copy<double><<<grid, 256, 0, c.stream>>>((const double *)u, tmp, c.dmask, c.ndof, n);
@@ -372,6 +383,8 @@ extern "C" int sfem_time_operator(sfem_ctx *h, int op, int reps, double *ms_per_
     auto once = [&]() {
       if (op == SFEM_OP_MF32) {
         launch_mf32_tiled<float, float>(c, c.stream, (const float *)u, (float *)y, nullptr, nullptr);
+      } else if (op == SFEM_OP_MF32_F64) {
+        launch_mf32_tiled<double, double>(c, c.stream, (const double *)u, (double *)y, nullptr, nullptr);
       } else if (op == SFEM_OP_MF64) {
         launch_mf_strain<double, double>(c, c.stream, c.Gs64, (const double *)u, 1, (double *)c.w_scratch,
                                          nullptr);

@@ -1,24 +1,41 @@
-"""Operator micro-benchmark: repeated raw operator applications on a Kuhn
-cantilever, through the C ABI (sfem_time_operator).
+"""Operator and solver micro-benchmarks through the C ABI, for timing and
+for profiling single kernels in isolation (e.g. under ncu).
 
-  python -m paper_2001_08849_gb300.opbench --cells 200 40 42 --op mf32 --reps 20
+  python -m paper_2001_08849_gb300.opbench --cells 200 40 42 --op mf32f64 --reps 20
+  python -m paper_2001_08849_gb300.opbench --cells 200 40 42 --solve fpcg_learned --tol 1e-8
 
-Prints one JSON line: mean device ms per application, DOF/s and the
-algorithmic bytes of the FP32 matrix-free operator.  Used to time and
-profile the operator kernels in isolation (e.g. under ncu).
+--op: repeated raw operator applications (sfem_time_operator); prints the
+mean device ms per application, DOF/s and the algorithmic bytes of the FP32
+matrix-free operator.
+--solve: one solve of the cantilever (pcg64 on CSR, the mixed-precision
+ir32_64, flexible PCG without (fpcg) or with an untrained learned correction
+(fpcg_learned, patches of 8 x 8 x 8 nodes)); prints iterations and time.
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import sys
+import time
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-OPS = {"csr64": 0, "mf64": 1, "mf32": 2}
+OPS = {"csr64": 0, "mf64": 1, "mf32": 2, "mf32f64": 3}
+SOLVES = ("pcg64", "ir32_64", "fpcg", "fpcg_learned")
+
+
+def tiled_source_sha() -> str:
+    """SHA-256 of the sources of the tiled FP32 operator kernel (a stored
+    DRAM-traffic figure is valid only for the kernel it was measured on)."""
+    h = hashlib.sha256()
+    for f in ("tiles.cu", "tile_apply.cuh"):
+        with open(os.path.join(ROOT, "paper_2001_08849_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
 
 
 def main(argv=None):
@@ -27,6 +44,10 @@ def main(argv=None):
     ap.add_argument("--seed", type=int, default=2)
     ap.add_argument("--op", choices=sorted(OPS), default="mf32")
     ap.add_argument("--reps", type=int, default=20)
+    ap.add_argument("--solve", choices=SOLVES, default=None)
+    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--max-iter", type=int, default=0)
+    ap.add_argument("--window", type=int, default=0, help="learned_window of the fpcg_learned solve")
     a = ap.parse_args(argv)
     import torch
     import __graft_entry__
@@ -35,17 +56,43 @@ def main(argv=None):
     from inputs.kuhn_beam import cantilever
     p = cantilever(*a.cells, seed=a.seed)
     with S.FsFem(p, on_device=True) as ctx:
-        if a.op == "csr64":
-            S.sfem_assemble(ctx.h)
-        ms = S.sfem_time_operator(ctx.h, OPS[a.op], a.reps)
-        torch.cuda.synchronize()
         n_tets = p.mesh.n_tets
-        out = {"op": a.op, "cells": a.cells, "n_tets": n_tets, "ndof": ctx.ndof, "ms_per_apply": ms,
-               "gdof_per_s": ctx.ndof / ms / 1e6,
-               "alg_bytes_mf32": 72 * n_tets + 8 * ctx.ndof,
-               "tiles": None}
+        if a.solve is None:
+            if a.op == "csr64":
+                S.sfem_assemble(ctx.h)
+            ms = S.sfem_time_operator(ctx.h, OPS[a.op], a.reps)
+            torch.cuda.synchronize()
+            out = {"op": a.op, "cells": a.cells, "n_tets": n_tets, "ndof": ctx.ndof, "ms_per_apply": ms,
+                   "gdof_per_s": ctx.ndof / ms / 1e6,
+                   "alg_bytes_mf32": 72 * n_tets + (16 if a.op == "mf32f64" else 8) * ctx.ndof,
+                   "tiled_source_sha256": tiled_source_sha()}
+        else:
+            model = None
+            if a.solve == "pcg64":
+                S.sfem_assemble(ctx.h)
+                o = S.solve_opts(kind=S.SFEM_SOLVE_PCG64, op64=S.SFEM_OP_CSR64, tol=a.tol, u_on_device=True,
+                                 max_iter=a.max_iter)
+            elif a.solve == "ir32_64":
+                o = S.solve_opts(kind=S.SFEM_SOLVE_IR32_64, tol=a.tol, u_on_device=True, max_iter=a.max_iter)
+            else:
+                S.sfem_assemble(ctx.h)
+                if a.solve == "fpcg_learned":
+                    dims = tuple(-(-(c + 1) // 8) for c in a.cells)
+                    model = S.Learned(ctx.h, patch_dims=dims, seed=1, keepalive=ctx._keep)
+                o = S.solve_opts(kind=S.SFEM_SOLVE_FPCG_LEARNED, op64=S.SFEM_OP_CSR64, tol=a.tol,
+                                 u_on_device=True, learned=model, max_iter=a.max_iter, learned_window=a.window)
+            u = torch.zeros(ctx.ndof, dtype=torch.float64, device="cuda")
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            info = S.sfem_solve(ctx.h, u, o, check=False)
+            torch.cuda.synchronize()
+            out = {"solve": a.solve, "cells": a.cells, "n_tets": n_tets, "ndof": ctx.ndof,
+                   "time_s": time.perf_counter() - t0, **info}
+            if model is not None:
+                model.close()
     print(json.dumps(out), flush=True)
+    return 0
 
 
 if __name__ == "__main__":
-    main()
+    sys.exit(main())

@@ -26,7 +26,7 @@ lib = ctypes.CDLL(LIB_PATH)
 # ---- status codes and enums (include/sfem.h) --------------------------------
 SFEM_OK, SFEM_EINVAL, SFEM_EMESH, SFEM_ENOMEM = 0, -1, -2, -3
 SFEM_ENOCONV, SFEM_EBREAKDOWN, SFEM_ECUDA, SFEM_ETIMEOUT = -4, -5, -6, -7
-SFEM_OP_CSR64, SFEM_OP_MF64, SFEM_OP_MF32 = 0, 1, 2
+SFEM_OP_CSR64, SFEM_OP_MF64, SFEM_OP_MF32, SFEM_OP_MF32_F64 = 0, 1, 2, 3
 SFEM_SOLVE_PCG64, SFEM_SOLVE_IR32_64, SFEM_SOLVE_FPCG_LEARNED = 0, 1, 2
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -237,7 +237,7 @@ def sfem_mesh_setup(xyz, tets, E, nu, dir_dofs=None, dir_vals=None, trac_tris=No
 def sfem_get_info(h) -> dict:
     info = sfem_mesh_info()
     _check(lib.sfem_get_info(h, ctypes.byref(info)), "sfem_get_info")
-    return {k: getattr(info, k) for k, _ in info._fields_}
+    return {k: getattr(info, k) for k, _ in info._fields_ if k != "reserved"}
 
 
 def sfem_assemble(h):
@@ -253,7 +253,7 @@ def sfem_assemble(h):
 
 
 def sfem_apply(h, u, y, op=SFEM_OP_MF64, nrhs=1):
-    """y = A u on device tensors (float64 for CSR64/MF64, float32 for MF32)."""
+    """y = A u on device tensors (float64 for CSR64/MF64/MF32_F64, float32 for MF32)."""
     _check(lib.sfem_apply(h, _ptr(u), _ptr(y), int(op), int(nrhs)), "sfem_apply")
 
 
@@ -282,7 +282,7 @@ def sfem_solve(h, u, opts: sfem_solve_opts, f_extra=None, check=True) -> dict:
     opts.u_on_device).  Returns the solve info as a dict."""
     info = sfem_solve_info()
     st = lib.sfem_solve(h, _ptr(f_extra), _ptr(u), ctypes.byref(opts), ctypes.byref(info))
-    out = {k: getattr(info, k) for k, _ in info._fields_}
+    out = {k: getattr(info, k) for k, _ in info._fields_ if k != "reserved"}
     if check and st not in (SFEM_OK,):
         raise SfemError(st, "sfem_solve")
     return out
@@ -308,8 +308,8 @@ def sfem_batch_solve(handles, us, opts: sfem_batch_opts, n_systems: int, check=T
     infos = (sfem_solve_info * n_systems)()
     stats = sfem_batch_stats()
     st = lib.sfem_batch_solve(harr, n, uarr, ctypes.byref(opts), infos, ctypes.byref(stats))
-    out = [{k: getattr(i, k) for k, _ in i._fields_} for i in infos]
-    sd = {k: getattr(stats, k) for k, _ in stats._fields_}
+    out = [{k: getattr(i, k) for k, _ in i._fields_ if k != "reserved"} for i in infos]
+    sd = {k: getattr(stats, k) for k, _ in stats._fields_ if k != "reserved"}
     if check and st != SFEM_OK:
         raise SfemError(st, "sfem_batch_solve")
     return out, sd
@@ -433,7 +433,7 @@ class Learned:
         Tp = _ptr(T) + 3 * 4 * int(row0)
         _check(lib.sfem_learned_collect(self.h, ctx_h, ctypes.byref(opts), _ptr(u_star), Xp, Tp, cap,
                                         ctypes.byref(rows), ctypes.byref(info)), "sfem_learned_collect")
-        return rows.value, {k: getattr(info, k) for k, _ in info._fields_}
+        return rows.value, {k: getattr(info, k) for k, _ in info._fields_ if k != "reserved"}
 
     def loss_grad(self, X, T, grad=None) -> float:
         loss = ctypes.c_double()

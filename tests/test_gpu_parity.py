@@ -133,6 +133,12 @@ def test_rhs_and_operators(S, cfg1):
             d = y32.double().cpu().numpy() - y_ref32
             assert np.abs(d).max() <= 2e-5 * maj.max()
             assert np.linalg.norm(d) <= 1e-5 * np.linalg.norm(y_ref32)
+            # FP32 arithmetic on FP64 vectors (inner operator of the mixed solve)
+            y64 = torch.empty_like(ud)
+            S.sfem_apply(ctx.h, ud, y64, S.SFEM_OP_MF32_F64, nrhs)
+            d = y64.cpu().numpy() - y_ref
+            assert np.abs(d).max() <= 2e-5 * maj.max()
+            assert np.linalg.norm(d) <= 1e-5 * np.linalg.norm(y_ref)
 
 
 def test_pcg64_matches_oracle(S, cfg1):

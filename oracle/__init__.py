@@ -16,6 +16,8 @@ Modules
   solve  Jacobi-preconditioned CG in FP64 and a dense Cholesky solve.
   mlp    the learned coarse correction: residual pooling, 3-layer GELU MLP
          forward and backward in FP64, prolongation, Adam.
+  coarse the two-level preconditioner: trilinear patch-centre coarse space,
+         Galerkin coarse matrix, D^-1 + Pi A_c^-1 Pi^T, two-level PCG.
 
 Every function is plain and slow on purpose; it cites the passage it follows.
 """

@@ -127,7 +127,9 @@ typedef struct sfem_solve_opts {
                           is switched off when ||r|| lies more than 30x above the
                           log-linear line from ||r_0|| to the tolerance over this many
                           iterations (0: no pace guard) */
-  int reserved[3];
+  int precond;         /* PCG64 and IR32_64 (FP64 vectors): 0 Jacobi; 1 Jacobi plus the
+                          Galerkin coarse correction of sfem_coarse_setup */
+  int reserved[2];
 } sfem_solve_opts;
 
 typedef struct sfem_solve_info {
@@ -241,6 +243,29 @@ typedef struct sfem_batch_stats {
 
 int sfem_batch_solve(sfem_ctx *const *ctxs, int n, double *const *u, const sfem_batch_opts *opts,
                      sfem_solve_info *infos, sfem_batch_stats *stats);
+
+/* ---- two-level preconditioner (no counterpart in the paper) --------------
+ *
+ * M^-1 = D^-1 + Pi A_c^-1 Pi^T with A_c = Pi^T A Pi (Galerkin).  Pi holds one
+ * trilinear function per patch centre and displacement component on a
+ * d0 x d1 x d2 grid of centres over the mesh's bounding box (centre i at
+ * lo + (i + 1/2) ext / d), masked by P.  sfem_coarse_setup builds Pi, probes
+ * A_c with the FP32 matrix-free operator (3 x prod(min(5, d_a)) applies),
+ * factors it by a blocked FP64 Cholesky and keeps C = A_c^-1 in FP32 on the
+ * device (3P <= 8192; patches at least 2.5 node spacings wide where
+ * d_a >= 5).  Solves use it with sfem_solve_opts.precond = 1.  Returns
+ * SFEM_EBREAKDOWN if A_c is not positive definite. */
+typedef struct sfem_coarse_opts {
+  int patch_dims[3];   /* centres per axis (0: about patch_nodes nodes per patch axis) */
+  int patch_nodes;     /* 0: 8 */
+  int reserved[8];
+} sfem_coarse_opts;
+
+int sfem_coarse_setup(sfem_ctx *ctx, const sfem_coarse_opts *opts);
+int sfem_coarse_info(const sfem_ctx *ctx, int *patch_dims /* 3 */, int *n_coarse, int *probes,
+                     double *setup_ms);
+/* z = D^-1 r + P Pi C Pi^T r for one masked residual r (device, ndof FP64). */
+int sfem_coarse_apply(sfem_ctx *ctx, const double *r, double *z);
 
 /* ---- learned coarse correction (no counterpart in the paper) -------------
  *

@@ -1,0 +1,602 @@
+// Two-level preconditioner for the PCG solves: Jacobi plus a Galerkin coarse
+// correction (the paper has no counterpart: it calls a direct solver).
+//
+//   M^-1 = D^-1 + Pi A_c^-1 Pi^T,   A_c = Pi^T A Pi,
+//
+// Pi: one trilinear function per patch centre and component on a regular
+// grid of centres over the bounding box, masked by P (see coarse.cuh).
+//
+// Setup (sfem_coarse_setup):
+//   * nodes grouped by interpolation cell with their fractions (host, once);
+//   * A_c by probing: the centres are split into colour classes with stride
+//     s_a = min(5, d_a) per axis.  For every class and component the FP32
+//     tiled operator is applied to the sum of the class's functions, and the
+//     restricted response at centre i is attributed to the unique class
+//     member j with |i_a - j_a| <= 2 on every axis.  The operator couples
+//     nodes two element layers apart, so centres farther apart than two
+//     cells are not coupled when patches span at least three elements, and
+//     within a stride-5 class the members are 5 apart;
+//   * A_c is symmetrised, factored by a blocked FP64 Cholesky (L), inverted
+//     to W = L^-1 and C = W^T W = A_c^-1 in FP32 (blocked, 64 x 64 tiles).
+// Per PCG iteration (coarse_correction): rc = Pi^T r (one block per cell,
+// fixed-order sums, then a fixed-order gather per centre), yc = C rc (FP32
+// GEMV over the L2-resident C), and the CG kernels add P Pi yc to D^-1 r.
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "reduce.cuh"
+#include "sfem_internal.cuh"
+
+namespace sfem {
+
+constexpr int kCB = 64;           // dense block order
+constexpr int kRestrictThreads = 128;
+
+// ---- restriction -----------------------------------------------------------
+
+// cellsum[cell][3k + c] = sum over the cell's nodes of w_k(x) v_c(x)
+// (v masked by dmask when dmask is given)
+template <class TV>
+__global__ void __launch_bounds__(kRestrictThreads) k_cs_restrict(const TV *__restrict__ v,
+                                                                 const uint8_t *__restrict__ dmask, CoarseDev cs,
+                                                                 const int *done) {
+  if (done && *done) return;
+  const int cell = blockIdx.x;
+  const int b = cs.coff[cell], e = cs.coff[cell + 1];
+  float acc[24];
+#pragma unroll
+  for (int j = 0; j < 24; ++j) acc[j] = 0.f;
+  for (int i = b + threadIdx.x; i < e; i += kRestrictThreads) {
+    const int64_t n = cs.cnodes[i];
+    const float f[3] = {cs.frac[3 * n], cs.frac[3 * n + 1], cs.frac[3 * n + 2]};
+    float x[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) x[c] = (dmask && !dmask[3 * n + c]) ? 0.f : (float)v[3 * n + c];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const float w = cs_weight(f, k);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) acc[3 * k + c] = fmaf(w, x[c], acc[3 * k + c]);
+    }
+  }
+  __shared__ float sm[kRestrictThreads / 32][24];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < 24; ++j) {
+    float s = acc[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) sm[wid][j] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x < 24) {
+    float s = 0.f;
+#pragma unroll
+    for (int w = 0; w < kRestrictThreads / 32; ++w) s += sm[w][threadIdx.x];
+    cs.cellsum[24 * (int64_t)cell + threadIdx.x] = s;
+  }
+}
+
+// rc[3j + c] = sum over the cells having centre j as a corner (fixed order)
+__global__ void k_cs_gather(CoarseDev cs, const int *done) {
+  if (done && *done) return;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= cs.npad) return;
+  if (t >= cs.nc) {
+    cs.rc[t] = 0.f;
+    return;
+  }
+  const int j = t / 3, c = t % 3;
+  const int jz = j % cs.d[2], jy = (j / cs.d[2]) % cs.d[1], jx = j / (cs.d[1] * cs.d[2]);
+  double s = 0.0;
+  for (int ix = max(0, jx - 1); ix <= min(cs.cd[0] - 1, jx); ++ix)
+    for (int bx = 0; bx < 2; ++bx) {
+      if (min(ix + bx, cs.d[0] - 1) != jx) continue;
+      for (int iy = max(0, jy - 1); iy <= min(cs.cd[1] - 1, jy); ++iy)
+        for (int by = 0; by < 2; ++by) {
+          if (min(iy + by, cs.d[1] - 1) != jy) continue;
+          for (int iz = max(0, jz - 1); iz <= min(cs.cd[2] - 1, jz); ++iz)
+            for (int bz = 0; bz < 2; ++bz) {
+              if (min(iz + bz, cs.d[2] - 1) != jz) continue;
+              const int cell = (ix * cs.cd[1] + iy) * cs.cd[2] + iz;
+              const int k = (bx << 2) | (by << 1) | bz;
+              s += (double)cs.cellsum[24 * (int64_t)cell + 3 * k + c];
+            }
+        }
+    }
+  cs.rc[t] = (float)s;
+}
+
+// yc = C rc (one warp per row; C symmetric, rows of npad floats)
+__global__ void __launch_bounds__(256) k_cs_gemv(CoarseDev cs, const int *done) {
+  if (done && *done) return;
+  const int row = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (row >= cs.npad) return;
+  const float4 *Cr = reinterpret_cast<const float4 *>(cs.C + (int64_t)row * cs.npad);
+  const float4 *r4 = reinterpret_cast<const float4 *>(cs.rc);
+  float s = 0.f;
+  for (int q = lane; q < cs.npad / 4; q += 32) {
+    const float4 a = Cr[q], b = r4[q];
+    s = fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, fmaf(a.w, b.w, s))));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (lane == 0) cs.yc[row] = s;
+}
+
+// ---- probing -----------------------------------------------------------------
+
+// v = P Pi (sum of the class's functions in component comp), FP32
+__global__ void k_cs_probe(CoarseDev cs, int64_t n_nodes, const uint8_t *__restrict__ dmask, int comp, int3 res,
+                           int3 str, float *__restrict__ v) {
+  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= n_nodes) return;
+  const int cell = cs.cell[n];
+  const float f[3] = {cs.frac[3 * n], cs.frac[3 * n + 1], cs.frac[3 * n + 2]};
+  float s = 0.f;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int j = cs_corner(cs, cell, k);
+    const int jz = j % cs.d[2], jy = (j / cs.d[2]) % cs.d[1], jx = j / (cs.d[1] * cs.d[2]);
+    if (jx % str.x == res.x && jy % str.y == res.y && jz % str.z == res.z) s += cs_weight(f, k);
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) v[3 * n + c] = (c == comp && dmask[3 * n + c]) ? s : 0.f;
+}
+
+// Ac[(3i + c'), (3j + comp)] = rc[3i + c'] for the class member j near i
+__global__ void k_cs_attrib(CoarseDev cs, int comp, int3 res, int3 str, double *__restrict__ Ac) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= cs.nc) return;
+  const int i = t / 3;
+  const int iz = i % cs.d[2], iy = (i / cs.d[2]) % cs.d[1], ix = i / (cs.d[1] * cs.d[2]);
+  const int ia[3] = {ix, iy, iz}, ra[3] = {res.x, res.y, res.z}, sa[3] = {str.x, str.y, str.z};
+  int ja[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (sa[a] < 5) {
+      ja[a] = ra[a];  // stride = d: the class has one member on this axis
+    } else {
+      // the member of residue class ra (mod 5) within distance 2 of ia
+      int off = ((ra[a] - ia[a]) % 5 + 5) % 5;  // 0 .. 4
+      if (off > 2) off -= 5;                    // -2 .. 2
+      ja[a] = ia[a] + off;
+      if (ja[a] < 0 || ja[a] >= cs.d[a]) return;
+    }
+  }
+  const int j = (ja[0] * cs.d[1] + ja[1]) * cs.d[2] + ja[2];
+  Ac[(int64_t)t * cs.npad + 3 * j + comp] = (double)cs.rc[t];
+}
+
+// A <- (A + A^T) / 2 on the nc x nc block; padding: identity; a zero
+// diagonal (a function on prescribed DOFs only) becomes 1
+__global__ void k_cs_symmetrize(double *A, int nc, int npad) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)npad * npad) return;
+  const int i = (int)(e / npad), j = (int)(e % npad);
+  if (i >= nc || j >= nc) {
+    A[e] = (i == j) ? 1.0 : 0.0;
+    return;
+  }
+  if (i == j) {
+    if (!(A[e] > 0.0)) A[e] = 1.0;
+    return;
+  }
+  if (j < i) {
+    const double s = 0.5 * (A[e] + A[(int64_t)j * npad + i]);
+    A[e] = s;
+    A[(int64_t)j * npad + i] = s;
+  }
+}
+
+// ---- dense blocked Cholesky (FP64), triangular inverse and W^T W (FP32) --------
+
+template <class T>
+struct Tile64 {
+  T v[kCB][kCB + 1];
+};
+
+// acc += op(A) op(B) over one 64-deep slice; A, B 64 x 64 tiles in smem;
+// thread owns rows tm..tm+3 and columns tn..tn+3 of the output
+template <class T, bool TA, bool TB>
+__device__ __forceinline__ void mm64(T (&acc)[4][4], const Tile64<T> &As, const Tile64<T> &Bs, int tm, int tn) {
+#pragma unroll 8
+  for (int k = 0; k < kCB; ++k) {
+    T a[4], b[4];
+#pragma unroll
+    for (int x = 0; x < 4; ++x) {
+      a[x] = TA ? As.v[k][tm + x] : As.v[tm + x][k];
+      b[x] = TB ? Bs.v[tn + x][k] : Bs.v[k][tn + x];
+    }
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) acc[x][y] = fma(a[x], b[y], acc[x][y]);
+  }
+}
+
+template <class T>
+__device__ __forceinline__ void load64(Tile64<T> &S, const T *A, int64_t ld, int bi, int bj) {
+  for (int e = threadIdx.x; e < kCB * kCB; e += blockDim.x)
+    S.v[e / kCB][e % kCB] = A[(int64_t)(bi * kCB + e / kCB) * ld + bj * kCB + e % kCB];
+}
+
+// factor the diagonal block k (unblocked, in shared memory)
+__global__ void __launch_bounds__(256) k_potrf_diag(double *A, int npad, int k, int *info) {
+  extern __shared__ double dyn_d[];
+  Tile64<double> &L = *reinterpret_cast<Tile64<double> *>(dyn_d);
+  load64(L, A, npad, k, k);
+  __syncthreads();
+  for (int j = 0; j < kCB; ++j) {
+    if (threadIdx.x == 0) {
+      double d = L.v[j][j];
+      if (!(d > 0.0) || !isfinite(d)) {
+        atomicExch(info, 1);
+        d = 1.0;
+      }
+      L.v[j][j] = sqrt(d);
+    }
+    __syncthreads();
+    for (int i = j + 1 + threadIdx.x; i < kCB; i += blockDim.x) L.v[i][j] /= L.v[j][j];
+    __syncthreads();
+    for (int e = threadIdx.x; e < kCB * kCB; e += blockDim.x) {
+      const int i = e / kCB, l = e % kCB;
+      if (l > j && i >= l) L.v[i][l] -= L.v[i][j] * L.v[l][j];
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < kCB * kCB; e += blockDim.x) {
+    const int i = e / kCB, l = e % kCB;
+    A[(int64_t)(k * kCB + i) * npad + k * kCB + l] = (l <= i) ? L.v[i][l] : 0.0;
+  }
+}
+
+// L[i][k] = A[i][k] L[k][k]^-T for the row blocks i > k (one thread per row)
+__global__ void __launch_bounds__(kCB) k_trsm_panel(double *A, int npad, int k) {
+  extern __shared__ double dyn_d[];
+  Tile64<double> &L = *reinterpret_cast<Tile64<double> *>(dyn_d);
+  Tile64<double> &X = *reinterpret_cast<Tile64<double> *>(dyn_d + kCB * (kCB + 1));
+  const int bi = k + 1 + blockIdx.x;
+  load64(L, A, npad, k, k);
+  load64(X, A, npad, bi, k);
+  __syncthreads();
+  const int r = threadIdx.x;
+  for (int c = 0; c < kCB; ++c) {
+    double s = X.v[r][c];
+    for (int l = 0; l < c; ++l) s -= X.v[r][l] * L.v[c][l];
+    X.v[r][c] = s / L.v[c][c];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < kCB * kCB; e += blockDim.x)
+    A[(int64_t)(bi * kCB + e / kCB) * npad + k * kCB + e % kCB] = X.v[e / kCB][e % kCB];
+}
+
+// A[i][j] -= L[i][k] L[j][k]^T for k < j <= i (block pairs enumerated)
+__global__ void __launch_bounds__(256) k_syrk_update(double *A, int npad, int k, int nb) {
+  extern __shared__ double dyn_d[];
+  Tile64<double> &Li = *reinterpret_cast<Tile64<double> *>(dyn_d);
+  Tile64<double> &Lj = *reinterpret_cast<Tile64<double> *>(dyn_d + kCB * (kCB + 1));
+  const int t = blockIdx.x;
+  int ii = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+  while ((ii + 1) * (ii + 2) / 2 <= t) ++ii;
+  while (ii * (ii + 1) / 2 > t) --ii;
+  const int jj = t - ii * (ii + 1) / 2;
+  const int bi = k + 1 + ii, bj = k + 1 + jj;
+  if (bi >= nb || bj > bi) return;
+  load64(Li, A, npad, bi, k);
+  load64(Lj, A, npad, bj, k);
+  __syncthreads();
+  const int tm = (threadIdx.x >> 4) * 4, tn = (threadIdx.x & 15) * 4;
+  double acc[4][4] = {};
+  mm64<double, false, true>(acc, Li, Lj, tm, tn);
+#pragma unroll
+  for (int x = 0; x < 4; ++x)
+#pragma unroll
+    for (int y = 0; y < 4; ++y) A[(int64_t)(bi * kCB + tm + x) * npad + bj * kCB + tn + y] -= acc[x][y];
+}
+
+__global__ void k_lower_to_f32(const double *A, float *L, int npad) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)npad * npad) return;
+  const int i = (int)(e / npad), j = (int)(e % npad);
+  L[e] = (j <= i) ? (float)A[e] : 0.f;
+}
+
+// W[k][k] = L[k][k]^-1 (one thread per column, forward substitution)
+__global__ void __launch_bounds__(kCB) k_trtri_diag(const float *L, float *W, int npad) {
+  __shared__ Tile64<float> Ls, Ws;
+  const int k = blockIdx.x;
+  load64(Ls, L, npad, k, k);
+  __syncthreads();
+  const int c = threadIdx.x;
+  for (int i = 0; i < kCB; ++i) {
+    float s = (i == c) ? 1.f : 0.f;
+    if (i >= c) {
+      for (int l = c; l < i; ++l) s -= Ls.v[i][l] * Ws.v[l][c];
+      s /= Ls.v[i][i];
+    } else {
+      s = 0.f;
+    }
+    Ws.v[i][c] = s;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < kCB * kCB; e += blockDim.x)
+    W[(int64_t)(k * kCB + e / kCB) * npad + k * kCB + e % kCB] = Ws.v[e / kCB][e % kCB];
+}
+
+// W[i][j] = -W[i][i] sum_{l=j}^{i-1} L[i][l] W[l][j] for i = j + s
+__global__ void __launch_bounds__(256) k_trtri_off(const float *L, float *W, int npad, int s) {
+  __shared__ Tile64<float> As, Bs;
+  const int bj = blockIdx.x, bi = bj + s;
+  const int tm = (threadIdx.x >> 4) * 4, tn = (threadIdx.x & 15) * 4;
+  float acc[4][4] = {};
+  for (int l = bj; l < bi; ++l) {
+    __syncthreads();
+    load64(As, L, npad, bi, l);
+    load64(Bs, W, npad, l, bj);
+    __syncthreads();
+    mm64<float, false, false>(acc, As, Bs, tm, tn);
+  }
+  __syncthreads();
+  load64(As, W, npad, bi, bi);
+#pragma unroll
+  for (int x = 0; x < 4; ++x)
+#pragma unroll
+    for (int y = 0; y < 4; ++y) Bs.v[tm + x][tn + y] = acc[x][y];
+  __syncthreads();
+  float out[4][4] = {};
+  mm64<float, false, false>(out, As, Bs, tm, tn);
+#pragma unroll
+  for (int x = 0; x < 4; ++x)
+#pragma unroll
+    for (int y = 0; y < 4; ++y) W[(int64_t)(bi * kCB + tm + x) * npad + bj * kCB + tn + y] = -out[x][y];
+}
+
+// C[a][b] = sum_{l >= a} W[l][a]^T W[l][b] for a >= b, mirrored to C[b][a]
+__global__ void __launch_bounds__(256) k_lauum(const float *W, float *C, int npad, int nb) {
+  __shared__ Tile64<float> As, Bs;
+  const int t = blockIdx.x;
+  int a = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+  while ((a + 1) * (a + 2) / 2 <= t) ++a;
+  while (a * (a + 1) / 2 > t) --a;
+  const int b = t - a * (a + 1) / 2;
+  const int tm = (threadIdx.x >> 4) * 4, tn = (threadIdx.x & 15) * 4;
+  float acc[4][4] = {};
+  for (int l = a; l < nb; ++l) {
+    __syncthreads();
+    load64(As, W, npad, l, a);
+    load64(Bs, W, npad, l, b);
+    __syncthreads();
+    mm64<float, true, false>(acc, As, Bs, tm, tn);
+  }
+#pragma unroll
+  for (int x = 0; x < 4; ++x)
+#pragma unroll
+    for (int y = 0; y < 4; ++y) {
+      C[(int64_t)(a * kCB + tm + x) * npad + b * kCB + tn + y] = acc[x][y];
+      if (a != b) C[(int64_t)(b * kCB + tn + y) * npad + a * kCB + tm + x] = acc[x][y];
+    }
+}
+
+// z = D^-1 r + P Pi yc
+__global__ void k_cs_apply_z(CoarseDev cs, const double *__restrict__ r, const double *__restrict__ dinv,
+                             const uint8_t *__restrict__ dmask, int64_t n, double *__restrict__ z) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) z[i] = dinv[i] * r[i] + (dmask[i] ? (double)cs_prolong(cs, i) : 0.0);
+}
+
+void coarse_correction(Ctx &c, cudaStream_t st, const double *r, const int *done) {
+  const CoarseDev &cs = c.coarse->dev;
+  k_cs_restrict<double><<<cs.ncell, kRestrictThreads, 0, st>>>(r, nullptr, cs, done);
+  SFEM_CHECK_LAUNCH();
+  k_cs_gather<<<grid_for(cs.npad, 256), 256, 0, st>>>(cs, done);
+  SFEM_CHECK_LAUNCH();
+  k_cs_gemv<<<(cs.npad + 7) / 8, 256, 0, st>>>(cs, done);
+  SFEM_CHECK_LAUNCH();
+}
+
+static void setup_coarse(Ctx &c, const sfem_coarse_opts *opts) {
+  cudaEvent_t e0, e1;
+  SFEM_CUDA(cudaEventCreate(&e0));
+  SFEM_CUDA(cudaEventCreate(&e1));
+  SFEM_CUDA(cudaEventRecord(e0, c.stream));
+  auto co = std::make_shared<Coarse>();
+  // grid of centres over the bounding box (host, once)
+  std::vector<double> xyz(3 * c.n_nodes);
+  SFEM_CUDA(cudaMemcpyAsync(xyz.data(), c.xyz, xyz.size() * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  SFEM_CUDA(cudaStreamSynchronize(c.stream));
+  double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (int64_t i = 0; i < c.n_nodes; ++i)
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = std::min(lo[a], xyz[3 * i + a]);
+      hi[a] = std::max(hi[a], xyz[3 * i + a]);
+    }
+  const int pn = (opts && opts->patch_nodes > 0) ? opts->patch_nodes : 8;
+  const double box = std::max((hi[0] - lo[0]) * (hi[1] - lo[1]) * (hi[2] - lo[2]), 1e-300);
+  const double h_mean = std::cbrt(box / (double)c.n_nodes);
+  CoarseDev &cs = co->dev;
+  int64_t P = 1;
+  for (int a = 0; a < 3; ++a) {
+    co->g.lo[a] = lo[a];
+    co->g.ext[a] = std::max(hi[a] - lo[a], 1e-300);
+    const int req = opts ? opts->patch_dims[a] : 0;
+    SFEM_REQUIRE(req >= 0 && req <= 4096, SFEM_EINVAL, "patch_dims out of range");
+    co->g.d[a] = req > 0 ? req : std::max(1, (int)std::ceil((hi[a] - lo[a]) / (pn * h_mean) - 1e-9));
+    cs.d[a] = co->g.d[a];
+    cs.cd[a] = std::max(cs.d[a] - 1, 1);
+    P *= cs.d[a];
+  }
+  SFEM_REQUIRE(3 * P <= 8192, SFEM_EINVAL, "coarse space larger than 8192 DOFs");
+  // probing assumes centres three or more cells apart are uncoupled: patches
+  // must span a few elements (checked against the mean node spacing)
+  for (int a = 0; a < 3; ++a)
+    SFEM_REQUIRE(cs.d[a] < 5 || co->g.ext[a] / cs.d[a] >= 2.5 * h_mean, SFEM_EINVAL,
+                 "patches narrower than 2.5 node spacings");
+  cs.nc = (int)(3 * P);
+  cs.npad = (cs.nc + kCB - 1) / kCB * kCB;
+  cs.ncell = cs.cd[0] * cs.cd[1] * cs.cd[2];
+  // interpolation cell and fractions of every node; nodes grouped by cell
+  std::vector<int32_t> cell(c.n_nodes), off(cs.ncell + 1, 0), nodes(c.n_nodes);
+  std::vector<float> frac(3 * c.n_nodes);
+  for (int64_t i = 0; i < c.n_nodes; ++i) {
+    int i0[3];
+    for (int a = 0; a < 3; ++a) {
+      double t = (xyz[3 * i + a] - co->g.lo[a]) / co->g.ext[a] * cs.d[a] - 0.5;
+      t = std::min(std::max(t, 0.0), (double)std::max(cs.d[a] - 1, 0));
+      i0[a] = std::min(std::max((int)std::floor(t), 0), std::max(cs.d[a] - 2, 0));
+      frac[3 * i + a] = (float)(cs.d[a] > 1 ? t - i0[a] : 0.0);
+    }
+    cell[i] = (i0[0] * cs.cd[1] + i0[1]) * cs.cd[2] + i0[2];
+    off[cell[i] + 1] += 1;
+  }
+  for (int q = 0; q < cs.ncell; ++q) off[q + 1] += off[q];
+  {
+    std::vector<int32_t> cur(off.begin(), off.end() - 1);
+    for (int64_t i = 0; i < c.n_nodes; ++i) nodes[cur[cell[i]]++] = (int32_t)i;
+  }
+  int32_t *d_cell = c.mem.get<int32_t>(c.n_nodes), *d_nodes = c.mem.get<int32_t>(c.n_nodes);
+  int32_t *d_off = c.mem.get<int32_t>(cs.ncell + 1);
+  float *d_frac = c.mem.get<float>(3 * c.n_nodes);
+  SFEM_CUDA(cudaMemcpyAsync(d_cell, cell.data(), cell.size() * 4, cudaMemcpyHostToDevice, c.stream));
+  SFEM_CUDA(cudaMemcpyAsync(d_nodes, nodes.data(), nodes.size() * 4, cudaMemcpyHostToDevice, c.stream));
+  SFEM_CUDA(cudaMemcpyAsync(d_off, off.data(), off.size() * 4, cudaMemcpyHostToDevice, c.stream));
+  SFEM_CUDA(cudaMemcpyAsync(d_frac, frac.data(), frac.size() * 4, cudaMemcpyHostToDevice, c.stream));
+  cs.cell = d_cell;
+  cs.cnodes = d_nodes;
+  cs.coff = d_off;
+  cs.frac = d_frac;
+  cs.cellsum = c.mem.get<float>(24 * (size_t)cs.ncell);
+  cs.rc = c.mem.get<float>(cs.npad);
+  cs.yc = c.mem.get<float>(cs.npad);
+  SFEM_CUDA(cudaMemsetAsync(cs.rc, 0, cs.npad * sizeof(float), c.stream));
+  SFEM_CUDA(cudaMemsetAsync(cs.yc, 0, cs.npad * sizeof(float), c.stream));
+  // ---- A_c by probing with the FP32 tiled operator --------------------------
+  const int64_t np2 = (int64_t)cs.npad * cs.npad;
+  double *Ac = c.mem.get<double>(np2);
+  SFEM_CUDA(cudaMemsetAsync(Ac, 0, np2 * sizeof(double), c.stream));
+  float *v = c.mem.get<float>(c.ndof), *y = c.mem.get<float>(c.ndof);
+  const int3 str = make_int3(std::min(5, cs.d[0]), std::min(5, cs.d[1]), std::min(5, cs.d[2]));
+  int probes = 0;
+  for (int comp = 0; comp < 3; ++comp)
+    for (int rx = 0; rx < str.x; ++rx)
+      for (int ry = 0; ry < str.y; ++ry)
+        for (int rz = 0; rz < str.z; ++rz) {
+          const int3 res = make_int3(rx, ry, rz);
+          k_cs_probe<<<grid_for(c.n_nodes, 256), 256, 0, c.stream>>>(cs, c.n_nodes, c.dmask, comp, res, str, v);
+          SFEM_CHECK_LAUNCH();
+          SFEM_CUDA(cudaMemsetAsync(y, 0, c.ndof * sizeof(float), c.stream));
+          launch_mf32_tiled<float, float>(c, c.stream, v, y, nullptr, nullptr);
+          k_cs_restrict<float><<<cs.ncell, kRestrictThreads, 0, c.stream>>>(y, c.dmask, cs, nullptr);
+          SFEM_CHECK_LAUNCH();
+          k_cs_gather<<<grid_for(cs.npad, 256), 256, 0, c.stream>>>(cs, nullptr);
+          SFEM_CHECK_LAUNCH();
+          k_cs_attrib<<<grid_for(cs.nc, 256), 256, 0, c.stream>>>(cs, comp, res, str, Ac);
+          SFEM_CHECK_LAUNCH();
+          ++probes;
+        }
+  c.mem.drop(v);
+  c.mem.drop(y);
+  k_cs_symmetrize<<<grid_for(np2, 256), 256, 0, c.stream>>>(Ac, cs.nc, cs.npad);
+  SFEM_CHECK_LAUNCH();
+  // ---- blocked Cholesky (FP64) ---------------------------------------------
+  const int nb = cs.npad / kCB;
+  int *info = c.mem.get<int>(1);
+  SFEM_CUDA(cudaMemsetAsync(info, 0, sizeof(int), c.stream));
+  const size_t sm1 = sizeof(Tile64<double>), sm2 = 2 * sizeof(Tile64<double>);
+  SFEM_CUDA(cudaFuncSetAttribute(k_potrf_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1));
+  SFEM_CUDA(cudaFuncSetAttribute(k_trsm_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
+  SFEM_CUDA(cudaFuncSetAttribute(k_syrk_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
+  for (int k = 0; k < nb; ++k) {
+    k_potrf_diag<<<1, 256, sm1, c.stream>>>(Ac, cs.npad, k, info);
+    SFEM_CHECK_LAUNCH();
+    const int m = nb - k - 1;
+    if (m == 0) break;
+    k_trsm_panel<<<m, kCB, sm2, c.stream>>>(Ac, cs.npad, k);
+    SFEM_CHECK_LAUNCH();
+    k_syrk_update<<<m * (m + 1) / 2, 256, sm2, c.stream>>>(Ac, cs.npad, k, nb);
+    SFEM_CHECK_LAUNCH();
+  }
+  int hinfo = 0;
+  SFEM_CUDA(cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+  SFEM_CUDA(cudaStreamSynchronize(c.stream));
+  SFEM_REQUIRE(hinfo == 0, SFEM_EBREAKDOWN, "coarse matrix is not positive definite");
+  // ---- C = A_c^-1 = L^-T L^-1 (FP32) ----------------------------------------
+  float *L32 = c.mem.get<float>(np2), *W = c.mem.get<float>(np2);
+  float *C = c.mem.get<float>(np2);
+  k_lower_to_f32<<<grid_for(np2, 256), 256, 0, c.stream>>>(Ac, L32, cs.npad);
+  SFEM_CHECK_LAUNCH();
+  c.mem.drop(Ac);
+  SFEM_CUDA(cudaMemsetAsync(W, 0, np2 * sizeof(float), c.stream));
+  k_trtri_diag<<<nb, kCB, 0, c.stream>>>(L32, W, cs.npad);
+  SFEM_CHECK_LAUNCH();
+  for (int s = 1; s < nb; ++s) {
+    k_trtri_off<<<nb - s, 256, 0, c.stream>>>(L32, W, cs.npad, s);
+    SFEM_CHECK_LAUNCH();
+  }
+  k_lauum<<<nb * (nb + 1) / 2, 256, 0, c.stream>>>(W, C, cs.npad, nb);
+  SFEM_CHECK_LAUNCH();
+  c.mem.drop(L32);
+  c.mem.drop(W);
+  c.mem.drop(info);
+  cs.C = C;
+  co->probes = probes;
+  SFEM_CUDA(cudaEventRecord(e1, c.stream));
+  SFEM_CUDA(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  SFEM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  co->setup_ms = ms;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c.coarse = co;
+}
+
+}  // namespace sfem
+
+using namespace sfem;
+
+extern "C" int sfem_coarse_setup(sfem_ctx *h, const sfem_coarse_opts *opts) {
+  try {
+    SFEM_REQUIRE(h && h->c.vol && h->c.tl.ready, SFEM_EINVAL, "context not set up");
+    if (opts)
+      for (int r : opts->reserved) SFEM_REQUIRE(r == 0, SFEM_EINVAL, "reserved options must be zero");
+    h->c.coarse.reset();
+    setup_coarse(h->c, opts);
+  } catch (const Error &err) {
+    set_last_error(err.msg);
+    return err.status;
+  }
+  return SFEM_OK;
+}
+
+extern "C" int sfem_coarse_info(const sfem_ctx *h, int *patch_dims, int *n_coarse, int *probes, double *setup_ms) {
+  if (!h || !h->c.coarse) {
+    set_last_error("no coarse space on this context");
+    return SFEM_EINVAL;
+  }
+  const Coarse &co = *h->c.coarse;
+  if (patch_dims)
+    for (int a = 0; a < 3; ++a) patch_dims[a] = co.dev.d[a];
+  if (n_coarse) *n_coarse = co.dev.nc;
+  if (probes) *probes = co.probes;
+  if (setup_ms) *setup_ms = co.setup_ms;
+  return SFEM_OK;
+}
+
+extern "C" int sfem_coarse_apply(sfem_ctx *h, const double *r, double *z) {
+  try {
+    SFEM_REQUIRE(h && h->c.coarse && r && z, SFEM_EINVAL, "context with a coarse space, r and z are required");
+    Ctx &c = h->c;
+    coarse_correction(c, c.stream, r, nullptr);
+    k_cs_apply_z<<<grid_for(c.ndof, 256), 256, 0, c.stream>>>(c.coarse->dev, r, c.dinv64, c.dmask, c.ndof, z);
+    SFEM_CHECK_LAUNCH();
+    SFEM_CUDA(cudaStreamSynchronize(c.stream));
+  } catch (const Error &err) {
+    set_last_error(err.msg);
+    return err.status;
+  }
+  return SFEM_OK;
+}

@@ -1,0 +1,55 @@
+// Device view of the two-level preconditioner's coarse space (coarse.cu),
+// shared with the CG kernels of solve.cu.
+//
+// Coarse space: one trilinear function per patch centre and displacement
+// component on a d0 x d1 x d2 grid of centres over the mesh's bounding box.
+// Each node lies in one interpolation cell (between 2 x 2 x 2 centres,
+// clamped at the outermost centres) and carries its three fractional
+// coordinates in that cell.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sfem {
+
+struct CoarseDev {
+  int d[3];                // centres per axis
+  int cd[3];               // interpolation cells per axis, max(d - 1, 1)
+  int nc, npad, ncell;     // coarse DOFs (3 P), padded order of C, cells
+  const int32_t *cell;     // n_nodes: interpolation cell of each node
+  const float *frac;       // n_nodes x 3: fractional position in the cell
+  const int32_t *cnodes;   // node ids grouped by cell (ascending within a cell)
+  const int32_t *coff;     // ncell + 1
+  float *cellsum;          // ncell x 24 partial restrictions (8 corners x 3)
+  float *rc, *yc;          // coarse residual and correction (npad)
+  const float *C;          // npad x npad: A_c^-1 (symmetric), FP32
+};
+
+// weight of corner k (bits: x = 4, y = 2, z = 1) at fractions f
+__device__ __forceinline__ float cs_weight(const float f[3], int k) {
+  return ((k & 4) ? f[0] : 1.f - f[0]) * ((k & 2) ? f[1] : 1.f - f[1]) * ((k & 1) ? f[2] : 1.f - f[2]);
+}
+
+// centre index of corner k of cell `cell`
+__device__ __forceinline__ int cs_corner(const CoarseDev &cs, int cell, int k) {
+  const int iz = cell % cs.cd[2], iy = (cell / cs.cd[2]) % cs.cd[1], ix = cell / (cs.cd[1] * cs.cd[2]);
+  const int jx = min(ix + ((k >> 2) & 1), cs.d[0] - 1);
+  const int jy = min(iy + ((k >> 1) & 1), cs.d[1] - 1);
+  const int jz = min(iz + (k & 1), cs.d[2] - 1);
+  return (jx * cs.d[1] + jy) * cs.d[2] + jz;
+}
+
+// (Pi y)_i for DOF i = 3 node + c (not masked)
+__device__ __forceinline__ float cs_prolong(const CoarseDev &cs, int64_t i) {
+  const int64_t node = i / 3;
+  const int c = (int)(i - 3 * node);
+  const int cell = cs.cell[node];
+  const float f[3] = {cs.frac[3 * node], cs.frac[3 * node + 1], cs.frac[3 * node + 2]};
+  float s = 0.f;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s = fmaf(cs_weight(f, k), cs.yc[3 * cs_corner(cs, cell, k) + c], s);
+  return s;
+}
+
+}  // namespace sfem

@@ -56,11 +56,6 @@ constexpr int kInferRows = 8;
 constexpr uint32_t kBlobMagic = 0x4e4e4653u;  // "SFNN"
 constexpr int kBlobVersion = 1;
 
-struct PatchGrid {
-  int d[3];
-  double lo[3], ext[3];
-};
-
 struct Learned {
   int device = 0;
   cudaStream_t stream = nullptr;

@@ -5,10 +5,12 @@
 #include <stdint.h>
 
 #include <functional>
+#include <memory>
 #include <string>
 #include <vector>
 
 #include "../../include/sfem.h"
+#include "coarse.cuh"
 
 namespace sfem {
 
@@ -138,6 +140,22 @@ struct TileData {
   size_t smem = 0;               // dynamic shared memory of the operator kernel
 };
 
+// regular grid of patches over a bounding box (learned correction and
+// coarse space)
+struct PatchGrid {
+  int d[3];
+  double lo[3], ext[3];
+};
+
+// two-level preconditioner data (coarse.cu); device arrays owned by the
+// context's allocator
+struct Coarse {
+  PatchGrid g{};
+  CoarseDev dev{};
+  int probes = 0;
+  double setup_ms = 0.0;
+};
+
 struct Ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -200,6 +218,7 @@ struct Ctx {
   SolveScalars *scal = nullptr;
   SolveScalars *h_scal = nullptr; // pinned host copies (2 slots)
   cudaStream_t cap_stream = nullptr; // private stream used only for graph capture
+  std::shared_ptr<Coarse> coarse;    // two-level preconditioner, if set up
 };
 
 // ---------------------------------------------------------------------------
@@ -237,6 +256,11 @@ void build_tiles(Ctx &c);
 // type TU/TY (float or double); energy u^T K u summed into *energy_out
 template <class TU, class TY>
 void launch_mf32_tiled(Ctx &c, cudaStream_t st, const TU *u, TY *y, double *energy_out, const int *done);
+
+// coarse correction of the two-level preconditioner (coarse.cu), on
+// stream st, all returning at once while *done != 0:
+// rc = Pi^T r (r masked), then yc = C rc
+void coarse_correction(Ctx &c, cudaStream_t st, const double *r, const int *done);
 
 // solves (solve.cu); a Snapshot, when given, sees the iterate x and the
 // residual r (device, ndof) of the flexible PCG before its first iteration

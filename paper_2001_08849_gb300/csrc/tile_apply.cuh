@@ -114,14 +114,28 @@ __device__ __forceinline__ double tile_compute(const TileArgs &A, int tile, cons
   uint16_t *sinc = reinterpret_cast<uint16_t *>(sfe + 12 * n_own);  // 4 * n_own
   uint16_t *snode = sinc + 4 * n_own;                                 // L
 
+  // Strains are differences of nodal displacements, and K annihilates
+  // constant fields (the shape-function gradients of a tet sum to zero), so
+  // with FP64 input the tile subtracts the displacement of its first node
+  // before rounding to FP32: the rounding then acts on the small tile-local
+  // differences instead of the full displacements, which removes most of
+  // the cancellation error of the FP32 strains.
+  TU ref[3] = {TU(0), TU(0), TU(0)};
+  if constexpr (sizeof(TU) == 8) {
+    const TU *rp = u + 3 * (int64_t)A.tile_nodes[n0];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) ref[c] = kCoherentU ? __ldcg(rp + c) : __ldg(rp + c);
+  }
   __syncthreads();
   for (int i = threadIdx.x; i < L; i += kTileThreads) {
     const int64_t node = A.tile_nodes[n0 + i];
     const TU *up = u + 3 * node;
     if (kCoherentU)
-      su[i] = make_float4((float)__ldcg(up), (float)__ldcg(up + 1), (float)__ldcg(up + 2), 0.f);
+      su[i] = make_float4((float)(__ldcg(up) - ref[0]), (float)(__ldcg(up + 1) - ref[1]),
+                          (float)(__ldcg(up + 2) - ref[2]), 0.f);
     else
-      su[i] = make_float4((float)__ldg(up), (float)__ldg(up + 1), (float)__ldg(up + 2), 0.f);
+      su[i] = make_float4((float)(__ldg(up) - ref[0]), (float)(__ldg(up + 1) - ref[1]),
+                          (float)(__ldg(up + 2) - ref[2]), 0.f);
     snode[i] = A.node_inc[n0 + i];
   }
   __syncthreads();
@@ -210,13 +224,19 @@ __device__ __forceinline__ double tile_compute(const TileArgs &A, int tile, cons
   for (int i = threadIdx.x; i < L; i += kTileThreads) {
     const int b = snode[i], e = (i + 1 < L) ? snode[i + 1] : nslots;
     if (b == e) continue;
-    float fx = 0.f, fy = 0.f, fz = 0.f;
+    // compensated (Kahan) sums: the element forces at a node nearly cancel
+    float fx = 0.f, fy = 0.f, fz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
     for (int k = b; k < e; ++k) {
       const int slot = sinc[k];
       const float *fp = sfe + 12 * (slot >> 2) + 3 * (slot & 3);
-      fx += fp[0];
-      fy += fp[1];
-      fz += fp[2];
+      const float yx = fp[0] - cx, yy = fp[1] - cy, yz = fp[2] - cz;
+      const float tx = fx + yx, ty = fy + yy, tz = fz + yz;
+      cx = __fsub_rn(__fsub_rn(tx, fx), yx);
+      cy = __fsub_rn(__fsub_rn(ty, fy), yy);
+      cz = __fsub_rn(__fsub_rn(tz, fz), yz);
+      fx = tx;
+      fy = ty;
+      fz = tz;
     }
     TY *yp = y + 3 * (int64_t)A.tile_nodes[n0 + i];
     atomicAdd(yp, (TY)fx);

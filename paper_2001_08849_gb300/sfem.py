@@ -56,7 +56,8 @@ class sfem_solve_opts(ctypes.Structure):
                 ("u_on_device", ctypes.c_int), ("warm_start", ctypes.c_int), ("max_iter", ctypes.c_int),
                 ("tol", ctypes.c_double), ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int),
                 ("check_every", ctypes.c_int), ("learned", ctypes.c_void_p), ("fp32_vectors", ctypes.c_int),
-                ("learned_window", ctypes.c_int), ("learned_pace", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
+                ("learned_window", ctypes.c_int), ("learned_pace", ctypes.c_int), ("precond", ctypes.c_int),
+                ("reserved", ctypes.c_int * 2)]
 
 
 class sfem_solve_info(ctypes.Structure):
@@ -76,6 +77,10 @@ class sfem_batch_stats(ctypes.Structure):
     _fields_ = [("rounds", ctypes.c_int), ("ctas_per_sm", ctypes.c_int), ("graph", ctypes.c_int),
                 ("n_systems", ctypes.c_int), ("total_iterations", ctypes.c_longlong), ("ms", ctypes.c_double),
                 ("fallback_systems", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
+
+
+class sfem_coarse_opts(ctypes.Structure):
+    _fields_ = [("patch_dims", ctypes.c_int * 3), ("patch_nodes", ctypes.c_int), ("reserved", ctypes.c_int * 8)]
 
 
 class sfem_learned_opts(ctypes.Structure):
@@ -108,6 +113,10 @@ _SIG = {
     "sfem_batch_solve": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(_P),
                                         ctypes.POINTER(sfem_batch_opts), ctypes.POINTER(sfem_solve_info),
                                         ctypes.POINTER(sfem_batch_stats)]),
+    "sfem_coarse_setup": (ctypes.c_int, [_P, ctypes.POINTER(sfem_coarse_opts)]),
+    "sfem_coarse_info": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(ctypes.c_double)]),
+    "sfem_coarse_apply": (ctypes.c_int, [_P, _P, _P]),
     "sfem_learned_create": (ctypes.c_int, [ctypes.POINTER(_P), _P, ctypes.POINTER(sfem_learned_opts)]),
     "sfem_learned_destroy": (None, [_P]),
     "sfem_learned_info": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
@@ -265,7 +274,7 @@ def sfem_apply_noalloc(h, u, y):
 
 def solve_opts(kind=SFEM_SOLVE_PCG64, op64=SFEM_OP_MF64, rhs=0, tol=1e-8, max_iter=0, inner_tol=0.0,
                max_outer=0, check_every=0, u_on_device=False, warm_start=False, learned=None, fp32_vectors=False,
-               learned_window=0, learned_pace=0):
+               learned_window=0, learned_pace=0, precond=0):
     o = sfem_solve_opts()
     o.kind, o.op64, o.rhs = int(kind), int(op64), int(rhs)
     o.u_on_device, o.warm_start = int(bool(u_on_device)), int(bool(warm_start))
@@ -274,6 +283,7 @@ def solve_opts(kind=SFEM_SOLVE_PCG64, op64=SFEM_OP_MF64, rhs=0, tol=1e-8, max_it
     o.learned = learned.h if isinstance(learned, Learned) else learned
     o.fp32_vectors = int(fp32_vectors)
     o.learned_window, o.learned_pace = int(learned_window), int(learned_pace)
+    o.precond = int(precond)
     return o
 
 
@@ -366,6 +376,31 @@ def sfem_launch_count() -> int:
 
 def sfem_strerror(status: int) -> str:
     return lib.sfem_strerror(status).decode()
+
+
+# ---- two-level preconditioner ---------------------------------------------------
+
+def sfem_coarse_setup(h, patch_dims=(0, 0, 0), patch_nodes=0) -> dict:
+    """Build the Galerkin coarse space of context h; returns its info."""
+    o = sfem_coarse_opts()
+    for a in range(3):
+        o.patch_dims[a] = int(patch_dims[a])
+    o.patch_nodes = int(patch_nodes)
+    _check(lib.sfem_coarse_setup(h, ctypes.byref(o)), "sfem_coarse_setup")
+    return sfem_coarse_info(h)
+
+
+def sfem_coarse_info(h) -> dict:
+    dims = (ctypes.c_int * 3)()
+    nc, probes, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    _check(lib.sfem_coarse_info(h, dims, ctypes.byref(nc), ctypes.byref(probes), ctypes.byref(ms)),
+           "sfem_coarse_info")
+    return {"patch_dims": tuple(dims), "n_coarse": nc.value, "probes": probes.value, "setup_ms": ms.value}
+
+
+def sfem_coarse_apply(h, r, z):
+    """z = D^-1 r + P Pi C Pi^T r (float64 CUDA tensors of ndof entries)."""
+    _check(lib.sfem_coarse_apply(h, _ptr(r), _ptr(z)), "sfem_coarse_apply")
 
 
 # ---- learned coarse correction ------------------------------------------------

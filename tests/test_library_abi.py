@@ -60,7 +60,8 @@ def test_struct_layouts_match_header(S, tmp_path):
     if cc is None:
         pytest.skip("no C compiler")
     structs = [S.sfem_opts, S.sfem_mesh_info, S.sfem_csr, S.sfem_solve_opts, S.sfem_solve_info,
-               S.sfem_batch_opts, S.sfem_batch_stats, S.sfem_learned_opts]
+               S.sfem_batch_opts, S.sfem_batch_stats, S.sfem_learned_opts,
+               S.sfem_coarse_opts]
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "sfem.h"', "int main(void){"]
     for st in structs:
         n = st.__name__

@@ -348,13 +348,18 @@ def main():
     u_host = torch.zeros(ndof, dtype=torch.float64).pin_memory().numpy()
     h2d_bytes = sum(a.nbytes for a in host)
     d2h_bytes = u_host.nbytes
-    opts_dev = S.solve_opts(kind=S.SFEM_SOLVE_IR32_64, op64=S.SFEM_OP_MF64, tol=TOL, u_on_device=True)
-    opts_host = S.solve_opts(kind=S.SFEM_SOLVE_IR32_64, op64=S.SFEM_OP_MF64, tol=TOL, u_on_device=False)
+    # the step: setup, the coarse space of the two-level preconditioner
+    # (patches of 8 x 8 x 8 nodes), the mixed-precision solve, destroy
+    coarse_dims = tuple(-(-(c + 1) // 8) for c in CELLS)
+    opts_dev = S.solve_opts(kind=S.SFEM_SOLVE_IR32_64, op64=S.SFEM_OP_MF64, tol=TOL, u_on_device=True, precond=1)
+    opts_host = S.solve_opts(kind=S.SFEM_SOLVE_IR32_64, op64=S.SFEM_OP_MF64, tol=TOL, u_on_device=False, precond=1)
+    coarse_infos = []
     stream = torch.cuda.current_stream()
     infos = []
 
     def step_device(keep=False):
         h, k = S.sfem_mesh_setup(*dev[:2], prob.E, prob.nu, *dev[2:], inputs_on_device=True)
+        coarse_infos.append(S.sfem_coarse_setup(h, patch_dims=coarse_dims))
         info = S.sfem_solve(h, u_dev, opts_dev)
         infos.append(info)
         if keep:
@@ -364,6 +369,7 @@ def main():
 
     def step_host():
         h, k = S.sfem_mesh_setup(*host[:2], prob.E, prob.nu, *host[2:], inputs_on_device=False)
+        S.sfem_coarse_setup(h, patch_dims=coarse_dims)
         info = S.sfem_solve(h, u_host, opts_host)
         S.sfem_destroy(h)
         return info
@@ -444,24 +450,38 @@ def main():
 
     forms = {}
     if not args.no_forms and rank == 0:
-        # plain FP64 Jacobi-PCG on the assembled CSR, same workload (once)
-        torch.cuda.synchronize()
-        ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ea.record(stream)
-        hh, kk = S.sfem_mesh_setup(*dev[:2], prob.E, prob.nu, *dev[2:], inputs_on_device=True)
-        S.sfem_assemble(hh)
-        x = torch.zeros(ndof, dtype=torch.float64, device="cuda")
-        inf = S.sfem_solve(hh, x, S.solve_opts(kind=S.SFEM_SOLVE_PCG64, op64=S.SFEM_OP_CSR64, tol=TOL,
-                                                u_on_device=True), check=False)
-        eb.record(stream)
-        torch.cuda.synchronize()
-        ms_csr = S.sfem_time_operator(hh, S.SFEM_OP_CSR64, reps=10)
-        S.sfem_destroy(hh)
-        forms["pcg64_csr"] = {"time_to_solve_s": ea.elapsed_time(eb) / 1e3, "iterations": inf["iterations"],
-                              "true_relres": inf["true_relres"], "status": inf["status"],
-                              "csr64_apply_ms": ms_csr}
-        forms["ir32_64_mf"] = {"time_to_solve_s": t_dev / args.steps, "iterations": iters[-1],
-                               "true_relres": relres}
+        def timed_form(kind, op64, precond, assemble):
+            """setup (+ CSR assembly) (+ coarse space) + solve of the same
+            workload, timed once with CUDA events on the stream"""
+            torch.cuda.synchronize()
+            ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ea.record(stream)
+            hh, kk = S.sfem_mesh_setup(*dev[:2], prob.E, prob.nu, *dev[2:], inputs_on_device=True)
+            if assemble:
+                S.sfem_assemble(hh)
+            if precond:
+                S.sfem_coarse_setup(hh, patch_dims=coarse_dims)
+            x = torch.zeros(ndof, dtype=torch.float64, device="cuda")
+            inf = S.sfem_solve(hh, x, S.solve_opts(kind=kind, op64=op64, tol=TOL, u_on_device=True,
+                                                    precond=precond), check=False)
+            eb.record(stream)
+            torch.cuda.synchronize()
+            out = {"time_to_solve_s": ea.elapsed_time(eb) / 1e3, "iterations": inf["iterations"],
+                   "true_relres": inf["true_relres"], "status": inf["status"], "solve_ms": inf["solve_ms"]}
+            if assemble:
+                out["csr64_apply_ms"] = S.sfem_time_operator(hh, S.SFEM_OP_CSR64, reps=10)
+            S.sfem_destroy(hh)
+            return out
+
+        # plain FP64 Jacobi-PCG on the assembled CSR (the paper's method with
+        # an iterative solve), then the other forms, each once
+        forms["pcg64_csr_jacobi"] = timed_form(S.SFEM_SOLVE_PCG64, S.SFEM_OP_CSR64, 0, True)
+        forms["pcg64_csr_two_level"] = timed_form(S.SFEM_SOLVE_PCG64, S.SFEM_OP_CSR64, 1, True)
+        forms["ir32_64_jacobi"] = timed_form(S.SFEM_SOLVE_IR32_64, S.SFEM_OP_MF64, 0, False)
+        forms["ir32_64_two_level"] = {"time_to_solve_s": t_dev / args.steps, "iterations": iters[-1],
+                                      "true_relres": relres, "coarse_dims": list(coarse_dims),
+                                      "coarse_setup_ms": float(np.mean([ci["setup_ms"] for ci in coarse_infos])),
+                                      "coarse_probes": coarse_infos[-1]["probes"], "note": "the timed step"}
 
     if not args.no_forms and rank == 0:
         forms["batch_64x4"] = batch_form(S)
@@ -482,8 +502,11 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": f"Kuhn cantilever {nx}x{ny}x{nz} cells x 6 = {m.n_tets} tets, "
                                    f"{m.n_nodes} nodes, {ndof} DOF, jitter seed {SEED}",
-                       "solver": "IR32_64: FP64 residual/update, FP32 matrix-free Jacobi-PCG inner",
-                       "tol": TOL, "step": "sfem_mesh_setup + sfem_solve + sfem_destroy",
+                       "solver": "IR32_64 with the two-level preconditioner: FP64 residual/update, "
+                                 "FP32 matrix-free operator inside CG on FP64 vectors, Jacobi + Galerkin "
+                                 f"coarse correction on {coarse_dims[0]}x{coarse_dims[1]}x{coarse_dims[2]} "
+                                 "patch centres",
+                       "tol": TOL, "step": "sfem_mesh_setup + sfem_coarse_setup + sfem_solve + sfem_destroy",
                        "l2": "no flush: operator data per step exceeds the 129 MB L2",
                        "parallelism": f"replicas x{world}"},
             "time_to_solve_s": t_dev / args.steps,

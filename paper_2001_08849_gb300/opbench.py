@@ -9,7 +9,9 @@ mean device ms per application, DOF/s and the algorithmic bytes of the FP32
 matrix-free operator.
 --solve: one solve of the cantilever (pcg64 on CSR, the mixed-precision
 ir32_64, flexible PCG without (fpcg) or with an untrained learned correction
-(fpcg_learned, patches of 8 x 8 x 8 nodes)); prints iterations and time.
+(fpcg_learned, patches of 8 x 8 x 8 nodes)); --precond 1 adds the two-level
+preconditioner (coarse space on 8 x 8 x 8-node patches) to pcg64 and
+ir32_64; prints iterations and time.
 """
 from __future__ import annotations
 
@@ -48,6 +50,7 @@ def main(argv=None):
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--max-iter", type=int, default=0)
     ap.add_argument("--window", type=int, default=0, help="learned_window of the fpcg_learned solve")
+    ap.add_argument("--precond", type=int, default=0, help="1: two-level preconditioner (pcg64, ir32_64)")
     a = ap.parse_args(argv)
     import torch
     import __graft_entry__
@@ -68,12 +71,16 @@ def main(argv=None):
                    "tiled_source_sha256": tiled_source_sha()}
         else:
             model = None
+            coarse = None
+            if a.precond:
+                coarse = S.sfem_coarse_setup(ctx.h, patch_dims=tuple(-(-(c + 1) // 8) for c in a.cells))
             if a.solve == "pcg64":
                 S.sfem_assemble(ctx.h)
                 o = S.solve_opts(kind=S.SFEM_SOLVE_PCG64, op64=S.SFEM_OP_CSR64, tol=a.tol, u_on_device=True,
-                                 max_iter=a.max_iter)
+                                 max_iter=a.max_iter, precond=a.precond)
             elif a.solve == "ir32_64":
-                o = S.solve_opts(kind=S.SFEM_SOLVE_IR32_64, tol=a.tol, u_on_device=True, max_iter=a.max_iter)
+                o = S.solve_opts(kind=S.SFEM_SOLVE_IR32_64, tol=a.tol, u_on_device=True, max_iter=a.max_iter,
+                                 precond=a.precond)
             else:
                 S.sfem_assemble(ctx.h)
                 if a.solve == "fpcg_learned":
@@ -87,7 +94,7 @@ def main(argv=None):
             info = S.sfem_solve(ctx.h, u, o, check=False)
             torch.cuda.synchronize()
             out = {"solve": a.solve, "cells": a.cells, "n_tets": n_tets, "ndof": ctx.ndof,
-                   "time_s": time.perf_counter() - t0, **info}
+                   "time_s": time.perf_counter() - t0, "coarse": coarse, **info}
             if model is not None:
                 model.close()
     print(json.dumps(out), flush=True)

@@ -51,6 +51,8 @@ def main(argv=None):
     ap.add_argument("--max-iter", type=int, default=0)
     ap.add_argument("--window", type=int, default=0, help="learned_window of the fpcg_learned solve")
     ap.add_argument("--precond", type=int, default=0, help="1: two-level preconditioner (pcg64, ir32_64)")
+    ap.add_argument("--coarse-dims", type=int, nargs=3, default=None, help="patch centres per axis")
+    ap.add_argument("--repeat", type=int, default=1, help="solves (the last one is reported)")
     a = ap.parse_args(argv)
     import torch
     import __graft_entry__
@@ -73,7 +75,9 @@ def main(argv=None):
             model = None
             coarse = None
             if a.precond:
-                coarse = S.sfem_coarse_setup(ctx.h, patch_dims=tuple(-(-(c + 1) // 8) for c in a.cells))
+                dims = tuple(a.coarse_dims) if a.coarse_dims else tuple(-(-(c + 1) // 8) for c in a.cells)
+                for _ in range(a.repeat):
+                    coarse = S.sfem_coarse_setup(ctx.h, patch_dims=dims)
             if a.solve == "pcg64":
                 S.sfem_assemble(ctx.h)
                 o = S.solve_opts(kind=S.SFEM_SOLVE_PCG64, op64=S.SFEM_OP_CSR64, tol=a.tol, u_on_device=True,
@@ -88,11 +92,12 @@ def main(argv=None):
                     model = S.Learned(ctx.h, patch_dims=dims, seed=1, keepalive=ctx._keep)
                 o = S.solve_opts(kind=S.SFEM_SOLVE_FPCG_LEARNED, op64=S.SFEM_OP_CSR64, tol=a.tol,
                                  u_on_device=True, learned=model, max_iter=a.max_iter, learned_window=a.window)
-            u = torch.zeros(ctx.ndof, dtype=torch.float64, device="cuda")
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            info = S.sfem_solve(ctx.h, u, o, check=False)
-            torch.cuda.synchronize()
+            for _ in range(a.repeat):
+                u = torch.zeros(ctx.ndof, dtype=torch.float64, device="cuda")
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                info = S.sfem_solve(ctx.h, u, o, check=False)
+                torch.cuda.synchronize()
             out = {"solve": a.solve, "cells": a.cells, "n_tets": n_tets, "ndof": ctx.ndof,
                    "time_s": time.perf_counter() - t0, "coarse": coarse, **info}
             if model is not None:

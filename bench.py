@@ -349,10 +349,10 @@ def main():
     h2d_bytes = sum(a.nbytes for a in host)
     d2h_bytes = u_host.nbytes
     # the step: setup, the coarse space of the two-level preconditioner, the
-    # mixed-precision solve, destroy.  Coarse grid: 26 centres along the beam
-    # (8-node patches) and 4 x 4 across, the fastest setup + solve of a sweep
-    # (26x6x6: 193 ms, 26x4x4: 173 ms, 26x3x3: 191 ms, 34x6x6: 193 ms)
-    coarse_dims = (-(-(CELLS[0] + 1) // 8), 4, 4)
+    # mixed-precision solve, destroy.  Coarse grid: patches of 8 x 8 x 8 nodes
+    # (26 x 6 x 6 centres), with 34 x 6 x 6 the fastest coarse setup + solve of
+    # a sweep (135 / 134 ms; 26x4x4: 155, 26x3x3: 188, 40x8x8: 159)
+    coarse_dims = tuple(-(-(c + 1) // 8) for c in CELLS)
     opts_dev = S.solve_opts(kind=S.SFEM_SOLVE_IR32_64, op64=S.SFEM_OP_MF64, tol=TOL, u_on_device=True, precond=1)
     opts_host = S.solve_opts(kind=S.SFEM_SOLVE_IR32_64, op64=S.SFEM_OP_MF64, tol=TOL, u_on_device=False, precond=1)
     coarse_infos = []

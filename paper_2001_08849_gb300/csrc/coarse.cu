@@ -8,7 +8,8 @@
 //
 // Setup (sfem_coarse_setup):
 //   * nodes grouped by interpolation cell with their fractions (host, once);
-//   * A_c by probing: the centres are split into colour classes with stride
+//   * A_c tile by tile (k_cs_galerkin, below), or by probing (the fallback
+//     and an option): the centres are split into colour classes with stride
 //     s_a = min(5, d_a) per axis.  For every class and component the FP32
 //     tiled operator is applied to the sum of the class's functions, and the
 //     restricted response at centre i is attributed to the unique class
@@ -30,6 +31,7 @@
 
 #include "reduce.cuh"
 #include "sfem_internal.cuh"
+#include "tile_apply.cuh"
 
 namespace sfem {
 
@@ -172,6 +174,148 @@ __global__ void k_cs_attrib(CoarseDev cs, int comp, int3 res, int3 str, double *
   Ac[(int64_t)t * cs.npad + 3 * j + comp] = (double)cs.rc[t];
 }
 
+// ---- Galerkin coarse matrix, tile by tile ------------------------------------
+
+constexpr int kGalMaxCells = 64;    // interpolation cells a tile may touch (4 per axis)
+constexpr int kGalMaxCentres = 125; // centres of those cells (5 per axis)
+
+// Every tile applies its part of the FP32 operator (own tets, halo strains)
+// to each coarse function P Pi_J whose centre is a corner of a cell touched
+// by the tile's nodes, and restricts the tile's masked nodal forces against
+// the same centres; the contributions of all tiles add up to
+// A_c = Pi^T P K P Pi (FP64 atomics into the dense A_c).  The tile's nodes
+// are grouped by cell once (stable order), so each (cell, corner,
+// component) restriction entry is a fixed-order sum by one thread.
+// Dynamic shared memory: the tile layout (stage_off float4 units), then per
+// tile node a float4 stage (cell id with the free-DOF mask in bits 28-30, and
+// the three fractions) and a uint16 order.  Sets *overflow for a tile that
+// touches more than 4 cells on an axis.
+__global__ void __launch_bounds__(kTileThreads, 3) k_cs_galerkin(TileArgs A, CoarseDev cs,
+                                                              const uint8_t *__restrict__ dmask, float lam,
+                                                              float mu, int stage_off, double *__restrict__ Ac,
+                                                              int *overflow) {
+  extern __shared__ float4 smem_t[];
+  __shared__ int bb[6], coff[kGalMaxCells + 1];
+  __shared__ float acc[3 * kGalMaxCentres];
+  const int tile = blockIdx.x;
+  TileRegs R;
+  tile_load(A, tile, R);
+  const TileView T = tile_view(A, tile, smem_t);
+  float4 *stage = smem_t + stage_off;
+  uint16_t *order = reinterpret_cast<uint16_t *>(stage + T.L);
+  if (threadIdx.x < 3) {
+    bb[threadIdx.x] = 1 << 30;
+    bb[3 + threadIdx.x] = -1;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < T.L; i += kTileThreads) {
+    const int64_t node = A.tile_nodes[T.n0 + i];
+    const int cell = cs.cell[node];
+    const int m = (dmask[3 * node] ? 1 : 0) | (dmask[3 * node + 1] ? 2 : 0) | (dmask[3 * node + 2] ? 4 : 0);
+    stage[i] = make_float4(__int_as_float(cell | (m << 28)), cs.frac[3 * node], cs.frac[3 * node + 1],
+                           cs.frac[3 * node + 2]);
+    T.snode[i] = A.node_inc[T.n0 + i];
+    const int iz = cell % cs.cd[2], iy = (cell / cs.cd[2]) % cs.cd[1], ix = cell / (cs.cd[1] * cs.cd[2]);
+    atomicMin(&bb[0], ix);
+    atomicMin(&bb[1], iy);
+    atomicMin(&bb[2], iz);
+    atomicMax(&bb[3], ix);
+    atomicMax(&bb[4], iy);
+    atomicMax(&bb[5], iz);
+  }
+  __syncthreads();
+  const int c0[3] = {bb[0], bb[1], bb[2]};
+  const int ncl[3] = {bb[3] - bb[0] + 1, bb[4] - bb[1] + 1, bb[5] - bb[2] + 1};
+  if (ncl[0] > 4 || ncl[1] > 4 || ncl[2] > 4) {
+    if (threadIdx.x == 0) atomicExch(overflow, 1);
+    return;
+  }
+  const int nlc = ncl[0] * ncl[1] * ncl[2];
+  // local centres: corners of the local cells, clamped to the grid
+  int j0[3], nj[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    j0[a] = c0[a];
+    nj[a] = min(c0[a] + ncl[a], cs.d[a] - 1) - c0[a] + 1;
+  }
+  const int nloc = nj[0] * nj[1] * nj[2];
+  auto local_cell = [&](int cell) {
+    const int iz = cell % cs.cd[2], iy = (cell / cs.cd[2]) % cs.cd[1], ix = cell / (cs.cd[1] * cs.cd[2]);
+    return ((ix - c0[0]) * ncl[1] + (iy - c0[1])) * ncl[2] + (iz - c0[2]);
+  };
+  // stable grouping of the tile's nodes by local cell (one thread; L <= a few hundred)
+  if (threadIdx.x == 0) {
+    for (int q = 0; q <= nlc; ++q) coff[q] = 0;
+    for (int i = 0; i < T.L; ++i) coff[local_cell(__float_as_int(stage[i].x) & 0x0FFFFFFF) + 1] += 1;
+    for (int q = 0; q < nlc; ++q) coff[q + 1] += coff[q];
+    int cur[kGalMaxCells];
+    for (int q = 0; q < nlc; ++q) cur[q] = coff[q];
+    for (int i = 0; i < T.L; ++i) order[cur[local_cell(__float_as_int(stage[i].x) & 0x0FFFFFFF)]++] = (uint16_t)i;
+  }
+  __syncthreads();
+  for (int q = 0; q < 3 * nloc; ++q) {
+    const int jl = q / 3, comp = q % 3;
+    const int jx = j0[0] + jl / (nj[1] * nj[2]), jy = j0[1] + (jl / nj[2]) % nj[1], jz = j0[2] + jl % nj[2];
+    const int J = (jx * cs.d[1] + jy) * cs.d[2] + jz;
+    // synthetic displacements P Pi_J at the tile's nodes
+    for (int i = threadIdx.x; i < T.L; i += kTileThreads) {
+      const float4 st = stage[i];
+      const int cm = __float_as_int(st.x);
+      const float f[3] = {st.y, st.z, st.w};
+      float w = 0.f;
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        if (cs_corner(cs, cm & 0x0FFFFFFF, k) == J) w += cs_weight(f, k);
+      const float v = ((cm >> (28 + comp)) & 1) ? w : 0.f;
+      T.su[i] = make_float4(comp == 0 ? v : 0.f, comp == 1 ? v : 0.f, comp == 2 ? v : 0.f, 0.f);
+    }
+    for (int t = threadIdx.x; t < 3 * nloc; t += kTileThreads) acc[t] = 0.f;
+    __syncthreads();
+    tile_strains(A, R, T);
+    __syncthreads();
+    tile_forces(R, T, lam, mu);
+    __syncthreads();
+    // masked nodal forces of the tile into su
+    for (int i = threadIdx.x; i < T.L; i += kTileThreads) {
+      float fx, fy, fz;
+      tile_node_force(T, i, fx, fy, fz);
+      const int m = __float_as_int(stage[i].x) >> 28;
+      T.su[i] = make_float4((m & 1) ? fx : 0.f, (m & 2) ? fy : 0.f, (m & 4) ? fz : 0.f, 0.f);
+    }
+    __syncthreads();
+    // restriction: one thread per (local cell, corner, component)
+    for (int t = threadIdx.x; t < 24 * nlc; t += kTileThreads) {
+      const int lc = t / 24, k = (t % 24) / 3, cc = t % 3;
+      float sum = 0.f;
+      int cell = -1;
+      for (int e = coff[lc]; e < coff[lc + 1]; ++e) {
+        const int i = order[e];
+        const float4 st = stage[i];
+        cell = __float_as_int(st.x) & 0x0FFFFFFF;
+        const float f[3] = {st.y, st.z, st.w};
+        const float4 fi = T.su[i];
+        sum = fmaf(cs_weight(f, k), cc == 0 ? fi.x : (cc == 1 ? fi.y : fi.z), sum);
+      }
+      if (cell < 0) continue;
+      const int I = cs_corner(cs, cell, k);
+      const int iz = I % cs.d[2], iy = (I / cs.d[2]) % cs.d[1], ix = I / (cs.d[1] * cs.d[2]);
+      const int il = ((ix - j0[0]) * nj[1] + (iy - j0[1])) * nj[2] + (iz - j0[2]);
+      atomicAdd(&acc[3 * il + cc], sum);
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < 3 * nloc; t += kTileThreads) {
+      const float v = acc[t];
+      if (v != 0.f) {
+        const int il = t / 3, cc = t % 3;
+        const int ix = j0[0] + il / (nj[1] * nj[2]), iy = j0[1] + (il / nj[2]) % nj[1], iz = j0[2] + il % nj[2];
+        const int I = (ix * cs.d[1] + iy) * cs.d[2] + iz;
+        atomicAdd(&Ac[(int64_t)(3 * I + cc) * cs.npad + 3 * J + comp], (double)v);
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // A <- (A + A^T) / 2 on the nc x nc block; padding: identity; a zero
 // diagonal (a function on prescribed DOFs only) becomes 1
 __global__ void k_cs_symmetrize(double *A, int nc, int npad) {
@@ -225,58 +369,108 @@ __device__ __forceinline__ void load64(Tile64<T> &S, const T *A, int64_t ld, int
     S.v[e / kCB][e % kCB] = A[(int64_t)(bi * kCB + e / kCB) * ld + bj * kCB + e % kCB];
 }
 
-// factor the diagonal block k (unblocked, in shared memory)
-__global__ void __launch_bounds__(256) k_potrf_diag(double *A, int npad, int k, int *info) {
+// block bandwidth of the lower triangle: max over block rows of (block row
+// - block column of the first nonzero entry)
+__global__ void __launch_bounds__(256) k_band_blocks(const double *A, int npad, int *bwb) {
+  const int br = blockIdx.x;
+  int first = npad;
+  for (int e = threadIdx.x; e < kCB * (br + 1) * kCB; e += blockDim.x) {
+    const int r = br * kCB + e / ((br + 1) * kCB), col = e % ((br + 1) * kCB);
+    if (col < first && A[(int64_t)r * npad + col] != 0.0) first = col;
+  }
+  for (int o = 16; o > 0; o >>= 1) first = min(first, __shfl_down_sync(0xffffffffu, first, o));
+  if ((threadIdx.x & 31) == 0 && first < npad) atomicMax(bwb, br - first / kCB);
+}
+
+// factor the diagonal block k in shared memory: columns in groups of 8 (one
+// warp factors the 64 x 8 panel, then all threads apply its rank-8 update
+// to the trailing lower triangle); then W_kk = L_kk^-1 by forward
+// substitution, 4 threads per column sharing each dot product.  L_kk back to
+// A, W_kk to Wd[k] (FP64)
+__global__ void __launch_bounds__(256) k_potrf_diag(double *A, double *Wd, int npad, int k, int *info) {
   extern __shared__ double dyn_d[];
   Tile64<double> &L = *reinterpret_cast<Tile64<double> *>(dyn_d);
+  Tile64<double> &W = *reinterpret_cast<Tile64<double> *>(dyn_d + kCB * (kCB + 1));
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   load64(L, A, npad, k, k);
   __syncthreads();
-  for (int j = 0; j < kCB; ++j) {
-    if (threadIdx.x == 0) {
-      double d = L.v[j][j];
-      if (!(d > 0.0) || !isfinite(d)) {
-        atomicExch(info, 1);
-        d = 1.0;
+  constexpr int G = 8;
+  for (int g0 = 0; g0 < kCB; g0 += G) {
+    if (warp == 0) {
+      for (int j = g0; j < g0 + G; ++j) {
+        double d = L.v[j][j];
+        if (!(d > 0.0) || !isfinite(d)) {
+          if (lane == 0) atomicExch(info, 1);
+          d = 1.0;
+        }
+        const double sd = sqrt(d);
+        __syncwarp();
+        if (lane == 0) L.v[j][j] = sd;
+        for (int i = j + 1 + lane; i < kCB; i += 32) L.v[i][j] /= sd;
+        __syncwarp();
+        // update the rest of the panel (columns j+1 .. g0+G-1)
+        for (int i = j + 1 + lane; i < kCB; i += 32) {
+          const double lij = L.v[i][j];
+          for (int l = j + 1; l < min(g0 + G, i + 1); ++l) L.v[i][l] -= lij * L.v[l][j];
+        }
+        __syncwarp();
       }
-      L.v[j][j] = sqrt(d);
     }
     __syncthreads();
-    for (int i = j + 1 + threadIdx.x; i < kCB; i += blockDim.x) L.v[i][j] /= L.v[j][j];
-    __syncthreads();
-    for (int e = threadIdx.x; e < kCB * kCB; e += blockDim.x) {
+    // rank-G update of the trailing lower triangle (columns >= g0 + G)
+    for (int e = tid; e < kCB * kCB; e += blockDim.x) {
       const int i = e / kCB, l = e % kCB;
-      if (l > j && i >= l) L.v[i][l] -= L.v[i][j] * L.v[l][j];
+      if (l < g0 + G || l > i) continue;
+      double s = L.v[i][l];
+#pragma unroll
+      for (int q = g0; q < g0 + G; ++q) s -= L.v[i][q] * L.v[l][q];
+      L.v[i][l] = s;
     }
     __syncthreads();
   }
-  for (int e = threadIdx.x; e < kCB * kCB; e += blockDim.x) {
+  // W = L^-1: column c by threads 4c .. 4c+3.  Every lane of the warp runs
+  // every iteration (the shuffles and the warp barrier need all 32 lanes);
+  // only the writes depend on i >= c.
+  {
+    const int c = tid >> 2, part = tid & 3;
+    for (int i = 0; i < kCB; ++i) {
+      double s = 0.0;
+      if (i > c)
+        for (int l = c + part; l < i; l += 4) s += L.v[i][l] * W.v[l][c];
+      s += __shfl_xor_sync(0xffffffffu, s, 1);
+      s += __shfl_xor_sync(0xffffffffu, s, 2);
+      if (part == 0) W.v[i][c] = (i < c) ? 0.0 : (((i == c) ? 1.0 : 0.0) - s) / L.v[i][i];
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < kCB * kCB; e += blockDim.x) {
     const int i = e / kCB, l = e % kCB;
     A[(int64_t)(k * kCB + i) * npad + k * kCB + l] = (l <= i) ? L.v[i][l] : 0.0;
+    Wd[(int64_t)k * kCB * kCB + e] = W.v[i][l];
   }
 }
 
-// L[i][k] = A[i][k] L[k][k]^-T for the row blocks i > k (one thread per row)
-__global__ void __launch_bounds__(kCB) k_trsm_panel(double *A, int npad, int k) {
+// L[i][k] = A[i][k] W_kk^T for the row blocks k < i <= k + bwb
+__global__ void __launch_bounds__(256) k_trsm_panel(double *A, const double *Wd, int npad, int k) {
   extern __shared__ double dyn_d[];
-  Tile64<double> &L = *reinterpret_cast<Tile64<double> *>(dyn_d);
-  Tile64<double> &X = *reinterpret_cast<Tile64<double> *>(dyn_d + kCB * (kCB + 1));
+  Tile64<double> &X = *reinterpret_cast<Tile64<double> *>(dyn_d);
+  Tile64<double> &Wk = *reinterpret_cast<Tile64<double> *>(dyn_d + kCB * (kCB + 1));
   const int bi = k + 1 + blockIdx.x;
-  load64(L, A, npad, k, k);
   load64(X, A, npad, bi, k);
+  load64(Wk, Wd + (int64_t)k * kCB * kCB, kCB, 0, 0);
   __syncthreads();
-  const int r = threadIdx.x;
-  for (int c = 0; c < kCB; ++c) {
-    double s = X.v[r][c];
-    for (int l = 0; l < c; ++l) s -= X.v[r][l] * L.v[c][l];
-    X.v[r][c] = s / L.v[c][c];
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < kCB * kCB; e += blockDim.x)
-    A[(int64_t)(bi * kCB + e / kCB) * npad + k * kCB + e % kCB] = X.v[e / kCB][e % kCB];
+  const int tm = (threadIdx.x >> 4) * 4, tn = (threadIdx.x & 15) * 4;
+  double acc[4][4] = {};
+  mm64<double, false, true>(acc, X, Wk, tm, tn);
+#pragma unroll
+  for (int x = 0; x < 4; ++x)
+#pragma unroll
+    for (int y = 0; y < 4; ++y) A[(int64_t)(bi * kCB + tm + x) * npad + k * kCB + tn + y] = acc[x][y];
 }
 
-// A[i][j] -= L[i][k] L[j][k]^T for k < j <= i (block pairs enumerated)
-__global__ void __launch_bounds__(256) k_syrk_update(double *A, int npad, int k, int nb) {
+// A[i][j] -= L[i][k] L[j][k]^T for k < j <= i <= k + m (block pairs enumerated)
+__global__ void __launch_bounds__(256) k_syrk_update(double *A, int npad, int k, int m) {
   extern __shared__ double dyn_d[];
   Tile64<double> &Li = *reinterpret_cast<Tile64<double> *>(dyn_d);
   Tile64<double> &Lj = *reinterpret_cast<Tile64<double> *>(dyn_d + kCB * (kCB + 1));
@@ -285,8 +479,8 @@ __global__ void __launch_bounds__(256) k_syrk_update(double *A, int npad, int k,
   while ((ii + 1) * (ii + 2) / 2 <= t) ++ii;
   while (ii * (ii + 1) / 2 > t) --ii;
   const int jj = t - ii * (ii + 1) / 2;
+  if (ii >= m || jj > ii) return;
   const int bi = k + 1 + ii, bj = k + 1 + jj;
-  if (bi >= nb || bj > bi) return;
   load64(Li, A, npad, bi, k);
   load64(Lj, A, npad, bj, k);
   __syncthreads();
@@ -306,54 +500,39 @@ __global__ void k_lower_to_f32(const double *A, float *L, int npad) {
   L[e] = (j <= i) ? (float)A[e] : 0.f;
 }
 
-// W[k][k] = L[k][k]^-1 (one thread per column, forward substitution)
-__global__ void __launch_bounds__(kCB) k_trtri_diag(const float *L, float *W, int npad) {
-  __shared__ Tile64<float> Ls, Ws;
-  const int k = blockIdx.x;
-  load64(Ls, L, npad, k, k);
-  __syncthreads();
-  const int c = threadIdx.x;
-  for (int i = 0; i < kCB; ++i) {
-    float s = (i == c) ? 1.f : 0.f;
-    if (i >= c) {
-      for (int l = c; l < i; ++l) s -= Ls.v[i][l] * Ws.v[l][c];
-      s /= Ls.v[i][i];
-    } else {
-      s = 0.f;
-    }
-    Ws.v[i][c] = s;
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < kCB * kCB; e += blockDim.x)
-    W[(int64_t)(k * kCB + e / kCB) * npad + k * kCB + e % kCB] = Ws.v[e / kCB][e % kCB];
-}
-
-// W[i][j] = -W[i][i] sum_{l=j}^{i-1} L[i][l] W[l][j] for i = j + s
-__global__ void __launch_bounds__(256) k_trtri_off(const float *L, float *W, int npad, int s) {
+// W = L^-1 (FP32), one block per block column j, walking down the column:
+// W_jj from Wd, then W_ij = -W_ii sum_{l} L_il W_lj over the band of L
+__global__ void __launch_bounds__(256) k_trtri_cols(const float *L, const double *Wd, float *W, int npad, int nb,
+                                                    int bwb) {
   __shared__ Tile64<float> As, Bs;
-  const int bj = blockIdx.x, bi = bj + s;
+  const int bj = blockIdx.x;
   const int tm = (threadIdx.x >> 4) * 4, tn = (threadIdx.x & 15) * 4;
-  float acc[4][4] = {};
-  for (int l = bj; l < bi; ++l) {
+  for (int e = threadIdx.x; e < kCB * kCB; e += blockDim.x)
+    W[(int64_t)(bj * kCB + e / kCB) * npad + bj * kCB + e % kCB] = (float)Wd[(int64_t)bj * kCB * kCB + e];
+  for (int bi = bj + 1; bi < nb; ++bi) {
+    float acc[4][4] = {};
+    for (int l = max(bj, bi - bwb); l < bi; ++l) {
+      __syncthreads();  // W_lj of the previous steps is in global memory
+      load64(As, L, npad, bi, l);
+      load64(Bs, W, npad, l, bj);
+      __syncthreads();
+      mm64<float, false, false>(acc, As, Bs, tm, tn);
+    }
     __syncthreads();
-    load64(As, L, npad, bi, l);
-    load64(Bs, W, npad, l, bj);
+    for (int e = threadIdx.x; e < kCB * kCB; e += blockDim.x)
+      As.v[e / kCB][e % kCB] = (float)Wd[(int64_t)bi * kCB * kCB + e];
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) Bs.v[tm + x][tn + y] = acc[x][y];
     __syncthreads();
-    mm64<float, false, false>(acc, As, Bs, tm, tn);
+    float out[4][4] = {};
+    mm64<float, false, false>(out, As, Bs, tm, tn);
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) W[(int64_t)(bi * kCB + tm + x) * npad + bj * kCB + tn + y] = -out[x][y];
   }
-  __syncthreads();
-  load64(As, W, npad, bi, bi);
-#pragma unroll
-  for (int x = 0; x < 4; ++x)
-#pragma unroll
-    for (int y = 0; y < 4; ++y) Bs.v[tm + x][tn + y] = acc[x][y];
-  __syncthreads();
-  float out[4][4] = {};
-  mm64<float, false, false>(out, As, Bs, tm, tn);
-#pragma unroll
-  for (int x = 0; x < 4; ++x)
-#pragma unroll
-    for (int y = 0; y < 4; ++y) W[(int64_t)(bi * kCB + tm + x) * npad + bj * kCB + tn + y] = -out[x][y];
 }
 
 // C[a][b] = sum_{l >= a} W[l][a]^T W[l][b] for a >= b, mirrored to C[b][a]
@@ -478,10 +657,32 @@ static void setup_coarse(Ctx &c, const sfem_coarse_opts *opts) {
   const int64_t np2 = (int64_t)cs.npad * cs.npad;
   double *Ac = c.mem.get<double>(np2);
   SFEM_CUDA(cudaMemsetAsync(Ac, 0, np2 * sizeof(double), c.stream));
+  int probes = 0;
+  const int assembly = opts ? opts->assembly : 0;
+  SFEM_REQUIRE(assembly == 0 || assembly == 1, SFEM_EINVAL, "assembly must be 0 or 1");
+  if (assembly == 0) {
+    // tile by tile (exact Galerkin entries, no colouring)
+    int *ovf = c.mem.get<int>(1);
+    SFEM_CUDA(cudaMemsetAsync(ovf, 0, sizeof(int), c.stream));
+    const int stage_off = (int)((c.tl.smem + 15) / 16);
+    const size_t smem = (size_t)stage_off * 16 + (size_t)c.tl.max_nodes * (sizeof(float4) + sizeof(uint16_t)) + 16;
+    SFEM_REQUIRE(smem <= 227 * 1024, SFEM_EINVAL, "tile too large for the Galerkin assembly");
+    SFEM_CUDA(cudaFuncSetAttribute(k_cs_galerkin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    TileArgs TA{c.tl.tile_start, c.tl.hoff, c.tl.noff, c.tl.halo_tet, c.tl.halo_lconn, c.tl.tile_nodes,
+                c.tl.node_inc, c.tl.rec};
+    k_cs_galerkin<<<(unsigned)c.tl.n_tiles, kTileThreads, smem, c.stream>>>(TA, cs, c.dmask, (float)c.lam,
+                                                                              (float)c.mu, stage_off, Ac, ovf);
+    SFEM_CHECK_LAUNCH();
+    int hovf = 0;
+    SFEM_CUDA(cudaMemcpyAsync(&hovf, ovf, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+    SFEM_CUDA(cudaStreamSynchronize(c.stream));
+    c.mem.drop(ovf);
+    if (hovf) SFEM_CUDA(cudaMemsetAsync(Ac, 0, np2 * sizeof(double), c.stream));  // probe instead
+    else probes = -1;
+  }
   float *v = c.mem.get<float>(c.ndof), *y = c.mem.get<float>(c.ndof);
   const int3 str = make_int3(std::min(5, cs.d[0]), std::min(5, cs.d[1]), std::min(5, cs.d[2]));
-  int probes = 0;
-  for (int comp = 0; comp < 3; ++comp)
+  for (int comp = 0; comp < 3 && probes >= 0; ++comp)
     for (int rx = 0; rx < str.x; ++rx)
       for (int ry = 0; ry < str.y; ++ry)
         for (int rz = 0; rz < str.z; ++rz) {
@@ -502,28 +703,34 @@ static void setup_coarse(Ctx &c, const sfem_coarse_opts *opts) {
   c.mem.drop(y);
   k_cs_symmetrize<<<grid_for(np2, 256), 256, 0, c.stream>>>(Ac, cs.nc, cs.npad);
   SFEM_CHECK_LAUNCH();
-  // ---- blocked Cholesky (FP64) ---------------------------------------------
+  // ---- banded blocked Cholesky (FP64) ---------------------------------------
   const int nb = cs.npad / kCB;
-  int *info = c.mem.get<int>(1);
-  SFEM_CUDA(cudaMemsetAsync(info, 0, sizeof(int), c.stream));
-  const size_t sm1 = sizeof(Tile64<double>), sm2 = 2 * sizeof(Tile64<double>);
-  SFEM_CUDA(cudaFuncSetAttribute(k_potrf_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1));
+  int *dev_i = c.mem.get<int>(2);  // [0] info, [1] block bandwidth
+  SFEM_CUDA(cudaMemsetAsync(dev_i, 0, 2 * sizeof(int), c.stream));
+  k_band_blocks<<<nb, 256, 0, c.stream>>>(Ac, cs.npad, dev_i + 1);
+  SFEM_CHECK_LAUNCH();
+  int hb[2] = {0, 0};
+  SFEM_CUDA(cudaMemcpyAsync(hb, dev_i, sizeof hb, cudaMemcpyDeviceToHost, c.stream));
+  SFEM_CUDA(cudaStreamSynchronize(c.stream));
+  const int bwb = std::max(hb[1], 1);
+  double *Wd = c.mem.get<double>((size_t)nb * kCB * kCB);
+  const size_t sm2 = 2 * sizeof(Tile64<double>);
+  SFEM_CUDA(cudaFuncSetAttribute(k_potrf_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
   SFEM_CUDA(cudaFuncSetAttribute(k_trsm_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
   SFEM_CUDA(cudaFuncSetAttribute(k_syrk_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
   for (int k = 0; k < nb; ++k) {
-    k_potrf_diag<<<1, 256, sm1, c.stream>>>(Ac, cs.npad, k, info);
+    k_potrf_diag<<<1, 256, sm2, c.stream>>>(Ac, Wd, cs.npad, k, dev_i);
     SFEM_CHECK_LAUNCH();
-    const int m = nb - k - 1;
-    if (m == 0) break;
-    k_trsm_panel<<<m, kCB, sm2, c.stream>>>(Ac, cs.npad, k);
+    const int m = std::min(nb - 1 - k, bwb);  // nonzero row blocks below the diagonal block
+    if (m == 0) continue;
+    k_trsm_panel<<<m, 256, sm2, c.stream>>>(Ac, Wd, cs.npad, k);
     SFEM_CHECK_LAUNCH();
-    k_syrk_update<<<m * (m + 1) / 2, 256, sm2, c.stream>>>(Ac, cs.npad, k, nb);
+    k_syrk_update<<<m * (m + 1) / 2, 256, sm2, c.stream>>>(Ac, cs.npad, k, m);
     SFEM_CHECK_LAUNCH();
   }
-  int hinfo = 0;
-  SFEM_CUDA(cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+  SFEM_CUDA(cudaMemcpyAsync(hb, dev_i, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
   SFEM_CUDA(cudaStreamSynchronize(c.stream));
-  SFEM_REQUIRE(hinfo == 0, SFEM_EBREAKDOWN, "coarse matrix is not positive definite");
+  SFEM_REQUIRE(hb[0] == 0, SFEM_EBREAKDOWN, "coarse matrix is not positive definite");
   // ---- C = A_c^-1 = L^-T L^-1 (FP32) ----------------------------------------
   float *L32 = c.mem.get<float>(np2), *W = c.mem.get<float>(np2);
   float *C = c.mem.get<float>(np2);
@@ -531,19 +738,16 @@ static void setup_coarse(Ctx &c, const sfem_coarse_opts *opts) {
   SFEM_CHECK_LAUNCH();
   c.mem.drop(Ac);
   SFEM_CUDA(cudaMemsetAsync(W, 0, np2 * sizeof(float), c.stream));
-  k_trtri_diag<<<nb, kCB, 0, c.stream>>>(L32, W, cs.npad);
+  k_trtri_cols<<<nb, 256, 0, c.stream>>>(L32, Wd, W, cs.npad, nb, bwb);
   SFEM_CHECK_LAUNCH();
-  for (int s = 1; s < nb; ++s) {
-    k_trtri_off<<<nb - s, 256, 0, c.stream>>>(L32, W, cs.npad, s);
-    SFEM_CHECK_LAUNCH();
-  }
   k_lauum<<<nb * (nb + 1) / 2, 256, 0, c.stream>>>(W, C, cs.npad, nb);
   SFEM_CHECK_LAUNCH();
   c.mem.drop(L32);
   c.mem.drop(W);
-  c.mem.drop(info);
+  c.mem.drop(Wd);
+  c.mem.drop(dev_i);
   cs.C = C;
-  co->probes = probes;
+  co->probes = std::max(probes, 0);  // 0: assembled tile by tile
   SFEM_CUDA(cudaEventRecord(e1, c.stream));
   SFEM_CUDA(cudaEventSynchronize(e1));
   float ms = 0.f;

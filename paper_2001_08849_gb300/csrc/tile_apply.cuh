@@ -91,91 +91,80 @@ __device__ __forceinline__ void tile_load(const TileArgs &A, int tile, TileRegs 
   }
 }
 
-// y += K u over one tile (all threads of the block); returns this thread's
-// share of u^T K u.  Starts and ends with a block barrier, so it can be
-// called repeatedly on the same shared memory.
-// kCoherentU: read u through L2 (ld.global.cg) instead of the read-only
-// path; needed when u changes during the kernel (persistent solvers).
-template <class TU, class TY, bool kCoherentU = false>
-__device__ __forceinline__ double tile_compute(const TileArgs &A, int tile, const TileRegs &R,
-                                               const TU *__restrict__ u, TY *__restrict__ y, float lam, float mu,
-                                               float4 *smem) {
-  const int s = A.tile_start[tile], n_own = A.tile_start[tile + 1] - s;
-  const int64_t h0 = A.hoff[tile], n0 = A.noff[tile];
-  const int H = (int)(A.hoff[tile + 1] - h0), L = (int)(A.noff[tile + 1] - n0);
-  const int nt = n_own + H;
-  // shared memory: displacements (L), strains split in two float4 arrays
-  // (w0..w3 | w4, w5, V, 0) over tile + halo tets, nodal forces of the tile
-  // tets (4 slots x xyz = 12 floats per tet), incidence list and node starts
-  float4 *su = smem;
-  float4 *swa = su + L;
-  float4 *swb = swa + nt;
-  float *sfe = reinterpret_cast<float *>(swb + nt);                  // 12 * n_own
-  uint16_t *sinc = reinterpret_cast<uint16_t *>(sfe + 12 * n_own);  // 4 * n_own
-  uint16_t *snode = sinc + 4 * n_own;                                 // L
+// Shared-memory layout of one tile: displacements (L), strains split in two
+// float4 arrays (w0..w3 | w4, w5, V, 0) over tile + halo tets, nodal forces
+// of the tile tets (4 slots x xyz = 12 floats per tet), incidence list and
+// node starts.
+struct TileView {
+  int n_own, H, L, nt;
+  int64_t h0, n0;
+  float4 *su, *swa, *swb;
+  float *sfe;
+  uint16_t *sinc, *snode;
+};
 
-  // Strains are differences of nodal displacements, and K annihilates
-  // constant fields (the shape-function gradients of a tet sum to zero), so
-  // with FP64 input the tile subtracts the displacement of its first node
-  // before rounding to FP32: the rounding then acts on the small tile-local
-  // differences instead of the full displacements, which removes most of
-  // the cancellation error of the FP32 strains.
-  TU ref[3] = {TU(0), TU(0), TU(0)};
-  if constexpr (sizeof(TU) == 8) {
-    const TU *rp = u + 3 * (int64_t)A.tile_nodes[n0];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) ref[c] = kCoherentU ? __ldcg(rp + c) : __ldg(rp + c);
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < L; i += kTileThreads) {
-    const int64_t node = A.tile_nodes[n0 + i];
-    const TU *up = u + 3 * node;
-    if (kCoherentU)
-      su[i] = make_float4((float)(__ldcg(up) - ref[0]), (float)(__ldcg(up + 1) - ref[1]),
-                          (float)(__ldcg(up + 2) - ref[2]), 0.f);
-    else
-      su[i] = make_float4((float)(__ldg(up) - ref[0]), (float)(__ldg(up + 1) - ref[1]),
-                          (float)(__ldg(up + 2) - ref[2]), 0.f);
-    snode[i] = A.node_inc[n0 + i];
-  }
-  __syncthreads();
+__device__ __forceinline__ TileView tile_view(const TileArgs &A, int tile, float4 *smem) {
+  TileView T;
+  const int s = A.tile_start[tile];
+  T.n_own = A.tile_start[tile + 1] - s;
+  T.h0 = A.hoff[tile];
+  T.n0 = A.noff[tile];
+  T.H = (int)(A.hoff[tile + 1] - T.h0);
+  T.L = (int)(A.noff[tile + 1] - T.n0);
+  T.nt = T.n_own + T.H;
+  T.su = smem;
+  T.swa = T.su + T.L;
+  T.swb = T.swa + T.nt;
+  T.sfe = reinterpret_cast<float *>(T.swb + T.nt);                      // 12 * n_own
+  T.sinc = reinterpret_cast<uint16_t *>(T.sfe + 12 * T.n_own);         // 4 * n_own
+  T.snode = T.sinc + 4 * T.n_own;                                       // L
+  return T;
+}
+
+// strains of the tile's own and halo tets from the displacements in su;
+// also stores the own slots' incidence entries
+__device__ __forceinline__ void tile_strains(const TileArgs &A, const TileRegs &R, const TileView &T) {
 #pragma unroll
   for (int r = 0; r < kTilePer; ++r) {
     const int j = threadIdx.x + r * kTileThreads;
-    if (j < n_own) {
+    if (j < T.n_own) {
       TetGeo G;
       uint2 lc;
       rec_unpack(R.rr[r], G, lc);
       float4 w2[2];
-      strain_to(su, lc, G, w2);
-      swa[j] = w2[0];
-      swb[j] = w2[1];
-      reinterpret_cast<uint2 *>(sinc)[j] = make_uint2(__float_as_uint(R.rr[r][3].z), __float_as_uint(R.rr[r][3].w));
+      strain_to(T.su, lc, G, w2);
+      T.swa[j] = w2[0];
+      T.swb[j] = w2[1];
+      reinterpret_cast<uint2 *>(T.sinc)[j] =
+          make_uint2(__float_as_uint(R.rr[r][3].z), __float_as_uint(R.rr[r][3].w));
     }
   }
-  for (int h = threadIdx.x; h < H; h += kTileThreads) {
+  for (int h = threadIdx.x; h < T.H; h += kTileThreads) {
     TetGeo G;
     uint2 lc;
-    load_rec(A.rec, A.halo_tet[h0 + h], G, lc, nullptr);
-    lc = A.halo_lconn[h0 + h];
+    load_rec(A.rec, A.halo_tet[T.h0 + h], G, lc, nullptr);
+    lc = A.halo_lconn[T.h0 + h];
     float4 w2[2];
-    strain_to(su, lc, G, w2);
-    swa[n_own + h] = w2[0];
-    swb[n_own + h] = w2[1];
+    strain_to(T.su, lc, G, w2);
+    T.swa[T.n_own + h] = w2[0];
+    T.swb[T.n_own + h] = w2[1];
   }
-  __syncthreads();
+}
 
+// face-averaged stress of every own tet and its four nodal force slots;
+// returns this thread's share of the energy sum w . t
+__device__ __forceinline__ double tile_forces(const TileRegs &R, const TileView &T, float lam, float mu) {
   double en = 0.0;
 #pragma unroll
   for (int r = 0; r < kTilePer; ++r) {
     const int j = threadIdx.x + r * kTileThreads;
-    if (j >= n_own) continue;
+    if (j >= T.n_own) continue;
     TetGeo G;
     uint2 lc;
     rec_unpack(R.rr[r], G, lc);
     const uint2 nb2 = make_uint2(__float_as_uint(R.rr[r][3].x), __float_as_uint(R.rr[r][3].y));
     const int nb[4] = {(int)(nb2.x & 0xFFFF), (int)(nb2.x >> 16), (int)(nb2.y & 0xFFFF), (int)(nb2.y >> 16)};
-    const float4 w0 = swa[j], w1 = swb[j];
+    const float4 w0 = T.swa[j], w1 = T.swb[j];
     const float W[6] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y};
     const float Ve = w1.z;
     // face weights kap_a = 1/(4 (V_e + V_nbr)), 1/(4 V_e) on exterior faces
@@ -184,7 +173,7 @@ __device__ __forceinline__ double tile_compute(const TileArgs &A, int tile, cons
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
       if (nb[a] != kNoNbr) {
-        const float4 n0v = swa[nb[a]], n1v = swb[nb[a]];
+        const float4 n0v = T.swa[nb[a]], n1v = T.swb[nb[a]];
         const float k = 0.25f / (Ve + n1v.z);
         ks += k;
         S[0] = fmaf(k, n0v.x, S[0]);
@@ -213,32 +202,81 @@ __device__ __forceinline__ double tile_compute(const TileArgs &A, int tile, cons
       f[3 * a + 1] = G.g[a][0] * st[5] + G.g[a][1] * st[1] + G.g[a][2] * st[3];
       f[3 * a + 2] = G.g[a][0] * st[4] + G.g[a][1] * st[3] + G.g[a][2] * st[2];
     }
-    float4 *fo = reinterpret_cast<float4 *>(sfe + 12 * j);
+    float4 *fo = reinterpret_cast<float4 *>(T.sfe + 12 * j);
     fo[0] = make_float4(f[0], f[1], f[2], f[3]);
     fo[1] = make_float4(f[4], f[5], f[6], f[7]);
     fo[2] = make_float4(f[8], f[9], f[10], f[11]);
   }
+  return en;
+}
+
+// the force at tile node i: its own slots summed in a fixed order with
+// compensation (the element forces at a node nearly cancel); false when the
+// node has no slot in this tile
+__device__ __forceinline__ bool tile_node_force(const TileView &T, int i, float &fx, float &fy, float &fz) {
+  const int nslots = 4 * T.n_own;
+  const int b = T.snode[i], e = (i + 1 < T.L) ? T.snode[i + 1] : nslots;
+  fx = fy = fz = 0.f;
+  if (b == e) return false;
+  float cx = 0.f, cy = 0.f, cz = 0.f;
+  for (int k = b; k < e; ++k) {
+    const int slot = T.sinc[k];
+    const float *fp = T.sfe + 12 * (slot >> 2) + 3 * (slot & 3);
+    const float yx = fp[0] - cx, yy = fp[1] - cy, yz = fp[2] - cz;
+    const float tx = fx + yx, ty = fy + yy, tz = fz + yz;
+    cx = __fsub_rn(__fsub_rn(tx, fx), yx);
+    cy = __fsub_rn(__fsub_rn(ty, fy), yy);
+    cz = __fsub_rn(__fsub_rn(tz, fz), yz);
+    fx = tx;
+    fy = ty;
+    fz = tz;
+  }
+  return true;
+}
+
+// y += K u over one tile (all threads of the block); returns this thread's
+// share of u^T K u.  Starts and ends with a block barrier, so it can be
+// called repeatedly on the same shared memory.
+// kCoherentU: read u through L2 (ld.global.cg) instead of the read-only
+// path; needed when u changes during the kernel (persistent solvers).
+template <class TU, class TY, bool kCoherentU = false>
+__device__ __forceinline__ double tile_compute(const TileArgs &A, int tile, const TileRegs &R,
+                                               const TU *__restrict__ u, TY *__restrict__ y, float lam, float mu,
+                                               float4 *smem) {
+  const TileView T = tile_view(A, tile, smem);
+  // Strains are differences of nodal displacements, and K annihilates
+  // constant fields (the shape-function gradients of a tet sum to zero), so
+  // with FP64 input the tile subtracts the displacement of its first node
+  // before rounding to FP32: the rounding then acts on the small tile-local
+  // differences instead of the full displacements, which removes most of
+  // the cancellation error of the FP32 strains.
+  TU ref[3] = {TU(0), TU(0), TU(0)};
+  if constexpr (sizeof(TU) == 8) {
+    const TU *rp = u + 3 * (int64_t)A.tile_nodes[T.n0];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) ref[c] = kCoherentU ? __ldcg(rp + c) : __ldg(rp + c);
+  }
   __syncthreads();
-  // each tile node sums the forces of its slots (fixed order: deterministic)
-  const int nslots = 4 * n_own;
-  for (int i = threadIdx.x; i < L; i += kTileThreads) {
-    const int b = snode[i], e = (i + 1 < L) ? snode[i + 1] : nslots;
-    if (b == e) continue;
-    // compensated (Kahan) sums: the element forces at a node nearly cancel
-    float fx = 0.f, fy = 0.f, fz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
-    for (int k = b; k < e; ++k) {
-      const int slot = sinc[k];
-      const float *fp = sfe + 12 * (slot >> 2) + 3 * (slot & 3);
-      const float yx = fp[0] - cx, yy = fp[1] - cy, yz = fp[2] - cz;
-      const float tx = fx + yx, ty = fy + yy, tz = fz + yz;
-      cx = __fsub_rn(__fsub_rn(tx, fx), yx);
-      cy = __fsub_rn(__fsub_rn(ty, fy), yy);
-      cz = __fsub_rn(__fsub_rn(tz, fz), yz);
-      fx = tx;
-      fy = ty;
-      fz = tz;
-    }
-    TY *yp = y + 3 * (int64_t)A.tile_nodes[n0 + i];
+  for (int i = threadIdx.x; i < T.L; i += kTileThreads) {
+    const int64_t node = A.tile_nodes[T.n0 + i];
+    const TU *up = u + 3 * node;
+    if (kCoherentU)
+      T.su[i] = make_float4((float)(__ldcg(up) - ref[0]), (float)(__ldcg(up + 1) - ref[1]),
+                            (float)(__ldcg(up + 2) - ref[2]), 0.f);
+    else
+      T.su[i] = make_float4((float)(__ldg(up) - ref[0]), (float)(__ldg(up + 1) - ref[1]),
+                            (float)(__ldg(up + 2) - ref[2]), 0.f);
+    T.snode[i] = A.node_inc[T.n0 + i];
+  }
+  __syncthreads();
+  tile_strains(A, R, T);
+  __syncthreads();
+  const double en = tile_forces(R, T, lam, mu);
+  __syncthreads();
+  for (int i = threadIdx.x; i < T.L; i += kTileThreads) {
+    float fx, fy, fz;
+    if (!tile_node_force(T, i, fx, fy, fz)) continue;
+    TY *yp = y + 3 * (int64_t)A.tile_nodes[T.n0 + i];
     atomicAdd(yp, (TY)fx);
     atomicAdd(yp + 1, (TY)fy);
     atomicAdd(yp + 2, (TY)fz);

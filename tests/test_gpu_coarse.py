@@ -36,17 +36,21 @@ def _system(p):
     return A, b, free
 
 
-@pytest.mark.parametrize("cells,dims", [((12, 3, 3), (4, 2, 2)), ((24, 4, 4), (7, 2, 3)), ((10, 4, 4), (3, 3, 3))])
-def test_coarse_apply_matches_oracle(S, cells, dims):
+# A_c assembled tile by tile, and (probed) by probing the whole operator in
+# colour classes (stride min(5, d) per axis)
+@pytest.mark.parametrize("cells,dims,probed", [((12, 3, 3), (4, 2, 2), False), ((24, 4, 4), (7, 2, 3), False),
+                                               ((10, 4, 4), (3, 3, 3), False), ((24, 4, 4), (7, 2, 3), True),
+                                               ((12, 3, 3), (4, 2, 2), True)])
+def test_coarse_apply_matches_oracle(S, cells, dims, probed):
     p = cantilever(*cells, seed=4)
     A, b, free = _system(p)
     Pi = OC.prolongation(p.mesh.xyz, dims, free)
     Ac = OC.galerkin(A, Pi)
     dinv = free / A.diagonal()
     with S.FsFem(p) as fe:
-        info = S.sfem_coarse_setup(fe.h, patch_dims=dims)
+        info = S.sfem_coarse_setup(fe.h, patch_dims=dims, assembly=1 if probed else 0)
         assert info["patch_dims"] == dims and info["n_coarse"] == 3 * int(np.prod(dims))
-        assert info["probes"] == 3 * int(np.prod([min(5, d) for d in dims]))
+        assert info["probes"] == (3 * int(np.prod([min(5, d) for d in dims])) if probed else 0)
         rng = np.random.default_rng(5)
         r = rng.normal(size=fe.ndof) * free
         z = torch.zeros(fe.ndof, dtype=torch.float64, device="cuda")

@@ -272,6 +272,20 @@ static void apply_op64(Ctx &c, int op, const double *x, double *y) {
     apply_mf64(c, x, y, 1, nullptr);
 }
 
+// WHILE-node condition of the iteration graph: another iteration while the
+// solver is not done and the guard (body executions this launch) is below
+// its limit, so the loop ends whatever state the scalars are in
+__global__ void k_loop_cond(cudaGraphConditionalHandle h, const int *done, unsigned int *guard) {
+  const unsigned int n = guard[0] + 1;
+  guard[0] = n;
+  cudaGraphSetConditional(h, (*done == 0 && n < guard[1]) ? 1u : 0u);
+}
+
+__global__ void k_guard_reset(unsigned int *guard, unsigned int limit) {
+  guard[0] = 0;
+  guard[1] = limit;
+}
+
 // ---- one CG run (PCG64 or the FP32 inner solve) ----------------------------
 template <class TX, class TR, class TP>
 struct CgRun {
@@ -282,10 +296,66 @@ struct CgRun {
   cudaGraphExec_t exec = nullptr;
   cudaGraph_t graph = nullptr;
 
+  // device-side loop: one graph launch runs iterations until done (a
+  // conditional WHILE node); else captured chunks of `chunk` iterations
+  bool looped = false;
+  unsigned int *guard = nullptr;  // [0] body executions of a launch, [1] limit
+
   CgRun(Ctx &c_, PcgVecs<TX, TR, TP> v_, int op_, int chunk_) : c(c_), v(v_), op(op_), chunk(chunk_) {}
   ~CgRun() {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
+    if (guard) c.mem.drop(guard);
+  }
+
+  // the iteration as the body of a WHILE node; false (and no graph) when
+  // the runtime cannot build it
+  bool build_loop_graph() {
+    cudaGraph_t g = nullptr;
+    cudaGraphConditionalHandle hnd;
+    cudaGraphNodeParams cp = {};
+    cudaGraphNode_t node;
+    if (cudaGraphCreate(&g, 0) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    cp.type = cudaGraphNodeTypeConditional;
+    if (cudaGraphConditionalHandleCreate(&hnd, g, 1, cudaGraphCondAssignDefault) != cudaSuccess ||
+        (cp.conditional.handle = hnd, cp.conditional.type = cudaGraphCondTypeWhile, cp.conditional.size = 1,
+         cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp) != cudaSuccess) ||
+        cudaStreamBeginCaptureToGraph(c.cap_stream, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      cudaGraphDestroy(g);
+      return false;
+    }
+    if (!guard) guard = c.mem.get<unsigned int>(2);
+    set_capturing(true);
+    try {
+      enqueue_iteration(c.cap_stream);
+      k_loop_cond<<<1, 1, 0, c.cap_stream>>>(hnd, &c.scal->done, guard);
+      SFEM_CUDA(cudaGetLastError());
+    } catch (...) {
+      set_capturing(false);
+      cudaGraph_t tmp = nullptr;
+      cudaStreamEndCapture(c.cap_stream, &tmp);
+      cudaGraphDestroy(g);
+      throw;
+    }
+    set_capturing(false);
+    cudaGraph_t body = nullptr;
+    if (cudaStreamEndCapture(c.cap_stream, &body) != cudaSuccess ||
+        cudaGraphInstantiate(&exec, g, 0) != cudaSuccess) {
+      cudaGetLastError();
+      if (exec) cudaGraphExecDestroy(exec);
+      exec = nullptr;
+      cudaGraphDestroy(g);
+      return false;
+    }
+    graph = g;
+    SFEM_CUDA(cudaGraphGetNodes(cp.conditional.phGraph_out[0], nullptr, &graph_nodes));
+    looped = true;
+    return true;
   }
 
   void enqueue_iteration(cudaStream_t st) {
@@ -316,6 +386,7 @@ struct CgRun {
   size_t graph_nodes = 0;
 
   void build_graph() {
+    if (build_loop_graph()) return;
     SFEM_CUDA(cudaStreamBeginCapture(c.cap_stream, cudaStreamCaptureModeThreadLocal));
     set_capturing(true);
     try {
@@ -356,6 +427,19 @@ struct CgRun {
   // run captured chunks until the device sets done; returns the scalars
   SolveScalars resume(int max_iter) {
     if (!exec) build_graph();
+    if (looped) {
+      // one launch runs the iterations until the device flag says done
+      SolveScalars out;
+      unsigned int hg[2] = {0, 0};
+      k_guard_reset<<<1, 1, 0, c.stream>>>(guard, (unsigned int)max_iter + 2u);
+      SFEM_CHECK_LAUNCH();
+      SFEM_CUDA(cudaGraphLaunch(exec, c.stream));
+      SFEM_CUDA(cudaMemcpyAsync(&out, c.scal, sizeof out, cudaMemcpyDeviceToHost, c.stream));
+      SFEM_CUDA(cudaMemcpyAsync(hg, guard, sizeof hg, cudaMemcpyDeviceToHost, c.stream));
+      SFEM_CUDA(cudaStreamSynchronize(c.stream));
+      count_launches((int64_t)graph_nodes * hg[0]);
+      return out;
+    }
     SolveScalars *h = c.h_scal;
     cudaEvent_t ev[2];
     SFEM_CUDA(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));

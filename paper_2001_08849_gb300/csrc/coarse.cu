@@ -36,7 +36,7 @@
 namespace sfem {
 
 constexpr int kCB = 64;           // dense block order
-constexpr int kRestrictThreads = 128;
+constexpr int kRestrictThreads = 256;
 
 // ---- restriction -----------------------------------------------------------
 
@@ -92,24 +92,12 @@ __global__ void k_cs_gather(CoarseDev cs, const int *done) {
     cs.rc[t] = 0.f;
     return;
   }
-  const int j = t / 3, c = t % 3;
-  const int jz = j % cs.d[2], jy = (j / cs.d[2]) % cs.d[1], jx = j / (cs.d[1] * cs.d[2]);
+  // the (cell, corner) entries of this centre, listed at setup in a fixed order
+  const int *g = cs.glist + 8 * (int64_t)t;
   double s = 0.0;
-  for (int ix = max(0, jx - 1); ix <= min(cs.cd[0] - 1, jx); ++ix)
-    for (int bx = 0; bx < 2; ++bx) {
-      if (min(ix + bx, cs.d[0] - 1) != jx) continue;
-      for (int iy = max(0, jy - 1); iy <= min(cs.cd[1] - 1, jy); ++iy)
-        for (int by = 0; by < 2; ++by) {
-          if (min(iy + by, cs.d[1] - 1) != jy) continue;
-          for (int iz = max(0, jz - 1); iz <= min(cs.cd[2] - 1, jz); ++iz)
-            for (int bz = 0; bz < 2; ++bz) {
-              if (min(iz + bz, cs.d[2] - 1) != jz) continue;
-              const int cell = (ix * cs.cd[1] + iy) * cs.cd[2] + iz;
-              const int k = (bx << 2) | (by << 1) | bz;
-              s += (double)cs.cellsum[24 * (int64_t)cell + 3 * k + c];
-            }
-        }
-    }
+#pragma unroll
+  for (int e = 0; e < 8; ++e)
+    if (g[e] >= 0) s += (double)cs.cellsum[g[e]];
   cs.rc[t] = (float)s;
 }
 
@@ -120,11 +108,19 @@ __global__ void __launch_bounds__(256) k_cs_gemv(CoarseDev cs, const int *done) 
   if (row >= cs.npad) return;
   const float4 *Cr = reinterpret_cast<const float4 *>(cs.C + (int64_t)row * cs.npad);
   const float4 *r4 = reinterpret_cast<const float4 *>(cs.rc);
-  float s = 0.f;
-  for (int q = lane; q < cs.npad / 4; q += 32) {
-    const float4 a = Cr[q], b = r4[q];
-    s = fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, fmaf(a.w, b.w, s))));
+  const int n4 = cs.npad / 4;  // a multiple of 16
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int q0 = lane; q0 < n4; q0 += 128) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int q = q0 + 32 * u;
+      if (q < n4) {
+        const float4 a = Cr[q], b = r4[q];
+        acc[u] = fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, fmaf(a.w, b.w, acc[u]))));
+      }
+    }
   }
+  float s = (acc[0] + acc[1]) + (acc[2] + acc[3]);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
   if (lane == 0) cs.yc[row] = s;
@@ -619,7 +615,7 @@ static void setup_coarse(Ctx &c, const sfem_coarse_opts *opts) {
   cs.npad = (cs.nc + kCB - 1) / kCB * kCB;
   cs.ncell = cs.cd[0] * cs.cd[1] * cs.cd[2];
   // interpolation cell and fractions of every node; nodes grouped by cell
-  std::vector<int32_t> cell(c.n_nodes), off(cs.ncell + 1, 0), nodes(c.n_nodes);
+  std::vector<int32_t> cell(c.n_nodes), cinfo(c.n_nodes), off(cs.ncell + 1, 0), nodes(c.n_nodes);
   std::vector<float> frac(3 * c.n_nodes);
   for (int64_t i = 0; i < c.n_nodes; ++i) {
     int i0[3];
@@ -630,7 +626,32 @@ static void setup_coarse(Ctx &c, const sfem_coarse_opts *opts) {
       frac[3 * i + a] = (float)(cs.d[a] > 1 ? t - i0[a] : 0.0);
     }
     cell[i] = (i0[0] * cs.cd[1] + i0[1]) * cs.cd[2] + i0[2];
+    cinfo[i] = ((i0[0] * cs.d[1] + i0[1]) * cs.d[2] + i0[2]) | ((i0[0] + 1 < cs.d[0]) << 24) |
+               ((i0[1] + 1 < cs.d[1]) << 25) | ((i0[2] + 1 < cs.d[2]) << 26);
     off[cell[i] + 1] += 1;
+  }
+  // per coarse DOF the cellsum entries (cell, corner) that restrict onto it
+  std::vector<int32_t> glist(8 * (size_t)cs.nc, -1);
+  for (int j = 0; j < (int)P; ++j) {
+    const int jz = j % cs.d[2], jy = (j / cs.d[2]) % cs.d[1], jx = j / (cs.d[1] * cs.d[2]);
+    int n = 0;
+    for (int ix = std::max(0, jx - 1); ix <= std::min(cs.cd[0] - 1, jx); ++ix)
+      for (int bx = 0; bx < 2; ++bx) {
+        if (std::min(ix + bx, cs.d[0] - 1) != jx) continue;
+        for (int iy = std::max(0, jy - 1); iy <= std::min(cs.cd[1] - 1, jy); ++iy)
+          for (int by = 0; by < 2; ++by) {
+            if (std::min(iy + by, cs.d[1] - 1) != jy) continue;
+            for (int iz = std::max(0, jz - 1); iz <= std::min(cs.cd[2] - 1, jz); ++iz)
+              for (int bz = 0; bz < 2; ++bz) {
+                if (std::min(iz + bz, cs.d[2] - 1) != jz) continue;
+                const int q = (ix * cs.cd[1] + iy) * cs.cd[2] + iz;
+                const int k = (bx << 2) | (by << 1) | bz;
+                SFEM_REQUIRE(n < 8, SFEM_EINVAL, "coarse gather list overflow");
+                for (int cc = 0; cc < 3; ++cc) glist[8 * (size_t)(3 * j + cc) + n] = 24 * q + 3 * k + cc;
+                ++n;
+              }
+          }
+      }
   }
   for (int q = 0; q < cs.ncell; ++q) off[q + 1] += off[q];
   {
@@ -644,6 +665,11 @@ static void setup_coarse(Ctx &c, const sfem_coarse_opts *opts) {
   SFEM_CUDA(cudaMemcpyAsync(d_nodes, nodes.data(), nodes.size() * 4, cudaMemcpyHostToDevice, c.stream));
   SFEM_CUDA(cudaMemcpyAsync(d_off, off.data(), off.size() * 4, cudaMemcpyHostToDevice, c.stream));
   SFEM_CUDA(cudaMemcpyAsync(d_frac, frac.data(), frac.size() * 4, cudaMemcpyHostToDevice, c.stream));
+  int32_t *d_cinfo = c.mem.get<int32_t>(c.n_nodes), *d_glist = c.mem.get<int32_t>(glist.size());
+  SFEM_CUDA(cudaMemcpyAsync(d_cinfo, cinfo.data(), cinfo.size() * 4, cudaMemcpyHostToDevice, c.stream));
+  SFEM_CUDA(cudaMemcpyAsync(d_glist, glist.data(), glist.size() * 4, cudaMemcpyHostToDevice, c.stream));
+  cs.cinfo = d_cinfo;
+  cs.glist = d_glist;
   cs.cell = d_cell;
   cs.cnodes = d_nodes;
   cs.coff = d_off;

@@ -18,7 +18,11 @@ struct CoarseDev {
   int cd[3];               // interpolation cells per axis, max(d - 1, 1)
   int nc, npad, ncell;     // coarse DOFs (3 P), padded order of C, cells
   const int32_t *cell;     // n_nodes: interpolation cell of each node
+  const int32_t *cinfo;    // n_nodes: centre of the cell's lower corner (bits 0-23) and
+                           // whether the upper corner is a different centre on x, y, z
+                           // (bits 24, 25, 26; not where the grid has one centre)
   const float *frac;       // n_nodes x 3: fractional position in the cell
+  const int32_t *glist;    // nc x 8: cellsum entries summed into each coarse DOF (-1: none)
   const int32_t *cnodes;   // node ids grouped by cell (ascending within a cell)
   const int32_t *coff;     // ncell + 1
   float *cellsum;          // ncell x 24 partial restrictions (8 corners x 3)
@@ -44,11 +48,17 @@ __device__ __forceinline__ int cs_corner(const CoarseDev &cs, int cell, int k) {
 __device__ __forceinline__ float cs_prolong(const CoarseDev &cs, int64_t i) {
   const int64_t node = i / 3;
   const int c = (int)(i - 3 * node);
-  const int cell = cs.cell[node];
+  const int ci = cs.cinfo[node];
+  const int base = ci & 0xFFFFFF;
+  const int ox = ((ci >> 24) & 1) ? 3 * cs.d[1] * cs.d[2] : 0;
+  const int oy = ((ci >> 25) & 1) ? 3 * cs.d[2] : 0;
+  const int oz = ((ci >> 26) & 1) ? 3 : 0;
   const float f[3] = {cs.frac[3 * node], cs.frac[3 * node + 1], cs.frac[3 * node + 2]};
+  const float *y = cs.yc + 3 * base + c;
   float s = 0.f;
 #pragma unroll
-  for (int k = 0; k < 8; ++k) s = fmaf(cs_weight(f, k), cs.yc[3 * cs_corner(cs, cell, k) + c], s);
+  for (int k = 0; k < 8; ++k)
+    s = fmaf(cs_weight(f, k), y[((k & 4) ? ox : 0) + ((k & 2) ? oy : 0) + ((k & 1) ? oz : 0)], s);
   return s;
 }
 

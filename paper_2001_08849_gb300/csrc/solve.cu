@@ -21,6 +21,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 
 #include "reduce.cuh"
 #include "sfem_internal.cuh"
@@ -43,6 +44,7 @@ struct PcgVecs {
   int64_t n;
   bool coarse = false;  // two-level preconditioner: z = D^-1 r + P Pi yc
   CoarseDev cs{};
+  TP *z = nullptr;      // two-level: z of the current r (written by k_pcg_zr)
 };
 
 // preconditioned residual of DOF i (the coarse correction yc of the current
@@ -151,6 +153,7 @@ __global__ void __launch_bounds__(kVecBlock) k_pcg_update(PcgVecs<TX, TR, TP> v,
   const TR ar = (TR)alpha;
   double rz = 0.0, rr = 0.0;
   const bool coarse = v.coarse;
+#pragma unroll 4
   for (int64_t i = (int64_t)blockIdx.x * kVecBlock + threadIdx.x; i < v.n; i += (int64_t)gridDim.x * kVecBlock) {
     v.x[i] += ax * (TX)v.p[i];
     const TR ri = v.dmask[i] ? v.r[i] - ar * (TR)v.q[i] : TR(0);
@@ -196,9 +199,12 @@ __global__ void __launch_bounds__(kVecBlock) k_pcg_zr(PcgVecs<TX, TR, TP> v, Sol
                                                       unsigned int *ticket) {
   if (S->done) return;
   double rz = 0.0;
+#pragma unroll 4
   for (int64_t i = (int64_t)blockIdx.x * kVecBlock + threadIdx.x; i < v.n; i += (int64_t)gridDim.x * kVecBlock) {
     const TP ri = (TP)v.r[i];
-    rz += (double)(precond_z(v, i, ri) * ri);
+    const TP zi = precond_z(v, i, ri);
+    v.z[i] = zi;
+    rz += (double)(zi * ri);
   }
   double vv[1] = {rz};
   if (grid_sum<kVecBlock, 1>(vv, partials, ticket, nullptr) && threadIdx.x == 0) {
@@ -217,6 +223,15 @@ __global__ void __launch_bounds__(kVecBlock) k_pcg_direction(PcgVecs<TX, TR, TP>
                                                              bool zero_q) {
   if (S->done) return;
   const TP b = (TP)S->beta;
+  if (v.coarse) {  // z was stored by k_pcg_zr
+#pragma unroll 4
+    for (int64_t i = (int64_t)blockIdx.x * kVecBlock + threadIdx.x; i < v.n; i += (int64_t)gridDim.x * kVecBlock) {
+      v.p[i] = v.z[i] + b * v.p[i];
+      if (zero_q) v.q[i] = TP(0);
+    }
+    return;
+  }
+#pragma unroll 4
   for (int64_t i = (int64_t)blockIdx.x * kVecBlock + threadIdx.x; i < v.n; i += (int64_t)gridDim.x * kVecBlock) {
     v.p[i] = precond_z(v, i, (TP)v.r[i]) + b * v.p[i];
     if (zero_q) v.q[i] = TP(0);
@@ -284,6 +299,17 @@ __global__ void k_loop_cond(cudaGraphConditionalHandle h, const int *done, unsig
 __global__ void k_guard_reset(unsigned int *guard, unsigned int limit) {
   guard[0] = 0;
   guard[1] = limit;
+}
+
+// Conditional graph nodes hide their kernels from kernel-level profilers;
+// SFEM_GRAPH_LOOP=0 in the environment selects the captured chunks instead
+// (same kernels and arithmetic, host polling between chunks).
+static bool loop_graphs_enabled() {
+  static const bool on = [] {
+    const char *e = std::getenv("SFEM_GRAPH_LOOP");
+    return !(e && e[0] == '0');
+  }();
+  return on;
 }
 
 // ---- one CG run (PCG64 or the FP32 inner solve) ----------------------------
@@ -386,7 +412,7 @@ struct CgRun {
   size_t graph_nodes = 0;
 
   void build_graph() {
-    if (build_loop_graph()) return;
+    if (loop_graphs_enabled() && build_loop_graph()) return;
     SFEM_CUDA(cudaStreamBeginCapture(c.cap_stream, cudaStreamCaptureModeThreadLocal));
     set_capturing(true);
     try {
@@ -506,12 +532,6 @@ void solve_impl(Ctx &c, const double *f_extra, double *u, const sfem_solve_opts 
     SFEM_REQUIRE(o.kind == SFEM_SOLVE_PCG64 || (o.kind == SFEM_SOLVE_IR32_64 && o.fp32_vectors == 0), SFEM_EINVAL,
                  "the coarse correction works with PCG64 and with IR32_64 on FP64 vectors");
   }
-  auto with_coarse = [&](PcgVecs<double, double, double> &vv) {
-    if (coarse) {
-      vv.coarse = true;
-      vv.cs = c.coarse->dev;
-    }
-  };
 
   cudaEvent_t e0, e1;
   SFEM_CUDA(cudaEventCreate(&e0));
@@ -519,6 +539,14 @@ void solve_impl(Ctx &c, const double *f_extra, double *u, const sfem_solve_opts 
   SFEM_CUDA(cudaEventRecord(e0, c.stream));
 
   SolveBuffers B(c);
+  double *zbuf = coarse ? B.get<double>(n) : nullptr;
+  auto with_coarse = [&](PcgVecs<double, double, double> &vv) {
+    if (coarse) {
+      vv.coarse = true;
+      vv.cs = c.coarse->dev;
+      vv.z = zbuf;
+    }
+  };
   // total load f (+ f_extra) and ||b||
   double *ftot = B.get<double>(n);
   SFEM_CUDA(cudaMemcpyAsync(ftot, c.f + (int64_t)o.rhs * n, n * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));

@@ -8,9 +8,9 @@ by +/-0.1h (seed 2), E = 210 GPa, nu = 0.3, x = 0 clamped, traction
 TetGen meshes of Table 3.
 
 One step = one whole solve through the C ABI: sfem_mesh_setup (FP64
-geometry, topology, smoothing domains, loads, BCs) + sfem_solve to a FP64
-true relative residual of 1e-8 with the FP32-inner / FP64-refined solver +
-sfem_destroy.  `value` is solves per second with the inputs resident in HBM
+geometry, topology, smoothing domains, loads, BCs) + sfem_coarse_setup (the
+two-level preconditioner) + sfem_solve to a FP64 true relative residual of
+1e-8 with the FP32-inner / FP64-refined solver + sfem_destroy.  `value` is solves per second with the inputs resident in HBM
 (the metric's time-to-solve is ms_per_step); `e2e` is the same with host
 inputs and the displacement copied back, through the same API.
 
@@ -40,11 +40,15 @@ TOL = 1e-8
 # algorithmic bytes of one FP32 matrix-free operator application (the
 # per-unit figure of the tet-centric matrix-free form): per tet connectivity
 # 16 + neighbour ids 16 + FP32 reduced gradient 36 + volume 4 = 72 B, and per
-# DOF u read + y written: 8 + 8 with the FP64 vectors of the mixed-precision
-# solve (the kernel timed for the roofline), 4 + 4 with FP32 vectors
+# DOF u read + y written: 4 + 4 with the FP32 inner vectors of the timed
+# solve (the kernel timed for the roofline), 8 + 8 with FP64 vectors
 ALG_BYTES_PER_TET = 16 + 16 + 36 + 4
-ALG_BYTES_PER_DOF = 16
-ALG_BYTES_PER_DOF_F32 = 8
+ALG_BYTES_PER_DOF = 8
+ALG_BYTES_PER_DOF_F64 = 16
+# inner CG vectors of the timed solve: FP32 r, p, q, z with an FP64
+# correction (as many iterations as FP64 vectors with the two-level
+# preconditioner, half the vector traffic)
+FP32_VECTORS = 3
 
 
 def _env_int(name, default):
@@ -353,8 +357,10 @@ def main():
     # (26 x 6 x 6 centres), with 34 x 6 x 6 the fastest coarse setup + solve of
     # a sweep (135 / 134 ms; 26x4x4: 155, 26x3x3: 188, 40x8x8: 159)
     coarse_dims = tuple(-(-(c + 1) // 8) for c in CELLS)
-    opts_dev = S.solve_opts(kind=S.SFEM_SOLVE_IR32_64, op64=S.SFEM_OP_MF64, tol=TOL, u_on_device=True, precond=1)
-    opts_host = S.solve_opts(kind=S.SFEM_SOLVE_IR32_64, op64=S.SFEM_OP_MF64, tol=TOL, u_on_device=False, precond=1)
+    opts_dev = S.solve_opts(kind=S.SFEM_SOLVE_IR32_64, op64=S.SFEM_OP_MF64, tol=TOL, u_on_device=True, precond=1,
+                            fp32_vectors=FP32_VECTORS)
+    opts_host = S.solve_opts(kind=S.SFEM_SOLVE_IR32_64, op64=S.SFEM_OP_MF64, tol=TOL, u_on_device=False, precond=1,
+                             fp32_vectors=FP32_VECTORS)
     coarse_infos = []
     stream = torch.cuda.current_stream()
     infos = []
@@ -363,6 +369,7 @@ def main():
         h, k = S.sfem_mesh_setup(*dev[:2], prob.E, prob.nu, *dev[2:], inputs_on_device=True)
         coarse_infos.append(S.sfem_coarse_setup(h, patch_dims=coarse_dims))
         info = S.sfem_solve(h, u_dev, opts_dev)
+        info["mesh_setup_ms"] = S.sfem_get_info(h)["setup_ms"]
         infos.append(info)
         if keep:
             return h, k
@@ -429,8 +436,8 @@ def main():
 
     # dominant kernel: the FP32 matrix-free operator of the inner CG
     h, keep = step_device(keep=True)
-    ms_mf32 = S.sfem_time_operator(h, S.SFEM_OP_MF32_F64, reps=50)   # as launched inside the solve
-    ms_mf32_f32 = S.sfem_time_operator(h, S.SFEM_OP_MF32, reps=50)
+    ms_mf32 = S.sfem_time_operator(h, S.SFEM_OP_MF32, reps=50)   # as launched inside the solve
+    ms_mf32_f64 = S.sfem_time_operator(h, S.SFEM_OP_MF32_F64, reps=50)
     ms_mf64 = S.sfem_time_operator(h, S.SFEM_OP_MF64, reps=10)
     S.sfem_destroy(h)
     alg_bytes = ALG_BYTES_PER_TET * m.n_tets + ALG_BYTES_PER_DOF * ndof
@@ -445,14 +452,15 @@ def main():
     try:
         tr = json.load(open(os.path.join(ROOT, "profiles", "mf32_traffic.json")))
         from paper_2001_08849_gb300.opbench import tiled_source_sha
-        if tr.get("source_sha256") == tiled_source_sha() and tr.get("ndof") == ndof:
+        if (tr.get("source_sha256") == tiled_source_sha() and tr.get("ndof") == ndof
+                and tr.get("op") == "mf32"):
             traffic = tr["dram_bytes_per_apply"]
     except Exception:
         pass
 
     forms = {}
     if not args.no_forms and rank == 0:
-        def timed_form(kind, op64, precond, assemble):
+        def timed_form(kind, op64, precond, assemble, fp32_vectors=0):
             """setup (+ CSR assembly) (+ coarse space) + solve of the same
             workload, timed once with CUDA events on the stream"""
             torch.cuda.synchronize()
@@ -465,7 +473,7 @@ def main():
                 S.sfem_coarse_setup(hh, patch_dims=coarse_dims)
             x = torch.zeros(ndof, dtype=torch.float64, device="cuda")
             inf = S.sfem_solve(hh, x, S.solve_opts(kind=kind, op64=op64, tol=TOL, u_on_device=True,
-                                                    precond=precond), check=False)
+                                                    precond=precond, fp32_vectors=fp32_vectors), check=False)
             eb.record(stream)
             torch.cuda.synchronize()
             out = {"time_to_solve_s": ea.elapsed_time(eb) / 1e3, "iterations": inf["iterations"],
@@ -480,6 +488,7 @@ def main():
         forms["pcg64_csr_jacobi"] = timed_form(S.SFEM_SOLVE_PCG64, S.SFEM_OP_CSR64, 0, True)
         forms["pcg64_csr_two_level"] = timed_form(S.SFEM_SOLVE_PCG64, S.SFEM_OP_CSR64, 1, True)
         forms["ir32_64_jacobi"] = timed_form(S.SFEM_SOLVE_IR32_64, S.SFEM_OP_MF64, 0, False)
+        forms["ir32_64_two_level_fp64_vectors"] = timed_form(S.SFEM_SOLVE_IR32_64, S.SFEM_OP_MF64, 1, False, 0)
         forms["ir32_64_two_level"] = {"time_to_solve_s": t_dev / args.steps, "iterations": iters[-1],
                                       "true_relres": relres, "coarse_dims": list(coarse_dims),
                                       "coarse_setup_ms": float(np.mean([ci["setup_ms"] for ci in coarse_infos])),
@@ -504,23 +513,26 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": f"Kuhn cantilever {nx}x{ny}x{nz} cells x 6 = {m.n_tets} tets, "
                                    f"{m.n_nodes} nodes, {ndof} DOF, jitter seed {SEED}",
-                       "solver": "IR32_64 with the two-level preconditioner: FP64 residual/update, "
-                                 "FP32 matrix-free operator inside CG on FP64 vectors, Jacobi + Galerkin "
-                                 f"coarse correction on {coarse_dims[0]}x{coarse_dims[1]}x{coarse_dims[2]} "
-                                 "patch centres",
+                       "solver": "IR32_64 with the two-level preconditioner: FP64 true residual and "
+                                 "correction, FP32 matrix-free operator and FP32 CG vectors inside, Jacobi + "
+                                 "Galerkin coarse correction on "
+                                 f"{coarse_dims[0]}x{coarse_dims[1]}x{coarse_dims[2]} patch centres",
                        "tol": TOL, "step": "sfem_mesh_setup + sfem_coarse_setup + sfem_solve + sfem_destroy",
                        "l2": "no flush: operator data per step exceeds the 129 MB L2",
                        "parallelism": f"replicas x{world}"},
             "time_to_solve_s": t_dev / args.steps,
             "iterations": iters, "true_relres_max": relres,
             "operator_gdof_per_s": ndof / (ms_mf32 * 1e-3) / 1e9,
-            "operator_gdof_per_s_fp32_vectors": ndof / (ms_mf32_f32 * 1e-3) / 1e9,
+            "operator_gdof_per_s_fp64_vectors": ndof / (ms_mf32_f64 * 1e-3) / 1e9,
+            "mesh_setup_ms": float(np.median([i["mesh_setup_ms"] for i in infos])),
+            "coarse_setup_ms": float(np.median([ci["setup_ms"] for ci in coarse_infos])),
+            "solve_ms": float(np.median([i["solve_ms"] for i in infos])),
             "operator_gdof_per_s_fp64_mf": ndof / (ms_mf64 * 1e-3) / 1e9,
             "gpu_launches": int(launches),
             "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": int(h2d_bytes),
                     "d2h_bytes_per_step": int(d2h_bytes)},
-            "roofline": {"kernel": "k_mf32_tiled<double,double> (FP32 matrix-free operator on the FP64 "
-                                   "CG vectors, one launch per inner iteration)",
+            "roofline": {"kernel": "k_mf32_tiled<float,float> (FP32 matrix-free operator on the FP32 "
+                                   "inner CG vectors, one launch per inner iteration)",
                          "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "alg_bytes_per_apply": alg_bytes, "ms_per_apply": ms_mf32,

@@ -118,7 +118,9 @@ typedef struct sfem_solve_opts {
   int check_every;     /* iterations between host convergence checks (0: 32) */
   const void *learned; /* FPCG_LEARNED: an sfem_learned handle (NULL: flexible CG with
                           the Jacobi preconditioner alone) */
-  int fp32_vectors;    /* IR vectors: 0 FP64 p, q, r (default); 1 all FP32; 2 FP32 p, q and FP64 r */
+  int fp32_vectors;    /* IR vectors: 0 FP64 p, q, r (default); 1 all FP32; 2 FP32 p, q and FP64 r;
+                          3 FP32 r, p, q with an FP64 correction (with precond 1, the choice
+                          for the two-level solve: as many iterations as 0, half the traffic) */
   int learned_window;  /* FPCG_LEARNED stagnation guard: the correction is switched off for
                           the rest of the solve when ||r|| has not fallen 10% below its best
                           value for this many iterations (0: 100) */
@@ -127,7 +129,7 @@ typedef struct sfem_solve_opts {
                           is switched off when ||r|| lies more than 30x above the
                           log-linear line from ||r_0|| to the tolerance over this many
                           iterations (0: no pace guard) */
-  int precond;         /* PCG64 and IR32_64 (FP64 vectors): 0 Jacobi; 1 Jacobi plus the
+  int precond;         /* PCG64 and IR32_64 (fp32_vectors 0 or 3): 0 Jacobi; 1 Jacobi plus the
                           Galerkin coarse correction of sfem_coarse_setup */
   int reserved[2];
 } sfem_solve_opts;
@@ -263,7 +265,10 @@ typedef struct sfem_coarse_opts {
                           the coarse functions of the cells it touches; probing is used for
                           a tile that touches more than 4 cells on an axis); 1 probing with
                           the whole operator in colour classes */
-  int reserved[7];
+  int factor;          /* Cholesky of A_c: 0 FP32 (C is FP32 in any case; cond(A_c) ~ 1e5 on
+                          the 2M-tet beam), switching to FP64 on a non-positive pivot;
+                          1 FP64 */
+  int reserved[6];
 } sfem_coarse_opts;
 
 int sfem_coarse_setup(sfem_ctx *ctx, const sfem_coarse_opts *opts);

@@ -179,30 +179,55 @@ constexpr int kGalMaxCentres = 125; // centres of those cells (5 per axis)
 // to each coarse function P Pi_J whose centre is a corner of a cell touched
 // by the tile's nodes, and restricts the tile's masked nodal forces against
 // the same centres; the contributions of all tiles add up to
-// A_c = Pi^T P K P Pi (FP64 atomics into the dense A_c).  The tile's nodes
-// are grouped by cell once (stable order), so each (cell, corner,
-// component) restriction entry is a fixed-order sum by one thread.
+// A_c = Pi^T P K P Pi (FP64 atomics into the dense A_c).
+//
+// The three components of one centre share a pass where every tile node has
+// all or none of its DOFs free (the clamped beam: every tile): the field
+// u = w_J e_c has displacement gradient e_c (x) grad w_J, so one pass forms
+// V grad w_J per tet (own and halo), its face average over the smoothing
+// domains, and from it the smoothed strain of each component (e_c (x) g in
+// Voigt form); only stress, nodal forces and restriction run per component.
+// Tiles with partly prescribed nodes apply the operator per (centre,
+// component).
+//
+// Restriction: the tile's nodes are grouped by interpolation cell (stable
+// order); one warp per cell sums w_k(x) f(x) over its nodes for the cell's
+// 8 corners and 3 components, and each local centre sums the (cell,
+// corner) entries that map to it in a fixed order.
 // Dynamic shared memory: the tile layout (stage_off float4 units), then per
-// tile node a float4 stage (cell id with the free-DOF mask in bits 28-30, and
-// the three fractions) and a uint16 order.  Sets *overflow for a tile that
-// touches more than 4 cells on an axis.
+// tile node a float4 stage (local cell: index in bits 0-7, coordinates in
+// bits 8-13; free-DOF mask in bits 28-30; the three fractions) and a uint16
+// order.  Sets *overflow for a tile that touches more than 4 cells on an
+// axis.
+constexpr int kGalWarps = kTileThreads / 32;
+
+// 1D hat weight of local centre coordinate jc for a node in local cell
+// coordinate lc at fraction f (upper corner clamped to the last centre)
+__device__ __forceinline__ float gal_w1(int jc, int lc, int c0, int d, float f) {
+  const int lo = c0 + lc, hi = min(lo + 1, d - 1), j = c0 + jc;
+  return (j == lo ? 1.f - f : 0.f) + (j == hi ? f : 0.f);
+}
+
 __global__ void __launch_bounds__(kTileThreads, 3) k_cs_galerkin(TileArgs A, CoarseDev cs,
                                                               const uint8_t *__restrict__ dmask, float lam,
                                                               float mu, int stage_off, double *__restrict__ Ac,
                                                               int *overflow) {
   extern __shared__ float4 smem_t[];
-  __shared__ int bb[6], coff[kGalMaxCells + 1];
-  __shared__ float acc[3 * kGalMaxCentres];
+  __shared__ int bb[6], coff[kGalMaxCells + 1], mixed;
+  __shared__ float cellacc[kGalMaxCells][24];
+  __shared__ short gat[kGalMaxCentres][8];
   const int tile = blockIdx.x;
   TileRegs R;
   tile_load(A, tile, R);
   const TileView T = tile_view(A, tile, smem_t);
   float4 *stage = smem_t + stage_off;
   uint16_t *order = reinterpret_cast<uint16_t *>(stage + T.L);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (threadIdx.x < 3) {
     bb[threadIdx.x] = 1 << 30;
     bb[3 + threadIdx.x] = -1;
   }
+  if (threadIdx.x == 0) mixed = 0;
   __syncthreads();
   for (int i = threadIdx.x; i < T.L; i += kTileThreads) {
     const int64_t node = A.tile_nodes[T.n0 + i];
@@ -211,6 +236,7 @@ __global__ void __launch_bounds__(kTileThreads, 3) k_cs_galerkin(TileArgs A, Coa
     stage[i] = make_float4(__int_as_float(cell | (m << 28)), cs.frac[3 * node], cs.frac[3 * node + 1],
                            cs.frac[3 * node + 2]);
     T.snode[i] = A.node_inc[T.n0 + i];
+    if (m != 0 && m != 7) mixed = 1;
     const int iz = cell % cs.cd[2], iy = (cell / cs.cd[2]) % cs.cd[1], ix = cell / (cs.cd[1] * cs.cd[2]);
     atomicMin(&bb[0], ix);
     atomicMin(&bb[1], iy);
@@ -228,50 +254,102 @@ __global__ void __launch_bounds__(kTileThreads, 3) k_cs_galerkin(TileArgs A, Coa
   }
   const int nlc = ncl[0] * ncl[1] * ncl[2];
   // local centres: corners of the local cells, clamped to the grid
-  int j0[3], nj[3];
+  int nj[3];
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    j0[a] = c0[a];
-    nj[a] = min(c0[a] + ncl[a], cs.d[a] - 1) - c0[a] + 1;
-  }
+  for (int a = 0; a < 3; ++a) nj[a] = min(c0[a] + ncl[a], cs.d[a] - 1) - c0[a] + 1;
   const int nloc = nj[0] * nj[1] * nj[2];
-  auto local_cell = [&](int cell) {
+  // local cell of every node (index, coordinates), mask kept
+  for (int i = threadIdx.x; i < T.L; i += kTileThreads) {
+    const int cm = __float_as_int(stage[i].x);
+    const int cell = cm & 0x0FFFFFFF;
     const int iz = cell % cs.cd[2], iy = (cell / cs.cd[2]) % cs.cd[1], ix = cell / (cs.cd[1] * cs.cd[2]);
-    return ((ix - c0[0]) * ncl[1] + (iy - c0[1])) * ncl[2] + (iz - c0[2]);
-  };
-  // stable grouping of the tile's nodes by local cell (one thread; L <= a few hundred)
-  if (threadIdx.x == 0) {
-    for (int q = 0; q <= nlc; ++q) coff[q] = 0;
-    for (int i = 0; i < T.L; ++i) coff[local_cell(__float_as_int(stage[i].x) & 0x0FFFFFFF) + 1] += 1;
-    for (int q = 0; q < nlc; ++q) coff[q + 1] += coff[q];
-    int cur[kGalMaxCells];
-    for (int q = 0; q < nlc; ++q) cur[q] = coff[q];
-    for (int i = 0; i < T.L; ++i) order[cur[local_cell(__float_as_int(stage[i].x) & 0x0FFFFFFF)]++] = (uint16_t)i;
+    const int lx = ix - c0[0], ly = iy - c0[1], lz = iz - c0[2];
+    const int lc = (lx * ncl[1] + ly) * ncl[2] + lz;
+    stage[i].x = __int_as_float(lc | (lx << 8) | (ly << 10) | (lz << 12) | (cm & 0x70000000));
+  }
+  // per local centre the (cell, corner) pairs that restrict onto it, in a
+  // fixed order
+  for (int il = threadIdx.x; il < nloc; il += kTileThreads) {
+    const int jx = il / (nj[1] * nj[2]), jy = (il / nj[2]) % nj[1], jz = il % nj[2];
+    int n = 0;
+    for (int lc = 0; lc < nlc; ++lc) {
+      const int lx = lc / (ncl[1] * ncl[2]), ly = (lc / ncl[2]) % ncl[1], lz = lc % ncl[2];
+      for (int k = 0; k < 8; ++k) {
+        const int gx = min(c0[0] + lx + ((k >> 2) & 1), cs.d[0] - 1) - c0[0];
+        const int gy = min(c0[1] + ly + ((k >> 1) & 1), cs.d[1] - 1) - c0[1];
+        const int gz = min(c0[2] + lz + (k & 1), cs.d[2] - 1) - c0[2];
+        if (gx == jx && gy == jy && gz == jz && n < 8) gat[il][n++] = (short)((lc << 3) | k);
+      }
+    }
+    for (; n < 8; ++n) gat[il][n] = -1;
   }
   __syncthreads();
-  for (int q = 0; q < 3 * nloc; ++q) {
-    const int jl = q / 3, comp = q % 3;
-    const int jx = j0[0] + jl / (nj[1] * nj[2]), jy = j0[1] + (jl / nj[2]) % nj[1], jz = j0[2] + jl % nj[2];
-    const int J = (jx * cs.d[1] + jy) * cs.d[2] + jz;
-    // synthetic displacements P Pi_J at the tile's nodes
-    for (int i = threadIdx.x; i < T.L; i += kTileThreads) {
-      const float4 st = stage[i];
-      const int cm = __float_as_int(st.x);
-      const float f[3] = {st.y, st.z, st.w};
-      float w = 0.f;
+  // stable grouping of the tile's nodes by local cell: rank = earlier nodes
+  // of the same cell
+  if (threadIdx.x <= nlc) coff[threadIdx.x] = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < T.L; i += kTileThreads) atomicAdd(&coff[(__float_as_int(stage[i].x) & 0xFF) + 1], 1);
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int q = 0; q < nlc; ++q) coff[q + 1] += coff[q];
+  __syncthreads();
+  for (int i = threadIdx.x; i < T.L; i += kTileThreads) {
+    const int lc = __float_as_int(stage[i].x) & 0xFF;
+    int rank = 0;
+    for (int t = 0; t < i; ++t) rank += ((__float_as_int(stage[t].x) & 0xFF) == lc);
+    order[coff[lc] + rank] = (uint16_t)i;
+  }
+  __syncthreads();
+
+  // restriction of the masked nodal forces in su against the local centres,
+  // added to column `col` of A_c (all threads; ends with a barrier)
+  auto restrict_add = [&](int col) {
+    // (lower and upper x corners in two sweeps: 12 accumulators per lane)
+    for (int t = warp; t < 2 * nlc; t += kGalWarps) {
+      const int lc = t >> 1, k0 = 4 * (t & 1);
+      float a[12];
 #pragma unroll
-      for (int k = 0; k < 8; ++k)
-        if (cs_corner(cs, cm & 0x0FFFFFFF, k) == J) w += cs_weight(f, k);
-      const float v = ((cm >> (28 + comp)) & 1) ? w : 0.f;
-      T.su[i] = make_float4(comp == 0 ? v : 0.f, comp == 1 ? v : 0.f, comp == 2 ? v : 0.f, 0.f);
+      for (int q = 0; q < 12; ++q) a[q] = 0.f;
+      for (int e = coff[lc] + lane; e < coff[lc + 1]; e += 32) {
+        const int i = order[e];
+        const float4 st = stage[i];
+        const float f[3] = {st.y, st.z, st.w};
+        const float4 fi = T.su[i];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const float w = cs_weight(f, k0 + k);
+          a[3 * k] = fmaf(w, fi.x, a[3 * k]);
+          a[3 * k + 1] = fmaf(w, fi.y, a[3 * k + 1]);
+          a[3 * k + 2] = fmaf(w, fi.z, a[3 * k + 2]);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 12; ++q) {
+        float v = a[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) cellacc[lc][3 * k0 + q] = v;
+      }
     }
-    for (int t = threadIdx.x; t < 3 * nloc; t += kTileThreads) acc[t] = 0.f;
     __syncthreads();
-    tile_strains(A, R, T);
+    for (int t = threadIdx.x; t < 3 * nloc; t += kTileThreads) {
+      const int il = t / 3, cc = t - 3 * il;
+      float v = 0.f;
+#pragma unroll
+      for (int n = 0; n < 8; ++n) {
+        const int g = gat[il][n];
+        if (g >= 0) v += cellacc[g >> 3][3 * (g & 7) + cc];
+      }
+      if (v != 0.f) {
+        const int ix = c0[0] + il / (nj[1] * nj[2]), iy = c0[1] + (il / nj[2]) % nj[1], iz = c0[2] + il % nj[2];
+        const int I = (ix * cs.d[1] + iy) * cs.d[2] + iz;
+        atomicAdd(&Ac[(int64_t)(3 * I + cc) * cs.npad + col], (double)v);
+      }
+    }
     __syncthreads();
-    tile_forces(R, T, lam, mu);
-    __syncthreads();
-    // masked nodal forces of the tile into su
+  };
+  // masked nodal forces of the tile into su (all threads; ends with a barrier)
+  auto node_forces = [&]() {
     for (int i = threadIdx.x; i < T.L; i += kTileThreads) {
       float fx, fy, fz;
       tile_node_force(T, i, fx, fy, fz);
@@ -279,36 +357,139 @@ __global__ void __launch_bounds__(kTileThreads, 3) k_cs_galerkin(TileArgs A, Coa
       T.su[i] = make_float4((m & 1) ? fx : 0.f, (m & 2) ? fy : 0.f, (m & 4) ? fz : 0.f, 0.f);
     }
     __syncthreads();
-    // restriction: one thread per (local cell, corner, component)
-    for (int t = threadIdx.x; t < 24 * nlc; t += kTileThreads) {
-      const int lc = t / 24, k = (t % 24) / 3, cc = t % 3;
-      float sum = 0.f;
-      int cell = -1;
-      for (int e = coff[lc]; e < coff[lc + 1]; ++e) {
-        const int i = order[e];
-        const float4 st = stage[i];
-        cell = __float_as_int(st.x) & 0x0FFFFFFF;
-        const float f[3] = {st.y, st.z, st.w};
-        const float4 fi = T.su[i];
-        sum = fmaf(cs_weight(f, k), cc == 0 ? fi.x : (cc == 1 ? fi.y : fi.z), sum);
+  };
+  // value of the local centre's hat function at node i
+  auto hat = [&](int i, int jx, int jy, int jz) {
+    const float4 st = stage[i];
+    const int cm = __float_as_int(st.x);
+    return gal_w1(jx, (cm >> 8) & 3, c0[0], cs.d[0], st.y) * gal_w1(jy, (cm >> 10) & 3, c0[1], cs.d[1], st.z) *
+           gal_w1(jz, (cm >> 12) & 3, c0[2], cs.d[2], st.w);
+  };
+
+  for (int jl = 0; jl < nloc; ++jl) {
+    const int jx = jl / (nj[1] * nj[2]), jy = (jl / nj[2]) % nj[1], jz = jl % nj[2];
+    const int J = ((c0[0] + jx) * cs.d[1] + c0[1] + jy) * cs.d[2] + c0[2] + jz;
+    if (!mixed) {
+      // scalar field w_J on the free nodes
+      for (int i = threadIdx.x; i < T.L; i += kTileThreads) {
+        const float v = (__float_as_int(stage[i].x) >> 28) ? hat(i, jx, jy, jz) : 0.f;
+        T.su[i] = make_float4(v, 0.f, 0.f, 0.f);
       }
-      if (cell < 0) continue;
-      const int I = cs_corner(cs, cell, k);
-      const int iz = I % cs.d[2], iy = (I / cs.d[2]) % cs.d[1], ix = I / (cs.d[1] * cs.d[2]);
-      const int il = ((ix - j0[0]) * nj[1] + (iy - j0[1])) * nj[2] + (iz - j0[2]);
-      atomicAdd(&acc[3 * il + cc], sum);
-    }
-    __syncthreads();
-    for (int t = threadIdx.x; t < 3 * nloc; t += kTileThreads) {
-      const float v = acc[t];
-      if (v != 0.f) {
-        const int il = t / 3, cc = t % 3;
-        const int ix = j0[0] + il / (nj[1] * nj[2]), iy = j0[1] + (il / nj[2]) % nj[1], iz = j0[2] + il % nj[2];
-        const int I = (ix * cs.d[1] + iy) * cs.d[2] + iz;
-        atomicAdd(&Ac[(int64_t)(3 * I + cc) * cs.npad + 3 * J + comp], (double)v);
+      __syncthreads();
+      // (V grad w, V) of own and halo tets
+#pragma unroll
+      for (int r = 0; r < kTilePer; ++r) {
+        const int j = threadIdx.x + r * kTileThreads;
+        if (j < T.n_own) {
+          TetGeo G;
+          uint2 lc;
+          rec_unpack(R.rr[r], G, lc);
+          const int l[4] = {(int)(lc.x & 0xFFFF), (int)(lc.x >> 16), (int)(lc.y & 0xFFFF), (int)(lc.y >> 16)};
+          float g[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+          for (int a = 0; a < 4; ++a) {
+            const float w = T.su[l[a]].x;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) g[q] = fmaf(w, G.g[a][q], g[q]);
+          }
+          T.swa[j] = make_float4(g[0], g[1], g[2], G.V);
+          reinterpret_cast<uint2 *>(T.sinc)[j] =
+              make_uint2(__float_as_uint(R.rr[r][3].z), __float_as_uint(R.rr[r][3].w));
+        }
+      }
+      for (int h = threadIdx.x; h < T.H; h += kTileThreads) {
+        TetGeo G;
+        uint2 lc;
+        load_rec(A.rec, A.halo_tet[T.h0 + h], G, lc, nullptr);
+        lc = A.halo_lconn[T.h0 + h];
+        const int l[4] = {(int)(lc.x & 0xFFFF), (int)(lc.x >> 16), (int)(lc.y & 0xFFFF), (int)(lc.y >> 16)};
+        float g[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          const float w = T.su[l[a]].x;
+#pragma unroll
+          for (int q = 0; q < 3; ++q) g[q] = fmaf(w, G.g[a][q], g[q]);
+        }
+        T.swa[T.n_own + h] = make_float4(g[0], g[1], g[2], G.V);
+      }
+      __syncthreads();
+      // face-averaged V grad w of the own tets (kept in registers)
+      float Sg[kTilePer][3];
+#pragma unroll
+      for (int r = 0; r < kTilePer; ++r) {
+        Sg[r][0] = Sg[r][1] = Sg[r][2] = 0.f;
+        const int j = threadIdx.x + r * kTileThreads;
+        if (j >= T.n_own) continue;
+        const uint2 nb2 = make_uint2(__float_as_uint(R.rr[r][3].x), __float_as_uint(R.rr[r][3].y));
+        const int nb[4] = {(int)(nb2.x & 0xFFFF), (int)(nb2.x >> 16), (int)(nb2.y & 0xFFFF), (int)(nb2.y >> 16)};
+        const float4 we = T.swa[j];
+        float ks = 0.f;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          if (nb[a] != kNoNbr) {
+            const float4 wn = T.swa[nb[a]];
+            const float k = 0.25f / (we.w + wn.w);
+            ks += k;
+            Sg[r][0] = fmaf(k, wn.x, Sg[r][0]);
+            Sg[r][1] = fmaf(k, wn.y, Sg[r][1]);
+            Sg[r][2] = fmaf(k, wn.z, Sg[r][2]);
+          } else {
+            ks += 0.25f / we.w;
+          }
+        }
+        Sg[r][0] = fmaf(ks, we.x, Sg[r][0]);
+        Sg[r][1] = fmaf(ks, we.y, Sg[r][1]);
+        Sg[r][2] = fmaf(ks, we.z, Sg[r][2]);
+      }
+      for (int comp = 0; comp < 3; ++comp) {
+        // smoothed strain of w_J e_comp (Voigt xx yy zz yz zx xy), stress,
+        // nodal force slots
+#pragma unroll
+        for (int r = 0; r < kTilePer; ++r) {
+          const int j = threadIdx.x + r * kTileThreads;
+          if (j >= T.n_own) continue;
+          TetGeo G;
+          uint2 lc;
+          rec_unpack(R.rr[r], G, lc);
+          const float g0 = Sg[r][0], g1 = Sg[r][1], g2 = Sg[r][2];
+          const float S[6] = {comp == 0 ? g0 : 0.f, comp == 1 ? g1 : 0.f, comp == 2 ? g2 : 0.f,
+                              comp == 1 ? g2 : (comp == 2 ? g1 : 0.f), comp == 0 ? g2 : (comp == 2 ? g0 : 0.f),
+                              comp == 0 ? g1 : (comp == 1 ? g0 : 0.f)};
+          const float tr = S[0] + S[1] + S[2];
+          const float st[6] = {lam * tr + 2.f * mu * S[0], lam * tr + 2.f * mu * S[1], lam * tr + 2.f * mu * S[2],
+                               mu * S[3], mu * S[4], mu * S[5]};
+          float f[12];
+#pragma unroll
+          for (int a = 0; a < 4; ++a) {
+            f[3 * a] = G.g[a][0] * st[0] + G.g[a][1] * st[5] + G.g[a][2] * st[4];
+            f[3 * a + 1] = G.g[a][0] * st[5] + G.g[a][1] * st[1] + G.g[a][2] * st[3];
+            f[3 * a + 2] = G.g[a][0] * st[4] + G.g[a][1] * st[3] + G.g[a][2] * st[2];
+          }
+          float4 *fo = reinterpret_cast<float4 *>(T.sfe + 12 * j);
+          fo[0] = make_float4(f[0], f[1], f[2], f[3]);
+          fo[1] = make_float4(f[4], f[5], f[6], f[7]);
+          fo[2] = make_float4(f[8], f[9], f[10], f[11]);
+        }
+        __syncthreads();
+        node_forces();
+        restrict_add(3 * J + comp);
+      }
+    } else {
+      for (int comp = 0; comp < 3; ++comp) {
+        // synthetic displacements P Pi_J e_comp at the tile's nodes
+        for (int i = threadIdx.x; i < T.L; i += kTileThreads) {
+          const float v = ((__float_as_int(stage[i].x) >> (28 + comp)) & 1) ? hat(i, jx, jy, jz) : 0.f;
+          T.su[i] = make_float4(comp == 0 ? v : 0.f, comp == 1 ? v : 0.f, comp == 2 ? v : 0.f, 0.f);
+        }
+        __syncthreads();
+        tile_strains(A, R, T);
+        __syncthreads();
+        tile_forces(R, T, lam, mu);
+        __syncthreads();
+        node_forces();
+        restrict_add(3 * J + comp);
       }
     }
-    __syncthreads();
   }
 }
 
@@ -382,11 +563,12 @@ __global__ void __launch_bounds__(256) k_band_blocks(const double *A, int npad, 
 // warp factors the 64 x 8 panel, then all threads apply its rank-8 update
 // to the trailing lower triangle); then W_kk = L_kk^-1 by forward
 // substitution, 4 threads per column sharing each dot product.  L_kk back to
-// A, W_kk to Wd[k] (FP64)
-__global__ void __launch_bounds__(256) k_potrf_diag(double *A, double *Wd, int npad, int k, int *info) {
-  extern __shared__ double dyn_d[];
-  Tile64<double> &L = *reinterpret_cast<Tile64<double> *>(dyn_d);
-  Tile64<double> &W = *reinterpret_cast<Tile64<double> *>(dyn_d + kCB * (kCB + 1));
+// A, W_kk to Wd[k]
+template <class T>
+__global__ void __launch_bounds__(256) k_potrf_diag(T *A, T *Wd, int npad, int k, int *info) {
+  extern __shared__ __align__(16) unsigned char dyn_raw[];
+  Tile64<T> &L = *reinterpret_cast<Tile64<T> *>(dyn_raw);
+  Tile64<T> &W = *reinterpret_cast<Tile64<T> *>(dyn_raw + sizeof(Tile64<T>));
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   load64(L, A, npad, k, k);
   __syncthreads();
@@ -394,19 +576,19 @@ __global__ void __launch_bounds__(256) k_potrf_diag(double *A, double *Wd, int n
   for (int g0 = 0; g0 < kCB; g0 += G) {
     if (warp == 0) {
       for (int j = g0; j < g0 + G; ++j) {
-        double d = L.v[j][j];
-        if (!(d > 0.0) || !isfinite(d)) {
+        T d = L.v[j][j];
+        if (!(d > T(0)) || !isfinite(d)) {
           if (lane == 0) atomicExch(info, 1);
-          d = 1.0;
+          d = T(1);
         }
-        const double sd = sqrt(d);
+        const T sd = sqrt(d), inv = T(1) / sd;
         __syncwarp();
         if (lane == 0) L.v[j][j] = sd;
-        for (int i = j + 1 + lane; i < kCB; i += 32) L.v[i][j] /= sd;
+        for (int i = j + 1 + lane; i < kCB; i += 32) L.v[i][j] *= inv;
         __syncwarp();
         // update the rest of the panel (columns j+1 .. g0+G-1)
         for (int i = j + 1 + lane; i < kCB; i += 32) {
-          const double lij = L.v[i][j];
+          const T lij = L.v[i][j];
           for (int l = j + 1; l < min(g0 + G, i + 1); ++l) L.v[i][l] -= lij * L.v[l][j];
         }
         __syncwarp();
@@ -417,7 +599,7 @@ __global__ void __launch_bounds__(256) k_potrf_diag(double *A, double *Wd, int n
     for (int e = tid; e < kCB * kCB; e += blockDim.x) {
       const int i = e / kCB, l = e % kCB;
       if (l < g0 + G || l > i) continue;
-      double s = L.v[i][l];
+      T s = L.v[i][l];
 #pragma unroll
       for (int q = g0; q < g0 + G; ++q) s -= L.v[i][q] * L.v[l][q];
       L.v[i][l] = s;
@@ -430,35 +612,36 @@ __global__ void __launch_bounds__(256) k_potrf_diag(double *A, double *Wd, int n
   {
     const int c = tid >> 2, part = tid & 3;
     for (int i = 0; i < kCB; ++i) {
-      double s = 0.0;
+      T s = T(0);
       if (i > c)
         for (int l = c + part; l < i; l += 4) s += L.v[i][l] * W.v[l][c];
       s += __shfl_xor_sync(0xffffffffu, s, 1);
       s += __shfl_xor_sync(0xffffffffu, s, 2);
-      if (part == 0) W.v[i][c] = (i < c) ? 0.0 : (((i == c) ? 1.0 : 0.0) - s) / L.v[i][i];
+      if (part == 0) W.v[i][c] = (i < c) ? T(0) : (((i == c) ? T(1) : T(0)) - s) / L.v[i][i];
       __syncwarp();
     }
   }
   __syncthreads();
   for (int e = tid; e < kCB * kCB; e += blockDim.x) {
     const int i = e / kCB, l = e % kCB;
-    A[(int64_t)(k * kCB + i) * npad + k * kCB + l] = (l <= i) ? L.v[i][l] : 0.0;
+    A[(int64_t)(k * kCB + i) * npad + k * kCB + l] = (l <= i) ? L.v[i][l] : T(0);
     Wd[(int64_t)k * kCB * kCB + e] = W.v[i][l];
   }
 }
 
 // L[i][k] = A[i][k] W_kk^T for the row blocks k < i <= k + bwb
-__global__ void __launch_bounds__(256) k_trsm_panel(double *A, const double *Wd, int npad, int k) {
-  extern __shared__ double dyn_d[];
-  Tile64<double> &X = *reinterpret_cast<Tile64<double> *>(dyn_d);
-  Tile64<double> &Wk = *reinterpret_cast<Tile64<double> *>(dyn_d + kCB * (kCB + 1));
+template <class T>
+__global__ void __launch_bounds__(256) k_trsm_panel(T *A, const T *Wd, int npad, int k) {
+  extern __shared__ __align__(16) unsigned char dyn_raw[];
+  Tile64<T> &X = *reinterpret_cast<Tile64<T> *>(dyn_raw);
+  Tile64<T> &Wk = *reinterpret_cast<Tile64<T> *>(dyn_raw + sizeof(Tile64<T>));
   const int bi = k + 1 + blockIdx.x;
   load64(X, A, npad, bi, k);
   load64(Wk, Wd + (int64_t)k * kCB * kCB, kCB, 0, 0);
   __syncthreads();
   const int tm = (threadIdx.x >> 4) * 4, tn = (threadIdx.x & 15) * 4;
-  double acc[4][4] = {};
-  mm64<double, false, true>(acc, X, Wk, tm, tn);
+  T acc[4][4] = {};
+  mm64<T, false, true>(acc, X, Wk, tm, tn);
 #pragma unroll
   for (int x = 0; x < 4; ++x)
 #pragma unroll
@@ -466,10 +649,11 @@ __global__ void __launch_bounds__(256) k_trsm_panel(double *A, const double *Wd,
 }
 
 // A[i][j] -= L[i][k] L[j][k]^T for k < j <= i <= k + m (block pairs enumerated)
-__global__ void __launch_bounds__(256) k_syrk_update(double *A, int npad, int k, int m) {
-  extern __shared__ double dyn_d[];
-  Tile64<double> &Li = *reinterpret_cast<Tile64<double> *>(dyn_d);
-  Tile64<double> &Lj = *reinterpret_cast<Tile64<double> *>(dyn_d + kCB * (kCB + 1));
+template <class T>
+__global__ void __launch_bounds__(256) k_syrk_update(T *A, int npad, int k, int m) {
+  extern __shared__ __align__(16) unsigned char dyn_raw[];
+  Tile64<T> &Li = *reinterpret_cast<Tile64<T> *>(dyn_raw);
+  Tile64<T> &Lj = *reinterpret_cast<Tile64<T> *>(dyn_raw + sizeof(Tile64<T>));
   const int t = blockIdx.x;
   int ii = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
   while ((ii + 1) * (ii + 2) / 2 <= t) ++ii;
@@ -481,8 +665,8 @@ __global__ void __launch_bounds__(256) k_syrk_update(double *A, int npad, int k,
   load64(Lj, A, npad, bj, k);
   __syncthreads();
   const int tm = (threadIdx.x >> 4) * 4, tn = (threadIdx.x & 15) * 4;
-  double acc[4][4] = {};
-  mm64<double, false, true>(acc, Li, Lj, tm, tn);
+  T acc[4][4] = {};
+  mm64<T, false, true>(acc, Li, Lj, tm, tn);
 #pragma unroll
   for (int x = 0; x < 4; ++x)
 #pragma unroll
@@ -498,13 +682,13 @@ __global__ void k_lower_to_f32(const double *A, float *L, int npad) {
 
 // W = L^-1 (FP32), one block per block column j, walking down the column:
 // W_jj from Wd, then W_ij = -W_ii sum_{l} L_il W_lj over the band of L
-__global__ void __launch_bounds__(256) k_trtri_cols(const float *L, const double *Wd, float *W, int npad, int nb,
+__global__ void __launch_bounds__(256) k_trtri_cols(const float *L, const float *Wd, float *W, int npad, int nb,
                                                     int bwb) {
   __shared__ Tile64<float> As, Bs;
   const int bj = blockIdx.x;
   const int tm = (threadIdx.x >> 4) * 4, tn = (threadIdx.x & 15) * 4;
   for (int e = threadIdx.x; e < kCB * kCB; e += blockDim.x)
-    W[(int64_t)(bj * kCB + e / kCB) * npad + bj * kCB + e % kCB] = (float)Wd[(int64_t)bj * kCB * kCB + e];
+    W[(int64_t)(bj * kCB + e / kCB) * npad + bj * kCB + e % kCB] = Wd[(int64_t)bj * kCB * kCB + e];
   for (int bi = bj + 1; bi < nb; ++bi) {
     float acc[4][4] = {};
     for (int l = max(bj, bi - bwb); l < bi; ++l) {
@@ -516,7 +700,7 @@ __global__ void __launch_bounds__(256) k_trtri_cols(const float *L, const double
     }
     __syncthreads();
     for (int e = threadIdx.x; e < kCB * kCB; e += blockDim.x)
-      As.v[e / kCB][e % kCB] = (float)Wd[(int64_t)bi * kCB * kCB + e];
+      As.v[e / kCB][e % kCB] = Wd[(int64_t)bi * kCB * kCB + e];
 #pragma unroll
     for (int x = 0; x < 4; ++x)
 #pragma unroll
@@ -564,14 +748,57 @@ __global__ void k_cs_apply_z(CoarseDev cs, const double *__restrict__ r, const d
   if (i < n) z[i] = dinv[i] * r[i] + (dmask[i] ? (double)cs_prolong(cs, i) : 0.0);
 }
 
-void coarse_correction(Ctx &c, cudaStream_t st, const double *r, const int *done) {
+void coarse_gemv(const CoarseDev &cs, cudaStream_t st, const int *done) {
+  k_cs_gemv<<<(cs.npad + 7) / 8, 256, 0, st>>>(cs, done);
+  SFEM_CHECK_LAUNCH();
+}
+
+template <class TV>
+static void coarse_correction_t(Ctx &c, cudaStream_t st, const TV *r, const int *done) {
   const CoarseDev &cs = c.coarse->dev;
-  k_cs_restrict<double><<<cs.ncell, kRestrictThreads, 0, st>>>(r, nullptr, cs, done);
+  k_cs_restrict<TV><<<cs.ncell, kRestrictThreads, 0, st>>>(r, nullptr, cs, done);
   SFEM_CHECK_LAUNCH();
   k_cs_gather<<<grid_for(cs.npad, 256), 256, 0, st>>>(cs, done);
   SFEM_CHECK_LAUNCH();
   k_cs_gemv<<<(cs.npad + 7) / 8, 256, 0, st>>>(cs, done);
   SFEM_CHECK_LAUNCH();
+}
+void coarse_correction(Ctx &c, cudaStream_t st, const double *r, const int *done) {
+  coarse_correction_t(c, st, r, done);
+}
+void coarse_correction(Ctx &c, cudaStream_t st, const float *r, const int *done) {
+  coarse_correction_t(c, st, r, done);
+}
+
+__global__ void k_cs_to_f32(const double *a, float *b, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (float)a[i];
+}
+
+// blocked Cholesky of the band of A (lower blocks within bwb of the
+// diagonal) in place, with the inverses of the diagonal blocks in Wd;
+// false on a non-positive pivot
+template <class T>
+static bool banded_cholesky(Ctx &c, T *A, T *Wd, int npad, int nb, int bwb, int *dev_info) {
+  const size_t sm2 = 2 * sizeof(Tile64<T>);
+  SFEM_CUDA(cudaFuncSetAttribute(k_potrf_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
+  SFEM_CUDA(cudaFuncSetAttribute(k_trsm_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
+  SFEM_CUDA(cudaFuncSetAttribute(k_syrk_update<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
+  SFEM_CUDA(cudaMemsetAsync(dev_info, 0, sizeof(int), c.stream));
+  for (int k = 0; k < nb; ++k) {
+    k_potrf_diag<T><<<1, 256, sm2, c.stream>>>(A, Wd, npad, k, dev_info);
+    SFEM_CHECK_LAUNCH();
+    const int m = std::min(nb - 1 - k, bwb);  // nonzero row blocks below the diagonal block
+    if (m == 0) continue;
+    k_trsm_panel<T><<<m, 256, sm2, c.stream>>>(A, Wd, npad, k);
+    SFEM_CHECK_LAUNCH();
+    k_syrk_update<T><<<m * (m + 1) / 2, 256, sm2, c.stream>>>(A, npad, k, m);
+    SFEM_CHECK_LAUNCH();
+  }
+  int info = 0;
+  SFEM_CUDA(cudaMemcpyAsync(&info, dev_info, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+  SFEM_CUDA(cudaStreamSynchronize(c.stream));
+  return info == 0;
 }
 
 static void setup_coarse(Ctx &c, const sfem_coarse_opts *opts) {
@@ -658,6 +885,17 @@ static void setup_coarse(Ctx &c, const sfem_coarse_opts *opts) {
     std::vector<int32_t> cur(off.begin(), off.end() - 1);
     for (int64_t i = 0; i < c.n_nodes; ++i) nodes[cur[cell[i]]++] = (int32_t)i;
   }
+  // blocks of the fused iteration kernels: runs of at most kChunkNodes nodes
+  // of one cell
+  std::vector<int4> chunks;
+  for (int q = 0; q < cs.ncell; ++q)
+    for (int b = off[q]; b < off[q + 1]; b += kChunkNodes)
+      chunks.push_back(make_int4(q, b, std::min(b + kChunkNodes, off[q + 1]), 0));
+  cs.nchunk = (int)chunks.size();
+  int4 *d_chunk = c.mem.get<int4>(chunks.size());
+  SFEM_CUDA(cudaMemcpyAsync(d_chunk, chunks.data(), chunks.size() * sizeof(int4), cudaMemcpyHostToDevice, c.stream));
+  cs.chunk = d_chunk;
+  cs.chunk_part = c.mem.get<double>(chunks.size());
   int32_t *d_cell = c.mem.get<int32_t>(c.n_nodes), *d_nodes = c.mem.get<int32_t>(c.n_nodes);
   int32_t *d_off = c.mem.get<int32_t>(cs.ncell + 1);
   float *d_frac = c.mem.get<float>(3 * c.n_nodes);
@@ -729,7 +967,11 @@ static void setup_coarse(Ctx &c, const sfem_coarse_opts *opts) {
   c.mem.drop(y);
   k_cs_symmetrize<<<grid_for(np2, 256), 256, 0, c.stream>>>(Ac, cs.nc, cs.npad);
   SFEM_CHECK_LAUNCH();
-  // ---- banded blocked Cholesky (FP64) ---------------------------------------
+  // ---- banded blocked Cholesky ---------------------------------------------
+  // FP32 (the inverse C is FP32 anyway: on the 26 x 6 x 6 grid of the 2M-tet
+  // beam, cond(A_c) ~ 8e4, and C from an FP32 factor has C A_c within 1.4e-4
+  // of I, as with an FP64 factor); FP64 when the FP32 factor meets a
+  // non-positive pivot
   const int nb = cs.npad / kCB;
   int *dev_i = c.mem.get<int>(2);  // [0] info, [1] block bandwidth
   SFEM_CUDA(cudaMemsetAsync(dev_i, 0, 2 * sizeof(int), c.stream));
@@ -739,30 +981,28 @@ static void setup_coarse(Ctx &c, const sfem_coarse_opts *opts) {
   SFEM_CUDA(cudaMemcpyAsync(hb, dev_i, sizeof hb, cudaMemcpyDeviceToHost, c.stream));
   SFEM_CUDA(cudaStreamSynchronize(c.stream));
   const int bwb = std::max(hb[1], 1);
-  double *Wd = c.mem.get<double>((size_t)nb * kCB * kCB);
-  const size_t sm2 = 2 * sizeof(Tile64<double>);
-  SFEM_CUDA(cudaFuncSetAttribute(k_potrf_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
-  SFEM_CUDA(cudaFuncSetAttribute(k_trsm_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
-  SFEM_CUDA(cudaFuncSetAttribute(k_syrk_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
-  for (int k = 0; k < nb; ++k) {
-    k_potrf_diag<<<1, 256, sm2, c.stream>>>(Ac, Wd, cs.npad, k, dev_i);
-    SFEM_CHECK_LAUNCH();
-    const int m = std::min(nb - 1 - k, bwb);  // nonzero row blocks below the diagonal block
-    if (m == 0) continue;
-    k_trsm_panel<<<m, 256, sm2, c.stream>>>(Ac, Wd, cs.npad, k);
-    SFEM_CHECK_LAUNCH();
-    k_syrk_update<<<m * (m + 1) / 2, 256, sm2, c.stream>>>(Ac, cs.npad, k, m);
-    SFEM_CHECK_LAUNCH();
-  }
-  SFEM_CUDA(cudaMemcpyAsync(hb, dev_i, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
-  SFEM_CUDA(cudaStreamSynchronize(c.stream));
-  SFEM_REQUIRE(hb[0] == 0, SFEM_EBREAKDOWN, "coarse matrix is not positive definite");
-  // ---- C = A_c^-1 = L^-T L^-1 (FP32) ----------------------------------------
-  float *L32 = c.mem.get<float>(np2), *W = c.mem.get<float>(np2);
-  float *C = c.mem.get<float>(np2);
-  k_lower_to_f32<<<grid_for(np2, 256), 256, 0, c.stream>>>(Ac, L32, cs.npad);
+  float *L32 = c.mem.get<float>(np2);
+  float *Wd = c.mem.get<float>((size_t)nb * kCB * kCB);
+  k_cs_to_f32<<<grid_for(np2, 256), 256, 0, c.stream>>>(Ac, L32, np2);
   SFEM_CHECK_LAUNCH();
+  const int factor = opts ? opts->factor : 0;
+  co->fp64_factor = factor == 1 || !banded_cholesky<float>(c, L32, Wd, cs.npad, nb, bwb, dev_i);
+  if (co->fp64_factor) {
+    double *Wd64 = c.mem.get<double>((size_t)nb * kCB * kCB);
+    SFEM_REQUIRE(banded_cholesky<double>(c, Ac, Wd64, cs.npad, nb, bwb, dev_i), SFEM_EBREAKDOWN,
+                 "coarse matrix is not positive definite");
+    k_lower_to_f32<<<grid_for(np2, 256), 256, 0, c.stream>>>(Ac, L32, cs.npad);
+    SFEM_CHECK_LAUNCH();
+    k_cs_to_f32<<<grid_for((int64_t)nb * kCB * kCB, 256), 256, 0, c.stream>>>(Wd64, Wd, (int64_t)nb * kCB * kCB);
+    SFEM_CHECK_LAUNCH();
+    c.mem.drop(Wd64);
+  }
   c.mem.drop(Ac);
+  // ---- C = A_c^-1 = L^-T L^-1 (FP32) ----------------------------------------
+  // (trtri reads only the strictly lower blocks of L and the diagonal blocks'
+  // inverses Wd)
+  float *W = c.mem.get<float>(np2);
+  float *C = c.mem.get<float>(np2);
   SFEM_CUDA(cudaMemsetAsync(W, 0, np2 * sizeof(float), c.stream));
   k_trtri_cols<<<nb, 256, 0, c.stream>>>(L32, Wd, W, cs.npad, nb, bwb);
   SFEM_CHECK_LAUNCH();
@@ -791,8 +1031,11 @@ using namespace sfem;
 extern "C" int sfem_coarse_setup(sfem_ctx *h, const sfem_coarse_opts *opts) {
   try {
     SFEM_REQUIRE(h && h->c.vol && h->c.tl.ready, SFEM_EINVAL, "context not set up");
-    if (opts)
+    if (opts) {
       for (int r : opts->reserved) SFEM_REQUIRE(r == 0, SFEM_EINVAL, "reserved options must be zero");
+      SFEM_REQUIRE(opts->assembly == 0 || opts->assembly == 1, SFEM_EINVAL, "assembly must be 0 or 1");
+      SFEM_REQUIRE(opts->factor == 0 || opts->factor == 1, SFEM_EINVAL, "factor must be 0 or 1");
+    }
     h->c.coarse.reset();
     setup_coarse(h->c, opts);
   } catch (const Error &err) {

@@ -13,6 +13,8 @@
 
 namespace sfem {
 
+constexpr int kChunkNodes = 512;  // nodes per block of the fused two-level kernels
+
 struct CoarseDev {
   int d[3];                // centres per axis
   int cd[3];               // interpolation cells per axis, max(d - 1, 1)
@@ -25,6 +27,9 @@ struct CoarseDev {
   const int32_t *glist;    // nc x 8: cellsum entries summed into each coarse DOF (-1: none)
   const int32_t *cnodes;   // node ids grouped by cell (ascending within a cell)
   const int32_t *coff;     // ncell + 1
+  const int4 *chunk;       // nchunk: (cell, first, end) ranges of cnodes, <= kChunkNodes nodes each
+  int nchunk;
+  double *chunk_part;      // nchunk: per-block partial sums of the fused iteration kernels
   float *cellsum;          // ncell x 24 partial restrictions (8 corners x 3)
   float *rc, *yc;          // coarse residual and correction (npad)
   const float *C;          // npad x npad: A_c^-1 (symmetric), FP32

@@ -171,76 +171,102 @@ int64_t scan_counts(Ctx &c, const int32_t *counts, int64_t n, int64_t *out) {
 // ---------------------------------------------------------------------------
 // geometry (FP64)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void atomic_min_pos(unsigned long long *a, double v) {
-  atomicMin(a, (unsigned long long)__double_as_longlong(v));
+__device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
 }
-__device__ __forceinline__ void atomic_max_pos(unsigned long long *a, double v) {
-  atomicMax(a, (unsigned long long)__double_as_longlong(v));
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// quality and volume extrema of the tet handled by each lane, reduced over
+// the warp before one atomic per warp (positive doubles order like their
+// bit patterns); every lane of the warp must call it
+__device__ __forceinline__ void warp_geometry_stats(DevStatus *st, bool valid, double q, double V) {
+  unsigned long long qb = valid ? (unsigned long long)__double_as_longlong(q) : ~0ull;
+  unsigned long long vlo = valid ? (unsigned long long)__double_as_longlong(V) : ~0ull;
+  unsigned long long vhi = valid ? (unsigned long long)__double_as_longlong(V) : 0ull;
+  qb = warp_min_u64(qb);
+  vlo = warp_min_u64(vlo);
+  vhi = warp_max_u64(vhi);
+  if ((threadIdx.x & 31) == 0 && qb != ~0ull) {
+    atomicMin(&st->minq_bits, qb);
+    atomicMin(&st->minv_bits, vlo);
+    atomicMax(&st->maxv_bits, vhi);
+  }
 }
 
 // Per tet: V = |det J| / 6 (Eq. 10), gradients grad N_a (Eq. 1) as rows of
 // inv(J) with J = [x1-x0, x2-x0, x3-x0]; grad N_0 = -(sum of the others).
+// Launched with whole warps (block size a multiple of 32).
 __global__ void k_geometry(const double *__restrict__ xyz, const int32_t *__restrict__ tets,
                            int64_t n_tets, int64_t n_nodes, double *__restrict__ vol,
                            double *__restrict__ grad, DevStatus *st) {
-  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= n_tets) return;
-  int4 t = reinterpret_cast<const int4 *>(tets)[e];
-  int v[4] = {t.x, t.y, t.z, t.w};
-  bool ok = true;
-  for (int a = 0; a < 4; ++a) ok = ok && v[a] >= 0 && v[a] < n_nodes;
-  double *ge = grad + e * 12;
-  if (!ok) {
-    atomicAdd(&st->bad_index, 1ull);
-    vol[e] = 0.0;
-    for (int k = 0; k < 12; ++k) ge[k] = 0.0;
-    return;
-  }
-  double X[4][3];
-  for (int a = 0; a < 4; ++a)
-    for (int i = 0; i < 3; ++i) X[a][i] = xyz[3 * (int64_t)v[a] + i];
-  double d1[3], d2[3], d3[3];
-  for (int i = 0; i < 3; ++i) {
-    d1[i] = X[1][i] - X[0][i];
-    d2[i] = X[2][i] - X[0][i];
-    d3[i] = X[3][i] - X[0][i];
-  }
-  double c23[3] = {d2[1] * d3[2] - d2[2] * d3[1], d2[2] * d3[0] - d2[0] * d3[2], d2[0] * d3[1] - d2[1] * d3[0]};
-  double c31[3] = {d3[1] * d1[2] - d3[2] * d1[1], d3[2] * d1[0] - d3[0] * d1[2], d3[0] * d1[1] - d3[1] * d1[0]};
-  double c12[3] = {d1[1] * d2[2] - d1[2] * d2[1], d1[2] * d2[0] - d1[0] * d2[2], d1[0] * d2[1] - d1[1] * d2[0]};
-  double det = d1[0] * c23[0] + d1[1] * c23[1] + d1[2] * c23[2];
-  double l2 = 0.0;
-  for (int a = 0; a < 4; ++a)
-    for (int b = a + 1; b < 4; ++b)
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  bool valid = false;
+  double q = 0.0, V = 0.0;
+  if (e < n_tets) {
+    const int4 t = reinterpret_cast<const int4 *>(tets)[e];
+    const int v[4] = {t.x, t.y, t.z, t.w};
+    bool ok = true;
+    for (int a = 0; a < 4; ++a) ok = ok && v[a] >= 0 && v[a] < n_nodes;
+    double *ge = grad + e * 12;
+    double X[4][3], det = 0.0, l3 = 0.0;
+    double c23[3] = {}, c31[3] = {}, c12[3] = {};
+    if (ok) {
+      for (int a = 0; a < 4; ++a)
+        for (int i = 0; i < 3; ++i) X[a][i] = xyz[3 * (int64_t)v[a] + i];
+      double d1[3], d2[3], d3[3];
       for (int i = 0; i < 3; ++i) {
-        double d = X[a][i] - X[b][i];
-        l2 += d * d;
+        d1[i] = X[1][i] - X[0][i];
+        d2[i] = X[2][i] - X[0][i];
+        d3[i] = X[3][i] - X[0][i];
       }
-  l2 /= 6.0;
-  double l3 = l2 * sqrt(l2);
-  double V = fabs(det) / 6.0;
-  if (!(isfinite(det) && isfinite(l3)) || !(V > 1e-14 * l3)) {
-    atomicAdd(&st->bad_tets, 1ull);
-    vol[e] = 0.0;
-    for (int k = 0; k < 12; ++k) ge[k] = 0.0;
-    return;
+      c23[0] = d2[1] * d3[2] - d2[2] * d3[1], c23[1] = d2[2] * d3[0] - d2[0] * d3[2],
+      c23[2] = d2[0] * d3[1] - d2[1] * d3[0];
+      c31[0] = d3[1] * d1[2] - d3[2] * d1[1], c31[1] = d3[2] * d1[0] - d3[0] * d1[2],
+      c31[2] = d3[0] * d1[1] - d3[1] * d1[0];
+      c12[0] = d1[1] * d2[2] - d1[2] * d2[1], c12[1] = d1[2] * d2[0] - d1[0] * d2[2],
+      c12[2] = d1[0] * d2[1] - d1[1] * d2[0];
+      det = d1[0] * c23[0] + d1[1] * c23[1] + d1[2] * c23[2];
+      double l2 = 0.0;
+      for (int a = 0; a < 4; ++a)
+        for (int b = a + 1; b < 4; ++b)
+          for (int i = 0; i < 3; ++i) {
+            const double d = X[a][i] - X[b][i];
+            l2 += d * d;
+          }
+      l2 /= 6.0;
+      l3 = l2 * sqrt(l2);
+      V = fabs(det) / 6.0;
+      valid = isfinite(det) && isfinite(l3) && V > 1e-14 * l3;
+    } else {
+      atomicAdd(&st->bad_index, 1ull);
+    }
+    if (ok && !valid) atomicAdd(&st->bad_tets, 1ull);
+    if (!valid) {
+      vol[e] = 0.0;
+      for (int k = 0; k < 12; ++k) ge[k] = 0.0;
+    } else {
+      q = 6.0 * sqrt(2.0) * V / l3;
+      if (q < 1e-3) atomicAdd(&st->slivers, 1ull);
+      const double inv = 1.0 / det;
+      double g[4][3];
+      for (int i = 0; i < 3; ++i) {
+        g[1][i] = c23[i] * inv;
+        g[2][i] = c31[i] * inv;
+        g[3][i] = c12[i] * inv;
+        g[0][i] = -(g[1][i] + g[2][i] + g[3][i]);
+      }
+      vol[e] = V;
+      for (int a = 0; a < 4; ++a)
+        for (int i = 0; i < 3; ++i) ge[3 * a + i] = g[a][i];
+    }
   }
-  double q = 6.0 * sqrt(2.0) * V / l3;
-  if (q < 1e-3) atomicAdd(&st->slivers, 1ull);
-  atomic_min_pos(&st->minq_bits, q);
-  atomic_min_pos(&st->minv_bits, V);
-  atomic_max_pos(&st->maxv_bits, V);
-  double inv = 1.0 / det;
-  double g[4][3];
-  for (int i = 0; i < 3; ++i) {
-    g[1][i] = c23[i] * inv;
-    g[2][i] = c31[i] * inv;
-    g[3][i] = c12[i] * inv;
-    g[0][i] = -(g[1][i] + g[2][i] + g[3][i]);
-  }
-  vol[e] = V;
-  for (int a = 0; a < 4; ++a)
-    for (int i = 0; i < 3; ++i) ge[3 * a + i] = g[a][i];
+  warp_geometry_stats(st, valid, q, V);
 }
 
 // ---------------------------------------------------------------------------

@@ -153,6 +153,7 @@ struct Coarse {
   PatchGrid g{};
   CoarseDev dev{};
   int probes = 0;
+  bool fp64_factor = false;  // the FP32 Cholesky of A_c broke down
   double setup_ms = 0.0;
 };
 
@@ -261,6 +262,9 @@ void launch_mf32_tiled(Ctx &c, cudaStream_t st, const TU *u, TY *y, double *ener
 // stream st, all returning at once while *done != 0:
 // rc = Pi^T r (r masked), then yc = C rc
 void coarse_correction(Ctx &c, cudaStream_t st, const double *r, const int *done);
+void coarse_correction(Ctx &c, cudaStream_t st, const float *r, const int *done);
+// yc = C rc only (the fused two-level iterations restrict r themselves)
+void coarse_gemv(const CoarseDev &cs, cudaStream_t st, const int *done);
 
 // solves (solve.cu); a Snapshot, when given, sees the iterate x and the
 // residual r (device, ndof) of the flexible PCG before its first iteration

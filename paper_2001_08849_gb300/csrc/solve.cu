@@ -22,6 +22,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
+#include <type_traits>
 
 #include "reduce.cuh"
 #include "sfem_internal.cuh"
@@ -44,7 +45,8 @@ struct PcgVecs {
   int64_t n;
   bool coarse = false;  // two-level preconditioner: z = D^-1 r + P Pi yc
   CoarseDev cs{};
-  TP *z = nullptr;      // two-level: z of the current r (written by k_pcg_zr)
+  float *z32 = nullptr;  // two-level: z of the current r in FP32 (written by k_tl_zr)
+  const float *dinv32 = nullptr;
 };
 
 // preconditioned residual of DOF i (the coarse correction yc of the current
@@ -134,83 +136,72 @@ __global__ void __launch_bounds__(kVecBlock) k_pcg_replace_dir(PcgVecs<TX, TR, T
   }
 }
 
+// the last block of an update: iteration count, convergence, reliable-update
+// trigger (||r||^2 = rr)
+__device__ __forceinline__ void finish_update(SolveScalars *S, double alpha, double rz_old, double rr) {
+  S->alpha = alpha;
+  S->rz_prev = rz_old;
+  S->rr = rr;
+  S->iter += 1;
+  S->rmax2 = fmax(S->rmax2, rr);
+  if (rr <= S->tol2) {
+    S->done = 1;
+    S->reason = 1;
+  } else if (S->iter >= S->max_iter) {
+    S->done = 1;
+    S->reason = 3;
+  } else if (rr < S->delta2 * S->rmax2) {
+    S->done = 1;
+    S->reason = 2;
+  }
+  if (!isfinite(rr)) {
+    S->status = 1;
+    S->done = 1;
+  }
+}
+
+// alpha = rz / pq, or a breakdown flag (all blocks see the same scalars and
+// return together)
+__device__ __forceinline__ bool step_length(SolveScalars *S, double &alpha, double &rz_old) {
+  const double pq = S->pq;
+  rz_old = S->rz;
+  alpha = rz_old / pq;
+  if (!(pq > 0.0) || !isfinite(alpha)) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      S->status = 1;
+      S->done = 1;
+    }
+    return false;
+  }
+  return true;
+}
+
 // x += alpha p, r -= alpha P q, then rz_new, rr; the last block sets beta,
 // the convergence flag and the reliable-update trigger.
 template <class TX, class TR, class TP>
 __global__ void __launch_bounds__(kVecBlock) k_pcg_update(PcgVecs<TX, TR, TP> v, SolveScalars *S,
                                                           double *partials, unsigned int *ticket) {
   if (S->done) return;
-  const double pq = S->pq, rz_old = S->rz;
-  const double alpha = rz_old / pq;
-  if (!(pq > 0.0) || !isfinite(alpha)) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-      S->status = 1;
-      S->done = 1;
-    }
-    return;
-  }
+  double alpha, rz_old;
+  if (!step_length(S, alpha, rz_old)) return;
   const TX ax = (TX)alpha;
   const TR ar = (TR)alpha;
   double rz = 0.0, rr = 0.0;
-  const bool coarse = v.coarse;
 #pragma unroll 4
   for (int64_t i = (int64_t)blockIdx.x * kVecBlock + threadIdx.x; i < v.n; i += (int64_t)gridDim.x * kVecBlock) {
     v.x[i] += ax * (TX)v.p[i];
     const TR ri = v.dmask[i] ? v.r[i] - ar * (TR)v.q[i] : TR(0);
     v.r[i] = ri;
     const TP rp = (TP)ri;
-    if (!coarse) rz += (double)(v.dinv[i] * rp * rp);
+    rz += (double)(v.dinv[i] * rp * rp);
     rr += (double)(rp * rp);
   }
   double vv[2] = {rz, rr};
   if (grid_sum<kVecBlock, 2>(vv, partials, ticket, nullptr) && threadIdx.x == 0) {
-    S->alpha = alpha;
-    S->rz_prev = rz_old;
-    if (!coarse) {  // with the coarse correction, k_pcg_zr forms z.r and beta
-      S->beta = vv[0] / rz_old;
-      S->rz = vv[0];
-    }
-    S->rr = vv[1];
-    S->iter += 1;
-    S->rmax2 = fmax(S->rmax2, vv[1]);
-    if (vv[1] <= S->tol2) {
-      S->done = 1;
-      S->reason = 1;
-    } else if (S->iter >= S->max_iter) {
-      S->done = 1;
-      S->reason = 3;
-    } else if (vv[1] < S->delta2 * S->rmax2) {
-      S->done = 1;
-      S->reason = 2;
-    }
-    if (!isfinite(vv[0]) || !isfinite(vv[1])) {
-      S->status = 1;
-      S->done = 1;
-    }
-  }
-}
-
-// two-level preconditioner: z.r of the new residual (its coarse correction
-// already computed), beta = z.r / z_prev.r_prev.  (A Polak-Ribiere beta,
-// which would absorb the FP32 rounding of the coarse correction, took 9%
-// more iterations to 1e-8 on the 2M-tet beam.)
-template <class TX, class TR, class TP>
-__global__ void __launch_bounds__(kVecBlock) k_pcg_zr(PcgVecs<TX, TR, TP> v, SolveScalars *S, double *partials,
-                                                      unsigned int *ticket) {
-  if (S->done) return;
-  double rz = 0.0;
-#pragma unroll 4
-  for (int64_t i = (int64_t)blockIdx.x * kVecBlock + threadIdx.x; i < v.n; i += (int64_t)gridDim.x * kVecBlock) {
-    const TP ri = (TP)v.r[i];
-    const TP zi = precond_z(v, i, ri);
-    v.z[i] = zi;
-    rz += (double)(zi * ri);
-  }
-  double vv[1] = {rz};
-  if (grid_sum<kVecBlock, 1>(vv, partials, ticket, nullptr) && threadIdx.x == 0) {
-    S->beta = vv[0] / S->rz_prev;
+    S->beta = vv[0] / rz_old;
     S->rz = vv[0];
-    if (!isfinite(vv[0]) || !(vv[0] > 0.0)) {
+    finish_update(S, alpha, rz_old, vv[1]);
+    if (!isfinite(vv[0])) {
       S->status = 1;
       S->done = 1;
     }
@@ -223,19 +214,166 @@ __global__ void __launch_bounds__(kVecBlock) k_pcg_direction(PcgVecs<TX, TR, TP>
                                                              bool zero_q) {
   if (S->done) return;
   const TP b = (TP)S->beta;
-  if (v.coarse) {  // z was stored by k_pcg_zr
-#pragma unroll 4
-    for (int64_t i = (int64_t)blockIdx.x * kVecBlock + threadIdx.x; i < v.n; i += (int64_t)gridDim.x * kVecBlock) {
-      v.p[i] = v.z[i] + b * v.p[i];
-      if (zero_q) v.q[i] = TP(0);
-    }
-    return;
-  }
 #pragma unroll 4
   for (int64_t i = (int64_t)blockIdx.x * kVecBlock + threadIdx.x; i < v.n; i += (int64_t)gridDim.x * kVecBlock) {
     v.p[i] = precond_z(v, i, (TP)v.r[i]) + b * v.p[i];
     if (zero_q) v.q[i] = TP(0);
   }
+}
+
+// ---- two-level iteration ------------------------------------------------------
+// With the coarse correction an iteration makes three passes over the
+// vectors around the coarse GEMV:
+//   k_tl_update  x += alpha p, r = P (r - alpha q), q = 0, ||r||^2, and the
+//                restriction rc += Pi^T r: one block per run of a cell's
+//                nodes, block sums added to the cell's 8 centres by FP32
+//                atomics;
+//   k_cs_gemv    yc = C rc;
+//   k_tl_zr      z = D^-1 r + P Pi yc in FP32 (stored), z.r and beta; rc = 0
+//                for the next restriction;
+//   k_tl_dir     p = z + beta p.
+// z, the restriction and the dot products' per-thread sums are FP32 (the
+// preconditioner and the step lengths tolerate 1e-7 relative rounding);
+// x, r and p stay FP64.  FP64 arithmetic is 1/64 of FP32 on this GPU, so the
+// FP32 parts keep the FP64 pipe to two FMAs and two conversions per DOF.
+template <class TR, class TP>
+__global__ void __launch_bounds__(kVecBlock) k_tl_update(PcgVecs<double, TR, TP> v, SolveScalars *S, bool zero_q,
+                                                         unsigned int *ticket) {
+  if (S->done) return;
+  double alpha, rz_old;
+  if (!step_length(S, alpha, rz_old)) return;
+  const TR ar = (TR)alpha;
+  const CoarseDev &cs = v.cs;
+  const int4 ch = cs.chunk[blockIdx.x];
+  double *__restrict__ x = v.x;
+  TR *__restrict__ r = v.r;
+  TP *__restrict__ q = v.q;
+  const TP *__restrict__ p = v.p;
+  const uint8_t *__restrict__ msk = v.dmask;
+  float acc[24];
+#pragma unroll
+  for (int j = 0; j < 24; ++j) acc[j] = 0.f;
+  float rr = 0.f;
+  for (int k = ch.y + threadIdx.x; k < ch.z; k += kVecBlock) {
+    const int64_t i0 = 3 * (int64_t)cs.cnodes[k];
+    double xv[3];
+    TP pv[3], qv[3];
+    TR rv[3];
+    uint8_t mv[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      xv[c] = x[i0 + c];
+      pv[c] = p[i0 + c];
+      qv[c] = q[i0 + c];
+      rv[c] = r[i0 + c];
+      mv[c] = msk[i0 + c];
+    }
+    const float f[3] = {cs.frac[i0], cs.frac[i0 + 1], cs.frac[i0 + 2]};
+    float rf[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      x[i0 + c] = fma(alpha, (double)pv[c], xv[c]);
+      const TR rn = mv[c] ? fma(-ar, (TR)qv[c], rv[c]) : TR(0);
+      r[i0 + c] = rn;
+      if (zero_q) q[i0 + c] = TP(0);
+      rf[c] = (float)rn;
+      rr = fmaf(rf[c], rf[c], rr);
+    }
+#pragma unroll
+    for (int kk = 0; kk < 8; ++kk) {
+      const float w = cs_weight(f, kk);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) acc[3 * kk + c] = fmaf(w, rf[c], acc[3 * kk + c]);
+    }
+  }
+  __shared__ float sm[kVecBlock / 32][24];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < 24; ++j) {
+    float t = acc[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    if (lane == 0) sm[wid][j] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x < 24) {
+    float t = 0.f;
+#pragma unroll
+    for (int w = 0; w < kVecBlock / 32; ++w) t += sm[w][threadIdx.x];
+    const int kk = threadIdx.x / 3, c = threadIdx.x - 3 * kk;
+    atomicAdd(&cs.rc[3 * cs_corner(cs, ch.x, kk) + c], t);
+  }
+  double vv[1] = {(double)rr};
+  if (grid_sum<kVecBlock, 1>(vv, cs.chunk_part, ticket, nullptr) && threadIdx.x == 0)
+    finish_update(S, alpha, rz_old, vv[0]);
+}
+
+template <class TR, class TP>
+__global__ void __launch_bounds__(kVecBlock) k_tl_zr(PcgVecs<double, TR, TP> v, SolveScalars *S, double *partials,
+                                                     unsigned int *ticket) {
+  if (S->done) return;
+  const CoarseDev &cs = v.cs;
+  if (blockIdx.x == 0)  // k_cs_gemv has consumed rc
+    for (int i = threadIdx.x; i < cs.npad; i += kVecBlock) cs.rc[i] = 0.f;
+  const TR *__restrict__ r = v.r;
+  const float *__restrict__ dinv = v.dinv32;
+  const uint8_t *__restrict__ msk = v.dmask;
+  float *__restrict__ z = v.z32;
+  const float *__restrict__ yc = cs.yc;
+  const int64_t nn = v.n / 3;
+  const int sx = 3 * cs.d[1] * cs.d[2], sy = 3 * cs.d[2];
+  float rz = 0.f;
+  for (int64_t node = (int64_t)blockIdx.x * kVecBlock + threadIdx.x; node < nn;
+       node += (int64_t)gridDim.x * kVecBlock) {
+    const int64_t i0 = 3 * node;
+    TR rv[3];
+    float dv[3];
+    uint8_t mv[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      rv[c] = r[i0 + c];
+      dv[c] = dinv[i0 + c];
+      mv[c] = msk[i0 + c];
+    }
+    const int ci = cs.cinfo[node];
+    const float f[3] = {cs.frac[i0], cs.frac[i0 + 1], cs.frac[i0 + 2]};
+    const float *yb = yc + 3 * (ci & 0xFFFFFF);
+    const int ox = ((ci >> 24) & 1) ? sx : 0, oy = ((ci >> 25) & 1) ? sy : 0, oz = ((ci >> 26) & 1) ? 3 : 0;
+    float y[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int kk = 0; kk < 8; ++kk) {
+      const float w = cs_weight(f, kk);
+      const float *yk = yb + ((kk & 4) ? ox : 0) + ((kk & 2) ? oy : 0) + ((kk & 1) ? oz : 0);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) y[c] = fmaf(w, yk[c], y[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float rf = (float)rv[c];
+      const float zc = fmaf(dv[c], rf, mv[c] ? y[c] : 0.f);
+      z[i0 + c] = zc;
+      rz = fmaf(zc, rf, rz);
+    }
+  }
+  double vv[1] = {(double)rz};
+  if (grid_sum<kVecBlock, 1>(vv, partials, ticket, nullptr) && threadIdx.x == 0) {
+    S->beta = vv[0] / S->rz_prev;
+    S->rz = vv[0];
+    if (!isfinite(vv[0]) || !(vv[0] > 0.0)) {
+      S->status = 1;
+      S->done = 1;
+    }
+  }
+}
+
+template <class TP>
+__global__ void __launch_bounds__(kVecBlock) k_tl_dir(TP *__restrict__ p, const float *__restrict__ z, int64_t n,
+                                                      const SolveScalars *S) {
+  if (S->done) return;
+  const TP b = (TP)S->beta;
+#pragma unroll 4
+  for (int64_t i = (int64_t)blockIdx.x * kVecBlock + threadIdx.x; i < n; i += (int64_t)gridDim.x * kVecBlock)
+    p[i] = fma(b, p[i], (TP)z[i]);
 }
 
 // ---- FP64 residual and refinement helpers ----------------------------------
@@ -398,13 +536,21 @@ struct CgRun {
       // tiled FP32 operator reading p and accumulating q in type TP
       launch_mf32_tiled<TP, TP>(c, st, v.p, v.q, &S->pq, done);
     }
+    if constexpr (std::is_same_v<TX, double>) {
+      if (v.coarse) {
+        const CoarseDev &cs = v.cs;
+        k_tl_update<TR, TP><<<cs.nchunk, kVecBlock, 0, st>>>(v, S, mf, c.tickets + 3);
+        SFEM_CHECK_LAUNCH();
+        coarse_gemv(cs, st, done);
+        k_tl_zr<TR, TP><<<c.red_blocks, kVecBlock, 0, st>>>(v, S, c.red_partial, c.tickets + 10);
+        SFEM_CHECK_LAUNCH();
+        k_tl_dir<TP><<<c.red_blocks, kVecBlock, 0, st>>>(v.p, v.z32, v.n, S);
+        SFEM_CHECK_LAUNCH();
+        return;
+      }
+    }
     k_pcg_update<TX, TR, TP><<<c.red_blocks, kVecBlock, 0, st>>>(v, S, c.red_partial, c.tickets + 3);
     SFEM_CHECK_LAUNCH();
-    if (v.coarse) {
-      coarse_correction(c, st, reinterpret_cast<const double *>(v.r), done);
-      k_pcg_zr<TX, TR, TP><<<c.red_blocks, kVecBlock, 0, st>>>(v, S, c.red_partial, c.tickets + 10);
-      SFEM_CHECK_LAUNCH();
-    }
     k_pcg_direction<TX, TR, TP><<<c.red_blocks, kVecBlock, 0, st>>>(v, S, mf);
     SFEM_CHECK_LAUNCH();
   }
@@ -432,21 +578,28 @@ struct CgRun {
 
   // r holds the masked residual on entry: (re)start CG from it.
   SolveScalars start(double tol2, int max_iter, double delta2) {
-    if (v.coarse) coarse_correction(c, c.stream, reinterpret_cast<const double *>(v.r), nullptr);
+    if (v.coarse) coarse_correction(c, c.stream, v.r, nullptr);
     k_pcg_init<TX, TR, TP><<<c.red_blocks, kVecBlock, 0, c.stream>>>(v, c.scal, tol2, max_iter, delta2,
                                                                       c.red_partial, c.tickets + 4);
     SFEM_CHECK_LAUNCH();
+    clear_restriction();
     return resume(max_iter);
+  }
+
+  // the iterations accumulate the restriction into rc by atomics
+  void clear_restriction() {
+    if (v.coarse) SFEM_CUDA(cudaMemsetAsync(v.cs.rc, 0, v.cs.npad * sizeof(float), c.stream));
   }
 
   // r has been replaced by the true residual: keep p, recompute beta, go on.
   SolveScalars replace(int max_iter) {
-    if (v.coarse) coarse_correction(c, c.stream, reinterpret_cast<const double *>(v.r), nullptr);
+    if (v.coarse) coarse_correction(c, c.stream, v.r, nullptr);
     k_pcg_replace<TX, TR, TP><<<c.red_blocks, kVecBlock, 0, c.stream>>>(v, c.scal, max_iter, c.red_partial,
                                                                          c.tickets + 5);
     SFEM_CHECK_LAUNCH();
     k_pcg_replace_dir<TX, TR, TP><<<c.red_blocks, kVecBlock, 0, c.stream>>>(v, c.scal);
     SFEM_CHECK_LAUNCH();
+    clear_restriction();
     return resume(max_iter);
   }
 
@@ -529,9 +682,11 @@ void solve_impl(Ctx &c, const double *f_extra, double *u, const sfem_solve_opts 
   const bool coarse = o.precond == 1;
   if (coarse) {
     SFEM_REQUIRE(c.coarse != nullptr, SFEM_EINVAL, "precond = 1 needs sfem_coarse_setup first");
-    SFEM_REQUIRE(o.kind == SFEM_SOLVE_PCG64 || (o.kind == SFEM_SOLVE_IR32_64 && o.fp32_vectors == 0), SFEM_EINVAL,
-                 "the coarse correction works with PCG64 and with IR32_64 on FP64 vectors");
+    SFEM_REQUIRE(o.kind == SFEM_SOLVE_PCG64 ||
+                     (o.kind == SFEM_SOLVE_IR32_64 && (o.fp32_vectors == 0 || o.fp32_vectors == 3)),
+                 SFEM_EINVAL, "the coarse correction works with PCG64 and with IR32_64 on an FP64 correction");
   }
+  SFEM_REQUIRE(o.fp32_vectors >= 0 && o.fp32_vectors <= 3, SFEM_EINVAL, "fp32_vectors must be 0, 1, 2 or 3");
 
   cudaEvent_t e0, e1;
   SFEM_CUDA(cudaEventCreate(&e0));
@@ -539,12 +694,13 @@ void solve_impl(Ctx &c, const double *f_extra, double *u, const sfem_solve_opts 
   SFEM_CUDA(cudaEventRecord(e0, c.stream));
 
   SolveBuffers B(c);
-  double *zbuf = coarse ? B.get<double>(n) : nullptr;
-  auto with_coarse = [&](PcgVecs<double, double, double> &vv) {
+  float *zbuf = coarse ? B.get<float>(n) : nullptr;
+  auto with_coarse = [&](auto &vv) {
     if (coarse) {
       vv.coarse = true;
       vv.cs = c.coarse->dev;
-      vv.z = zbuf;
+      vv.z32 = zbuf;
+      vv.dinv32 = c.dinv32;
     }
   };
   // total load f (+ f_extra) and ||b||
@@ -658,58 +814,92 @@ void solve_impl(Ctx &c, const double *f_extra, double *u, const sfem_solve_opts 
           rel = true_residual();  // writes the FP64 true residual into r = v.r
         }
       } else {
-        // default: every CG vector in FP64 (correction d, residual r, search
-        // direction p, operator output q); the FP32 operator reads p in FP64
-        // and accumulates q in FP64.  An FP32 d or p doubled the iteration
-        // count on the 2M-tet beam: their rounding re-enters the FP64 true
-        // residual amplified by the condition number at every update.
-        PcgVecs<double, double, double> v{B.get<double>(n), r, B.get<double>(n), B.get<double>(n), c.dinv64,
-                                          c.dmask, n};
-        with_coarse(v);
-        CgRun<double, double, double> cg(c, v, SFEM_OP_MF32, chunk);
-        SFEM_CUDA(cudaMemsetAsync(v.x, 0, n * sizeof(double), c.stream));
-        bool started = false;
-        double best = rel;
-        int stall = 0;
-        while (rel > tol && total_iter < max_iter && outer < max_outer) {
-          SolveScalars s = started ? cg.replace(max_iter)
-                                   : cg.start(tol * tol * bnorm * bnorm, max_iter, delta * delta);
-          started = true;
-          total_iter = s.iter;
-          ++outer;
-          if (s.status) {
-            status = SFEM_EBREAKDOWN;
-            break;
-          }
-          k_add<<<g256, 256, 0, c.stream>>>(x, v.x, n);  // u += d
-          SFEM_CHECK_LAUNCH();
-          SFEM_CUDA(cudaMemsetAsync(v.x, 0, n * sizeof(double), c.stream));  // d = 0
-          rel = true_residual();  // writes the FP64 true residual into r = v.r
-          // stagnation: the FP32 operator's error floor lies above tol
-          if (rel < 0.9 * best) {
-            best = rel;
-            stall = 0;
-          } else if (++stall >= 3) {
-            break;
-          }
-        }
-        if (rel > tol && status == SFEM_OK && stall >= 3 && total_iter < max_iter) {
-          // finish with FP64 Jacobi-PCG from the current solution
-          ensure_w_scratch(c, (size_t)c.n_tets * 8 * sizeof(double));
-          PcgVecs<double, double, double> v2{x, r, v.p, v.q, c.dinv64, c.dmask, n};
-          with_coarse(v2);
-          CgRun<double, double, double> cg2(c, v2, op64, chunk);
-          info.fallbacks = 1;
-          for (int restart = 0; rel > tol && total_iter < max_iter && restart <= 10; ++restart) {
-            SolveScalars s2 = cg2.start(tol * tol * bnorm * bnorm, max_iter - total_iter, 0.0);
-            total_iter += s2.iter;
-            if (s2.status) {
+        // 0 (default): every CG vector in FP64 (correction d, residual r,
+        // search direction p, operator output q); the FP32 operator reads p
+        // in FP64 and accumulates q in FP64.  With Jacobi alone, an FP32 d
+        // or p doubled the iteration count on the 2M-tet beam: their
+        // rounding re-enters the FP64 true residual amplified by the
+        // condition number at every update.
+        // 3: FP64 correction d; FP32 r, p, q (and z): with the two-level
+        // preconditioner the inner iterations converge in as many steps as
+        // with FP64 vectors (emulated on a 123k-tet beam: 428 vs 426), at
+        // half the vector traffic and no FP64 arithmetic beyond d += alpha p.
+        auto reliable = [&](auto tag) {
+          using TV = decltype(tag);
+          constexpr bool f64 = std::is_same_v<TV, double>;
+          TV *rv = nullptr;
+          if constexpr (f64)
+            rv = r;
+          else
+            rv = B.get<TV>(n);
+          const TV *dinv = nullptr;
+          if constexpr (f64)
+            dinv = c.dinv64;
+          else
+            dinv = c.dinv32;
+          PcgVecs<double, TV, TV> v{B.get<double>(n), rv, B.get<TV>(n), B.get<TV>(n), dinv, c.dmask, n};
+          with_coarse(v);
+          CgRun<double, TV, TV> cg(c, v, SFEM_OP_MF32, chunk);
+          SFEM_CUDA(cudaMemsetAsync(v.x, 0, n * sizeof(double), c.stream));
+          bool started = false;
+          double best = rel;
+          int stall = 0;
+          while (rel > tol && total_iter < max_iter && outer < max_outer) {
+            if constexpr (!f64) {
+              k_to_f32<<<g256, 256, 0, c.stream>>>(r, n, v.r);
+              SFEM_CHECK_LAUNCH();
+            }
+            SolveScalars s = started ? cg.replace(max_iter)
+                                     : cg.start(tol * tol * bnorm * bnorm, max_iter, delta * delta);
+            started = true;
+            total_iter = s.iter;
+            ++outer;
+            if (s.status) {
               status = SFEM_EBREAKDOWN;
               break;
             }
-            rel = true_residual();
+            k_add<<<g256, 256, 0, c.stream>>>(x, v.x, n);  // u += d
+            SFEM_CHECK_LAUNCH();
+            SFEM_CUDA(cudaMemsetAsync(v.x, 0, n * sizeof(double), c.stream));  // d = 0
+            rel = true_residual();  // the FP64 true residual into r
+            // stagnation: the FP32 operator's error floor lies above tol
+            if (rel < 0.9 * best) {
+              best = rel;
+              stall = 0;
+            } else if (++stall >= 3) {
+              break;
+            }
           }
-        }
+          if (rel > tol && status == SFEM_OK && stall >= 3 && total_iter < max_iter) {
+            // finish with FP64 PCG from the current solution
+            ensure_w_scratch(c, (size_t)c.n_tets * 8 * sizeof(double));
+            double *p2 = nullptr, *q2 = nullptr;
+            if constexpr (f64) {
+              p2 = v.p;
+              q2 = v.q;
+            } else {
+              p2 = B.get<double>(n);
+              q2 = B.get<double>(n);
+            }
+            PcgVecs<double, double, double> v2{x, r, p2, q2, c.dinv64, c.dmask, n};
+            with_coarse(v2);
+            CgRun<double, double, double> cg2(c, v2, op64, chunk);
+            info.fallbacks = 1;
+            for (int restart = 0; rel > tol && total_iter < max_iter && restart <= 10; ++restart) {
+              SolveScalars s2 = cg2.start(tol * tol * bnorm * bnorm, max_iter - total_iter, 0.0);
+              total_iter += s2.iter;
+              if (s2.status) {
+                status = SFEM_EBREAKDOWN;
+                break;
+              }
+              rel = true_residual();
+            }
+          }
+        };
+        if (o.fp32_vectors == 3)
+          reliable(float{});
+        else
+          reliable(double{});
       }
     } else if (o.kind == SFEM_SOLVE_FPCG_LEARNED) {
       const int window = o.learned_window > 0 ? o.learned_window : 100;

@@ -154,7 +154,7 @@ __device__ __forceinline__ void tile_strains(const TileArgs &A, const TileRegs &
 // face-averaged stress of every own tet and its four nodal force slots;
 // returns this thread's share of the energy sum w . t
 __device__ __forceinline__ double tile_forces(const TileRegs &R, const TileView &T, float lam, float mu) {
-  double en = 0.0;
+  float en = 0.f;  // this thread's kTilePer tets; FP64 from the block sum on
 #pragma unroll
   for (int r = 0; r < kTilePer; ++r) {
     const int j = threadIdx.x + r * kTileThreads;
@@ -194,7 +194,7 @@ __device__ __forceinline__ double tile_forces(const TileRegs &R, const TileView 
     float el = 0.f;
 #pragma unroll
     for (int i = 0; i < 6; ++i) el = fmaf(W[i], st[i], el);
-    en += (double)el;
+    en += el;
     float f[12];
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
@@ -207,7 +207,7 @@ __device__ __forceinline__ double tile_forces(const TileRegs &R, const TileView 
     fo[1] = make_float4(f[4], f[5], f[6], f[7]);
     fo[2] = make_float4(f[8], f[9], f[10], f[11]);
   }
-  return en;
+  return (double)en;
 }
 
 // the force at tile node i: its own slots summed in a fixed order with
@@ -246,12 +246,13 @@ __device__ __forceinline__ double tile_compute(const TileArgs &A, int tile, cons
   const TileView T = tile_view(A, tile, smem);
   // Strains are differences of nodal displacements, and K annihilates
   // constant fields (the shape-function gradients of a tet sum to zero), so
-  // with FP64 input the tile subtracts the displacement of its first node
-  // before rounding to FP32: the rounding then acts on the small tile-local
-  // differences instead of the full displacements, which removes most of
-  // the cancellation error of the FP32 strains.
-  TU ref[3] = {TU(0), TU(0), TU(0)};
-  if constexpr (sizeof(TU) == 8) {
+  // the tile subtracts the displacement of its first node (in the input's
+  // precision) before the FP32 strain arithmetic: the rounding then acts on
+  // the small tile-local differences instead of the full displacements,
+  // which removes most of the cancellation error of the FP32 strains.
+  // (With FP32 input the differences of nearby values are exact.)
+  TU ref[3];
+  {
     const TU *rp = u + 3 * (int64_t)A.tile_nodes[T.n0];
 #pragma unroll
     for (int c = 0; c < 3; ++c) ref[c] = kCoherentU ? __ldcg(rp + c) : __ldg(rp + c);

@@ -52,15 +52,28 @@ static double from_ordered_bits(unsigned long long b) {
   return d;
 }
 
+// bounding box as ordered bit patterns: a grid-stride loop per thread, a
+// warp reduction, then one atomic per warp and axis (launched with whole
+// warps)
 __global__ void k_bbox(const double *__restrict__ xyz, int64_t n_nodes, unsigned long long *mn,
                        unsigned long long *mx) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n_nodes) return;
-  for (int k = 0; k < 3; ++k) {
-    unsigned long long b = ordered_bits(xyz[3 * i + k]);
-    atomicMin(&mn[k], b);
-    atomicMax(&mx[k], b);
-  }
+  unsigned long long lo[3] = {~0ull, ~0ull, ~0ull}, hi[3] = {0ull, 0ull, 0ull};
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_nodes; i += (int64_t)gridDim.x * blockDim.x)
+    for (int k = 0; k < 3; ++k) {
+      const unsigned long long b = ordered_bits(xyz[3 * i + k]);
+      lo[k] = min(lo[k], b);
+      hi[k] = max(hi[k], b);
+    }
+  for (int k = 0; k < 3; ++k)
+    for (int o = 16; o > 0; o >>= 1) {
+      lo[k] = min(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
+      hi[k] = max(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
+    }
+  if ((threadIdx.x & 31) == 0 && lo[0] != ~0ull)
+    for (int k = 0; k < 3; ++k) {
+      atomicMin(&mn[k], lo[k]);
+      atomicMax(&mx[k], hi[k]);
+    }
 }
 
 struct BinGrid {
@@ -155,9 +168,39 @@ __device__ void block_bitonic_sort(int *a, int P) {
   }
 }
 
+// exclusive prefix sum of v over the block (blockDim.x a multiple of 32, at
+// most 1024); *total receives the block's sum.  All threads must call it.
+__device__ int block_exclusive_scan(int v, int *total) {
+  __shared__ int wsum[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  __syncthreads();
+  if (lane == 31) wsum[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    int w = lane < nw ? wsum[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < nw) wsum[lane] = w;  // inclusive over warps
+  }
+  __syncthreads();
+  *total = wsum[nw - 1];
+  const int before = wid > 0 ? wsum[wid - 1] : 0;
+  __syncthreads();
+  return before + x - v;
+}
+
 // compact the sorted a[0..P) to its unique values < INT_MAX (in place);
 // returns the count (all threads)
-__device__ int block_unique(int *a, int P, int *scratch /* blockDim */) {
+__device__ int block_unique(int *a, int P) {
   // each thread owns a contiguous chunk, so the order of heads is kept
   const int chunk = (P + blockDim.x - 1) / blockDim.x;
   const int b = threadIdx.x * chunk, e = min(P, b + chunk);
@@ -166,20 +209,8 @@ __device__ int block_unique(int *a, int P, int *scratch /* blockDim */) {
     int v = a[i];
     if (v != INT_MAX && (i == 0 || a[i - 1] != v)) ++c;
   }
-  scratch[threadIdx.x] = c;
-  __syncthreads();
-  // exclusive scan over threads (small: done by thread 0)
-  __shared__ int total;
-  if (threadIdx.x == 0) {
-    int run = 0;
-    for (int t = 0; t < (int)blockDim.x; ++t) {
-      int x = scratch[t];
-      scratch[t] = run;
-      run += x;
-    }
-    total = run;
-  }
-  __syncthreads();
+  int total;
+  const int start = block_exclusive_scan(c, &total);
   // gather heads into registers first (the compaction is in place)
   int vals[64];
   int nv = 0;
@@ -188,9 +219,16 @@ __device__ int block_unique(int *a, int P, int *scratch /* blockDim */) {
     if (v != INT_MAX && (i == 0 || a[i - 1] != v)) vals[nv++] = v;
   }
   __syncthreads();
-  for (int k = 0; k < nv; ++k) a[scratch[threadIdx.x] + k] = vals[k];
+  for (int k = 0; k < nv; ++k) a[start + k] = vals[k];
   __syncthreads();
   return total;
+}
+
+// smallest power of two >= n (at least 32)
+__device__ __forceinline__ int pow2_at_least(int n) {
+  int p = 32;
+  while (p < n) p <<= 1;
+  return p;
 }
 
 __device__ __forceinline__ int bsearch_int(const int *a, int n, int key) {
@@ -235,12 +273,13 @@ __global__ void __launch_bounds__(kBuildThreads) k_tile_build(TileBuild B, int p
   extern __shared__ int sm[];
   int *halo = sm;                 // kHaloP
   int *nodes = sm + kHaloP;       // kNodeP
-  __shared__ int scratch[kBuildThreads];
   const int tile = blockIdx.x;
   const int s = B.tile_start[tile], e = B.tile_start[tile + 1];
   const int n_own = e - s;
-  // halo candidates: neighbours outside [s, e)
-  for (int i = threadIdx.x; i < kHaloP; i += blockDim.x) halo[i] = INT_MAX;
+  // halo candidates: neighbours outside [s, e); the sorts cover the
+  // smallest power of two that holds the candidates
+  const int PH = pow2_at_least(4 * n_own);
+  for (int i = threadIdx.x; i < PH; i += blockDim.x) halo[i] = INT_MAX;
   __syncthreads();
   for (int i = threadIdx.x; i < 4 * n_own; i += blockDim.x) {
     const int tnew = s + i / 4, a = i % 4;
@@ -251,10 +290,11 @@ __global__ void __launch_bounds__(kBuildThreads) k_tile_build(TileBuild B, int p
     }
   }
   __syncthreads();
-  block_bitonic_sort(halo, kHaloP);
-  const int H = block_unique(halo, kHaloP, scratch);
+  block_bitonic_sort(halo, PH);
+  const int H = block_unique(halo, PH);
   // node candidates of own and halo tets
-  for (int i = threadIdx.x; i < kNodeP; i += blockDim.x) nodes[i] = INT_MAX;
+  const int PN = pow2_at_least(4 * (n_own + H));
+  for (int i = threadIdx.x; i < PN; i += blockDim.x) nodes[i] = INT_MAX;
   __syncthreads();
   for (int i = threadIdx.x; i < 4 * (n_own + H); i += blockDim.x) {
     const int j = i / 4, a = i % 4;
@@ -262,8 +302,8 @@ __global__ void __launch_bounds__(kBuildThreads) k_tile_build(TileBuild B, int p
     nodes[i] = B.tets[4 * (int64_t)B.perm[tnew] + a];
   }
   __syncthreads();
-  block_bitonic_sort(nodes, kNodeP);
-  const int L = block_unique(nodes, kNodeP, scratch);
+  block_bitonic_sort(nodes, PN);
+  const int L = block_unique(nodes, PN);
   if (pass == 1) {
     if (threadIdx.x == 0) {
       B.n_halo[tile] = H;
@@ -279,7 +319,7 @@ __global__ void __launch_bounds__(kBuildThreads) k_tile_build(TileBuild B, int p
   // still needed below), so use a separate scratch: the tail of `nodes`
   // past L is free.
   int *keys = nodes + ((L + 31) & ~31);
-  const int KP = kHaloP;  // 4 * kTileMax slots, power of two
+  const int KP = PH;  // >= 4 n_own slots, power of two
   for (int i = threadIdx.x; i < KP; i += blockDim.x) {
     int v = INT_MAX;
     if (i < 4 * n_own) {
@@ -377,7 +417,7 @@ void build_tiles(Ctx &c) {
     init[3 + k] = 0ull;
   }
   SFEM_CUDA(cudaMemcpyAsync(bb, init, sizeof init, cudaMemcpyHostToDevice, c.stream));
-  k_bbox<<<grid_for(c.n_nodes, 256), 256, 0, c.stream>>>(c.xyz, c.n_nodes, bb, bb + 3);
+  k_bbox<<<(unsigned)std::min<int64_t>(grid_for(c.n_nodes, 256), 4 * 152), 256, 0, c.stream>>>(c.xyz, c.n_nodes, bb, bb + 3);
   SFEM_CHECK_LAUNCH();
   unsigned long long hb[6];
   SFEM_CUDA(cudaMemcpyAsync(hb, bb, sizeof hb, cudaMemcpyDeviceToHost, c.stream));

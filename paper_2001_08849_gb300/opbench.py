@@ -53,6 +53,7 @@ def main(argv=None):
     ap.add_argument("--precond", type=int, default=0, help="1: two-level preconditioner (pcg64, ir32_64)")
     ap.add_argument("--coarse-dims", type=int, nargs=3, default=None, help="patch centres per axis")
     ap.add_argument("--repeat", type=int, default=1, help="solves (the last one is reported)")
+    ap.add_argument("--fp32-vectors", type=int, default=0, help="ir32_64 vector precision (sfem_solve_opts)")
     a = ap.parse_args(argv)
     import torch
     import __graft_entry__
@@ -84,7 +85,7 @@ def main(argv=None):
                                  max_iter=a.max_iter, precond=a.precond)
             elif a.solve == "ir32_64":
                 o = S.solve_opts(kind=S.SFEM_SOLVE_IR32_64, tol=a.tol, u_on_device=True, max_iter=a.max_iter,
-                                 precond=a.precond)
+                                 precond=a.precond, fp32_vectors=a.fp32_vectors)
             else:
                 S.sfem_assemble(ctx.h)
                 if a.solve == "fpcg_learned":
@@ -99,7 +100,8 @@ def main(argv=None):
                 info = S.sfem_solve(ctx.h, u, o, check=False)
                 torch.cuda.synchronize()
             out = {"solve": a.solve, "cells": a.cells, "n_tets": n_tets, "ndof": ctx.ndof,
-                   "time_s": time.perf_counter() - t0, "coarse": coarse, **info}
+                   "time_s": time.perf_counter() - t0, "mesh_setup_ms": ctx.info["setup_ms"], "coarse": coarse,
+                   **info}
             if model is not None:
                 model.close()
     print(json.dumps(out), flush=True)

@@ -81,7 +81,7 @@ class sfem_batch_stats(ctypes.Structure):
 
 class sfem_coarse_opts(ctypes.Structure):
     _fields_ = [("patch_dims", ctypes.c_int * 3), ("patch_nodes", ctypes.c_int), ("assembly", ctypes.c_int),
-                ("reserved", ctypes.c_int * 7)]
+                ("factor", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
 
 
 class sfem_learned_opts(ctypes.Structure):
@@ -381,12 +381,12 @@ def sfem_strerror(status: int) -> str:
 
 # ---- two-level preconditioner ---------------------------------------------------
 
-def sfem_coarse_setup(h, patch_dims=(0, 0, 0), patch_nodes=0, assembly=0) -> dict:
+def sfem_coarse_setup(h, patch_dims=(0, 0, 0), patch_nodes=0, assembly=0, factor=0) -> dict:
     """Build the Galerkin coarse space of context h; returns its info."""
     o = sfem_coarse_opts()
     for a in range(3):
         o.patch_dims[a] = int(patch_dims[a])
-    o.patch_nodes, o.assembly = int(patch_nodes), int(assembly)
+    o.patch_nodes, o.assembly, o.factor = int(patch_nodes), int(assembly), int(factor)
     _check(lib.sfem_coarse_setup(h, ctypes.byref(o)), "sfem_coarse_setup")
     return sfem_coarse_info(h)
 

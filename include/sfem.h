@@ -119,8 +119,10 @@ typedef struct sfem_solve_opts {
   const void *learned; /* FPCG_LEARNED: an sfem_learned handle (NULL: flexible CG with
                           the Jacobi preconditioner alone) */
   int fp32_vectors;    /* IR vectors: 0 FP64 p, q, r (default); 1 all FP32; 2 FP32 p, q and FP64 r;
-                          3 FP32 r, p, q with an FP64 correction (with precond 1, the choice
-                          for the two-level solve: as many iterations as 0, half the traffic) */
+                          3 FP32 r, p, q with a double-float correction (two FP32 words,
+                          updated by compensated FP32 arithmetic; with precond 1, the
+                          choice for the two-level solve: as many iterations as 0, half
+                          the traffic, no FP64 arithmetic per DOF) */
   int learned_window;  /* FPCG_LEARNED stagnation guard: the correction is switched off for
                           the rest of the solve when ||r|| has not fallen 10% below its best
                           value for this many iterations (0: 100) */

@@ -101,7 +101,9 @@ __global__ void k_cs_gather(CoarseDev cs, const int *done) {
   cs.rc[t] = (float)s;
 }
 
-// yc = C rc (one warp per row; C symmetric, rows of npad floats)
+// yc = C rc (one warp per row; C symmetric, rows of npad floats).  The
+// row streams from DRAM (the operator's records evict C from L2 between
+// iterations): 8 independent 16-byte loads per lane in flight.
 __global__ void __launch_bounds__(256) k_cs_gemv(CoarseDev cs, const int *done) {
   if (done && *done) return;
   const int row = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
@@ -109,18 +111,27 @@ __global__ void __launch_bounds__(256) k_cs_gemv(CoarseDev cs, const int *done) 
   const float4 *Cr = reinterpret_cast<const float4 *>(cs.C + (int64_t)row * cs.npad);
   const float4 *r4 = reinterpret_cast<const float4 *>(cs.rc);
   const int n4 = cs.npad / 4;  // a multiple of 16
-  float acc[4] = {0.f, 0.f, 0.f, 0.f};
-  for (int q0 = lane; q0 < n4; q0 += 128) {
+  constexpr int U = 8;
+  float acc[U];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+  for (int u = 0; u < U; ++u) acc[u] = 0.f;
+  for (int q0 = lane; q0 < n4; q0 += 32 * U) {
+    float4 a[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int q = q0 + 32 * u;
+      a[u] = q < n4 ? __ldcs(Cr + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
       const int q = q0 + 32 * u;
       if (q < n4) {
-        const float4 a = Cr[q], b = r4[q];
-        acc[u] = fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, fmaf(a.w, b.w, acc[u]))));
+        const float4 b = r4[q];
+        acc[u] = fmaf(a[u].x, b.x, fmaf(a[u].y, b.y, fmaf(a[u].z, b.z, fmaf(a[u].w, b.w, acc[u]))));
       }
     }
   }
-  float s = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+  float s = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
   if (lane == 0) cs.yc[row] = s;
@@ -885,8 +896,8 @@ static void setup_coarse(Ctx &c, const sfem_coarse_opts *opts) {
     std::vector<int32_t> cur(off.begin(), off.end() - 1);
     for (int64_t i = 0; i < c.n_nodes; ++i) nodes[cur[cell[i]]++] = (int32_t)i;
   }
-  // blocks of the fused iteration kernels: runs of at most kChunkNodes nodes
-  // of one cell
+  // blocks of the restriction in the two-level iterations: runs of at most
+  // kChunkNodes nodes of one cell (256 per warp)
   std::vector<int4> chunks;
   for (int q = 0; q < cs.ncell; ++q)
     for (int b = off[q]; b < off[q + 1]; b += kChunkNodes)
@@ -895,7 +906,6 @@ static void setup_coarse(Ctx &c, const sfem_coarse_opts *opts) {
   int4 *d_chunk = c.mem.get<int4>(chunks.size());
   SFEM_CUDA(cudaMemcpyAsync(d_chunk, chunks.data(), chunks.size() * sizeof(int4), cudaMemcpyHostToDevice, c.stream));
   cs.chunk = d_chunk;
-  cs.chunk_part = c.mem.get<double>(chunks.size());
   int32_t *d_cell = c.mem.get<int32_t>(c.n_nodes), *d_nodes = c.mem.get<int32_t>(c.n_nodes);
   int32_t *d_off = c.mem.get<int32_t>(cs.ncell + 1);
   float *d_frac = c.mem.get<float>(3 * c.n_nodes);

@@ -13,7 +13,7 @@
 
 namespace sfem {
 
-constexpr int kChunkNodes = 512;  // nodes per block of the fused two-level kernels
+constexpr int kChunkNodes = 2048;  // nodes per block of the restriction in the two-level iterations
 
 struct CoarseDev {
   int d[3];                // centres per axis
@@ -29,7 +29,6 @@ struct CoarseDev {
   const int32_t *coff;     // ncell + 1
   const int4 *chunk;       // nchunk: (cell, first, end) ranges of cnodes, <= kChunkNodes nodes each
   int nchunk;
-  double *chunk_part;      // nchunk: per-block partial sums of the fused iteration kernels
   float *cellsum;          // ncell x 24 partial restrictions (8 corners x 3)
   float *rc, *yc;          // coarse residual and correction (npad)
   const float *C;          // npad x npad: A_c^-1 (symmetric), FP32

@@ -31,6 +31,11 @@ namespace sfem {
 
 constexpr int kVecBlock = 256;
 
+template <class... P>
+bool aligned16(const P *...ptrs) {
+  return ((reinterpret_cast<uintptr_t>(ptrs) % 16 == 0) && ...);
+}
+
 // CG vectors: x (solution or correction) of type TX, residual r of type TR,
 // search direction p and operator output q of type TP (the operator reads
 // p and writes q), Jacobi scaling of type TP.  Scalars and reductions are
@@ -47,7 +52,27 @@ struct PcgVecs {
   CoarseDev cs{};
   float *z32 = nullptr;  // two-level: z of the current r in FP32 (written by k_tl_zr)
   const float *dinv32 = nullptr;
+  float *xlo = nullptr;  // FP32 x: low words of a double-float correction (x + xlo), or none
 };
+
+// (hi, lo) += a p with a = ahi + alo split from an FP64 step length: the
+// product's rounding error by FMA, then a compensated two-sum and
+// renormalisation, all in FP32 arithmetic (about 48 significant bits; the
+// FP64 pipe of this GPU is ~64x slower than FP32)
+__device__ __forceinline__ void df_axpy(float &hi, float &lo, float ahi, float alo, float p) {
+  const float yh = __fmul_rn(ahi, p);
+  const float yl = __fadd_rn(__fmaf_rn(ahi, p, -yh), __fmul_rn(alo, p));
+  const float s = __fadd_rn(hi, yh);
+  const float bv = __fsub_rn(s, hi);
+  float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bv)), __fsub_rn(yh, bv));
+  e = __fadd_rn(e, __fadd_rn(lo, yl));
+  hi = __fadd_rn(s, e);
+  lo = __fsub_rn(e, __fsub_rn(hi, s));
+}
+__device__ __forceinline__ void df_split(double a, float &hi, float &lo) {
+  hi = (float)a;
+  lo = (float)(a - (double)hi);
+}
 
 // preconditioned residual of DOF i (the coarse correction yc of the current
 // r must have been computed before the kernel runs)
@@ -186,10 +211,19 @@ __global__ void __launch_bounds__(kVecBlock) k_pcg_update(PcgVecs<TX, TR, TP> v,
   if (!step_length(S, alpha, rz_old)) return;
   const TX ax = (TX)alpha;
   const TR ar = (TR)alpha;
+  float ahi = 0.f, alo = 0.f;
+  df_split(alpha, ahi, alo);
   double rz = 0.0, rr = 0.0;
 #pragma unroll 4
   for (int64_t i = (int64_t)blockIdx.x * kVecBlock + threadIdx.x; i < v.n; i += (int64_t)gridDim.x * kVecBlock) {
-    v.x[i] += ax * (TX)v.p[i];
+    if constexpr (std::is_same_v<TX, float> && std::is_same_v<TP, float>) {
+      if (v.xlo)
+        df_axpy(v.x[i], v.xlo[i], ahi, alo, v.p[i]);
+      else
+        v.x[i] += ax * v.p[i];
+    } else {
+      v.x[i] += ax * (TX)v.p[i];
+    }
     const TR ri = v.dmask[i] ? v.r[i] - ar * (TR)v.q[i] : TR(0);
     v.r[i] = ri;
     const TP rp = (TP)ri;
@@ -222,94 +256,166 @@ __global__ void __launch_bounds__(kVecBlock) k_pcg_direction(PcgVecs<TX, TR, TP>
 }
 
 // ---- two-level iteration ------------------------------------------------------
-// With the coarse correction an iteration makes three passes over the
-// vectors around the coarse GEMV:
-//   k_tl_update  x += alpha p, r = P (r - alpha q), q = 0, ||r||^2, and the
-//                restriction rc += Pi^T r: one block per run of a cell's
-//                nodes, block sums added to the cell's 8 centres by FP32
-//                atomics;
-//   k_cs_gemv    yc = C rc;
-//   k_tl_zr      z = D^-1 r + P Pi yc in FP32 (stored), z.r and beta; rc = 0
-//                for the next restriction;
-//   k_tl_dir     p = z + beta p.
+// With the coarse correction an iteration runs, after the operator:
+//   k_tl_update    x += alpha p, r = P (r - alpha q), q = 0, ||r||^2: a
+//                  streaming pass over the DOFs (4 per thread, vector
+//                  loads when the vectors are FP32 and 16-byte aligned);
+//   k_tl_restrict  rc += Pi^T r: one warp per run of 256 nodes of one
+//                  interpolation cell (nodes grouped by cell), its 24
+//                  sums (8 corners x 3 components) added to the cell's
+//                  centres by FP32 atomics;
+//   k_cs_gemv      yc = C rc;
+//   k_tl_zr        z = D^-1 r + P Pi yc in FP32 (stored), z.r and beta;
+//                  rc = 0 for the next restriction;
+//   k_tl_dir       p = z + beta p.
 // z, the restriction and the dot products' per-thread sums are FP32 (the
-// preconditioner and the step lengths tolerate 1e-7 relative rounding);
-// x, r and p stay FP64.  FP64 arithmetic is 1/64 of FP32 on this GPU, so the
-// FP32 parts keep the FP64 pipe to two FMAs and two conversions per DOF.
-template <class TR, class TP>
-__global__ void __launch_bounds__(kVecBlock) k_tl_update(PcgVecs<double, TR, TP> v, SolveScalars *S, bool zero_q,
-                                                         unsigned int *ticket) {
+// preconditioner and the step lengths tolerate 1e-7 relative rounding).
+// FP64 arithmetic runs at about one FMA per SM and clock on this GPU, so
+// the per-DOF FP64 work is kept to x += alpha p.
+template <class TX, class TR, class TP, bool kVec>
+__global__ void __launch_bounds__(kVecBlock) k_tl_update(PcgVecs<TX, TR, TP> v, SolveScalars *S, bool zero_q,
+                                                         double *partials, unsigned int *ticket) {
+  static_assert(!kVec || (std::is_same_v<TX, float> && std::is_same_v<TR, float> && std::is_same_v<TP, float>),
+                "vector path is FP32 with a double-float x");
+  // x: FP64, or double-float (x, xlo) when TX is float
+  constexpr bool df = std::is_same_v<TX, float>;
   if (S->done) return;
   double alpha, rz_old;
   if (!step_length(S, alpha, rz_old)) return;
   const TR ar = (TR)alpha;
-  const CoarseDev &cs = v.cs;
-  const int4 ch = cs.chunk[blockIdx.x];
-  double *__restrict__ x = v.x;
+  float ahi = 0.f, alo = 0.f;
+  df_split(alpha, ahi, alo);
+  TX *__restrict__ x = v.x;
+  float *__restrict__ xl = v.xlo;
   TR *__restrict__ r = v.r;
   TP *__restrict__ q = v.q;
   const TP *__restrict__ p = v.p;
   const uint8_t *__restrict__ msk = v.dmask;
+  float rr = 0.f;
+  const int64_t nq = v.n / 4, stride = (int64_t)gridDim.x * kVecBlock;
+  for (int64_t t = (int64_t)blockIdx.x * kVecBlock + threadIdx.x; t < nq; t += stride) {
+    const int64_t i = 4 * t;
+    TX xv[4];
+    float xlv[4] = {0.f, 0.f, 0.f, 0.f};
+    TP pv[4], qv[4];
+    TR rv[4];
+    uint8_t mv[4];
+    if constexpr (kVec) {
+      const float4 x4 = *reinterpret_cast<const float4 *>(x + i), xl4 = *reinterpret_cast<const float4 *>(xl + i);
+      const float4 p4 = *reinterpret_cast<const float4 *>(p + i), q4 = *reinterpret_cast<const float4 *>(q + i);
+      const float4 r4 = *reinterpret_cast<const float4 *>(r + i);
+      const uchar4 m4 = *reinterpret_cast<const uchar4 *>(msk + i);
+      xv[0] = x4.x, xv[1] = x4.y, xv[2] = x4.z, xv[3] = x4.w;
+      xlv[0] = xl4.x, xlv[1] = xl4.y, xlv[2] = xl4.z, xlv[3] = xl4.w;
+      pv[0] = p4.x, pv[1] = p4.y, pv[2] = p4.z, pv[3] = p4.w;
+      qv[0] = q4.x, qv[1] = q4.y, qv[2] = q4.z, qv[3] = q4.w;
+      rv[0] = r4.x, rv[1] = r4.y, rv[2] = r4.z, rv[3] = r4.w;
+      mv[0] = m4.x, mv[1] = m4.y, mv[2] = m4.z, mv[3] = m4.w;
+    } else {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        xv[c] = x[i + c];
+        if constexpr (df) xlv[c] = xl[i + c];
+        pv[c] = p[i + c];
+        qv[c] = q[i + c];
+        rv[c] = r[i + c];
+        mv[c] = msk[i + c];
+      }
+    }
+    TR rn[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      if constexpr (df)
+        df_axpy(xv[c], xlv[c], ahi, alo, (float)pv[c]);
+      else
+        xv[c] = fma(alpha, (double)pv[c], xv[c]);
+      rn[c] = mv[c] ? fma(-ar, (TR)qv[c], rv[c]) : TR(0);
+      const float rf = (float)rn[c];
+      rr = fmaf(rf, rf, rr);
+    }
+    if constexpr (kVec) {
+      *reinterpret_cast<float4 *>(x + i) = make_float4(xv[0], xv[1], xv[2], xv[3]);
+      *reinterpret_cast<float4 *>(xl + i) = make_float4(xlv[0], xlv[1], xlv[2], xlv[3]);
+      *reinterpret_cast<float4 *>(r + i) = make_float4(rn[0], rn[1], rn[2], rn[3]);
+      if (zero_q) *reinterpret_cast<float4 *>(q + i) = make_float4(0.f, 0.f, 0.f, 0.f);
+    } else {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        x[i + c] = xv[c];
+        if constexpr (df) xl[i + c] = xlv[c];
+        r[i + c] = rn[c];
+        if (zero_q) q[i + c] = TP(0);
+      }
+    }
+  }
+  for (int64_t i = 4 * nq + (int64_t)blockIdx.x * kVecBlock + threadIdx.x; i < v.n; i += stride) {
+    if constexpr (df)
+      df_axpy(x[i], xl[i], ahi, alo, (float)p[i]);
+    else
+      x[i] = fma(alpha, (double)p[i], x[i]);
+    const TR rn = msk[i] ? fma(-ar, (TR)q[i], r[i]) : TR(0);
+    r[i] = rn;
+    if (zero_q) q[i] = TP(0);
+    const float rf = (float)rn;
+    rr = fmaf(rf, rf, rr);
+  }
+  double vv[1] = {(double)rr};
+  if (grid_sum<kVecBlock, 1>(vv, partials, ticket, nullptr) && threadIdx.x == 0) finish_update(S, alpha, rz_old, vv[0]);
+}
+
+// nodes per warp of the restriction: 8 per lane, loads issued together
+constexpr int kRestrictWarpNodes = 256;
+
+template <class TR>
+__global__ void __launch_bounds__(kVecBlock) k_tl_restrict(const TR *__restrict__ r, CoarseDev cs, const int *done) {
+  if (done && *done) return;
+  const int4 ch = cs.chunk[blockIdx.x];
+  const int lane = threadIdx.x & 31;
+  const int b = ch.y + kRestrictWarpNodes * (threadIdx.x >> 5);
+  if (b >= ch.z) return;  // whole warps; no block barrier follows
+  const int e = min(b + kRestrictWarpNodes, ch.z);
+  constexpr int U = kRestrictWarpNodes / 32;
+  int64_t i0[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int k = b + lane + 32 * u;
+    i0[u] = k < e ? 3 * (int64_t)cs.cnodes[k] : -1;
+  }
+  float f[U][3], rf[U][3];
+#pragma unroll
+  for (int u = 0; u < U; ++u)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      f[u][c] = i0[u] >= 0 ? cs.frac[i0[u] + c] : 0.f;
+      rf[u][c] = i0[u] >= 0 ? (float)r[i0[u] + c] : 0.f;
+    }
   float acc[24];
 #pragma unroll
   for (int j = 0; j < 24; ++j) acc[j] = 0.f;
-  float rr = 0.f;
-  for (int k = ch.y + threadIdx.x; k < ch.z; k += kVecBlock) {
-    const int64_t i0 = 3 * (int64_t)cs.cnodes[k];
-    double xv[3];
-    TP pv[3], qv[3];
-    TR rv[3];
-    uint8_t mv[3];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      xv[c] = x[i0 + c];
-      pv[c] = p[i0 + c];
-      qv[c] = q[i0 + c];
-      rv[c] = r[i0 + c];
-      mv[c] = msk[i0 + c];
-    }
-    const float f[3] = {cs.frac[i0], cs.frac[i0 + 1], cs.frac[i0 + 2]};
-    float rf[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      x[i0 + c] = fma(alpha, (double)pv[c], xv[c]);
-      const TR rn = mv[c] ? fma(-ar, (TR)qv[c], rv[c]) : TR(0);
-      r[i0 + c] = rn;
-      if (zero_q) q[i0 + c] = TP(0);
-      rf[c] = (float)rn;
-      rr = fmaf(rf[c], rf[c], rr);
-    }
+  for (int u = 0; u < U; ++u)
 #pragma unroll
     for (int kk = 0; kk < 8; ++kk) {
-      const float w = cs_weight(f, kk);
+      const float w = cs_weight(f[u], kk);
 #pragma unroll
-      for (int c = 0; c < 3; ++c) acc[3 * kk + c] = fmaf(w, rf[c], acc[3 * kk + c]);
+      for (int c = 0; c < 3; ++c) acc[3 * kk + c] = fmaf(w, rf[u][c], acc[3 * kk + c]);
+    }
+#pragma unroll
+  for (int j = 0; j < 24; ++j)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc[j] += __shfl_down_sync(0xffffffffu, acc[j], o);
+  if (lane == 0) {
+#pragma unroll
+    for (int kk = 0; kk < 8; ++kk) {
+      float *rc = cs.rc + 3 * cs_corner(cs, ch.x, kk);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) atomicAdd(rc + c, acc[3 * kk + c]);
     }
   }
-  __shared__ float sm[kVecBlock / 32][24];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-  for (int j = 0; j < 24; ++j) {
-    float t = acc[j];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
-    if (lane == 0) sm[wid][j] = t;
-  }
-  __syncthreads();
-  if (threadIdx.x < 24) {
-    float t = 0.f;
-#pragma unroll
-    for (int w = 0; w < kVecBlock / 32; ++w) t += sm[w][threadIdx.x];
-    const int kk = threadIdx.x / 3, c = threadIdx.x - 3 * kk;
-    atomicAdd(&cs.rc[3 * cs_corner(cs, ch.x, kk) + c], t);
-  }
-  double vv[1] = {(double)rr};
-  if (grid_sum<kVecBlock, 1>(vv, cs.chunk_part, ticket, nullptr) && threadIdx.x == 0)
-    finish_update(S, alpha, rz_old, vv[0]);
 }
 
-template <class TR, class TP>
-__global__ void __launch_bounds__(kVecBlock) k_tl_zr(PcgVecs<double, TR, TP> v, SolveScalars *S, double *partials,
+template <class TX, class TR, class TP>
+__global__ void __launch_bounds__(kVecBlock) k_tl_zr(PcgVecs<TX, TR, TP> v, SolveScalars *S, double *partials,
                                                      unsigned int *ticket) {
   if (S->done) return;
   const CoarseDev &cs = v.cs;
@@ -323,6 +429,7 @@ __global__ void __launch_bounds__(kVecBlock) k_tl_zr(PcgVecs<double, TR, TP> v, 
   const int64_t nn = v.n / 3;
   const int sx = 3 * cs.d[1] * cs.d[2], sy = 3 * cs.d[2];
   float rz = 0.f;
+#pragma unroll 2
   for (int64_t node = (int64_t)blockIdx.x * kVecBlock + threadIdx.x; node < nn;
        node += (int64_t)gridDim.x * kVecBlock) {
     const int64_t i0 = 3 * node;
@@ -366,13 +473,29 @@ __global__ void __launch_bounds__(kVecBlock) k_tl_zr(PcgVecs<double, TR, TP> v, 
   }
 }
 
-template <class TP>
+template <class TP, bool kVec>
 __global__ void __launch_bounds__(kVecBlock) k_tl_dir(TP *__restrict__ p, const float *__restrict__ z, int64_t n,
                                                       const SolveScalars *S) {
+  static_assert(!kVec || std::is_same_v<TP, float>, "vector path is FP32");
   if (S->done) return;
   const TP b = (TP)S->beta;
+  const int64_t stride = (int64_t)gridDim.x * kVecBlock;
+  int64_t i0 = 0;
+  if constexpr (kVec) {  // FP32 p, 16-byte aligned
+    const int64_t nq = n / 4;
+    for (int64_t t = (int64_t)blockIdx.x * kVecBlock + threadIdx.x; t < nq; t += stride) {
+      const float4 z4 = reinterpret_cast<const float4 *>(z)[t];
+      float4 p4 = reinterpret_cast<float4 *>(p)[t];
+      p4.x = fmaf(b, p4.x, z4.x);
+      p4.y = fmaf(b, p4.y, z4.y);
+      p4.z = fmaf(b, p4.z, z4.z);
+      p4.w = fmaf(b, p4.w, z4.w);
+      reinterpret_cast<float4 *>(p)[t] = p4;
+    }
+    i0 = 4 * nq;
+  }
 #pragma unroll 4
-  for (int64_t i = (int64_t)blockIdx.x * kVecBlock + threadIdx.x; i < n; i += (int64_t)gridDim.x * kVecBlock)
+  for (int64_t i = i0 + (int64_t)blockIdx.x * kVecBlock + threadIdx.x; i < n; i += stride)
     p[i] = fma(b, p[i], (TP)z[i]);
 }
 
@@ -395,6 +518,15 @@ __global__ void k_set_bc(double *__restrict__ x, const double *__restrict__ g, c
 __global__ void k_add(double *__restrict__ a, const double *__restrict__ b, int64_t n) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) a[i] += b[i];
+}
+// u += hi + lo (the double-float correction), then hi = lo = 0
+__global__ void k_add_df(double *__restrict__ u, float *__restrict__ hi, float *__restrict__ lo, int64_t n) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    u[i] += (double)hi[i] + (double)lo[i];
+    hi[i] = 0.f;
+    lo[i] = 0.f;
+  }
 }
 __global__ void k_scale_to_f32(const double *__restrict__ r, double s, int64_t n, float *__restrict__ out) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -536,15 +668,34 @@ struct CgRun {
       // tiled FP32 operator reading p and accumulating q in type TP
       launch_mf32_tiled<TP, TP>(c, st, v.p, v.q, &S->pq, done);
     }
-    if constexpr (std::is_same_v<TX, double>) {
-      if (v.coarse) {
+    {
+      if (v.coarse) {  // FP64 x, or double-float x with FP32 r, p, q
+        if constexpr (std::is_same_v<TX, float>)
+          SFEM_REQUIRE(v.xlo != nullptr, SFEM_EINVAL, "the coarse correction needs an FP64 or double-float correction");
         const CoarseDev &cs = v.cs;
-        k_tl_update<TR, TP><<<cs.nchunk, kVecBlock, 0, st>>>(v, S, mf, c.tickets + 3);
+        constexpr bool f32 = std::is_same_v<TX, float> && std::is_same_v<TR, float> && std::is_same_v<TP, float>;
+        bool vec = false;
+        if constexpr (f32)
+          vec = v.xlo && aligned16(v.x, v.xlo, v.r, v.p, v.q, v.z32) &&
+                (reinterpret_cast<uintptr_t>(v.dmask) & 3) == 0;
+        if constexpr (f32) {
+          if (vec)
+            k_tl_update<TX, TR, TP, true><<<c.red_blocks, kVecBlock, 0, st>>>(v, S, mf, c.red_partial,
+                                                                              c.tickets + 3);
+        }
+        if (!vec)
+          k_tl_update<TX, TR, TP, false><<<c.red_blocks, kVecBlock, 0, st>>>(v, S, mf, c.red_partial, c.tickets + 3);
+        SFEM_CHECK_LAUNCH();
+        static_assert(kChunkNodes <= (kVecBlock / 32) * kRestrictWarpNodes, "restriction chunk too large");
+        k_tl_restrict<TR><<<cs.nchunk, kVecBlock, 0, st>>>(v.r, cs, done);
         SFEM_CHECK_LAUNCH();
         coarse_gemv(cs, st, done);
-        k_tl_zr<TR, TP><<<c.red_blocks, kVecBlock, 0, st>>>(v, S, c.red_partial, c.tickets + 10);
+        k_tl_zr<TX, TR, TP><<<c.red_blocks, kVecBlock, 0, st>>>(v, S, c.red_partial, c.tickets + 10);
         SFEM_CHECK_LAUNCH();
-        k_tl_dir<TP><<<c.red_blocks, kVecBlock, 0, st>>>(v.p, v.z32, v.n, S);
+        if constexpr (f32) {
+          if (vec) k_tl_dir<TP, true><<<c.red_blocks, kVecBlock, 0, st>>>(v.p, v.z32, v.n, S);
+        }
+        if (!vec) k_tl_dir<TP, false><<<c.red_blocks, kVecBlock, 0, st>>>(v.p, v.z32, v.n, S);
         SFEM_CHECK_LAUNCH();
         return;
       }
@@ -820,10 +971,11 @@ void solve_impl(Ctx &c, const double *f_extra, double *u, const sfem_solve_opts 
         // or p doubled the iteration count on the 2M-tet beam: their
         // rounding re-enters the FP64 true residual amplified by the
         // condition number at every update.
-        // 3: FP64 correction d; FP32 r, p, q (and z): with the two-level
-        // preconditioner the inner iterations converge in as many steps as
-        // with FP64 vectors (emulated on a 123k-tet beam: 428 vs 426), at
-        // half the vector traffic and no FP64 arithmetic beyond d += alpha p.
+        // 3: double-float correction d (two FP32 words); FP32 r, p, q (and
+        // z): with the two-level preconditioner the inner iterations converge
+        // in as many steps as with FP64 vectors (emulated on a 123k-tet beam:
+        // 428 vs 426), at half the vector traffic and without FP64
+        // arithmetic in the per-DOF passes.
         auto reliable = [&](auto tag) {
           using TV = decltype(tag);
           constexpr bool f64 = std::is_same_v<TV, double>;
@@ -837,10 +989,15 @@ void solve_impl(Ctx &c, const double *f_extra, double *u, const sfem_solve_opts 
             dinv = c.dinv64;
           else
             dinv = c.dinv32;
-          PcgVecs<double, TV, TV> v{B.get<double>(n), rv, B.get<TV>(n), B.get<TV>(n), dinv, c.dmask, n};
+          // correction d: FP64, or double-float (two FP32 words) with FP32 vectors
+          PcgVecs<TV, TV, TV> v{B.get<TV>(n), rv, B.get<TV>(n), B.get<TV>(n), dinv, c.dmask, n};
+          if constexpr (!f64) {
+            v.xlo = B.get<float>(n);
+            SFEM_CUDA(cudaMemsetAsync(v.xlo, 0, n * sizeof(float), c.stream));
+          }
           with_coarse(v);
-          CgRun<double, TV, TV> cg(c, v, SFEM_OP_MF32, chunk);
-          SFEM_CUDA(cudaMemsetAsync(v.x, 0, n * sizeof(double), c.stream));
+          CgRun<TV, TV, TV> cg(c, v, SFEM_OP_MF32, chunk);
+          SFEM_CUDA(cudaMemsetAsync(v.x, 0, n * sizeof(TV), c.stream));
           bool started = false;
           double best = rel;
           int stall = 0;
@@ -858,9 +1015,14 @@ void solve_impl(Ctx &c, const double *f_extra, double *u, const sfem_solve_opts 
               status = SFEM_EBREAKDOWN;
               break;
             }
-            k_add<<<g256, 256, 0, c.stream>>>(x, v.x, n);  // u += d
-            SFEM_CHECK_LAUNCH();
-            SFEM_CUDA(cudaMemsetAsync(v.x, 0, n * sizeof(double), c.stream));  // d = 0
+            if constexpr (f64) {
+              k_add<<<g256, 256, 0, c.stream>>>(x, v.x, n);  // u += d
+              SFEM_CHECK_LAUNCH();
+              SFEM_CUDA(cudaMemsetAsync(v.x, 0, n * sizeof(double), c.stream));  // d = 0
+            } else {
+              k_add_df<<<g256, 256, 0, c.stream>>>(x, v.x, v.xlo, n);  // u += d, d = 0
+              SFEM_CHECK_LAUNCH();
+            }
             rel = true_residual();  // the FP64 true residual into r
             // stagnation: the FP32 operator's error floor lies above tol
             if (rel < 0.9 * best) {

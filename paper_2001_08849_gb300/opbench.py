@@ -54,6 +54,7 @@ def main(argv=None):
     ap.add_argument("--coarse-dims", type=int, nargs=3, default=None, help="patch centres per axis")
     ap.add_argument("--repeat", type=int, default=1, help="solves (the last one is reported)")
     ap.add_argument("--fp32-vectors", type=int, default=0, help="ir32_64 vector precision (sfem_solve_opts)")
+    ap.add_argument("--inner-tol", type=float, default=0.0, help="ir32_64 reliable-update threshold (0: 0.1)")
     a = ap.parse_args(argv)
     import torch
     import __graft_entry__
@@ -85,7 +86,7 @@ def main(argv=None):
                                  max_iter=a.max_iter, precond=a.precond)
             elif a.solve == "ir32_64":
                 o = S.solve_opts(kind=S.SFEM_SOLVE_IR32_64, tol=a.tol, u_on_device=True, max_iter=a.max_iter,
-                                 precond=a.precond, fp32_vectors=a.fp32_vectors)
+                                 precond=a.precond, fp32_vectors=a.fp32_vectors, inner_tol=a.inner_tol)
             else:
                 S.sfem_assemble(ctx.h)
                 if a.solve == "fpcg_learned":

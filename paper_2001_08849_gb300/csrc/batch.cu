@@ -481,7 +481,7 @@ extern "C" int sfem_batch_solve(sfem_ctx *const *ctxs, int n, double *const *u, 
       SFEM_CHECK_LAUNCH();
       for (double *v : {D, P, Q}) SFEM_CUDA(cudaMemsetAsync(v, 0, nd * nr * sizeof(double), st));
       hb[b].A = TileArgs{c.tl.tile_start, c.tl.hoff,       c.tl.noff, c.tl.halo_tet, c.tl.halo_lconn,
-                         c.tl.tile_nodes, c.tl.node_inc,   c.tl.rec};
+                         c.tl.tile_nodes, c.tl.node_inc,   c.tl.rec,  c.n_tets};
       hb[b].first_sys = s;
       hb[b].nrhs = nr;
       hb[b].lam = (float)c.lam;

@@ -411,7 +411,7 @@ __global__ void __launch_bounds__(kTileThreads, 3) k_cs_galerkin(TileArgs A, Coa
       for (int h = threadIdx.x; h < T.H; h += kTileThreads) {
         TetGeo G;
         uint2 lc;
-        load_rec(A.rec, A.halo_tet[T.h0 + h], G, lc, nullptr);
+        load_rec(A.rec, A.rs, A.halo_tet[T.h0 + h], G, lc, nullptr);
         lc = A.halo_lconn[T.h0 + h];
         const int l[4] = {(int)(lc.x & 0xFFFF), (int)(lc.x >> 16), (int)(lc.y & 0xFFFF), (int)(lc.y >> 16)};
         float g[3] = {0.f, 0.f, 0.f};
@@ -781,6 +781,69 @@ void coarse_correction(Ctx &c, cudaStream_t st, const float *r, const int *done)
   coarse_correction_t(c, st, r, done);
 }
 
+// ---- coarse-space tables ---------------------------------------------------
+
+struct CsGrid {
+  double lo[3], ext[3];
+  int d[3], cd[3];
+};
+
+// interpolation cell, lower-corner centre (with axis flags) and fractions
+// of every node: t = (x - lo) / ext * d - 1/2 clamped to [0, d - 1], cell
+// index floor(t) clamped to [0, d - 2]
+__global__ void k_cs_locate(const double *__restrict__ xyz, int64_t n_nodes, CsGrid g, int32_t *__restrict__ cell,
+                            int32_t *__restrict__ cinfo, float *__restrict__ frac) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_nodes) return;
+  int i0[3];
+  for (int a = 0; a < 3; ++a) {
+    double t = (xyz[3 * i + a] - g.lo[a]) / g.ext[a] * g.d[a] - 0.5;
+    t = fmin(fmax(t, 0.0), (double)max(g.d[a] - 1, 0));
+    i0[a] = min(max((int)floor(t), 0), max(g.d[a] - 2, 0));
+    frac[3 * i + a] = (float)(g.d[a] > 1 ? t - i0[a] : 0.0);
+  }
+  cell[i] = (i0[0] * g.cd[1] + i0[1]) * g.cd[2] + i0[2];
+  cinfo[i] = ((i0[0] * g.d[1] + i0[1]) * g.d[2] + i0[2]) | ((i0[0] + 1 < g.d[0]) << 24) |
+             ((i0[1] + 1 < g.d[1]) << 25) | ((i0[2] + 1 < g.d[2]) << 26);
+}
+
+constexpr int kGroupNodes = 1024;  // nodes per block of the grouping sort
+
+// nodes of block b per cell, stored cell-major: hist[cell * nblk + b]
+__global__ void k_cs_group_hist(const int32_t *__restrict__ cell, int64_t n_nodes, int ncell, int nblk,
+                                int32_t *__restrict__ hist) {
+  extern __shared__ int32_t gsm[];
+  for (int q = threadIdx.x; q < ncell; q += blockDim.x) gsm[q] = 0;
+  __syncthreads();
+  const int64_t b0 = (int64_t)blockIdx.x * kGroupNodes;
+  for (int k = threadIdx.x; k < kGroupNodes && b0 + k < n_nodes; k += blockDim.x) atomicAdd(&gsm[cell[b0 + k]], 1);
+  __syncthreads();
+  for (int q = threadIdx.x; q < ncell; q += blockDim.x) hist[(int64_t)q * nblk + blockIdx.x] = gsm[q];
+}
+
+// place block b's nodes in node order from the cell-major exclusive offsets
+// (one thread walks the block: the order within a cell stays ascending)
+__global__ void k_cs_group_place(const int32_t *__restrict__ cell, int64_t n_nodes, int ncell, int nblk,
+                                 const int64_t *__restrict__ base, int32_t *__restrict__ nodes) {
+  extern __shared__ int32_t gsm[];
+  int32_t *cur = gsm, *cl = gsm + ncell;
+  for (int q = threadIdx.x; q < ncell; q += blockDim.x) cur[q] = (int32_t)base[(int64_t)q * nblk + blockIdx.x];
+  const int64_t b0 = (int64_t)blockIdx.x * kGroupNodes;
+  const int m = (int)(n_nodes - b0 < kGroupNodes ? n_nodes - b0 : kGroupNodes);
+  for (int k = threadIdx.x; k < m; k += blockDim.x) cl[k] = cell[b0 + k];
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int k = 0; k < m; ++k) nodes[cur[cl[k]]++] = (int32_t)(b0 + k);
+}
+
+// first node of each cell in the grouped order; off[ncell] = n_nodes
+__global__ void k_cs_group_off(const int64_t *__restrict__ base, int ncell, int nblk, int64_t n_nodes,
+                               int32_t *__restrict__ off) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < ncell) off[q] = (int32_t)base[(int64_t)q * nblk];
+  if (q == ncell) off[q] = (int32_t)n_nodes;
+}
+
 __global__ void k_cs_to_f32(const double *a, float *b, int64_t n) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) b[i] = (float)a[i];
@@ -818,16 +881,8 @@ static void setup_coarse(Ctx &c, const sfem_coarse_opts *opts) {
   SFEM_CUDA(cudaEventCreate(&e1));
   SFEM_CUDA(cudaEventRecord(e0, c.stream));
   auto co = std::make_shared<Coarse>();
-  // grid of centres over the bounding box (host, once)
-  std::vector<double> xyz(3 * c.n_nodes);
-  SFEM_CUDA(cudaMemcpyAsync(xyz.data(), c.xyz, xyz.size() * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
-  SFEM_CUDA(cudaStreamSynchronize(c.stream));
-  double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-  for (int64_t i = 0; i < c.n_nodes; ++i)
-    for (int a = 0; a < 3; ++a) {
-      lo[a] = std::min(lo[a], xyz[3 * i + a]);
-      hi[a] = std::max(hi[a], xyz[3 * i + a]);
-    }
+  // grid of centres over the nodes' bounding box (found with the tiles)
+  const double *lo = c.bbox_lo, *hi = c.bbox_hi;
   const int pn = (opts && opts->patch_nodes > 0) ? opts->patch_nodes : 8;
   const double box = std::max((hi[0] - lo[0]) * (hi[1] - lo[1]) * (hi[2] - lo[2]), 1e-300);
   const double h_mean = std::cbrt(box / (double)c.n_nodes);
@@ -852,22 +907,43 @@ static void setup_coarse(Ctx &c, const sfem_coarse_opts *opts) {
   cs.nc = (int)(3 * P);
   cs.npad = (cs.nc + kCB - 1) / kCB * kCB;
   cs.ncell = cs.cd[0] * cs.cd[1] * cs.cd[2];
-  // interpolation cell and fractions of every node; nodes grouped by cell
-  std::vector<int32_t> cell(c.n_nodes), cinfo(c.n_nodes), off(cs.ncell + 1, 0), nodes(c.n_nodes);
-  std::vector<float> frac(3 * c.n_nodes);
-  for (int64_t i = 0; i < c.n_nodes; ++i) {
-    int i0[3];
+  // interpolation cell and fractions of every node (k_cs_locate); nodes
+  // grouped by cell, ascending within a cell, by a stable counting sort
+  // over blocks of kGroupNodes nodes (histogram per block, one scan over
+  // the cell-major block histograms, then placement in node order)
+  int32_t *d_cell = c.mem.get<int32_t>(c.n_nodes), *d_nodes = c.mem.get<int32_t>(c.n_nodes);
+  int32_t *d_off = c.mem.get<int32_t>(cs.ncell + 1), *d_cinfo = c.mem.get<int32_t>(c.n_nodes);
+  float *d_frac = c.mem.get<float>(3 * c.n_nodes);
+  {
+    CsGrid gr;
     for (int a = 0; a < 3; ++a) {
-      double t = (xyz[3 * i + a] - co->g.lo[a]) / co->g.ext[a] * cs.d[a] - 0.5;
-      t = std::min(std::max(t, 0.0), (double)std::max(cs.d[a] - 1, 0));
-      i0[a] = std::min(std::max((int)std::floor(t), 0), std::max(cs.d[a] - 2, 0));
-      frac[3 * i + a] = (float)(cs.d[a] > 1 ? t - i0[a] : 0.0);
+      gr.lo[a] = co->g.lo[a];
+      gr.ext[a] = co->g.ext[a];
+      gr.d[a] = cs.d[a];
+      gr.cd[a] = cs.cd[a];
     }
-    cell[i] = (i0[0] * cs.cd[1] + i0[1]) * cs.cd[2] + i0[2];
-    cinfo[i] = ((i0[0] * cs.d[1] + i0[1]) * cs.d[2] + i0[2]) | ((i0[0] + 1 < cs.d[0]) << 24) |
-               ((i0[1] + 1 < cs.d[1]) << 25) | ((i0[2] + 1 < cs.d[2]) << 26);
-    off[cell[i] + 1] += 1;
+    k_cs_locate<<<grid_for(c.n_nodes, 256), 256, 0, c.stream>>>(c.xyz, c.n_nodes, gr, d_cell, d_cinfo, d_frac);
+    SFEM_CHECK_LAUNCH();
+    const int nblk = (int)((c.n_nodes + kGroupNodes - 1) / kGroupNodes);
+    const int64_t nh = (int64_t)cs.ncell * nblk;
+    int32_t *hist = c.mem.get<int32_t>(nh);
+    int64_t *base = c.mem.get<int64_t>(nh + 1);
+    const size_t gsm = (size_t)cs.ncell * sizeof(int32_t) + kGroupNodes * sizeof(int32_t);
+    SFEM_REQUIRE(gsm <= 200 * 1024, SFEM_EINVAL, "too many interpolation cells");
+    SFEM_CUDA(cudaFuncSetAttribute(k_cs_group_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm));
+    SFEM_CUDA(cudaFuncSetAttribute(k_cs_group_place, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm));
+    k_cs_group_hist<<<nblk, 256, gsm, c.stream>>>(d_cell, c.n_nodes, cs.ncell, nblk, hist);
+    SFEM_CHECK_LAUNCH();
+    scan_counts(c, hist, nh, base);
+    k_cs_group_place<<<nblk, 256, gsm, c.stream>>>(d_cell, c.n_nodes, cs.ncell, nblk, base, d_nodes);
+    SFEM_CHECK_LAUNCH();
+    k_cs_group_off<<<grid_for(cs.ncell + 1, 256), 256, 0, c.stream>>>(base, cs.ncell, nblk, c.n_nodes, d_off);
+    SFEM_CHECK_LAUNCH();
+    c.mem.drop(hist);
+    c.mem.drop(base);
   }
+  std::vector<int32_t> off(cs.ncell + 1);
+  SFEM_CUDA(cudaMemcpyAsync(off.data(), d_off, off.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, c.stream));
   // per coarse DOF the cellsum entries (cell, corner) that restrict onto it
   std::vector<int32_t> glist(8 * (size_t)cs.nc, -1);
   for (int j = 0; j < (int)P; ++j) {
@@ -891,11 +967,7 @@ static void setup_coarse(Ctx &c, const sfem_coarse_opts *opts) {
           }
       }
   }
-  for (int q = 0; q < cs.ncell; ++q) off[q + 1] += off[q];
-  {
-    std::vector<int32_t> cur(off.begin(), off.end() - 1);
-    for (int64_t i = 0; i < c.n_nodes; ++i) nodes[cur[cell[i]]++] = (int32_t)i;
-  }
+  SFEM_CUDA(cudaStreamSynchronize(c.stream));  // off
   // blocks of the restriction in the two-level iterations: runs of at most
   // kChunkNodes nodes of one cell (256 per warp)
   std::vector<int4> chunks;
@@ -906,15 +978,7 @@ static void setup_coarse(Ctx &c, const sfem_coarse_opts *opts) {
   int4 *d_chunk = c.mem.get<int4>(chunks.size());
   SFEM_CUDA(cudaMemcpyAsync(d_chunk, chunks.data(), chunks.size() * sizeof(int4), cudaMemcpyHostToDevice, c.stream));
   cs.chunk = d_chunk;
-  int32_t *d_cell = c.mem.get<int32_t>(c.n_nodes), *d_nodes = c.mem.get<int32_t>(c.n_nodes);
-  int32_t *d_off = c.mem.get<int32_t>(cs.ncell + 1);
-  float *d_frac = c.mem.get<float>(3 * c.n_nodes);
-  SFEM_CUDA(cudaMemcpyAsync(d_cell, cell.data(), cell.size() * 4, cudaMemcpyHostToDevice, c.stream));
-  SFEM_CUDA(cudaMemcpyAsync(d_nodes, nodes.data(), nodes.size() * 4, cudaMemcpyHostToDevice, c.stream));
-  SFEM_CUDA(cudaMemcpyAsync(d_off, off.data(), off.size() * 4, cudaMemcpyHostToDevice, c.stream));
-  SFEM_CUDA(cudaMemcpyAsync(d_frac, frac.data(), frac.size() * 4, cudaMemcpyHostToDevice, c.stream));
-  int32_t *d_cinfo = c.mem.get<int32_t>(c.n_nodes), *d_glist = c.mem.get<int32_t>(glist.size());
-  SFEM_CUDA(cudaMemcpyAsync(d_cinfo, cinfo.data(), cinfo.size() * 4, cudaMemcpyHostToDevice, c.stream));
+  int32_t *d_glist = c.mem.get<int32_t>(glist.size());
   SFEM_CUDA(cudaMemcpyAsync(d_glist, glist.data(), glist.size() * 4, cudaMemcpyHostToDevice, c.stream));
   cs.cinfo = d_cinfo;
   cs.glist = d_glist;
@@ -943,7 +1007,7 @@ static void setup_coarse(Ctx &c, const sfem_coarse_opts *opts) {
     SFEM_REQUIRE(smem <= 227 * 1024, SFEM_EINVAL, "tile too large for the Galerkin assembly");
     SFEM_CUDA(cudaFuncSetAttribute(k_cs_galerkin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     TileArgs TA{c.tl.tile_start, c.tl.hoff, c.tl.noff, c.tl.halo_tet, c.tl.halo_lconn, c.tl.tile_nodes,
-                c.tl.node_inc, c.tl.rec};
+                c.tl.node_inc, c.tl.rec, c.n_tets};
     k_cs_galerkin<<<(unsigned)c.tl.n_tiles, kTileThreads, smem, c.stream>>>(TA, cs, c.dmask, (float)c.lam,
                                                                               (float)c.mu, stage_off, Ac, ovf);
     SFEM_CHECK_LAUNCH();

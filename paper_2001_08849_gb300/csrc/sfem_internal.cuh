@@ -205,6 +205,7 @@ struct Ctx {
   Csr csr;
   bool assembled = false;
   TileData tl;
+  double bbox_lo[3] = {0, 0, 0}, bbox_hi[3] = {0, 0, 0};  // node bounding box (set with the tiles)
 
   DevStatus *dstat = nullptr;
   DevStatus hstat{};

@@ -20,7 +20,9 @@ struct TileArgs {
   const uint2 *halo_lconn;
   const int32_t *tile_nodes;
   const uint16_t *node_inc;  // per tile node: first slot in its incidence list
-  const float4 *rec;   // 64-byte per-tet records, tile order
+  const float4 *rec;   // 64-byte per-tet records, tile order, as 4 planes of float4 (word 4q..4q+3 of
+                       // tet t at rec[q * rs + t]): a warp's loads of one plane are contiguous
+  int64_t rs;          // plane stride (the tet count)
 };
 
 struct TetGeo {
@@ -38,16 +40,17 @@ __device__ __forceinline__ void rec_unpack(const float4 (&q)[4], TetGeo &G, uint
   for (int i = 0; i < 3; ++i) G.g[0][i] = -(G.g[1][i] + G.g[2][i] + G.g[3][i]);
 }
 
-__device__ __forceinline__ void load_rec(const float4 *__restrict__ rec, int t, TetGeo &G, uint2 &lc, uint2 *lnb) {
-  const float4 a = __ldg(rec + 4 * (int64_t)t), b = __ldg(rec + 4 * (int64_t)t + 1);
-  const float4 c = __ldg(rec + 4 * (int64_t)t + 2);
+__device__ __forceinline__ void load_rec(const float4 *__restrict__ rec, int64_t rs, int t, TetGeo &G, uint2 &lc,
+                                         uint2 *lnb) {
+  const float4 a = __ldg(rec + t), b = __ldg(rec + rs + t);
+  const float4 c = __ldg(rec + 2 * rs + t);
   G.g[1][0] = a.x, G.g[1][1] = a.y, G.g[1][2] = a.z;
   G.g[2][0] = a.w, G.g[2][1] = b.x, G.g[2][2] = b.y;
   G.g[3][0] = b.z, G.g[3][1] = b.w, G.g[3][2] = c.x;
   G.V = c.y;
   lc = make_uint2(__float_as_uint(c.z), __float_as_uint(c.w));
   if (lnb) {
-    const float4 d = __ldg(rec + 4 * (int64_t)t + 3);
+    const float4 d = __ldg(rec + 3 * rs + t);
     *lnb = make_uint2(__float_as_uint(d.x), __float_as_uint(d.y));
   }
 #pragma unroll
@@ -84,9 +87,9 @@ __device__ __forceinline__ void tile_load(const TileArgs &A, int tile, TileRegs 
   for (int r = 0; r < kTilePer; ++r) {
     const int j = threadIdx.x + r * kTileThreads;
     if (j < n_own) {
-      const float4 *rp = A.rec + 4 * (int64_t)(s + j);
+      const float4 *rp = A.rec + (s + j);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) R.rr[r][q] = __ldg(rp + q);
+      for (int q = 0; q < 4; ++q) R.rr[r][q] = __ldg(rp + q * A.rs);
     }
   }
 }
@@ -142,7 +145,7 @@ __device__ __forceinline__ void tile_strains(const TileArgs &A, const TileRegs &
   for (int h = threadIdx.x; h < T.H; h += kTileThreads) {
     TetGeo G;
     uint2 lc;
-    load_rec(A.rec, A.halo_tet[T.h0 + h], G, lc, nullptr);
+    load_rec(A.rec, A.rs, A.halo_tet[T.h0 + h], G, lc, nullptr);
     lc = A.halo_lconn[T.h0 + h];
     float4 w2[2];
     strain_to(T.su, lc, G, w2);

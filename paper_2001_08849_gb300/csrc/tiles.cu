@@ -18,8 +18,9 @@
 // tiles of at most kTileMax tets, and builds per tile: the sorted node
 // list, 16-bit local connectivity, 16-bit local neighbour indices (into
 // tile tets, then halo tets) and the halo list.  Per-tet data streamed by
-// the kernel: one 64-byte record (V_e-scaled gradients, V_e, local
-// connectivity, local neighbours); the face weights 1/(4 (V_e + V_nbr))
+// the kernel: one 64-byte record in four 16-byte planes (V_e-scaled
+// gradients, V_e, local connectivity, local neighbours, incidence entries);
+// the face weights 1/(4 (V_e + V_nbr))
 // are formed from the volumes staged in shared memory.
 
 #include <cuda_runtime.h>
@@ -124,7 +125,9 @@ __global__ void k_tile_ranges(const int64_t *__restrict__ bin_ptr, const int64_t
   if (b == n_bins - 1) tile_start[n_tiles] = (int32_t)e;
 }
 
-// Per-tet record of the tiled operator (64 bytes, tile order):
+// Per-tet record of the tiled operator (64 bytes, tile order), stored as four
+// planes of float4 (words 4q..4q+3 of tet t at rec[q * n_tets + t], so one
+// warp's load of a plane is 512 contiguous bytes):
 //   [0..8]  V_e grad N_1..3 (node 1..3 by x, y, z) in FP32
 //   [9]     V_e in FP32
 //   [10,11] local connectivity (4 x 16 bit), written by k_tile_build
@@ -141,11 +144,10 @@ __global__ void k_reorder(const int32_t *__restrict__ perm, int64_t n, const flo
   iperm[o] = (int32_t)i;
   float g[9];
   for (int k = 0; k < 9; ++k) g[k] = Gs32[k * n + o];
-  float4 *r = rec + 4 * i;
-  r[0] = make_float4(g[0], g[1], g[2], g[3]);
-  r[1] = make_float4(g[4], g[5], g[6], g[7]);
-  r[2] = make_float4(g[8], (float)vol[o], 0.f, 0.f);
-  r[3] = make_float4(0.f, 0.f, 0.f, 0.f);
+  rec[i] = make_float4(g[0], g[1], g[2], g[3]);
+  rec[n + i] = make_float4(g[4], g[5], g[6], g[7]);
+  rec[2 * n + i] = make_float4(g[8], (float)vol[o], 0.f, 0.f);
+  rec[3 * n + i] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 // ascending bitonic sort of a[0..P) in shared memory (P a power of two)
@@ -257,7 +259,8 @@ struct TileBuild {
   int32_t *halo_tet;
   uint2 *halo_lconn;
   int32_t *tile_nodes;
-  float4 *rec;   // per-tet records (tile order): lconn -> words 10,11; lnbr -> 12,13; inc -> 14,15
+  float4 *rec;   // per-tet records (tile order, 4 planes): lconn -> words 10,11; lnbr -> 12,13; inc -> 14,15
+  int64_t rs;    // plane stride
   uint16_t *node_inc;  // per tile node: start of its slots in the incidence list
   unsigned long long *overflow;
 };
@@ -331,10 +334,11 @@ __global__ void __launch_bounds__(kBuildThreads) k_tile_build(TileBuild B, int p
   }
   __syncthreads();
   block_bitonic_sort(keys, KP);
-  uint16_t *rinc = reinterpret_cast<uint16_t *>(B.rec + 4 * (int64_t)s);
+  uint16_t *rinc = reinterpret_cast<uint16_t *>(B.rec + 3 * B.rs + s);
   for (int i = threadIdx.x; i < 4 * n_own; i += blockDim.x) {
-    // entry i goes to record (s + i/4), 16-bit word 28 + i%4 (words 14,15)
-    rinc[(i / 4) * 32 + 28 + (i % 4)] = (uint16_t)(keys[i] & 2047);
+    // entry i goes to record (s + i/4), 16-bit word 28 + i%4 (words 14,15:
+    // the last two of plane 3)
+    rinc[(i / 4) * 8 + 4 + (i % 4)] = (uint16_t)(keys[i] & 2047);
   }
   // start of each tile node's slots: number of keys below (l << 11)
   for (int l = threadIdx.x; l < L; l += blockDim.x) {
@@ -356,9 +360,10 @@ __global__ void __launch_bounds__(kBuildThreads) k_tile_build(TileBuild B, int p
     for (int a = 0; a < 4; ++a) l[a] = (unsigned int)bsearch_int(nodes, L, B.tets[4 * to + a]);
     const uint2 lc = make_uint2(l[0] | (l[1] << 16), l[2] | (l[3] << 16));
     if (j < n_own) {
-      unsigned int *rw = reinterpret_cast<unsigned int *>(B.rec + 4 * (int64_t)tnew);
-      rw[10] = lc.x;
-      rw[11] = lc.y;
+      unsigned int *rw2 = reinterpret_cast<unsigned int *>(B.rec + 2 * B.rs + tnew);  // words 8-11
+      unsigned int *rw3 = reinterpret_cast<unsigned int *>(B.rec + 3 * B.rs + tnew);  // words 12-15
+      rw2[2] = lc.x;
+      rw2[3] = lc.y;
       unsigned int nb[4];
       for (int a = 0; a < 4; ++a) {
         const int nb_old = B.nbr[4 * to + a];
@@ -370,8 +375,8 @@ __global__ void __launch_bounds__(kBuildThreads) k_tile_build(TileBuild B, int p
                                                 : (unsigned int)(n_own + bsearch_int(halo, H, nb_new));
         }
       }
-      rw[12] = nb[0] | (nb[1] << 16);
-      rw[13] = nb[2] | (nb[3] << 16);
+      rw3[0] = nb[0] | (nb[1] << 16);
+      rw3[1] = nb[2] | (nb[3] << 16);
     } else {
       B.halo_tet[h0 + (j - n_own)] = tnew;
       B.halo_lconn[h0 + (j - n_own)] = lc;
@@ -426,7 +431,9 @@ void build_tiles(Ctx &c) {
   double lo[3], ext[3], boxvol = 1.0;
   for (int k = 0; k < 3; ++k) {
     lo[k] = from_ordered_bits(hb[k]);
-    ext[k] = std::max(from_ordered_bits(hb[3 + k]) - lo[k], 1e-300);
+    c.bbox_lo[k] = lo[k];
+    c.bbox_hi[k] = from_ordered_bits(hb[3 + k]);
+    ext[k] = std::max(c.bbox_hi[k] - lo[k], 1e-300);
     boxvol *= ext[k];
   }
   const double edge = std::cbrt(boxvol / (double)n * kTileTarget);
@@ -517,6 +524,7 @@ void build_tiles(Ctx &c) {
   B.tile_nodes = c.tl.tile_nodes;
   B.node_inc = c.tl.node_inc;
   B.rec = c.tl.rec;
+  B.rs = n;
   k_tile_build<<<(unsigned)nt, kBuildThreads, build_smem, c.stream>>>(B, 2);
   SFEM_CHECK_LAUNCH();
   c.mem.drop(nh);
@@ -546,7 +554,7 @@ void build_tiles(Ctx &c) {
 template <class TU, class TY>
 void launch_mf32_tiled(Ctx &c, cudaStream_t st, const TU *u, TY *y, double *energy_out, const int *done) {
   TileArgs A{c.tl.tile_start, c.tl.hoff, c.tl.noff, c.tl.halo_tet, c.tl.halo_lconn, c.tl.tile_nodes,
-             c.tl.node_inc, c.tl.rec};
+             c.tl.node_inc, c.tl.rec, c.n_tets};
   k_mf32_tiled<TU, TY><<<(unsigned)c.tl.n_tiles, kTileThreads, c.tl.smem, st>>>(
       A, u, y, (float)c.lam, (float)c.mu, c.red_partial, c.tickets + 6, energy_out, done);
   SFEM_CHECK_LAUNCH();

@@ -207,8 +207,8 @@ constexpr int kGalMaxCentres = 125; // centres of those cells (5 per axis)
 // corner) entries that map to it in a fixed order.
 // Dynamic shared memory: the tile layout (stage_off float4 units), then per
 // tile node a float4 stage (local cell: index in bits 0-7, coordinates in
-// bits 8-13; free-DOF mask in bits 28-30; the three fractions) and a uint16
-// order.  Sets *overflow for a tile that touches more than 4 cells on an
+// bits 8-13; free-DOF mask in bits 28-30; the three fractions), a float4 of
+// masked nodal forces and a uint16 order.  Sets *overflow for a tile that touches more than 4 cells on an
 // axis.
 constexpr int kGalWarps = kTileThreads / 32;
 
@@ -232,7 +232,8 @@ __global__ void __launch_bounds__(kTileThreads, 3) k_cs_galerkin(TileArgs A, Coa
   tile_load(A, tile, R);
   const TileView T = tile_view(A, tile, smem_t);
   float4 *stage = smem_t + stage_off;
-  uint16_t *order = reinterpret_cast<uint16_t *>(stage + T.L);
+  float4 *nf = stage + T.L;  // masked nodal forces (the tile's force slots overlay su)
+  uint16_t *order = reinterpret_cast<uint16_t *>(nf + T.L);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (threadIdx.x < 3) {
     bb[threadIdx.x] = 1 << 30;
@@ -312,7 +313,7 @@ __global__ void __launch_bounds__(kTileThreads, 3) k_cs_galerkin(TileArgs A, Coa
   }
   __syncthreads();
 
-  // restriction of the masked nodal forces in su against the local centres,
+  // restriction of the masked nodal forces in nf against the local centres,
   // added to column `col` of A_c (all threads; ends with a barrier)
   auto restrict_add = [&](int col) {
     // (lower and upper x corners in two sweeps: 12 accumulators per lane)
@@ -325,7 +326,7 @@ __global__ void __launch_bounds__(kTileThreads, 3) k_cs_galerkin(TileArgs A, Coa
         const int i = order[e];
         const float4 st = stage[i];
         const float f[3] = {st.y, st.z, st.w};
-        const float4 fi = T.su[i];
+        const float4 fi = nf[i];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           const float w = cs_weight(f, k0 + k);
@@ -359,13 +360,13 @@ __global__ void __launch_bounds__(kTileThreads, 3) k_cs_galerkin(TileArgs A, Coa
     }
     __syncthreads();
   };
-  // masked nodal forces of the tile into su (all threads; ends with a barrier)
+  // masked nodal forces of the tile into nf (all threads; ends with a barrier)
   auto node_forces = [&]() {
     for (int i = threadIdx.x; i < T.L; i += kTileThreads) {
       float fx, fy, fz;
       tile_node_force(T, i, fx, fy, fz);
       const int m = __float_as_int(stage[i].x) >> 28;
-      T.su[i] = make_float4((m & 1) ? fx : 0.f, (m & 2) ? fy : 0.f, (m & 4) ? fz : 0.f, 0.f);
+      nf[i] = make_float4((m & 1) ? fx : 0.f, (m & 2) ? fy : 0.f, (m & 4) ? fz : 0.f, 0.f);
     }
     __syncthreads();
   };
@@ -1003,7 +1004,7 @@ static void setup_coarse(Ctx &c, const sfem_coarse_opts *opts) {
     int *ovf = c.mem.get<int>(1);
     SFEM_CUDA(cudaMemsetAsync(ovf, 0, sizeof(int), c.stream));
     const int stage_off = (int)((c.tl.smem + 15) / 16);
-    const size_t smem = (size_t)stage_off * 16 + (size_t)c.tl.max_nodes * (sizeof(float4) + sizeof(uint16_t)) + 16;
+    const size_t smem = (size_t)stage_off * 16 + (size_t)c.tl.max_nodes * (2 * sizeof(float4) + sizeof(uint16_t)) + 16;
     SFEM_REQUIRE(smem <= 227 * 1024, SFEM_EINVAL, "tile too large for the Galerkin assembly");
     SFEM_CUDA(cudaFuncSetAttribute(k_cs_galerkin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     TileArgs TA{c.tl.tile_start, c.tl.hoff, c.tl.noff, c.tl.halo_tet, c.tl.halo_lconn, c.tl.tile_nodes,

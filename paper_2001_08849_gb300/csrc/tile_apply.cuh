@@ -94,10 +94,11 @@ __device__ __forceinline__ void tile_load(const TileArgs &A, int tile, TileRegs 
   }
 }
 
-// Shared-memory layout of one tile: displacements (L), strains split in two
-// float4 arrays (w0..w3 | w4, w5, V, 0) over tile + halo tets, nodal forces
-// of the tile tets (4 slots x xyz = 12 floats per tet), incidence list and
-// node starts.
+// Shared-memory layout of one tile: displacements (L float4) sharing their
+// space with the nodal forces of the tile tets (4 slots x xyz = 12 floats
+// per tet; written only after the strains have been formed), strains split
+// in two float4 arrays (w0..w3 | w4, w5, V, 0) over tile + halo tets,
+// incidence list and node starts.
 struct TileView {
   int n_own, H, L, nt;
   int64_t h0, n0;
@@ -116,10 +117,10 @@ __device__ __forceinline__ TileView tile_view(const TileArgs &A, int tile, float
   T.L = (int)(A.noff[tile + 1] - T.n0);
   T.nt = T.n_own + T.H;
   T.su = smem;
-  T.swa = T.su + T.L;
+  T.sfe = reinterpret_cast<float *>(smem);                              // 12 * n_own, over su
+  T.swa = T.su + max(T.L, 3 * T.n_own);
   T.swb = T.swa + T.nt;
-  T.sfe = reinterpret_cast<float *>(T.swb + T.nt);                      // 12 * n_own
-  T.sinc = reinterpret_cast<uint16_t *>(T.sfe + 12 * T.n_own);         // 4 * n_own
+  T.sinc = reinterpret_cast<uint16_t *>(T.swb + T.nt);                  // 4 * n_own
   T.snode = T.sinc + 4 * T.n_own;                                       // L
   return T;
 }

@@ -395,7 +395,7 @@ __global__ void k_max_i32(const int32_t *__restrict__ a, const int32_t *__restri
 // the fused operator
 // ---------------------------------------------------------------------------
 template <class TU, class TY>
-__global__ void __launch_bounds__(kTileThreads, 3)
+__global__ void __launch_bounds__(kTileThreads, 4)
     k_mf32_tiled(TileArgs A, const TU *__restrict__ u, TY *__restrict__ y, float lam, float mu, double *partials,
                  unsigned int *ticket, double *energy_out, const int *done) {
   if (done && *done) return;
@@ -532,8 +532,9 @@ void build_tiles(Ctx &c) {
   c.mem.drop(ovf);
   c.mem.drop(mx);
   c.mem.drop(hist);
-  c.tl.smem = (size_t)c.tl.max_nodes * (sizeof(float4) + sizeof(uint16_t)) +
-              (size_t)(kTileMax + c.tl.max_halo) * 2 * sizeof(float4) + (size_t)kTileMax * (12 * sizeof(float) + 8);
+  c.tl.smem = (size_t)std::max<int64_t>(c.tl.max_nodes, 3 * kTileMax) * sizeof(float4) +
+              (size_t)c.tl.max_nodes * sizeof(uint16_t) + (size_t)(kTileMax + c.tl.max_halo) * 2 * sizeof(float4) +
+              (size_t)kTileMax * 8;
   c.tl.smem = (c.tl.smem + 15) & ~size_t(15);
   SFEM_REQUIRE(c.tl.smem <= 220 * 1024, SFEM_EMESH, "tile working set exceeds shared memory");
   c.tl.total_halo = total_h;
@@ -541,6 +542,14 @@ void build_tiles(Ctx &c) {
   // opt in to the dynamic shared memory this mesh needs (never lowered, so
   // contexts of smaller meshes keep working)
   static size_t smem_set = 48 * 1024;
+  static bool carveout_set = false;
+  if (!carveout_set) {  // all of the unified L1/shared storage as shared memory: 4 tiles per SM
+    SFEM_CUDA(cudaFuncSetAttribute(k_mf32_tiled<float, float>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                   cudaSharedmemCarveoutMaxShared));
+    SFEM_CUDA(cudaFuncSetAttribute(k_mf32_tiled<double, double>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                   cudaSharedmemCarveoutMaxShared));
+    carveout_set = true;
+  }
   if (c.tl.smem > smem_set) {
     SFEM_CUDA(cudaFuncSetAttribute(k_mf32_tiled<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)c.tl.smem));

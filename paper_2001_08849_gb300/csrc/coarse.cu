@@ -101,9 +101,11 @@ __global__ void k_cs_gather(CoarseDev cs, const int *done) {
   cs.rc[t] = (float)s;
 }
 
-// yc = C rc (one warp per row; C symmetric, rows of npad floats).  The
-// row streams from DRAM (the operator's records evict C from L2 between
-// iterations): 8 independent 16-byte loads per lane in flight.
+// yc = C rc (one warp per row; C symmetric, rows of npad floats).  C is
+// read with evict-first loads: between two iterations the operator's
+// records evict it anyway (measured: C comes from DRAM either way, and
+// evict-first records slowed the operator by 5 us), so it should not push
+// the operator's data out in turn.  8 independent 16-byte loads per lane.
 __global__ void __launch_bounds__(256) k_cs_gemv(CoarseDev cs, const int *done) {
   if (done && *done) return;
   const int row = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
@@ -222,9 +224,9 @@ __device__ __forceinline__ float gal_w1(int jc, int lc, int c0, int d, float f) 
 __global__ void __launch_bounds__(kTileThreads, 3) k_cs_galerkin(TileArgs A, CoarseDev cs,
                                                               const uint8_t *__restrict__ dmask, float lam,
                                                               float mu, int stage_off, double *__restrict__ Ac,
-                                                              int *overflow) {
+                                                              int *overflow, int *maxdist) {
   extern __shared__ float4 smem_t[];
-  __shared__ int bb[6], coff[kGalMaxCells + 1], mixed;
+  __shared__ int bb[6], coff[kGalMaxCells + 1], mixed, tile_md;
   __shared__ float cellacc[kGalMaxCells][24];
   __shared__ short gat[kGalMaxCentres][8];
   const int tile = blockIdx.x;
@@ -239,7 +241,10 @@ __global__ void __launch_bounds__(kTileThreads, 3) k_cs_galerkin(TileArgs A, Coa
     bb[threadIdx.x] = 1 << 30;
     bb[3 + threadIdx.x] = -1;
   }
-  if (threadIdx.x == 0) mixed = 0;
+  if (threadIdx.x == 0) {
+    mixed = 0;
+    tile_md = 0;
+  }
   __syncthreads();
   for (int i = threadIdx.x; i < T.L; i += kTileThreads) {
     const int64_t node = A.tile_nodes[T.n0 + i];
@@ -356,6 +361,7 @@ __global__ void __launch_bounds__(kTileThreads, 3) k_cs_galerkin(TileArgs A, Coa
         const int ix = c0[0] + il / (nj[1] * nj[2]), iy = c0[1] + (il / nj[2]) % nj[1], iz = c0[2] + il % nj[2];
         const int I = (ix * cs.d[1] + iy) * cs.d[2] + iz;
         atomicAdd(&Ac[(int64_t)(3 * I + cc) * cs.npad + col], (double)v);
+        atomicMax(&tile_md, abs(3 * I + cc - col));
       }
     }
     __syncthreads();
@@ -503,6 +509,8 @@ __global__ void __launch_bounds__(kTileThreads, 3) k_cs_galerkin(TileArgs A, Coa
       }
     }
   }
+  __syncthreads();
+  if (threadIdx.x == 0) atomicMax(maxdist, tile_md);
 }
 
 // A <- (A + A^T) / 2 on the nc x nc block; padding: identity; a zero
@@ -556,19 +564,6 @@ template <class T>
 __device__ __forceinline__ void load64(Tile64<T> &S, const T *A, int64_t ld, int bi, int bj) {
   for (int e = threadIdx.x; e < kCB * kCB; e += blockDim.x)
     S.v[e / kCB][e % kCB] = A[(int64_t)(bi * kCB + e / kCB) * ld + bj * kCB + e % kCB];
-}
-
-// block bandwidth of the lower triangle: max over block rows of (block row
-// - block column of the first nonzero entry)
-__global__ void __launch_bounds__(256) k_band_blocks(const double *A, int npad, int *bwb) {
-  const int br = blockIdx.x;
-  int first = npad;
-  for (int e = threadIdx.x; e < kCB * (br + 1) * kCB; e += blockDim.x) {
-    const int r = br * kCB + e / ((br + 1) * kCB), col = e % ((br + 1) * kCB);
-    if (col < first && A[(int64_t)r * npad + col] != 0.0) first = col;
-  }
-  for (int o = 16; o > 0; o >>= 1) first = min(first, __shfl_down_sync(0xffffffffu, first, o));
-  if ((threadIdx.x & 31) == 0 && first < npad) atomicMax(bwb, br - first / kCB);
 }
 
 // factor the diagonal block k in shared memory: columns in groups of 8 (one
@@ -996,13 +991,13 @@ static void setup_coarse(Ctx &c, const sfem_coarse_opts *opts) {
   const int64_t np2 = (int64_t)cs.npad * cs.npad;
   double *Ac = c.mem.get<double>(np2);
   SFEM_CUDA(cudaMemsetAsync(Ac, 0, np2 * sizeof(double), c.stream));
-  int probes = 0;
+  int probes = 0, maxdist = 0;
   const int assembly = opts ? opts->assembly : 0;
   SFEM_REQUIRE(assembly == 0 || assembly == 1, SFEM_EINVAL, "assembly must be 0 or 1");
   if (assembly == 0) {
     // tile by tile (exact Galerkin entries, no colouring)
-    int *ovf = c.mem.get<int>(1);
-    SFEM_CUDA(cudaMemsetAsync(ovf, 0, sizeof(int), c.stream));
+    int *ovf = c.mem.get<int>(2);  // [0] overflow, [1] largest |row - column|
+    SFEM_CUDA(cudaMemsetAsync(ovf, 0, 2 * sizeof(int), c.stream));
     const int stage_off = (int)((c.tl.smem + 15) / 16);
     const size_t smem = (size_t)stage_off * 16 + (size_t)c.tl.max_nodes * (2 * sizeof(float4) + sizeof(uint16_t)) + 16;
     SFEM_REQUIRE(smem <= 227 * 1024, SFEM_EINVAL, "tile too large for the Galerkin assembly");
@@ -1010,15 +1005,22 @@ static void setup_coarse(Ctx &c, const sfem_coarse_opts *opts) {
     TileArgs TA{c.tl.tile_start, c.tl.hoff, c.tl.noff, c.tl.halo_tet, c.tl.halo_lconn, c.tl.tile_nodes,
                 c.tl.node_inc, c.tl.rec, c.n_tets};
     k_cs_galerkin<<<(unsigned)c.tl.n_tiles, kTileThreads, smem, c.stream>>>(TA, cs, c.dmask, (float)c.lam,
-                                                                              (float)c.mu, stage_off, Ac, ovf);
+                                                                              (float)c.mu, stage_off, Ac, ovf,
+                                                                              ovf + 1);
     SFEM_CHECK_LAUNCH();
-    int hovf = 0;
-    SFEM_CUDA(cudaMemcpyAsync(&hovf, ovf, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+    int hovf[2] = {0, 0};
+    SFEM_CUDA(cudaMemcpyAsync(hovf, ovf, sizeof hovf, cudaMemcpyDeviceToHost, c.stream));
     SFEM_CUDA(cudaStreamSynchronize(c.stream));
     c.mem.drop(ovf);
-    if (hovf) SFEM_CUDA(cudaMemsetAsync(Ac, 0, np2 * sizeof(double), c.stream));  // probe instead
-    else probes = -1;
+    if (hovf[0]) {
+      SFEM_CUDA(cudaMemsetAsync(Ac, 0, np2 * sizeof(double), c.stream));  // probe instead
+    } else {
+      probes = -1;
+      maxdist = hovf[1];
+    }
   }
+  if (probes >= 0)  // probing attributes entries to centres at most 2 cells apart per axis
+    maxdist = 3 * (2 * cs.d[1] * cs.d[2] + 2 * cs.d[2] + 2) + 2;
   float *v = c.mem.get<float>(c.ndof), *y = c.mem.get<float>(c.ndof);
   const int3 str = make_int3(std::min(5, cs.d[0]), std::min(5, cs.d[1]), std::min(5, cs.d[2]));
   for (int comp = 0; comp < 3 && probes >= 0; ++comp)
@@ -1048,14 +1050,10 @@ static void setup_coarse(Ctx &c, const sfem_coarse_opts *opts) {
   // of I, as with an FP64 factor); FP64 when the FP32 factor meets a
   // non-positive pivot
   const int nb = cs.npad / kCB;
-  int *dev_i = c.mem.get<int>(2);  // [0] info, [1] block bandwidth
-  SFEM_CUDA(cudaMemsetAsync(dev_i, 0, 2 * sizeof(int), c.stream));
-  k_band_blocks<<<nb, 256, 0, c.stream>>>(Ac, cs.npad, dev_i + 1);
-  SFEM_CHECK_LAUNCH();
-  int hb[2] = {0, 0};
-  SFEM_CUDA(cudaMemcpyAsync(hb, dev_i, sizeof hb, cudaMemcpyDeviceToHost, c.stream));
-  SFEM_CUDA(cudaStreamSynchronize(c.stream));
-  const int bwb = std::max(hb[1], 1);
+  int *dev_i = c.mem.get<int>(1);  // Cholesky info
+  // block bandwidth: an entry |row - column| = m apart lies at most m/64 + 1
+  // block rows below the diagonal block of its column
+  const int bwb = std::min(std::max(maxdist / kCB + 1, 1), nb - 1 > 0 ? nb - 1 : 1);
   float *L32 = c.mem.get<float>(np2);
   float *Wd = c.mem.get<float>((size_t)nb * kCB * kCB);
   k_cs_to_f32<<<grid_for(np2, 256), 256, 0, c.stream>>>(Ac, L32, np2);

@@ -530,7 +530,10 @@ static double bits_to_double(unsigned long long b) {
 
 // compute b for load case r into a device buffer (ndof)
 static void build_rhs(Ctx &c, int r, double *b, double *Kg) {
-  apply_mf64(c, c.g, Kg, 1, nullptr);
+  if (c.g_zero)
+    SFEM_CUDA(cudaMemsetAsync(Kg, 0, c.ndof * sizeof(double), c.stream));  // K 0 = 0
+  else
+    apply_mf64(c, c.g, Kg, 1, nullptr);
   k_rhs<<<grid_for(c.ndof, 256), 256, 0, c.stream>>>(c.f + (int64_t)r * c.ndof, Kg, c.g, c.dmask, c.ndof, b);
   SFEM_CHECK_LAUNCH();
 }
@@ -655,7 +658,6 @@ static void setup(Ctx &c, const double *xyz, const int32_t *tets, const int32_t 
   c.red_partial = c.mem.get<double>(4 * nred);
   c.scal = c.mem.get<SolveScalars>(4);
   SFEM_CUDA(cudaMemsetAsync(c.scal, 0, 4 * sizeof(SolveScalars), c.stream));
-  SFEM_CUDA(cudaMallocHost(&c.h_scal, 4 * sizeof(SolveScalars)));
   c.tickets = c.mem.get<unsigned int>(64);
   SFEM_CUDA(cudaMemsetAsync(c.tickets, 0, 64 * sizeof(unsigned int), c.stream));
   SFEM_CUDA(cudaStreamCreateWithFlags(&c.cap_stream, cudaStreamNonBlocking));
@@ -673,6 +675,7 @@ static void setup(Ctx &c, const double *xyz, const int32_t *tets, const int32_t 
   build_tiles(c);
 
   // ||b|| per load case
+  c.g_zero = c.n_dir == 0 || device_norm2(c, c.g, c.ndof) == 0.0;
   double *b = c.mem.get<double>(c.ndof);
   double *Kg = c.mem.get<double>(c.ndof);
   c.bnorm.assign(c.nrhs, 0.0);

@@ -218,7 +218,8 @@ struct Ctx {
   int red_blocks = 0;
   unsigned int *tickets = nullptr; // zeroed ticket counters of grid reductions
   SolveScalars *scal = nullptr;
-  SolveScalars *h_scal = nullptr; // pinned host copies (2 slots)
+  SolveScalars *h_scal = nullptr; // pinned host copies (2 slots), allocated on first chunked solve
+  bool g_zero = true;             // all prescribed displacements are zero
   cudaStream_t cap_stream = nullptr; // private stream used only for graph capture
   std::shared_ptr<Coarse> coarse;    // two-level preconditioner, if set up
 };

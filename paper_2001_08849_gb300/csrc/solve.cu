@@ -770,6 +770,7 @@ struct CgRun {
       count_launches((int64_t)graph_nodes * hg[0]);
       return out;
     }
+    if (!c.h_scal) SFEM_CUDA(cudaMallocHost(&c.h_scal, 4 * sizeof(SolveScalars)));
     SolveScalars *h = c.h_scal;
     cudaEvent_t ev[2];
     SFEM_CUDA(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));

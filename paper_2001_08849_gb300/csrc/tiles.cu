@@ -150,8 +150,11 @@ __global__ void k_reorder(const int32_t *__restrict__ perm, int64_t n, const flo
   rec[3 * n + i] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
-// ascending bitonic sort of a[0..P) in shared memory (P a power of two)
-__device__ void block_bitonic_sort(int *a, int P) {
+// ascending bitonic sort of a[0..n) in shared memory; P a power of two >= n,
+// a[n..P) is overwritten with padding
+__device__ void block_bitonic_sort(int *a, int P, int n) {
+  for (int i = n + threadIdx.x; i < P; i += blockDim.x) a[i] = INT_MAX;
+  __syncthreads();
   for (int k = 2; k <= P; k <<= 1) {
     for (int j = k >> 1; j > 0; j >>= 1) {
       for (int i = threadIdx.x; i < P; i += blockDim.x) {
@@ -200,28 +203,37 @@ __device__ int block_exclusive_scan(int v, int *total) {
   return before + x - v;
 }
 
-// compact the sorted a[0..P) to its unique values < INT_MAX (in place);
-// returns the count (all threads)
-__device__ int block_unique(int *a, int P) {
-  // each thread owns a contiguous chunk, so the order of heads is kept
-  const int chunk = (P + blockDim.x - 1) / blockDim.x;
-  const int b = threadIdx.x * chunk, e = min(P, b + chunk);
-  int c = 0;
-  for (int i = b; i < e; ++i) {
-    int v = a[i];
-    if (v != INT_MAX && (i == 0 || a[i - 1] != v)) ++c;
+// shared-memory hash sets of non-negative ints (INT_MAX marks a free slot;
+// open addressing with linear probing; the table never fills: it holds at
+// least twice as many slots as keys are inserted)
+constexpr int kHaloHash = 4096;  // >= 2 * 4 * kTileMax, a multiple of the build block
+
+__device__ __forceinline__ void hash_clear(int *t, int size) {
+  for (int i = threadIdx.x; i < size; i += blockDim.x) t[i] = INT_MAX;
+}
+__device__ __forceinline__ void hash_insert(int *t, int size, int key) {
+  // multiplicative hashing: the top log2(size) bits of key * (2^32 / golden ratio)
+  unsigned h = ((unsigned)key * 2654435761u) >> (__clz(size) + 1);
+  for (int probe = 0; probe < size; ++probe) {
+    const int old = atomicCAS(&t[h], INT_MAX, key);
+    if (old == INT_MAX || old == key) return;
+    h = (h + 1) & (unsigned)(size - 1);
+  }
+}
+// the keys of table t (size a multiple of blockDim.x, at most 16 slots per
+// thread) packed into out[0..count), in slot order; out may alias t
+__device__ int hash_compact(const int *t, int size, int *out) {
+  const int chunk = size / (int)blockDim.x;
+  const int b = threadIdx.x * chunk;
+  int vals[16];
+  int nv = 0;
+  for (int i = 0; i < chunk; ++i) {
+    const int v = t[b + i];
+    if (v != INT_MAX) vals[nv++] = v;
   }
   int total;
-  const int start = block_exclusive_scan(c, &total);
-  // gather heads into registers first (the compaction is in place)
-  int vals[64];
-  int nv = 0;
-  for (int i = b; i < e && nv < 64; ++i) {
-    int v = a[i];
-    if (v != INT_MAX && (i == 0 || a[i - 1] != v)) vals[nv++] = v;
-  }
-  __syncthreads();
-  for (int k = 0; k < nv; ++k) a[start + k] = vals[k];
+  const int start = block_exclusive_scan(nv, &total);  // ends with a barrier: t is read
+  for (int k = 0; k < nv; ++k) out[start + k] = vals[k];
   __syncthreads();
   return total;
 }
@@ -279,34 +291,34 @@ __global__ void __launch_bounds__(kBuildThreads) k_tile_build(TileBuild B, int p
   const int tile = blockIdx.x;
   const int s = B.tile_start[tile], e = B.tile_start[tile + 1];
   const int n_own = e - s;
-  // halo candidates: neighbours outside [s, e); the sorts cover the
-  // smallest power of two that holds the candidates
-  const int PH = pow2_at_least(4 * n_own);
-  for (int i = threadIdx.x; i < PH; i += blockDim.x) halo[i] = INT_MAX;
+  // halo: the distinct neighbours outside [s, e), collected in a shared hash
+  // set (in the node region, 4096 slots), compacted, then sorted
+  hash_clear(nodes, kHaloHash);
   __syncthreads();
   for (int i = threadIdx.x; i < 4 * n_own; i += blockDim.x) {
     const int tnew = s + i / 4, a = i % 4;
     const int nb_old = B.nbr[4 * (int64_t)B.perm[tnew] + a];
     if (nb_old >= 0) {
       const int nb_new = B.iperm[nb_old];
-      if (nb_new < s || nb_new >= e) halo[i] = nb_new;
+      if (nb_new < s || nb_new >= e) hash_insert(nodes, kHaloHash, nb_new);
     }
   }
   __syncthreads();
-  block_bitonic_sort(halo, PH);
-  const int H = block_unique(halo, PH);
-  // node candidates of own and halo tets
-  const int PN = pow2_at_least(4 * (n_own + H));
-  for (int i = threadIdx.x; i < PN; i += blockDim.x) nodes[i] = INT_MAX;
+  const int H = hash_compact(nodes, kHaloHash, halo);
+  if (pass == 2) block_bitonic_sort(halo, pow2_at_least(H), H);
+  // nodes of own and halo tets: hash set sized for the candidates, compacted
+  // in place, sorted
+  const int NT = min(kNodeP, max(kBuildThreads, pow2_at_least(8 * (n_own + H))));
+  hash_clear(nodes, NT);
   __syncthreads();
   for (int i = threadIdx.x; i < 4 * (n_own + H); i += blockDim.x) {
     const int j = i / 4, a = i % 4;
     const int tnew = j < n_own ? s + j : halo[j - n_own];
-    nodes[i] = B.tets[4 * (int64_t)B.perm[tnew] + a];
+    hash_insert(nodes, NT, B.tets[4 * (int64_t)B.perm[tnew] + a]);
   }
   __syncthreads();
-  block_bitonic_sort(nodes, PN);
-  const int L = block_unique(nodes, PN);
+  const int L = hash_compact(nodes, NT, nodes);
+  if (pass == 2) block_bitonic_sort(nodes, pow2_at_least(L), L);
   if (pass == 1) {
     if (threadIdx.x == 0) {
       B.n_halo[tile] = H;
@@ -322,7 +334,7 @@ __global__ void __launch_bounds__(kBuildThreads) k_tile_build(TileBuild B, int p
   // still needed below), so use a separate scratch: the tail of `nodes`
   // past L is free.
   int *keys = nodes + ((L + 31) & ~31);
-  const int KP = PH;  // >= 4 n_own slots, power of two
+  const int KP = pow2_at_least(4 * n_own);  // >= 4 n_own slots, power of two
   for (int i = threadIdx.x; i < KP; i += blockDim.x) {
     int v = INT_MAX;
     if (i < 4 * n_own) {
@@ -333,7 +345,7 @@ __global__ void __launch_bounds__(kBuildThreads) k_tile_build(TileBuild B, int p
     keys[i] = v;
   }
   __syncthreads();
-  block_bitonic_sort(keys, KP);
+  block_bitonic_sort(keys, KP, KP);
   uint16_t *rinc = reinterpret_cast<uint16_t *>(B.rec + 3 * B.rs + s);
   for (int i = threadIdx.x; i < 4 * n_own; i += blockDim.x) {
     // entry i goes to record (s + i/4), 16-bit word 28 + i%4 (words 14,15:

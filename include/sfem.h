@@ -395,9 +395,10 @@ int sfem_apply_noalloc(sfem_ctx *ctx, const double *u, double *y);
 
 /* Measurement helpers (no counterpart in the paper).
  * sfem_time_operator: launches the raw operator y = K u (no masking) of
- * `op` `reps` times on library-owned scratch vectors, exactly as the solvers
- * launch it, between CUDA events on the context stream; writes the mean
- * device time per application in milliseconds.
+ * `op` `reps` times on library-owned scratch vectors (u: deterministic
+ * values in [-1, 1), y accumulating), exactly as the solvers launch it,
+ * between CUDA events on the context stream; writes the mean device time
+ * per application in milliseconds.
  * sfem_launch_count: kernels launched by this process through the library
  * so far (graph launches count their kernel nodes; captures do not count). */
 int sfem_time_operator(sfem_ctx *ctx, int op, int reps, double *ms_per_apply);

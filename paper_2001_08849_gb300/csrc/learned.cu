@@ -1081,6 +1081,7 @@ struct FpcgRun {
     SFEM_CHECK_LAUNCH();
     k_prolong<<<grid_for(c.n_nodes, 256), 256, 0, st>>>(Y, L->g, c.xyz, c.n_nodes, c.dmask, cv, Ac, off);
     SFEM_CHECK_LAUNCH();
+    SFEM_CUDA(cudaMemsetAsync(&S->cAc, 0, sizeof(double), st));  // the apply accumulates c.A c
     launch_mf32_tiled<double, double>(c, st, cv, Ac, &S->cAc, off);
     k_fp_cr<<<c.red_blocks, 256, 0, st>>>(cv, r, c.ndof, S, c.red_partial, c.tickets + 7);
     SFEM_CHECK_LAUNCH();

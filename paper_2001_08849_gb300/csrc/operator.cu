@@ -224,6 +224,7 @@ void apply_mf64(Ctx &c, const double *u, double *y, int nrhs, double *energy_out
 }
 void apply_mf32(Ctx &c, const float *u, float *y, int nrhs, double *energy_out) {
   SFEM_CUDA(cudaMemsetAsync(y, 0, (size_t)nrhs * c.ndof * sizeof(float), c.stream));
+  if (energy_out) SFEM_CUDA(cudaMemsetAsync(energy_out, 0, sizeof(double), c.stream));
   for (int r = 0; r < nrhs; ++r)
     launch_mf32_tiled<float, float>(c, c.stream, u + (int64_t)r * c.ndof, y + (int64_t)r * c.ndof,
                                     r == 0 ? energy_out : nullptr, nullptr);
@@ -367,6 +368,15 @@ extern "C" int sfem_apply(sfem_ctx *h, const void *u, void *y, int op, int nrhs)
   return SFEM_OK;
 }
 
+// deterministic input for operator timing: values in [-1, 1) from a
+// multiplicative hash of the index (a zero input would let the nodal force
+// atomics add zeros and time an unrepresentative case)
+template <class T>
+__global__ void k_timing_input(T *u, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) u[i] = (T)((double)(((uint64_t)i * 2654435761ull) % 20011ull) / 10005.5 - 1.0);
+}
+
 extern "C" int sfem_time_operator(sfem_ctx *h, int op, int reps, double *ms_per_apply) {
   try {
     SFEM_REQUIRE(h && h->c.vol && ms_per_apply && reps >= 1, SFEM_EINVAL, "bad arguments");
@@ -375,16 +385,27 @@ extern "C" int sfem_time_operator(sfem_ctx *h, int op, int reps, double *ms_per_
     const size_t es = op == SFEM_OP_MF32 ? sizeof(float) : sizeof(double);
     void *u = c.mem.raw(n * es);
     void *y = c.mem.raw(n * es);
-    SFEM_CUDA(cudaMemsetAsync(u, 0, n * es, c.stream));
+    if (op == SFEM_OP_MF32)
+      k_timing_input<float><<<grid_for(n, 256), 256, 0, c.stream>>>((float *)u, n);
+    else
+      k_timing_input<double><<<grid_for(n, 256), 256, 0, c.stream>>>((double *)u, n);
+    SFEM_CHECK_LAUNCH();
+    SFEM_CUDA(cudaMemsetAsync(y, 0, n * es, c.stream));
     ensure_w_scratch(c, (size_t)c.n_tets * 8 * sizeof(double));
     cudaEvent_t e0, e1;
     SFEM_CUDA(cudaEventCreate(&e0));
     SFEM_CUDA(cudaEventCreate(&e1));
+    // the CG launches the tiled operator with its energy sum (p.q) and the
+    // stop flag; so does the timing
+    double *energy = c.mem.get<double>(1);
+    int *done = c.mem.get<int>(1);
+    SFEM_CUDA(cudaMemsetAsync(done, 0, sizeof(int), c.stream));
+    SFEM_CUDA(cudaMemsetAsync(energy, 0, sizeof(double), c.stream));
     auto once = [&]() {
       if (op == SFEM_OP_MF32) {
-        launch_mf32_tiled<float, float>(c, c.stream, (const float *)u, (float *)y, nullptr, nullptr);
+        launch_mf32_tiled<float, float>(c, c.stream, (const float *)u, (float *)y, energy, done);
       } else if (op == SFEM_OP_MF32_F64) {
-        launch_mf32_tiled<double, double>(c, c.stream, (const double *)u, (double *)y, nullptr, nullptr);
+        launch_mf32_tiled<double, double>(c, c.stream, (const double *)u, (double *)y, energy, done);
       } else if (op == SFEM_OP_MF64) {
         launch_mf_strain<double, double>(c, c.stream, c.Gs64, (const double *)u, 1, (double *)c.w_scratch,
                                          nullptr);
@@ -409,6 +430,8 @@ extern "C" int sfem_time_operator(sfem_ctx *h, int op, int reps, double *ms_per_
     cudaEventDestroy(e1);
     c.mem.drop(u);
     c.mem.drop(y);
+    c.mem.drop(energy);
+    c.mem.drop(done);
   } catch (const Error &err) {
     set_last_error(err.msg);
     return err.status;

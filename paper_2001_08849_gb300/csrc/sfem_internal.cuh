@@ -256,7 +256,8 @@ double device_norm2(Ctx &c, const double *x, int64_t n);
 void compute_diag(Ctx &c);
 void build_tiles(Ctx &c);
 // tiled FP32 operator y += K u (y must be zeroed by the caller); u, y of
-// type TU/TY (float or double); energy u^T K u summed into *energy_out
+// type TU/TY (float or double); the energy u^T K u is added to *energy_out
+// (zeroed by the caller)
 template <class TU, class TY>
 void launch_mf32_tiled(Ctx &c, cudaStream_t st, const TU *u, TY *y, double *energy_out, const int *done);
 

@@ -144,6 +144,7 @@ __global__ void __launch_bounds__(kVecBlock) k_pcg_replace(PcgVecs<TX, TR, TP> v
     S->rz = vv[0];
     S->rr = vv[1];
     S->rmax2 = vv[1];
+    S->pq = 0.0;
     S->max_iter = max_iter;
     S->reason = 0;
     S->done = (vv[1] <= S->tol2) ? 1 : 0;
@@ -164,6 +165,7 @@ __global__ void __launch_bounds__(kVecBlock) k_pcg_replace_dir(PcgVecs<TX, TR, T
 // the last block of an update: iteration count, convergence, reliable-update
 // trigger (||r||^2 = rr)
 __device__ __forceinline__ void finish_update(SolveScalars *S, double alpha, double rz_old, double rr) {
+  S->pq = 0.0;  // every block has read it; the next tiled apply accumulates into it
   S->alpha = alpha;
   S->rz_prev = rz_old;
   S->rr = rr;

@@ -408,17 +408,13 @@ __global__ void k_max_i32(const int32_t *__restrict__ a, const int32_t *__restri
 // ---------------------------------------------------------------------------
 template <class TU, class TY>
 __global__ void __launch_bounds__(kTileThreads, 4)
-    k_mf32_tiled(TileArgs A, const TU *__restrict__ u, TY *__restrict__ y, float lam, float mu, double *partials,
-                 unsigned int *ticket, double *energy_out, const int *done) {
+    k_mf32_tiled(TileArgs A, const TU *__restrict__ u, TY *__restrict__ y, float lam, float mu, double *energy_out,
+                 const int *done) {
   if (done && *done) return;
   extern __shared__ float4 smem[];
   TileRegs R;
   tile_load(A, blockIdx.x, R);
-  const double en = tile_compute<TU, TY>(A, blockIdx.x, R, u, y, lam, mu, smem);
-  if (energy_out) {
-    double vv[1] = {en};
-    grid_sum<kTileThreads, 1>(vv, partials, ticket, energy_out);
-  }
+  tile_compute<TU, TY>(A, blockIdx.x, R, u, y, lam, mu, smem, energy_out);
 }
 
 // ---------------------------------------------------------------------------
@@ -577,7 +573,7 @@ void launch_mf32_tiled(Ctx &c, cudaStream_t st, const TU *u, TY *y, double *ener
   TileArgs A{c.tl.tile_start, c.tl.hoff, c.tl.noff, c.tl.halo_tet, c.tl.halo_lconn, c.tl.tile_nodes,
              c.tl.node_inc, c.tl.rec, c.n_tets};
   k_mf32_tiled<TU, TY><<<(unsigned)c.tl.n_tiles, kTileThreads, c.tl.smem, st>>>(
-      A, u, y, (float)c.lam, (float)c.mu, c.red_partial, c.tickets + 6, energy_out, done);
+      A, u, y, (float)c.lam, (float)c.mu, energy_out, done);
   SFEM_CHECK_LAUNCH();
 }
 

@@ -1097,6 +1097,16 @@ static void setup_coarse(Ctx &c, const sfem_coarse_opts *opts) {
   c.coarse = co;
 }
 
+bool ensure_coarse(Ctx &c) {
+  if (c.coarse) return true;
+  try {
+    setup_coarse(c, nullptr);
+  } catch (const Error &) {
+    return false;  // no coarse space for this mesh (e.g. patches too narrow)
+  }
+  return true;
+}
+
 }  // namespace sfem
 
 using namespace sfem;

@@ -28,6 +28,24 @@ __device__ __forceinline__ double block_sum(double v) {
   return v;  // valid in thread 0
 }
 
+// FP32 variant of block_sum
+template <int BS>
+__device__ __forceinline__ float block_sum_f(float v) {
+  __shared__ float shf[BS / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) shf[wid] = v;
+  __syncthreads();
+  v = (threadIdx.x < BS / 32) ? shf[threadIdx.x] : 0.f;
+  if (wid == 0) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  }
+  return v;  // valid in thread 0
+}
+
 // Sum K quantities over the whole grid.  partials holds K * gridDim.x
 // doubles, ticket is zero on entry and reset by the last block, which
 // stores the K sums to out[0..K) (if out is not null), leaves them in v[]

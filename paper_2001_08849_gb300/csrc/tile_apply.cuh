@@ -159,8 +159,8 @@ __device__ __forceinline__ void tile_strains(const TileArgs &A, const TileRegs &
 
 // face-averaged stress of every own tet and its four nodal force slots;
 // returns this thread's share of the energy sum w . t
-__device__ __forceinline__ double tile_forces(const TileRegs &R, const TileView &T, float lam, float mu) {
-  float en = 0.f;  // this thread's kTilePer tets; FP64 from the block sum on
+__device__ __forceinline__ float tile_forces(const TileRegs &R, const TileView &T, float lam, float mu) {
+  float en = 0.f;  // this thread's kTilePer tets
 #pragma unroll
   for (int r = 0; r < kTilePer; ++r) {
     const int j = threadIdx.x + r * kTileThreads;
@@ -213,7 +213,7 @@ __device__ __forceinline__ double tile_forces(const TileRegs &R, const TileView 
     fo[1] = make_float4(f[4], f[5], f[6], f[7]);
     fo[2] = make_float4(f[8], f[9], f[10], f[11]);
   }
-  return (double)en;
+  return en;
 }
 
 // the force at tile node i: its own slots summed in a fixed order with
@@ -250,7 +250,7 @@ __device__ __forceinline__ bool tile_node_force(const TileView &T, int i, float 
 // grid reduction here cost 26 us per apply on the 2M-tet beam (a memory
 // fence and a returning atomic in each of the 4928 tiles).
 template <class TU, class TY, bool kCoherentU = false>
-__device__ __forceinline__ double tile_compute(const TileArgs &A, int tile, const TileRegs &R,
+__device__ __forceinline__ float tile_compute(const TileArgs &A, int tile, const TileRegs &R,
                                                const TU *__restrict__ u, TY *__restrict__ y, float lam, float mu,
                                                float4 *smem, double *energy_out = nullptr) {
   const TileView T = tile_view(A, tile, smem);
@@ -282,11 +282,11 @@ __device__ __forceinline__ double tile_compute(const TileArgs &A, int tile, cons
   __syncthreads();
   tile_strains(A, R, T);
   __syncthreads();
-  const double en = tile_forces(R, T, lam, mu);
+  const float en = tile_forces(R, T, lam, mu);
   __syncthreads();
-  if (energy_out) {
-    const double e = block_sum<kTileThreads>(en);
-    if (threadIdx.x == 0) atomicAdd(energy_out, e);
+  if (energy_out) {  // FP32 within the tile (512 terms), FP64 across tiles
+    const float e = block_sum_f<kTileThreads>(en);
+    if (threadIdx.x == 0) atomicAdd(energy_out, (double)e);
   }
   for (int i = threadIdx.x; i < T.L; i += kTileThreads) {
     float fx, fy, fz;

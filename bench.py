@@ -227,6 +227,21 @@ def batch_form(S):
         infos, stats = S.sfem_batch_solve([c.h for c in ctxs], us, opts, n_sys, check=False)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
+        # the per-system two-level mode on the same batch (coarse spaces built
+        # inside the timed call on the first run, reused after that)
+        opts2 = S.batch_opts(tol=TOL, u_on_device=True, precond=1)
+        for u in us:
+            u.zero_()
+        S.sfem_batch_solve([c.h for c in ctxs], us, opts2, n_sys, check=False)
+        for u in us:
+            u.zero_()
+        torch.cuda.synchronize()
+        infos2, stats2 = S.sfem_batch_solve([c.h for c in ctxs], us, opts2, n_sys, check=False)
+        two_level = {"time_s": stats2["ms"] / 1e3, "solves_per_s": n_sys / (stats2["ms"] / 1e3),
+                     "converged": sum(1 for i in infos2 if i["status"] == 0),
+                     "max_true_relres": max(i["true_relres"] for i in infos2),
+                     "total_iterations": stats2["total_iterations"], "fallback_systems": stats2["fallback_systems"],
+                     "note": "precond=1: each system by the two-level mixed solve of its context"}
         tets = sum(p.mesh.n_tets for p in probs)
         # effective operator bytes: every CG iteration of every system reads its
         # beam's operator data (72 B/tet) and two FP64 vectors (16 B/DOF)
@@ -238,7 +253,7 @@ def batch_form(S):
                 "time_s": stats["ms"] / 1e3, "wall_s": wall, "solves_per_s": n_sys / (stats["ms"] / 1e3),
                 "rounds": stats["rounds"], "ctas_per_sm": stats["ctas_per_sm"], "graph": stats["graph"],
                 "fallback_systems": stats["fallback_systems"], "total_iterations": stats["total_iterations"],
-                "effective_operator_GBps": eff / (stats["ms"] / 1e3) / 1e9}
+                "effective_operator_GBps": eff / (stats["ms"] / 1e3) / 1e9, "two_level": two_level}
     finally:
         for c in ctxs:
             c.close()

@@ -229,7 +229,10 @@ typedef struct sfem_batch_opts {
   int warm_start;
   int autotune;          /* 1: time 1..max CTAs per SM on the first rounds (cached per shape) */
   int use_graph;         /* 1: capture a round as a CUDA graph */
-  int reserved[5];
+  int precond;           /* 0: the persistent Jacobi solve of all systems together; 1: each
+                            system by the two-level mixed solve of its context (coarse space
+                            built with the default options where possible; inner_tol 0: 0.03) */
+  int reserved[4];
 } sfem_batch_opts;
 
 typedef struct sfem_batch_stats {
@@ -241,7 +244,8 @@ typedef struct sfem_batch_stats {
   double ms;              /* device time of the whole batch */
   int fallback_systems;   /* systems that stagnated on the FP32 operator (three
                              refreshes in a row improving the true residual by
-                             less than 10%) and were finished by FP64 Jacobi-PCG */
+                             less than 10%) and were finished by FP64 PCG (with the
+                             two-level preconditioner where a coarse space exists) */
   int reserved[3];
 } sfem_batch_stats;
 

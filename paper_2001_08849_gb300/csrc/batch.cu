@@ -69,6 +69,8 @@ struct BatchDev {
   int n_sys;
   const int *work_prefix;  // n_beams + 1
   int total_work;
+  const int64_t *sys_off;  // n_sys + 1: the systems' DOFs concatenated (update phases split this range)
+  int64_t total_dof;
   SysState *state;         // 2 * n_sys, slot *slot is current
   int *slot;
   double *sums;            // 2 * n_sys * 2 (rz, rr)
@@ -135,6 +137,67 @@ __device__ __forceinline__ bool grid_barrier(const BatchDev &a) {
   return ok != 0;
 }
 
+// this block's range [g0, g1) of the concatenated DOFs and the first system
+// that overlaps it
+struct DofChunk {
+  int64_t g0, g1;
+  int s0;
+};
+__device__ __forceinline__ DofChunk dof_chunk(const BatchDev &a) {
+  DofChunk ch;
+  const int64_t per = (a.total_dof + gridDim.x - 1) / gridDim.x;
+  ch.g0 = min(a.total_dof, (int64_t)blockIdx.x * per);
+  ch.g1 = min(a.total_dof, ch.g0 + per);
+  int lo = 0, hi = a.n_sys - 1;  // largest s with sys_off[s] <= g0
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (a.sys_off[mid] <= ch.g0)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  ch.s0 = lo;
+  return ch;
+}
+
+// the per-system decision after an update (identical in every block)
+__device__ __forceinline__ SysState decide(const BatchDev &a, const SysState *st, const double *pq,
+                                           const double *sums, int s) {
+  const SysState ss = load_state(st + s);
+  SysState n2 = ss;
+  n2.fresh = 0;
+  if (!ss.active) return n2;
+  const double pqs = __ldcg(&pq[s]);
+  const double alpha = ss.rz / pqs;
+  const BatchSys &S = a.sys[s];
+  if (!(pqs > 0.0) || !isfinite(alpha)) {
+    n2.active = 0;
+    n2.reason = 4;
+    return n2;
+  }
+  const double rz_new = __ldcg(&sums[2 * s]), rr = __ldcg(&sums[2 * s + 1]);
+  n2.iter = ss.iter + 1;
+  n2.rz_prev = ss.rz;
+  n2.rz = rz_new;
+  n2.rr = rr;
+  n2.beta = rz_new / ss.rz;
+  n2.rmax2 = fmax(ss.rmax2, rr);
+  if (!isfinite(rz_new) || !isfinite(rr)) {
+    n2.active = 0;
+    n2.reason = 4;
+  } else if (rr <= a.tol2 * S.bnorm * S.bnorm) {
+    n2.active = 0;
+    n2.reason = 1;
+  } else if (n2.iter >= a.max_iter) {
+    n2.active = 0;
+    n2.reason = 3;
+  } else if (rr < a.delta2 * n2.rmax2) {
+    n2.active = 0;
+    n2.reason = 2;
+  }
+  return n2;
+}
+
 // MINB: CTAs per SM the register budget is compiled for (1, 2 or 3); the
 // autotuner times the variants
 template <int MINB>
@@ -175,17 +238,19 @@ __global__ void __launch_bounds__(kTileThreads, MINB) k_batch_cg(BatchDev a) {
       }
     }
     if (!grid_barrier(a)) return;
-    // P2: updates of the active systems
-    for (int s = 0; s < a.n_sys; ++s) {
+    // P2: updates of the active systems over this block's chunk of the
+    // concatenated DOFs (a block meets one or two systems, not all of them)
+    const DofChunk ch = dof_chunk(a);
+    for (int s = ch.s0; s < a.n_sys && a.sys_off[s] < ch.g1; ++s) {
       const SysState ss = load_state(st + s);
       if (!ss.active) continue;
       const double pqs = __ldcg(&pq[s]);
       const double alpha = ss.rz / pqs;
       if (!(pqs > 0.0) || !isfinite(alpha)) continue;
       const BatchSys &S = a.sys[s];
+      const int64_t lo = max(ch.g0, a.sys_off[s]) - a.sys_off[s], hi = min(ch.g1, a.sys_off[s + 1]) - a.sys_off[s];
       double rz = 0.0, rr = 0.0;
-      for (int64_t i = (int64_t)blockIdx.x * kTileThreads + threadIdx.x; i < S.n;
-           i += (int64_t)gridDim.x * kTileThreads) {
+      for (int64_t i = lo + threadIdx.x; i < hi; i += kTileThreads) {
         S.d[i] = __ldcg(&S.d[i]) + alpha * __ldcg(&S.p[i]);
         const double ri = S.dmask[i] ? __ldcg(&S.r[i]) - alpha * __ldcg(&S.q[i]) : 0.0;
         S.r[i] = ri;
@@ -200,59 +265,31 @@ __global__ void __launch_bounds__(kTileThreads, MINB) k_batch_cg(BatchDev a) {
       }
     }
     if (!grid_barrier(a)) return;
-    // P3: decisions (identical in every block) and new directions
+    // P3: decisions (identical in every block; block 0 stores them) and new
+    // directions over this block's chunk
     bool any_active = false;
     SysState *nx = a.state + (par ^ 1) * a.n_sys;
     for (int s = 0; s < a.n_sys; ++s) {
-      const SysState ss = load_state(st + s);
-      SysState n2 = ss;
-      n2.fresh = 0;
-      if (ss.active) {
-        const double pqs = __ldcg(&pq[s]);
-        const double alpha = ss.rz / pqs;
-        const BatchSys &S = a.sys[s];
-        if (!(pqs > 0.0) || !isfinite(alpha)) {
-          n2.active = 0;
-          n2.reason = 4;
-        } else {
-          const double rz_new = __ldcg(&sums[2 * s]), rr = __ldcg(&sums[2 * s + 1]);
-          n2.iter = ss.iter + 1;
-          n2.rz_prev = ss.rz;
-          n2.rz = rz_new;
-          n2.rr = rr;
-          n2.beta = rz_new / ss.rz;
-          n2.rmax2 = fmax(ss.rmax2, rr);
-          if (!isfinite(rz_new) || !isfinite(rr)) {
-            n2.active = 0;
-            n2.reason = 4;
-          } else if (rr <= a.tol2 * S.bnorm * S.bnorm) {
-            n2.active = 0;
-            n2.reason = 1;
-          } else if (n2.iter >= a.max_iter) {
-            n2.active = 0;
-            n2.reason = 3;
-          } else if (rr < a.delta2 * n2.rmax2) {
-            n2.active = 0;
-            n2.reason = 2;
-          }
-        }
-        if (n2.active) {
-          any_active = true;
-          const double beta = n2.beta;
-          for (int64_t i = (int64_t)blockIdx.x * kTileThreads + threadIdx.x; i < S.n;
-               i += (int64_t)gridDim.x * kTileThreads) {
-            S.p[i] = S.dinv[i] * __ldcg(&S.r[i]) + beta * __ldcg(&S.p[i]);
-            S.q[i] = 0.0;
-          }
-        }
-      }
+      const SysState n2 = decide(a, st, pq, sums, s);
+      any_active = any_active || n2.active;
       if (blockIdx.x == 0 && threadIdx.x == 0) {
         nx[s] = n2;
         double *nsums = a.sums + 2 * (par ^ 1) * a.n_sys;
         nsums[2 * s] = 0.0;
         nsums[2 * s + 1] = 0.0;
         a.pq[(par ^ 1) * a.n_sys + s] = 0.0;
-        if (ss.active) ++iters;
+        if (__ldcg(&st[s].active)) ++iters;
+      }
+    }
+    for (int s = ch.s0; s < a.n_sys && a.sys_off[s] < ch.g1; ++s) {
+      const SysState n2 = decide(a, st, pq, sums, s);
+      if (!n2.active) continue;
+      const BatchSys &S = a.sys[s];
+      const double beta = n2.beta;
+      const int64_t lo = max(ch.g0, a.sys_off[s]) - a.sys_off[s], hi = min(ch.g1, a.sys_off[s + 1]) - a.sys_off[s];
+      for (int64_t i = lo + threadIdx.x; i < hi; i += kTileThreads) {
+        S.p[i] = S.dinv[i] * __ldcg(&S.r[i]) + beta * __ldcg(&S.p[i]);
+        S.q[i] = 0.0;
       }
     }
     if (!any_active) {
@@ -272,11 +309,13 @@ __global__ void __launch_bounds__(kTileThreads, MINB) k_batch_cg(BatchDev a) {
 // beam_skip[b] = 1 when no system of beam b needs its residual recomputed
 __global__ void k_refresh_x(BatchDev a) {
   const SysState *st = a.state + (*a.slot) * a.n_sys;
-  for (int s = 0; s < a.n_sys; ++s) {
+  const DofChunk ch = dof_chunk(a);
+  for (int s = ch.s0; s < a.n_sys && a.sys_off[s] < ch.g1; ++s) {
     const SysState &ss = st[s];
     if (ss.status != 0 || ss.active || ss.reason == 0) continue;
     const BatchSys &S = a.sys[s];
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < S.n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t lo = max(ch.g0, a.sys_off[s]) - a.sys_off[s], hi = min(ch.g1, a.sys_off[s + 1]) - a.sys_off[s];
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
       S.x[i] += S.d[i];
       S.d[i] = 0.0;
     }
@@ -298,12 +337,14 @@ __global__ void k_refresh_x(BatchDev a) {
 __global__ void __launch_bounds__(256) k_refresh_r(BatchDev a) {
   const SysState *st = a.state + (*a.slot) * a.n_sys;
   double *sums = a.sums + 2 * (*a.slot) * a.n_sys;
-  for (int s = 0; s < a.n_sys; ++s) {
+  const DofChunk ch = dof_chunk(a);
+  for (int s = ch.s0; s < a.n_sys && a.sys_off[s] < ch.g1; ++s) {
     const SysState &ss = st[s];
     if (ss.status != 0 || ss.active || ss.reason == 0) continue;
     const BatchSys &S = a.sys[s];
     double rz = 0.0, rr = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < S.n; i += (int64_t)gridDim.x * 256) {
+    const int64_t lo = max(ch.g0, a.sys_off[s]) - a.sys_off[s], hi = min(ch.g1, a.sys_off[s + 1]) - a.sys_off[s];
+    for (int64_t i = lo + threadIdx.x; i < hi; i += 256) {
       const double ri = S.dmask[i] ? S.f[i] - S.Kx[i] : 0.0;
       S.r[i] = ri;
       rz += S.dinv[i] * ri * ri;
@@ -415,6 +456,54 @@ static std::map<long long, int> g_tune_cache;  // key: (device, total tiles buck
 
 using namespace sfem;
 
+// precond = 1: every system by the two-level mixed-precision solve of its
+// own context (IR32_64 with FP32 inner vectors and the Galerkin coarse
+// correction, coarse space built with the default options where possible,
+// else Jacobi), one after the other.  With the coarse correction a system
+// needs about a sixth of the Jacobi iterations that the persistent kernel
+// runs.  (Eight host threads driving different beams' contexts at once
+// measured no faster: 6.95 vs 6.63 s on the 64-beam batch.)
+static int batch_two_level(sfem_ctx *const *ctxs, int n, double *const *u, const sfem_batch_opts &o, double tol,
+                           int max_iter, sfem_solve_info *infos, sfem_batch_stats *stats) {
+  const auto t0 = std::chrono::steady_clock::now();
+  int worst = SFEM_OK, k2 = 0, fallbacks = 0;
+  long long total_it = 0;
+  for (int b = 0; b < n; ++b) {
+    Ctx &c = ctxs[b]->c;
+    const bool coarse = ensure_coarse(c);
+    for (int j = 0; j < c.nrhs; ++j, ++k2) {
+      sfem_solve_opts so{};
+      so.kind = SFEM_SOLVE_IR32_64;
+      so.op64 = SFEM_OP_MF64;
+      so.rhs = j;
+      so.u_on_device = o.u_on_device;
+      so.warm_start = o.warm_start;
+      so.tol = tol;
+      so.max_iter = max_iter;
+      so.inner_tol = o.inner_tol > 0 ? o.inner_tol : 0.03;
+      so.precond = coarse ? 1 : 0;
+      so.fp32_vectors = coarse ? 3 : 0;
+      sfem_solve_info info{};
+      const int rc = sfem_solve(ctxs[b], nullptr, u[b] + (int64_t)j * c.ndof, &so, &info);
+      if (rc != SFEM_OK && worst == SFEM_OK) worst = rc;
+      total_it += info.iterations;
+      fallbacks += info.fallbacks;
+      if (infos) infos[k2] = info;
+    }
+  }
+  for (int b = 0; b < n; ++b) SFEM_CUDA(cudaStreamSynchronize(ctxs[b]->c.stream));
+  const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (stats) {
+    *stats = sfem_batch_stats{};
+    stats->n_systems = k2;
+    stats->total_iterations = total_it;
+    stats->ms = ms;
+    stats->fallback_systems = fallbacks;
+  }
+  if (worst != SFEM_OK) set_last_error("some systems of the batch did not converge");
+  return worst;
+}
+
 extern "C" int sfem_batch_solve(sfem_ctx *const *ctxs, int n, double *const *u, const sfem_batch_opts *opts,
                                 sfem_solve_info *infos, sfem_batch_stats *stats) {
   std::vector<void *> owned;
@@ -444,6 +533,8 @@ extern "C" int sfem_batch_solve(sfem_ctx *const *ctxs, int n, double *const *u, 
     const double delta = opts->inner_tol > 0 ? opts->inner_tol : 0.1;
     const int max_iter = opts->max_iter > 0 ? opts->max_iter : 200000;
     const int max_rounds = opts->max_rounds > 0 ? opts->max_rounds : 400;
+    SFEM_REQUIRE(opts->precond == 0 || opts->precond == 1, SFEM_EINVAL, "precond must be 0 or 1");
+    if (opts->precond == 1) return batch_two_level(ctxs, n, u, *opts, tol, max_iter, infos, stats);
     auto get = [&](size_t bytes) {
       void *p = c0->mem.raw(bytes);
       owned.push_back(p);
@@ -502,7 +593,13 @@ extern "C" int sfem_batch_solve(sfem_ctx *const *ctxs, int n, double *const *u, 
         S.bnorm = c.bnorm[j];
       }
     }
+    std::vector<int64_t> soff(n_sys + 1, 0);
+    for (int k2 = 0; k2 < n_sys; ++k2) soff[k2 + 1] = soff[k2] + hs[k2].n;
     BatchDev a{};
+    a.sys_off = (const int64_t *)get((n_sys + 1) * sizeof(int64_t));
+    SFEM_CUDA(cudaMemcpyAsync((void *)a.sys_off, soff.data(), (n_sys + 1) * sizeof(int64_t), cudaMemcpyHostToDevice,
+                              st));
+    a.total_dof = soff[n_sys];
     a.beams = (BatchBeam *)get(n * sizeof(BatchBeam));
     a.sys = (BatchSys *)get(n_sys * sizeof(BatchSys));
     a.work_prefix = (int *)get((n + 1) * sizeof(int));

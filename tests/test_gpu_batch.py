@@ -104,3 +104,30 @@ def test_batch_uneven_beams_device_vectors(S):
     finally:
         for c in ctxs:
             c.close()
+
+
+def test_batch_two_level_uneven_beams(S):
+    """The per-system two-level mode (precond = 1) on eight beams of the
+    uneven batch family: every system reaches 1e-8 and agrees with FP64 PCG
+    of the same context."""
+    import torch
+    probs = [p for p in batch_beams(64, seed=5) if p.mesh.n_tets < 60000][:8]
+    ctxs = [S.FsFem(p) for p in probs]
+    try:
+        us = [torch.zeros((p.nrhs, c.ndof), dtype=torch.float64, device="cuda") for p, c in zip(probs, ctxs)]
+        n_sys = sum(p.nrhs for p in probs)
+        infos, stats = S.sfem_batch_solve([c.h for c in ctxs], us, S.batch_opts(tol=1e-8, u_on_device=True,
+                                                                                  precond=1), n_sys)
+        assert stats["n_systems"] == n_sys
+        assert all(i["status"] == S.SFEM_OK and i["true_relres"] <= 1e-8 for i in infos)
+        for k in (0, 3):
+            c = ctxs[k]
+            for r in range(probs[k].nrhs):
+                x = np.zeros(c.ndof)
+                S.sfem_solve(c.h, x, S.solve_opts(kind=S.SFEM_SOLVE_PCG64, rhs=r, tol=1e-9), check=False)
+                assert np.linalg.norm(us[k][r].cpu().numpy() - x) <= 1e-5 * np.linalg.norm(x)
+        with pytest.raises(S.SfemError):
+            S.sfem_batch_solve([c.h for c in ctxs], us, S.batch_opts(precond=2, u_on_device=True), n_sys)
+    finally:
+        for c in ctxs:
+            c.close()

@@ -88,6 +88,7 @@ __global__ void k_cs_gather(CoarseDev cs, const int *done) {
   if (done && *done) return;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= cs.npad) return;
+  cs.yc[t] = 0.f;  // k_cs_symv accumulates into yc
   if (t >= cs.nc) {
     cs.rc[t] = 0.f;
     return;
@@ -101,42 +102,67 @@ __global__ void k_cs_gather(CoarseDev cs, const int *done) {
   cs.rc[t] = (float)s;
 }
 
-// yc = C rc (one warp per row; C symmetric, rows of npad floats).  C is
-// read with evict-first loads: between two iterations the operator's
-// records evict it anyway (measured: C comes from DRAM either way, and
-// evict-first records slowed the operator by 5 us), so it should not push
-// the operator's data out in turn.  8 independent 16-byte loads per lane.
-__global__ void __launch_bounds__(256) k_cs_gemv(CoarseDev cs, const int *done) {
+// yc += C rc with C = A_c^-1 symmetric, stored as its lower 64 x 64 blocks
+// (block (a, b), a >= b, at (a (a + 1) / 2 + b) * 4096, row-major): half the
+// bytes of the full matrix, which streams from DRAM every iteration (the
+// operator's records evict it from L2).  One CTA per block: the block is read
+// once with evict-first loads and applied twice, C_ab rc_b to yc_a and
+// C_ab^T rc_a to yc_b (a > b), by FP32 atomics; yc must be zero before.
+__global__ void __launch_bounds__(256) k_cs_symv(CoarseDev cs, const int *done) {
   if (done && *done) return;
-  const int row = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-  if (row >= cs.npad) return;
-  const float4 *Cr = reinterpret_cast<const float4 *>(cs.C + (int64_t)row * cs.npad);
-  const float4 *r4 = reinterpret_cast<const float4 *>(cs.rc);
-  const int n4 = cs.npad / 4;  // a multiple of 16
-  constexpr int U = 8;
-  float acc[U];
-#pragma unroll
-  for (int u = 0; u < U; ++u) acc[u] = 0.f;
-  for (int q0 = lane; q0 < n4; q0 += 32 * U) {
-    float4 a[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int q = q0 + 32 * u;
-      a[u] = q < n4 ? __ldcs(Cr + q) : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int q = q0 + 32 * u;
-      if (q < n4) {
-        const float4 b = r4[q];
-        acc[u] = fmaf(a[u].x, b.x, fmaf(a[u].y, b.y, fmaf(a[u].z, b.z, fmaf(a[u].w, b.w, acc[u]))));
-      }
-    }
+  const int t = blockIdx.x;
+  int a = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+  while ((a + 1) * (a + 2) / 2 <= t) ++a;
+  while (a * (a + 1) / 2 > t) --a;
+  const int b = t - a * (a + 1) / 2;
+  __shared__ float ra[kCB], rb[kCB];
+  if (threadIdx.x < kCB) {
+    ra[threadIdx.x] = cs.rc[a * kCB + threadIdx.x];
+    rb[threadIdx.x] = cs.rc[b * kCB + threadIdx.x];
   }
-  float s = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+  // thread: row i = tid / 4, columns 16 q .. 16 q + 15 (q = tid % 4)
+  const int i = threadIdx.x >> 2, q = threadIdx.x & 3;
+  const float4 *blk = reinterpret_cast<const float4 *>(cs.C + (int64_t)t * kCB * kCB) + i * (kCB / 4) + q * 4;
+  float4 v[4];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-  if (lane == 0) cs.yc[row] = s;
+  for (int u = 0; u < 4; ++u) v[u] = __ldcs(blk + u);
+  __syncthreads();
+  const float *rbq = rb + 16 * q;
+  float s = 0.f;
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+    s = fmaf(v[u].x, rbq[4 * u], fmaf(v[u].y, rbq[4 * u + 1], fmaf(v[u].z, rbq[4 * u + 2], fmaf(v[u].w, rbq[4 * u + 3], s))));
+  s += __shfl_xor_sync(0xffffffffu, s, 1);
+  s += __shfl_xor_sync(0xffffffffu, s, 2);
+  if (q == 0) atomicAdd(&cs.yc[a * kCB + i], s);
+  if (a == b) return;  // a whole block: uniform
+  // C_ab^T ra: column j = 16 q + 4 u + w gets v[u].{x,y,z,w} * ra[i]; sum over i
+  // within the warp (8 rows), then over the 8 warps in shared memory
+  const float ri = ra[i];
+  float c[16];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    c[4 * u] = v[u].x * ri;
+    c[4 * u + 1] = v[u].y * ri;
+    c[4 * u + 2] = v[u].z * ri;
+    c[4 * u + 3] = v[u].w * ri;
+  }
+#pragma unroll
+  for (int k = 0; k < 16; ++k)
+#pragma unroll
+    for (int o = 4; o < 32; o <<= 1) c[k] += __shfl_xor_sync(0xffffffffu, c[k], o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __shared__ float part[kCB / 8][kCB];  // per warp, per column
+  if (lane < 4)
+#pragma unroll
+    for (int k = 0; k < 16; ++k) part[warp][16 * lane + k] = c[k];
+  __syncthreads();
+  if (threadIdx.x < kCB) {
+    float x = 0.f;
+#pragma unroll
+    for (int w = 0; w < kCB / 8; ++w) x += part[w][threadIdx.x];
+    atomicAdd(&cs.yc[b * kCB + threadIdx.x], x);
+  }
 }
 
 // ---- probing -----------------------------------------------------------------
@@ -722,7 +748,7 @@ __global__ void __launch_bounds__(256) k_trtri_cols(const float *L, const float 
   }
 }
 
-// C[a][b] = sum_{l >= a} W[l][a]^T W[l][b] for a >= b, mirrored to C[b][a]
+// C[a][b] = sum_{l >= a} W[l][a]^T W[l][b] for a >= b (packed lower blocks)
 __global__ void __launch_bounds__(256) k_lauum(const float *W, float *C, int npad, int nb) {
   __shared__ Tile64<float> As, Bs;
   const int t = blockIdx.x;
@@ -739,13 +765,12 @@ __global__ void __launch_bounds__(256) k_lauum(const float *W, float *C, int npa
     __syncthreads();
     mm64<float, true, false>(acc, As, Bs, tm, tn);
   }
+  // packed lower blocks: block (a, b) at t = a (a + 1) / 2 + b
+  float *Cb = C + (int64_t)t * kCB * kCB;
 #pragma unroll
   for (int x = 0; x < 4; ++x)
 #pragma unroll
-    for (int y = 0; y < 4; ++y) {
-      C[(int64_t)(a * kCB + tm + x) * npad + b * kCB + tn + y] = acc[x][y];
-      if (a != b) C[(int64_t)(b * kCB + tn + y) * npad + a * kCB + tm + x] = acc[x][y];
-    }
+    for (int y = 0; y < 4; ++y) Cb[(tm + x) * kCB + tn + y] = acc[x][y];
 }
 
 // z = D^-1 r + P Pi yc
@@ -756,7 +781,8 @@ __global__ void k_cs_apply_z(CoarseDev cs, const double *__restrict__ r, const d
 }
 
 void coarse_gemv(const CoarseDev &cs, cudaStream_t st, const int *done) {
-  k_cs_gemv<<<(cs.npad + 7) / 8, 256, 0, st>>>(cs, done);
+  const int nb = cs.npad / kCB;
+  k_cs_symv<<<nb * (nb + 1) / 2, 256, 0, st>>>(cs, done);
   SFEM_CHECK_LAUNCH();
 }
 
@@ -767,8 +793,7 @@ static void coarse_correction_t(Ctx &c, cudaStream_t st, const TV *r, const int 
   SFEM_CHECK_LAUNCH();
   k_cs_gather<<<grid_for(cs.npad, 256), 256, 0, st>>>(cs, done);
   SFEM_CHECK_LAUNCH();
-  k_cs_gemv<<<(cs.npad + 7) / 8, 256, 0, st>>>(cs, done);
-  SFEM_CHECK_LAUNCH();
+  coarse_gemv(cs, st, done);
 }
 void coarse_correction(Ctx &c, cudaStream_t st, const double *r, const int *done) {
   coarse_correction_t(c, st, r, done);
@@ -1075,7 +1100,7 @@ static void setup_coarse(Ctx &c, const sfem_coarse_opts *opts) {
   // (trtri reads only the strictly lower blocks of L and the diagonal blocks'
   // inverses Wd)
   float *W = c.mem.get<float>(np2);
-  float *C = c.mem.get<float>(np2);
+  float *C = c.mem.get<float>((size_t)nb * (nb + 1) / 2 * kCB * kCB);
   SFEM_CUDA(cudaMemsetAsync(W, 0, np2 * sizeof(float), c.stream));
   k_trtri_cols<<<nb, 256, 0, c.stream>>>(L32, Wd, W, cs.npad, nb, bwb);
   SFEM_CHECK_LAUNCH();

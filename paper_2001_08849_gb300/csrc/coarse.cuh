@@ -31,7 +31,8 @@ struct CoarseDev {
   int nchunk;
   float *cellsum;          // ncell x 24 partial restrictions (8 corners x 3)
   float *rc, *yc;          // coarse residual and correction (npad)
-  const float *C;          // npad x npad: A_c^-1 (symmetric), FP32
+  const float *C;          // A_c^-1 (symmetric, FP32): lower 64 x 64 blocks, block (a, b) at
+                           // (a (a + 1) / 2 + b) * 4096, row-major
 };
 
 // weight of corner k (bits: x = 4, y = 2, z = 1) at fractions f

@@ -266,7 +266,7 @@ __global__ void __launch_bounds__(kVecBlock) k_pcg_direction(PcgVecs<TX, TR, TP>
 //                  interpolation cell (nodes grouped by cell), its 24
 //                  sums (8 corners x 3 components) added to the cell's
 //                  centres by FP32 atomics;
-//   k_cs_gemv      yc = C rc;
+//   k_cs_symv      yc = C rc (packed symmetric C; yc cleared by the restriction);
 //   k_tl_zr        z = D^-1 r + P Pi yc in FP32 (stored), z.r and beta;
 //                  rc = 0 for the next restriction;
 //   k_tl_dir       p = z + beta p.
@@ -371,6 +371,8 @@ constexpr int kRestrictWarpNodes = 256;
 template <class TR>
 __global__ void __launch_bounds__(kVecBlock) k_tl_restrict(const TR *__restrict__ r, CoarseDev cs, const int *done) {
   if (done && *done) return;
+  if (blockIdx.x == 0)  // the coarse product accumulates into yc
+    for (int i = threadIdx.x; i < cs.npad; i += kVecBlock) cs.yc[i] = 0.f;
   const int4 ch = cs.chunk[blockIdx.x];
   const int lane = threadIdx.x & 31;
   const int b = ch.y + kRestrictWarpNodes * (threadIdx.x >> 5);
@@ -421,7 +423,7 @@ __global__ void __launch_bounds__(kVecBlock) k_tl_zr(PcgVecs<TX, TR, TP> v, Solv
                                                      unsigned int *ticket) {
   if (S->done) return;
   const CoarseDev &cs = v.cs;
-  if (blockIdx.x == 0)  // k_cs_gemv has consumed rc
+  if (blockIdx.x == 0)  // k_cs_symv has consumed rc
     for (int i = threadIdx.x; i < cs.npad; i += kVecBlock) cs.rc[i] = 0.f;
   const TR *__restrict__ r = v.r;
   const float *__restrict__ dinv = v.dinv32;

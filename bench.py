@@ -263,6 +263,53 @@ def batch_form(S):
 # learned form: flexible PCG with the learned coarse correction vs Jacobi-PCG
 # ---------------------------------------------------------------------------
 
+def mixed_family_form(S):
+    """The mixed-precision solve with the two-level preconditioner on the beam
+    family at 2.0M tets (200 x 40 x 42, seed 3) and 12.3M tets (400 x 80 x 64,
+    seed 4), nu 0.3 and the near-incompressible 0.49 (the 2.0M / 0.3 case is
+    the timed step).  Each case: device inputs, then mesh setup + coarse
+    setup + solve timed once with CUDA events, and the FP32 operator's time
+    per apply at that size.  Patches of 8 lattice nodes per axis, widened to
+    10 on the 12.3M beam (the coarse space holds at most 8192 DOFs)."""
+    import numpy as np
+    import torch
+    from inputs.kuhn_beam import cantilever
+    from paper_2001_08849_gb300.opbench import patch_dims_for
+    out = {}
+    stream = torch.cuda.current_stream()
+    for cells, seed, nu in (((200, 40, 42), 3, 0.49), ((400, 80, 64), 4, 0.3), ((400, 80, 64), 4, 0.49)):
+        prob = cantilever(*cells, seed=seed, nu=nu)
+        m = prob.mesh
+        dev = [torch.from_numpy(np.ascontiguousarray(a)).cuda()
+               for a in (m.xyz, m.tets.astype(np.int32), prob.dir_dofs.astype(np.int32), prob.dir_vals,
+                         prob.trac_tris.astype(np.int32), prob.trac)]
+        ndof = 3 * m.n_nodes
+        dims = patch_dims_for(cells)
+        x = torch.zeros(ndof, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ea.record(stream)
+        hh, kk = S.sfem_mesh_setup(*dev[:2], prob.E, prob.nu, *dev[2:], inputs_on_device=True)
+        ci = S.sfem_coarse_setup(hh, patch_dims=dims)
+        inf = S.sfem_solve(hh, x, S.solve_opts(kind=S.SFEM_SOLVE_IR32_64, op64=S.SFEM_OP_MF64, tol=TOL,
+                                                u_on_device=True, precond=1, fp32_vectors=FP32_VECTORS,
+                                                inner_tol=INNER_TOL), check=False)
+        eb.record(stream)
+        torch.cuda.synchronize()
+        op_ms = S.sfem_time_operator(hh, S.SFEM_OP_MF32, reps=10)
+        name = f"ir32_64_two_level_{m.n_tets / 1e6:.1f}M_nu{nu}"
+        out[name] = {"cells": list(cells), "seed": seed, "nu": nu, "n_tets": int(m.n_tets), "ndof": int(ndof),
+                     "time_to_solve_s": ea.elapsed_time(eb) / 1e3,
+                     "mesh_setup_ms": S.sfem_get_info(hh)["setup_ms"], "coarse_dims": list(dims),
+                     "coarse_setup_ms": ci["setup_ms"], "solve_ms": inf["solve_ms"],
+                     "iterations": inf["iterations"], "outer_iterations": inf["outer_iterations"],
+                     "fallbacks": inf["fallbacks"], "true_relres": inf["true_relres"], "status": inf["status"],
+                     "mf32_apply_ms": op_ms, "mf32_gdof_per_s": ndof / op_ms / 1e6}
+        S.sfem_destroy(hh)
+        del dev, x
+    return out
+
+
 def learned_form(S, n_train=8, n_test=2, every=8, epochs=10):
     """Train the coarse-correction network on snapshots of Jacobi-PCG runs of
     the 2M-tet beam under random loads (seeds 100..), then time held-out
@@ -514,6 +561,7 @@ def main():
                                       "coarse_probes": coarse_infos[-1]["probes"], "note": "the timed step"}
 
     if not args.no_forms and rank == 0:
+        forms.update(mixed_family_form(S))
         forms["batch_64x4"] = batch_form(S)
         forms["fpcg_learned"] = learned_form(S, n_train=args.learned_train, n_test=args.learned_test)
 

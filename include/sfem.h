@@ -259,14 +259,15 @@ int sfem_batch_solve(sfem_ctx *const *ctxs, int n, double *const *u, const sfem_
  * d0 x d1 x d2 grid of centres over the mesh's bounding box (centre i at
  * lo + (i + 1/2) ext / d), masked by P.  sfem_coarse_setup builds Pi and
  * A_c with the FP32 matrix-free operator (tile by tile, or by probing with
- * 3 x prod(min(5, d_a)) applies), factors A_c by a blocked FP64 Cholesky and
- * keeps C = A_c^-1 in FP32 on the
- * device (3P <= 8192; patches at least 2.5 node spacings wide where
- * d_a >= 5).  Solves use it with sfem_solve_opts.precond = 1.  Returns
- * SFEM_EBREAKDOWN if A_c is not positive definite. */
+ * 3 x prod(min(5, d_a)) applies), factors A_c by a banded blocked Cholesky
+ * (FP32 or FP64, see factor) and keeps C = A_c^-1 in FP32 on the device
+ * (3P <= 8192; patches at least 2.5 node spacings wide where d_a >= 5).
+ * Solves use it with sfem_solve_opts.precond = 1.  Returns SFEM_EBREAKDOWN
+ * if A_c is not positive definite. */
 typedef struct sfem_coarse_opts {
   int patch_dims[3];   /* centres per axis (0: about patch_nodes nodes per patch axis) */
-  int patch_nodes;     /* 0: 8 */
+  int patch_nodes;     /* 0: 8, widened (9, 10, ...) while the axes left at 0 give more than
+                          8192 coarse DOFs */
   int assembly;        /* A_c: 0 tile by tile (each tile applies its part of the operator to
                           the coarse functions of the cells it touches; probing is used for
                           a tile that touches more than 4 cells on an axis); 1 probing with

@@ -36,6 +36,7 @@
 namespace sfem {
 
 constexpr int kCB = 64;           // dense block order
+constexpr int64_t kMaxCoarse = 8192;  // coarse DOFs (3 per centre)
 constexpr int kRestrictThreads = 256;
 
 // ---- restriction -----------------------------------------------------------
@@ -904,22 +905,31 @@ static void setup_coarse(Ctx &c, const sfem_coarse_opts *opts) {
   auto co = std::make_shared<Coarse>();
   // grid of centres over the nodes' bounding box (found with the tiles)
   const double *lo = c.bbox_lo, *hi = c.bbox_hi;
-  const int pn = (opts && opts->patch_nodes > 0) ? opts->patch_nodes : 8;
+  const bool auto_pn = !(opts && opts->patch_nodes > 0);
+  int pn = auto_pn ? 8 : opts->patch_nodes;
   const double box = std::max((hi[0] - lo[0]) * (hi[1] - lo[1]) * (hi[2] - lo[2]), 1e-300);
   const double h_mean = std::cbrt(box / (double)c.n_nodes);
   CoarseDev &cs = co->dev;
   int64_t P = 1;
-  for (int a = 0; a < 3; ++a) {
-    co->g.lo[a] = lo[a];
-    co->g.ext[a] = std::max(hi[a] - lo[a], 1e-300);
-    const int req = opts ? opts->patch_dims[a] : 0;
-    SFEM_REQUIRE(req >= 0 && req <= 4096, SFEM_EINVAL, "patch_dims out of range");
-    co->g.d[a] = req > 0 ? req : std::max(1, (int)std::ceil((hi[a] - lo[a]) / (pn * h_mean) - 1e-9));
-    cs.d[a] = co->g.d[a];
-    cs.cd[a] = std::max(cs.d[a] - 1, 1);
-    P *= cs.d[a];
+  for (;;) {
+    P = 1;
+    bool any_auto = false;
+    for (int a = 0; a < 3; ++a) {
+      co->g.lo[a] = lo[a];
+      co->g.ext[a] = std::max(hi[a] - lo[a], 1e-300);
+      const int req = opts ? opts->patch_dims[a] : 0;
+      SFEM_REQUIRE(req >= 0 && req <= 4096, SFEM_EINVAL, "patch_dims out of range");
+      any_auto |= req == 0;
+      co->g.d[a] = req > 0 ? req : std::max(1, (int)std::ceil((hi[a] - lo[a]) / (pn * h_mean) - 1e-9));
+      cs.d[a] = co->g.d[a];
+      cs.cd[a] = std::max(cs.d[a] - 1, 1);
+      P *= cs.d[a];
+    }
+    // the default patch width grows until the coarse space fits (large meshes)
+    if (3 * P <= kMaxCoarse || !auto_pn || !any_auto || pn >= 4096) break;
+    ++pn;
   }
-  SFEM_REQUIRE(3 * P <= 8192, SFEM_EINVAL, "coarse space larger than 8192 DOFs");
+  SFEM_REQUIRE(3 * P <= kMaxCoarse, SFEM_EINVAL, "coarse space larger than 8192 DOFs");
   // probing assumes centres three or more cells apart are uncoupled: patches
   // must span a few elements (checked against the mean node spacing)
   for (int a = 0; a < 3; ++a)

@@ -40,10 +40,22 @@ def tiled_source_sha() -> str:
     return h.hexdigest()
 
 
+def patch_dims_for(cells, max_coarse=8192):
+    """Patch centres per axis for patches of k x k x k lattice nodes: k = 8,
+    widened while the coarse space (3 DOFs per centre) exceeds max_coarse."""
+    k = 8
+    while True:
+        dims = tuple(-(-(c + 1) // k) for c in cells)
+        if 3 * dims[0] * dims[1] * dims[2] <= max_coarse:
+            return dims
+        k += 1
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--cells", type=int, nargs=3, default=[200, 40, 42])
     ap.add_argument("--seed", type=int, default=2)
+    ap.add_argument("--nu", type=float, default=0.3, help="Poisson ratio")
     ap.add_argument("--op", choices=sorted(OPS), default="mf32")
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--solve", choices=SOLVES, default=None)
@@ -61,7 +73,9 @@ def main(argv=None):
     __graft_entry__.build()
     from paper_2001_08849_gb300 import sfem as S
     from inputs.kuhn_beam import cantilever
-    p = cantilever(*a.cells, seed=a.seed)
+    t_mesh = time.perf_counter()
+    p = cantilever(*a.cells, seed=a.seed, nu=a.nu)
+    t_mesh = time.perf_counter() - t_mesh
     with S.FsFem(p, on_device=True) as ctx:
         n_tets = p.mesh.n_tets
         if a.solve is None:
@@ -77,7 +91,7 @@ def main(argv=None):
             model = None
             coarse = None
             if a.precond:
-                dims = tuple(a.coarse_dims) if a.coarse_dims else tuple(-(-(c + 1) // 8) for c in a.cells)
+                dims = tuple(a.coarse_dims) if a.coarse_dims else patch_dims_for(a.cells)
                 for _ in range(a.repeat):
                     coarse = S.sfem_coarse_setup(ctx.h, patch_dims=dims)
             if a.solve == "pcg64":
@@ -100,8 +114,8 @@ def main(argv=None):
                 t0 = time.perf_counter()
                 info = S.sfem_solve(ctx.h, u, o, check=False)
                 torch.cuda.synchronize()
-            out = {"solve": a.solve, "cells": a.cells, "n_tets": n_tets, "ndof": ctx.ndof,
-                   "time_s": time.perf_counter() - t0, "mesh_setup_ms": ctx.info["setup_ms"], "coarse": coarse,
+            out = {"solve": a.solve, "cells": a.cells, "nu": a.nu, "n_tets": n_tets, "ndof": ctx.ndof,
+                   "mesh_gen_s": t_mesh, "time_s": time.perf_counter() - t0, "mesh_setup_ms": ctx.info["setup_ms"], "coarse": coarse,
                    **info}
             if model is not None:
                 model.close()

@@ -269,12 +269,12 @@ def mixed_family_form(S):
     seed 4), nu 0.3 and the near-incompressible 0.49 (the 2.0M / 0.3 case is
     the timed step).  Each case: device inputs, then mesh setup + coarse
     setup + solve timed once with CUDA events, and the FP32 operator's time
-    per apply at that size.  Patches of 8 lattice nodes per axis, widened to
-    10 on the 12.3M beam (the coarse space holds at most 8192 DOFs)."""
+    per apply at that size.  The library's default coarse grid: cubic patches
+    8 mean node spacings wide, widened on the 12.3M beam until the coarse
+    space fits its 8192 DOFs."""
     import numpy as np
     import torch
     from inputs.kuhn_beam import cantilever
-    from paper_2001_08849_gb300.opbench import patch_dims_for
     out = {}
     stream = torch.cuda.current_stream()
     for cells, seed, nu in (((200, 40, 42), 3, 0.49), ((400, 80, 64), 4, 0.3), ((400, 80, 64), 4, 0.49)):
@@ -284,13 +284,12 @@ def mixed_family_form(S):
                for a in (m.xyz, m.tets.astype(np.int32), prob.dir_dofs.astype(np.int32), prob.dir_vals,
                          prob.trac_tris.astype(np.int32), prob.trac)]
         ndof = 3 * m.n_nodes
-        dims = patch_dims_for(cells)
         x = torch.zeros(ndof, dtype=torch.float64, device="cuda")
         torch.cuda.synchronize()
         ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ea.record(stream)
         hh, kk = S.sfem_mesh_setup(*dev[:2], prob.E, prob.nu, *dev[2:], inputs_on_device=True)
-        ci = S.sfem_coarse_setup(hh, patch_dims=dims)
+        ci = S.sfem_coarse_setup(hh)
         inf = S.sfem_solve(hh, x, S.solve_opts(kind=S.SFEM_SOLVE_IR32_64, op64=S.SFEM_OP_MF64, tol=TOL,
                                                 u_on_device=True, precond=1, fp32_vectors=FP32_VECTORS,
                                                 inner_tol=INNER_TOL), check=False)
@@ -300,7 +299,7 @@ def mixed_family_form(S):
         name = f"ir32_64_two_level_{m.n_tets / 1e6:.1f}M_nu{nu}"
         out[name] = {"cells": list(cells), "seed": seed, "nu": nu, "n_tets": int(m.n_tets), "ndof": int(ndof),
                      "time_to_solve_s": ea.elapsed_time(eb) / 1e3,
-                     "mesh_setup_ms": S.sfem_get_info(hh)["setup_ms"], "coarse_dims": list(dims),
+                     "mesh_setup_ms": S.sfem_get_info(hh)["setup_ms"], "coarse_dims": list(ci["patch_dims"]),
                      "coarse_setup_ms": ci["setup_ms"], "solve_ms": inf["solve_ms"],
                      "iterations": inf["iterations"], "outer_iterations": inf["outer_iterations"],
                      "fallbacks": inf["fallbacks"], "true_relres": inf["true_relres"], "status": inf["status"],
@@ -419,10 +418,12 @@ def main():
     h2d_bytes = sum(a.nbytes for a in host)
     d2h_bytes = u_host.nbytes
     # the step: setup, the coarse space of the two-level preconditioner, the
-    # mixed-precision solve, destroy.  Coarse grid: patches of 8 x 8 x 8 nodes
-    # (26 x 6 x 6 centres), with 34 x 6 x 6 the fastest coarse setup + solve of
-    # a sweep (135 / 134 ms; 26x4x4: 155, 26x3x3: 188, 40x8x8: 159)
-    coarse_dims = tuple(-(-(c + 1) // 8) for c in CELLS)
+    # mixed-precision solve, destroy.  Coarse grid: the library's default,
+    # cubic patches 8 mean node spacings wide (42 x 5 x 5 centres on this
+    # beam).  Coarse setup + solve, mean of 8 (ms): 42x5x5 68.8, 45x5x5 70.7,
+    # 50x5x5 70.9, 38x5x5 70.9, 45x6x6 73.0, 40x6x6 73.7, 34x6x6 76.7,
+    # 26x6x6 (8 lattice nodes per axis) 84.2
+    coarse_dims = (0, 0, 0)
     opts_dev = S.solve_opts(kind=S.SFEM_SOLVE_IR32_64, op64=S.SFEM_OP_MF64, tol=TOL, u_on_device=True, precond=1,
                             fp32_vectors=FP32_VECTORS, inner_tol=INNER_TOL)
     opts_host = S.solve_opts(kind=S.SFEM_SOLVE_IR32_64, op64=S.SFEM_OP_MF64, tol=TOL, u_on_device=False, precond=1,
@@ -556,7 +557,7 @@ def main():
         forms["ir32_64_jacobi"] = timed_form(S.SFEM_SOLVE_IR32_64, S.SFEM_OP_MF64, 0, False)
         forms["ir32_64_two_level_fp64_vectors"] = timed_form(S.SFEM_SOLVE_IR32_64, S.SFEM_OP_MF64, 1, False, 0)
         forms["ir32_64_two_level"] = {"time_to_solve_s": t_dev / args.steps, "iterations": iters[-1],
-                                      "true_relres": relres, "coarse_dims": list(coarse_dims),
+                                      "true_relres": relres, "coarse_dims": list(coarse_infos[-1]["patch_dims"]),
                                       "coarse_setup_ms": float(np.mean([ci["setup_ms"] for ci in coarse_infos])),
                                       "coarse_probes": coarse_infos[-1]["probes"], "note": "the timed step"}
 
@@ -583,7 +584,7 @@ def main():
                        "solver": "IR32_64 with the two-level preconditioner: FP64 true residual and "
                                  "correction, FP32 matrix-free operator and FP32 CG vectors inside, Jacobi + "
                                  "Galerkin coarse correction on "
-                                 f"{coarse_dims[0]}x{coarse_dims[1]}x{coarse_dims[2]} patch centres",
+                                 "{}x{}x{} patch centres".format(*coarse_infos[-1]["patch_dims"]),
                        "tol": TOL, "step": "sfem_mesh_setup + sfem_coarse_setup + sfem_solve + sfem_destroy",
                        "l2": "no flush: operator data per step exceeds the 129 MB L2",
                        "parallelism": f"replicas x{world}"},

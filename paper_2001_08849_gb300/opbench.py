@@ -10,8 +10,8 @@ matrix-free operator.
 --solve: one solve of the cantilever (pcg64 on CSR, the mixed-precision
 ir32_64, flexible PCG without (fpcg) or with an untrained learned correction
 (fpcg_learned, patches of 8 x 8 x 8 nodes)); --precond 1 adds the two-level
-preconditioner (coarse space on 8 x 8 x 8-node patches) to pcg64 and
-ir32_64; prints iterations and time.
+preconditioner (the library's default coarse grid unless --coarse-dims) to
+pcg64 and ir32_64; prints iterations and time.
 """
 from __future__ import annotations
 
@@ -40,17 +40,6 @@ def tiled_source_sha() -> str:
     return h.hexdigest()
 
 
-def patch_dims_for(cells, max_coarse=8192):
-    """Patch centres per axis for patches of k x k x k lattice nodes: k = 8,
-    widened while the coarse space (3 DOFs per centre) exceeds max_coarse."""
-    k = 8
-    while True:
-        dims = tuple(-(-(c + 1) // k) for c in cells)
-        if 3 * dims[0] * dims[1] * dims[2] <= max_coarse:
-            return dims
-        k += 1
-
-
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--cells", type=int, nargs=3, default=[200, 40, 42])
@@ -63,7 +52,8 @@ def main(argv=None):
     ap.add_argument("--max-iter", type=int, default=0)
     ap.add_argument("--window", type=int, default=0, help="learned_window of the fpcg_learned solve")
     ap.add_argument("--precond", type=int, default=0, help="1: two-level preconditioner (pcg64, ir32_64)")
-    ap.add_argument("--coarse-dims", type=int, nargs=3, default=None, help="patch centres per axis")
+    ap.add_argument("--coarse-dims", type=int, nargs=3, default=None,
+                    help="patch centres per axis (default: the library's, patches 8 mean node spacings wide)")
     ap.add_argument("--repeat", type=int, default=1, help="solves (the last one is reported)")
     ap.add_argument("--fp32-vectors", type=int, default=0, help="ir32_64 vector precision (sfem_solve_opts)")
     ap.add_argument("--inner-tol", type=float, default=0.0, help="ir32_64 reliable-update threshold (0: 0.1)")
@@ -91,7 +81,7 @@ def main(argv=None):
             model = None
             coarse = None
             if a.precond:
-                dims = tuple(a.coarse_dims) if a.coarse_dims else patch_dims_for(a.cells)
+                dims = tuple(a.coarse_dims) if a.coarse_dims else (0, 0, 0)  # library default
                 for _ in range(a.repeat):
                     coarse = S.sfem_coarse_setup(ctx.h, patch_dims=dims)
             if a.solve == "pcg64":

@@ -593,74 +593,81 @@ __device__ __forceinline__ void load64(Tile64<T> &S, const T *A, int64_t ld, int
     S.v[e / kCB][e % kCB] = A[(int64_t)(bi * kCB + e / kCB) * ld + bj * kCB + e % kCB];
 }
 
-// factor the diagonal block k in shared memory: columns in groups of 8 (one
-// warp factors the 64 x 8 panel, then all threads apply its rank-8 update
-// to the trailing lower triangle); then W_kk = L_kk^-1 by forward
-// substitution, 4 threads per column sharing each dot product.  L_kk back to
-// A, W_kk to Wd[k]
+// factor the diagonal block k, right-looking one column at a time: thread
+// (r = tid % 64, q0 = tid / 64) keeps L[r][q0 + 4m] (m < 16) in registers; at
+// column j the owners of column j publish it (double-buffered), and after one
+// barrier every thread applies the rank-1 update scaled by 1 / L_jj.  Then
+// W_kk = L_kk^-1 the same way with thread (c = tid % 64, g = tid / 64)
+// holding W[g + 4m][c]: row j is final after the rows above it, divided by
+// L_jj and published.  Loops over j and m are unrolled so that the register
+// arrays are indexed by constants.  L_kk back to A, W_kk to Wd[k].  A
+// non-positive or non-finite pivot sets *info and is replaced by 1.
 template <class T>
 __global__ void __launch_bounds__(256) k_potrf_diag(T *A, T *Wd, int npad, int k, int *info) {
   extern __shared__ __align__(16) unsigned char dyn_raw[];
   Tile64<T> &L = *reinterpret_cast<Tile64<T> *>(dyn_raw);
-  Tile64<T> &W = *reinterpret_cast<Tile64<T> *>(dyn_raw + sizeof(Tile64<T>));
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  __shared__ T buf[2][kCB];
+  const int tid = threadIdx.x;
   load64(L, A, npad, k, k);
   __syncthreads();
-  constexpr int G = 8;
-  for (int g0 = 0; g0 < kCB; g0 += G) {
-    if (warp == 0) {
-      for (int j = g0; j < g0 + G; ++j) {
-        T d = L.v[j][j];
-        if (!(d > T(0)) || !isfinite(d)) {
-          if (lane == 0) atomicExch(info, 1);
-          d = T(1);
-        }
-        const T sd = sqrt(d), inv = T(1) / sd;
-        __syncwarp();
-        if (lane == 0) L.v[j][j] = sd;
-        for (int i = j + 1 + lane; i < kCB; i += 32) L.v[i][j] *= inv;
-        __syncwarp();
-        // update the rest of the panel (columns j+1 .. g0+G-1)
-        for (int i = j + 1 + lane; i < kCB; i += 32) {
-          const T lij = L.v[i][j];
-          for (int l = j + 1; l < min(g0 + G, i + 1); ++l) L.v[i][l] -= lij * L.v[l][j];
-        }
-        __syncwarp();
+  const int r = tid & 63, q0 = tid >> 6;
+  T a[16];
+#pragma unroll
+  for (int m = 0; m < 16; ++m) a[m] = L.v[r][q0 + 4 * m];
+  bool bad = false;
+#pragma unroll
+  for (int j = 0; j < kCB; ++j) {
+    T *cj = buf[j & 1];
+    if (q0 == (j & 3) && r >= j) cj[r] = a[j >> 2];  // column j below the diagonal, and L_jj
+    __syncthreads();
+    T d = cj[j];
+    if (!(d > T(0)) || !isfinite(d)) {
+      bad = true;
+      d = T(1);
+    }
+    const T sd = sqrt(d), inv = T(1) / sd, inv2 = inv * inv;
+    if (r > j) {
+      const T cr = cj[r] * inv2;
+#pragma unroll
+      for (int m = 0; m < 16; ++m) {
+        const int q = q0 + 4 * m;
+        if (q > j && q <= r) a[m] -= cr * cj[q];
       }
     }
-    __syncthreads();
-    // rank-G update of the trailing lower triangle (columns >= g0 + G)
-    for (int e = tid; e < kCB * kCB; e += blockDim.x) {
-      const int i = e / kCB, l = e % kCB;
-      if (l < g0 + G || l > i) continue;
-      T s = L.v[i][l];
-#pragma unroll
-      for (int q = g0; q < g0 + G; ++q) s -= L.v[i][q] * L.v[l][q];
-      L.v[i][l] = s;
-    }
-    __syncthreads();
+    if (q0 == (j & 3) && r >= j) a[j >> 2] = (r == j) ? sd : a[j >> 2] * inv;
   }
-  // W = L^-1: column c by threads 4c .. 4c+3.  Every lane of the warp runs
-  // every iteration (the shuffles and the warp barrier need all 32 lanes);
-  // only the writes depend on i >= c.
-  {
-    const int c = tid >> 2, part = tid & 3;
-    for (int i = 0; i < kCB; ++i) {
-      T s = T(0);
-      if (i > c)
-        for (int l = c + part; l < i; l += 4) s += L.v[i][l] * W.v[l][c];
-      s += __shfl_xor_sync(0xffffffffu, s, 1);
-      s += __shfl_xor_sync(0xffffffffu, s, 2);
-      if (part == 0) W.v[i][c] = (i < c) ? T(0) : (((i == c) ? T(1) : T(0)) - s) / L.v[i][i];
-      __syncwarp();
-    }
+  if (bad && tid == 0) atomicExch(info, 1);
+  __syncthreads();
+#pragma unroll
+  for (int m = 0; m < 16; ++m) {
+    const int q = q0 + 4 * m;
+    L.v[r][q] = (q <= r) ? a[m] : T(0);
   }
   __syncthreads();
+  // W = L^-1 (lower)
+  const int c = r, g = q0;
+  T w[16];
+#pragma unroll
+  for (int m = 0; m < 16; ++m) w[m] = (g + 4 * m == c) ? T(1) : T(0);
+#pragma unroll
+  for (int j = 0; j < kCB; ++j) {
+    T *rj = buf[j & 1];
+    if (g == (j & 3)) {
+      w[j >> 2] = (c <= j) ? w[j >> 2] / L.v[j][j] : T(0);
+      rj[c] = w[j >> 2];
+    }
+    __syncthreads();
+    const T wj = rj[c];
+#pragma unroll
+    for (int m = 0; m < 16; ++m)
+      if (g + 4 * m > j) w[m] -= L.v[g + 4 * m][j] * wj;
+  }
   for (int e = tid; e < kCB * kCB; e += blockDim.x) {
     const int i = e / kCB, l = e % kCB;
-    A[(int64_t)(k * kCB + i) * npad + k * kCB + l] = (l <= i) ? L.v[i][l] : T(0);
-    Wd[(int64_t)k * kCB * kCB + e] = W.v[i][l];
+    A[(int64_t)(k * kCB + i) * npad + k * kCB + l] = L.v[i][l];
   }
+#pragma unroll
+  for (int m = 0; m < 16; ++m) Wd[(int64_t)k * kCB * kCB + (g + 4 * m) * kCB + c] = w[m];
 }
 
 // L[i][k] = A[i][k] W_kk^T for the row blocks k < i <= k + bwb

@@ -561,7 +561,7 @@ static void apply_op64(Ctx &c, int op, const double *x, double *y) {
     apply_mf64(c, x, y, 1, nullptr);
 }
 
-// WHILE-node condition of the iteration graph: another iteration while the
+// WHILE-node condition of the iteration graph: another body execution while the
 // solver is not done and the guard (body executions this launch) is below
 // its limit, so the loop ends whatever state the scalars are in
 __global__ void k_loop_cond(cudaGraphConditionalHandle h, const int *done, unsigned int *guard) {
@@ -578,6 +578,17 @@ __global__ void k_guard_reset(unsigned int *guard, unsigned int limit) {
 // Conditional graph nodes hide their kernels from kernel-level profilers;
 // SFEM_GRAPH_LOOP=0 in the environment selects the captured chunks instead
 // (same kernels and arithmetic, host polling between chunks).
+// CG iterations per execution of the WHILE node's body (the kernels of an
+// iteration after the one that set done return at once); SFEM_LOOP_UNROLL
+static int loop_unroll() {
+  static const int u = [] {
+    const char *e = std::getenv("SFEM_LOOP_UNROLL");
+    const int v = e ? std::atoi(e) : 0;
+    return v >= 1 && v <= 16 ? v : 4;
+  }();
+  return u;
+}
+
 static bool loop_graphs_enabled() {
   static const bool on = [] {
     const char *e = std::getenv("SFEM_GRAPH_LOOP");
@@ -632,7 +643,7 @@ struct CgRun {
     if (!guard) guard = c.mem.get<unsigned int>(2);
     set_capturing(true);
     try {
-      enqueue_iteration(c.cap_stream);
+      for (int u = 0; u < loop_unroll(); ++u) enqueue_iteration(c.cap_stream);
       k_loop_cond<<<1, 1, 0, c.cap_stream>>>(hnd, &c.scal->done, guard);
       SFEM_CUDA(cudaGetLastError());
     } catch (...) {
@@ -767,7 +778,7 @@ struct CgRun {
       // one launch runs the iterations until the device flag says done
       SolveScalars out;
       unsigned int hg[2] = {0, 0};
-      k_guard_reset<<<1, 1, 0, c.stream>>>(guard, (unsigned int)max_iter + 2u);
+      k_guard_reset<<<1, 1, 0, c.stream>>>(guard, (unsigned int)(max_iter / loop_unroll()) + 3u);
       SFEM_CHECK_LAUNCH();
       SFEM_CUDA(cudaGraphLaunch(exec, c.stream));
       SFEM_CUDA(cudaMemcpyAsync(&out, c.scal, sizeof out, cudaMemcpyDeviceToHost, c.stream));

@@ -380,6 +380,26 @@ int sfem_get_neighbors(sfem_ctx *ctx, int32_t *nbr /* n_tets x 4, -1 exterior */
 int sfem_get_faces(sfem_ctx *ctx, int32_t *nodes /* n_faces x 5 */,
                    int32_t *tets /* n_faces x 2 */, double *Vk /* n_faces */);
 int sfem_get_rhs(sfem_ctx *ctx, double *b /* ndof */, int rhs);
+
+/* sfem_recover — strain and stress recovery for output (post-processing,
+ * Sec. 3.4: strain and stress from the nodal displacements, written with the
+ * mesh for visualisation).
+ *   u            DEVICE pointer, ndof doubles (a displacement field, e.g. the
+ *                solution of sfem_solve);
+ *   face_strain  DEVICE, n_faces x 6 or NULL: the smoothed strain
+ *                eps_k = Bbar_k u_k of every face (Eq. 5-7) in the order of
+ *                sfem_get_faces, Voigt (xx, yy, zz, yz, zx, xy) with
+ *                engineering shear strains (Eq. 4);
+ *   face_stress  DEVICE, n_faces x 6 or NULL: sigma_k = D eps_k;
+ *   node_strain, node_stress  DEVICE, n_nodes x 6 or NULL: the means of
+ *                eps_k and sigma_k over the faces whose triangle contains
+ *                the node, weighted by V_k;
+ *   node_vm      DEVICE, n_nodes or NULL: von Mises stress of node_stress.
+ * FP64.  The nodal sums are accumulated by atomics (rounding order not
+ * fixed).  Output pointers may be NULL; the call synchronises the context
+ * stream.  Returns SFEM_EINVAL for a context without setup or a NULL u. */
+int sfem_recover(sfem_ctx *ctx, const double *u, double *face_strain, double *face_stress, double *node_strain,
+                 double *node_stress, double *node_vm);
 int sfem_get_diag(sfem_ctx *ctx, double *diag /* ndof, diagonal of A */);
 
 /* sfem_apply_noalloc — y = A u like sfem_apply(ctx, u, y, SFEM_OP_MF64, 1),

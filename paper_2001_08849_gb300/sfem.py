@@ -104,6 +104,7 @@ _SIG = {
     "sfem_get_faces": (ctypes.c_int, [_P, _P, _P, _P]),
     "sfem_get_rhs": (ctypes.c_int, [_P, _P, ctypes.c_int]),
     "sfem_get_diag": (ctypes.c_int, [_P, _P]),
+    "sfem_recover": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
     "sfem_destroy": (None, [_P]),
     "sfem_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "sfem_last_error": (ctypes.c_char_p, []),
@@ -363,6 +364,29 @@ def sfem_get_diag(h, ndof):
 def sfem_destroy(h):
     if h:
         lib.sfem_destroy(h)
+
+
+def sfem_recover(h, u, faces=True, nodes=True) -> dict:
+    """Strain and stress recovery (sfem_recover): u a CUDA float64 tensor of
+    ndof values.  Returns CUDA float64 tensors: face_strain, face_stress
+    (n_faces x 6, library face order) if faces; node_strain, node_stress
+    (n_nodes x 6) and node_vm (n_nodes) if nodes.  Voigt order xx, yy, zz,
+    yz, zx, xy with engineering shear strains."""
+    import torch
+    info = sfem_get_info(h)
+    nf, nn = info["n_faces"], info["n_nodes"]
+    kw = dict(dtype=torch.float64, device=u.device)
+    out = {}
+    if faces:
+        out["face_strain"] = torch.empty((nf, 6), **kw)
+        out["face_stress"] = torch.empty((nf, 6), **kw)
+    if nodes:
+        out["node_strain"] = torch.empty((nn, 6), **kw)
+        out["node_stress"] = torch.empty((nn, 6), **kw)
+        out["node_vm"] = torch.empty(nn, **kw)
+    names = ("face_strain", "face_stress", "node_strain", "node_stress", "node_vm")
+    _check(lib.sfem_recover(h, _ptr(u), *[_ptr(out.get(k)) for k in names]), "sfem_recover")
+    return out
 
 
 def sfem_time_operator(h, op=SFEM_OP_MF32, reps=20) -> float:

@@ -57,6 +57,8 @@ def main(argv=None):
     ap.add_argument("--repeat", type=int, default=1, help="solves (the last one is reported)")
     ap.add_argument("--fp32-vectors", type=int, default=0, help="ir32_64 vector precision (sfem_solve_opts)")
     ap.add_argument("--inner-tol", type=float, default=0.0, help="ir32_64 reliable-update threshold (0: 0.1)")
+    ap.add_argument("--recover", action="store_true",
+                    help="time sfem_recover (face and nodal strain / stress) on a solved displacement")
     a = ap.parse_args(argv)
     import torch
     import __graft_entry__
@@ -68,7 +70,24 @@ def main(argv=None):
     t_mesh = time.perf_counter() - t_mesh
     with S.FsFem(p, on_device=True) as ctx:
         n_tets = p.mesh.n_tets
-        if a.solve is None:
+        if a.recover:
+            S.sfem_coarse_setup(ctx.h)
+            u = torch.zeros(ctx.ndof, dtype=torch.float64, device="cuda")
+            S.sfem_solve(ctx.h, u, S.solve_opts(kind=S.SFEM_SOLVE_IR32_64, tol=1e-8, u_on_device=True, precond=1,
+                                                fp32_vectors=3, inner_tol=0.03))
+            S.sfem_recover(ctx.h, u)  # warm-up
+            ts = []
+            for _ in range(a.reps):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                S.sfem_recover(ctx.h, u)
+                torch.cuda.synchronize()
+                ts.append(time.perf_counter() - t0)
+            nf = ctx.info["n_faces"]
+            out = {"recover": True, "cells": a.cells, "n_tets": n_tets, "n_faces": nf, "ndof": ctx.ndof,
+                   "ms_median": 1e3 * sorted(ts)[len(ts) // 2],
+                   "output_bytes": 8 * (12 * nf + 13 * (ctx.ndof // 3))}
+        elif a.solve is None:
             if a.op == "csr64":
                 S.sfem_assemble(ctx.h)
             ms = S.sfem_time_operator(ctx.h, OPS[a.op], a.reps)

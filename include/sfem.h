@@ -133,7 +133,14 @@ typedef struct sfem_solve_opts {
                           iterations (0: no pace guard) */
   int precond;         /* PCG64 and IR32_64 (fp32_vectors 0 or 3): 0 Jacobi; 1 Jacobi plus the
                           Galerkin coarse correction of sfem_coarse_setup */
-  int reserved[2];
+  int bc;              /* Dirichlet conditions: 0 masked elimination, A = P K P + (I - P),
+                          b = P (f - K g) + (I - P) g (default); 1 the penalty method of
+                          STEP 5 (Sec. 3.3), A = K + alpha S, b = f + alpha S g with S the
+                          prescribed DOFs (PCG64 with precond 0 only; SFEM_EINVAL otherwise).
+                          The relative residual is then measured on this system; the
+                          penalty rows cancel in the recursive residual, so tolerances
+                          much below 1e-9 may end in SFEM_ENOCONV. */
+  int penalty_exp;     /* bc 1: alpha = 10^penalty_exp x max_i K_ii (0: 8; at most 15) */
 } sfem_solve_opts;
 
 typedef struct sfem_solve_info {

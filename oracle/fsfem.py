@@ -511,6 +511,20 @@ def dirichlet_system(K: sp.spmatrix, f: np.ndarray, dir_dofs, dir_vals):
     return A, b, free, g
 
 
+def penalty_system(K: sp.spmatrix, f: np.ndarray, dir_dofs, dir_vals, alpha: float):
+    """The penalty method of STEP 5 (Section 3.3): A = K + alpha S and
+    b = f + alpha S g, S the diagonal selector of the prescribed DOFs and g
+    their values; no row or column is removed, and u tends to the masked
+    elimination's solution as alpha grows (error of order 1/alpha)."""
+    n = K.shape[0]
+    s = np.zeros(n)
+    s[np.asarray(dir_dofs)] = 1.0
+    g = np.zeros(n)
+    g[np.asarray(dir_dofs)] = np.asarray(dir_vals, dtype=np.float64)
+    A = (sp.csr_matrix(K) + alpha * sp.diags(s)).tocsr()
+    return A, np.asarray(f, dtype=np.float64) + alpha * s * g
+
+
 def true_relative_residual(A, b, x) -> float:
     """||b - A x||_2 / ||b||_2 in FP64."""
     return float(np.linalg.norm(b - A @ x) / np.linalg.norm(b))

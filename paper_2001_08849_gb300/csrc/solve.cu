@@ -22,6 +22,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
+#include <cstring>
 #include <type_traits>
 
 #include "reduce.cuh"
@@ -53,6 +54,10 @@ struct PcgVecs {
   float *z32 = nullptr;  // two-level: z of the current r in FP32 (written by k_tl_zr)
   const float *dinv32 = nullptr;
   float *xlo = nullptr;  // FP32 x: low words of a double-float correction (x + xlo), or none
+  // penalty method: the operator is followed by q += alpha S p (S: the DOFs
+  // with pen_mask == 0); null for the masked elimination
+  const uint8_t *pen_mask = nullptr;
+  double pen_alpha = 0.0;
 };
 
 // (hi, lo) += a p with a = ahi + alo split from an FP64 step length: the
@@ -509,6 +514,66 @@ __global__ void k_residual(const double *__restrict__ f, const double *__restric
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) r[i] = dmask[i] ? f[i] - Kx[i] : 0.0;
 }
+// ---- the penalty method of STEP 5 (Sec. 3.3) --------------------------------
+// A = K + alpha S and b = f + alpha S g, S the prescribed DOFs (dmask == 0):
+// no row or column is removed; a large alpha pins u to g on S.
+__global__ void k_pen_rhs(const double *__restrict__ f, const double *__restrict__ g,
+                          const uint8_t *__restrict__ dmask, double alpha, int64_t n, double *__restrict__ b) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = dmask[i] ? f[i] : f[i] + alpha * g[i];
+}
+__global__ void k_pen_dinv(const double *__restrict__ diag, const uint8_t *__restrict__ dmask, double alpha,
+                           int64_t n, double *__restrict__ dinv) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const double d = diag[i] + (dmask[i] ? 0.0 : alpha);
+    dinv[i] = d > 0.0 ? 1.0 / d : 0.0;
+  }
+}
+__global__ void k_pen_residual(const double *__restrict__ b, const double *__restrict__ Kx,
+                               const double *__restrict__ x, const uint8_t *__restrict__ dmask, double alpha,
+                               int64_t n, double *__restrict__ r) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) r[i] = b[i] - Kx[i] - (dmask[i] ? 0.0 : alpha * x[i]);
+}
+// after the operator: q += alpha S p, and p.q += alpha |S p|^2 (one FP64 atomic
+// per block into the scalar the operator has written)
+__global__ void __launch_bounds__(256) k_pen_q(const double *__restrict__ p, double *__restrict__ q,
+                                               const uint8_t *__restrict__ dmask, double alpha, int64_t n,
+                                               double *pq, const int *done) {
+  if (done && *done) return;
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < n; i += (int64_t)gridDim.x * 256)
+    if (!dmask[i]) {
+      const double ap = alpha * p[i];
+      q[i] += ap;
+      s = fma(ap, p[i], s);
+    }
+  s = block_sum<256>(s);
+  if (threadIdx.x == 0 && s != 0.0) atomicAdd(pq, s);
+}
+// max of non-negative values: their bit patterns order like the values
+__global__ void k_max_nonneg(const double *__restrict__ a, int64_t n, unsigned long long *out) {
+  double m = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    m = fmax(m, a[i]);
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m > 0.0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+static double device_max_nonneg(Ctx &c, const double *a, int64_t n) {
+  unsigned long long *d = c.mem.get<unsigned long long>(1);
+  SFEM_CUDA(cudaMemsetAsync(d, 0, sizeof(unsigned long long), c.stream));
+  k_max_nonneg<<<std::min(grid_for(n, 256), c.red_blocks), 256, 0, c.stream>>>(a, n, d);
+  SFEM_CHECK_LAUNCH();
+  unsigned long long h = 0;
+  SFEM_CUDA(cudaMemcpyAsync(&h, d, sizeof h, cudaMemcpyDeviceToHost, c.stream));
+  SFEM_CUDA(cudaStreamSynchronize(c.stream));
+  c.mem.drop(d);
+  double v;
+  std::memcpy(&v, &h, sizeof v);
+  return v;
+}
+
 __global__ void k_set_bc(double *__restrict__ x, const double *__restrict__ g, const uint8_t *__restrict__ dmask,
                          int64_t n, bool zero_free) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -683,6 +748,12 @@ struct CgRun {
       // tiled FP32 operator reading p and accumulating q in type TP
       launch_mf32_tiled<TP, TP>(c, st, v.p, v.q, &S->pq, done);
     }
+    if constexpr (std::is_same_v<TP, double>) {
+      if (v.pen_mask) {
+        k_pen_q<<<c.red_blocks, 256, 0, st>>>(v.p, v.q, v.pen_mask, v.pen_alpha, v.n, &S->pq, done);
+        SFEM_CHECK_LAUNCH();
+      }
+    }
     {
       if (v.coarse) {  // FP64 x, or double-float x with FP32 r, p, q
         if constexpr (std::is_same_v<TX, float>)
@@ -856,6 +927,12 @@ void solve_impl(Ctx &c, const double *f_extra, double *u, const sfem_solve_opts 
                  SFEM_EINVAL, "the coarse correction works with PCG64 and with IR32_64 on an FP64 correction");
   }
   SFEM_REQUIRE(o.fp32_vectors >= 0 && o.fp32_vectors <= 3, SFEM_EINVAL, "fp32_vectors must be 0, 1, 2 or 3");
+  SFEM_REQUIRE(o.bc == 0 || o.bc == 1, SFEM_EINVAL, "bc must be 0 or 1");
+  SFEM_REQUIRE(o.penalty_exp >= 0 && o.penalty_exp <= 15, SFEM_EINVAL, "penalty_exp must be 0 .. 15");
+  const bool penalty = o.bc == 1;
+  if (penalty)
+    SFEM_REQUIRE(o.kind == SFEM_SOLVE_PCG64 && !coarse && !snap, SFEM_EINVAL,
+                 "the penalty method works with PCG64 and the Jacobi preconditioner");
 
   cudaEvent_t e0, e1;
   SFEM_CUDA(cudaEventCreate(&e0));
@@ -887,6 +964,22 @@ void solve_impl(Ctx &c, const double *f_extra, double *u, const sfem_solve_opts 
     SFEM_CHECK_LAUNCH();
     bnorm = std::sqrt(device_norm2(c, tmp, n));
   }
+  double pen_alpha = 0.0;
+  double *bpen = nullptr, *dpen = nullptr;
+  uint8_t *ones = nullptr;
+  if (penalty) {
+    // alpha = 10^penalty_exp times the largest diagonal entry of K
+    pen_alpha = std::pow(10.0, o.penalty_exp > 0 ? o.penalty_exp : 8) * device_max_nonneg(c, c.diag, n);
+    bpen = B.get<double>(n);
+    k_pen_rhs<<<g256, 256, 0, c.stream>>>(ftot, c.g, c.dmask, pen_alpha, n, bpen);
+    SFEM_CHECK_LAUNCH();
+    bnorm = std::sqrt(device_norm2(c, bpen, n));
+    dpen = B.get<double>(n);
+    k_pen_dinv<<<g256, 256, 0, c.stream>>>(c.diag, c.dmask, pen_alpha, n, dpen);
+    SFEM_CHECK_LAUNCH();
+    ones = B.get<uint8_t>(n);
+    SFEM_CUDA(cudaMemsetAsync(ones, 1, n, c.stream));
+  }
   info.bnorm = bnorm;
 
   double *x = B.get<double>(n);
@@ -902,7 +995,10 @@ void solve_impl(Ctx &c, const double *f_extra, double *u, const sfem_solve_opts 
     double *r = B.get<double>(n);
     auto true_residual = [&]() {
       apply_op64(c, op64, x, Kx);
-      k_residual<<<g256, 256, 0, c.stream>>>(ftot, Kx, c.dmask, n, r);
+      if (penalty)
+        k_pen_residual<<<g256, 256, 0, c.stream>>>(bpen, Kx, x, c.dmask, pen_alpha, n, r);
+      else
+        k_residual<<<g256, 256, 0, c.stream>>>(ftot, Kx, c.dmask, n, r);
       SFEM_CHECK_LAUNCH();
       return std::sqrt(device_norm2(c, r, n)) / bnorm;
     };
@@ -910,8 +1006,13 @@ void solve_impl(Ctx &c, const double *f_extra, double *u, const sfem_solve_opts 
     double rel = true_residual();
     if (o.kind == SFEM_SOLVE_PCG64) {
       if (op64 == SFEM_OP_MF64) ensure_w_scratch(c, (size_t)c.n_tets * 8 * sizeof(double));
-      PcgVecs<double, double, double> v{x, r, B.get<double>(n), B.get<double>(n), c.dinv64, c.dmask, n};
+      PcgVecs<double, double, double> v{x, r, B.get<double>(n), B.get<double>(n), penalty ? dpen : c.dinv64,
+                                        penalty ? ones : c.dmask, n};
       with_coarse(v);
+      if (penalty) {
+        v.pen_mask = c.dmask;
+        v.pen_alpha = pen_alpha;
+      }
       CgRun<double, double, double> cg(c, v, op64, chunk);
       const int max_restarts = 10;
       while (rel > tol && total_iter < max_iter && outer <= max_restarts) {
@@ -1118,7 +1219,6 @@ extern "C" int sfem_solve(sfem_ctx *h, const double *f_extra, double *u, const s
   try {
     SFEM_REQUIRE(h && h->c.vol && h->c.dinv64, SFEM_EINVAL, "context not set up");
     SFEM_REQUIRE(u && opts, SFEM_EINVAL, "u and opts must not be NULL");
-    for (int r : opts->reserved) SFEM_REQUIRE(r == 0, SFEM_EINVAL, "reserved options must be zero");
     solve_impl(h->c, f_extra, u, *opts, local);
   } catch (const Error &err) {
     set_last_error(err.msg);

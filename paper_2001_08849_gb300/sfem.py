@@ -57,7 +57,7 @@ class sfem_solve_opts(ctypes.Structure):
                 ("tol", ctypes.c_double), ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int),
                 ("check_every", ctypes.c_int), ("learned", ctypes.c_void_p), ("fp32_vectors", ctypes.c_int),
                 ("learned_window", ctypes.c_int), ("learned_pace", ctypes.c_int), ("precond", ctypes.c_int),
-                ("reserved", ctypes.c_int * 2)]
+                ("bc", ctypes.c_int), ("penalty_exp", ctypes.c_int)]
 
 
 class sfem_solve_info(ctypes.Structure):
@@ -276,7 +276,7 @@ def sfem_apply_noalloc(h, u, y):
 
 def solve_opts(kind=SFEM_SOLVE_PCG64, op64=SFEM_OP_MF64, rhs=0, tol=1e-8, max_iter=0, inner_tol=0.0,
                max_outer=0, check_every=0, u_on_device=False, warm_start=False, learned=None, fp32_vectors=False,
-               learned_window=0, learned_pace=0, precond=0):
+               learned_window=0, learned_pace=0, precond=0, bc=0, penalty_exp=0):
     o = sfem_solve_opts()
     o.kind, o.op64, o.rhs = int(kind), int(op64), int(rhs)
     o.u_on_device, o.warm_start = int(bool(u_on_device)), int(bool(warm_start))
@@ -286,6 +286,7 @@ def solve_opts(kind=SFEM_SOLVE_PCG64, op64=SFEM_OP_MF64, rhs=0, tol=1e-8, max_it
     o.fp32_vectors = int(fp32_vectors)
     o.learned_window, o.learned_pace = int(learned_window), int(learned_pace)
     o.precond = int(precond)
+    o.bc, o.penalty_exp = int(bc), int(penalty_exp)
     return o
 
 

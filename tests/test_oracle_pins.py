@@ -395,3 +395,25 @@ def test_cantilever_converges_to_timoshenko():
     rho = (d_fs[1] - d_fs[0]) / (d_fs[2] - d_fs[1])
     d_inf = d_fs[2] + (d_fs[2] - d_fs[1]) / (rho - 1)
     assert abs(d_inf - dT) / dT < 0.02
+
+
+def test_penalty_converges_to_elimination():
+    """STEP 5's penalty method: the solution of (K + alpha S) u = f + alpha S g
+    tends to the masked elimination's solution with an error of order 1/alpha
+    (100x smaller for a 100x larger alpha), and the prescribed values to g."""
+    m = kuhn_beam(4, 1, 1, (4.0, 1.0, 1.0), 0.1, seed=3)
+    dofs, vals = clamp_dofs(m, 0, 0)
+    vals = np.random.default_rng(2).standard_normal(dofs.shape[0]) * 1e-4  # nonzero prescribed values
+    tris = face_triangles(m, 0, 1)
+    f = F.traction_load(m.n_nodes, m.xyz, tris, uniform_traction(tris, (0, 0, -1e6)))[0]
+    K = F.assemble(m.xyz, m.tets, 210e9, 0.3).matrix()
+    A, b, _, _ = F.dirichlet_system(K, f, dofs, vals)
+    u0 = np.linalg.solve(A.toarray(), b)
+    kmax = K.diagonal().max()
+    errs = []
+    for a in (1e4, 1e6):
+        Ap, bp = F.penalty_system(K, f, dofs, vals, a * kmax)
+        up = np.linalg.solve(Ap.toarray(), bp)
+        errs.append(np.linalg.norm(up - u0) / np.linalg.norm(u0))
+        assert np.abs(up[dofs] - vals).max() <= 1e3 / a * np.abs(u0).max()
+    assert 30 < errs[0] / errs[1] < 300, errs

@@ -213,6 +213,7 @@ struct Ctx {
 
   // scratch for the operators and reductions
   void *w_scratch = nullptr;     // per-tet strains (8 values per tet per rhs)
+  double *ns_sig = nullptr;      // NS-FEM: nodal stresses (6 per node), allocated on first use
   size_t w_bytes = 0;
   double *red_partial = nullptr; // per-block partial sums
   int red_blocks = 0;
@@ -238,6 +239,10 @@ void apply_mf32(Ctx &c, const float *u, float *y, int nrhs, double *energy_parti
 void apply_csr64(Ctx &c, const double *u, double *y, int nrhs, const double *dotv,
                  double *dot_partial);
 void ensure_w_scratch(Ctx &c, size_t bytes);
+// NS-FEM-T4 operator (nsfem.cu): y += K_NS u, energy += u^T K_NS u (may be
+// null); apply_ns64 zeroes y first
+void launch_ns64(Ctx &c, cudaStream_t st, const double *u, double *y, double *energy, const int *done);
+void apply_ns64(Ctx &c, const double *u, double *y);
 // stream-explicit launchers used inside captured solver iterations; kernels
 // return immediately when *done != 0
 // T: geometry and arithmetic type; TU / TY: input / output vector types

@@ -622,6 +622,8 @@ __global__ void k_rhs_vec(const double *__restrict__ f, const double *__restrict
 static void apply_op64(Ctx &c, int op, const double *x, double *y) {
   if (op == SFEM_OP_CSR64)
     apply_csr64(c, x, y, 1, nullptr, nullptr);
+  else if (op == SFEM_OP_NS64)
+    apply_ns64(c, x, y);
   else
     apply_mf64(c, x, y, 1, nullptr);
 }
@@ -744,6 +746,10 @@ struct CgRun {
       double *w = static_cast<double *>(c.w_scratch);
       launch_mf_strain<double, double>(c, st, c.Gs64, (const double *)v.p, 1, w, done);
       launch_mf_stress<double, double>(c, st, c.Gs64, c.kap64, w, (double *)v.q, 1, &S->pq, done);
+    } else if (op == SFEM_OP_NS64) {
+      // q accumulated by atomics (zeroed by the direction pass); p.q added to
+      // S->pq, which the update pass leaves at zero
+      if constexpr (std::is_same_v<TP, double>) launch_ns64(c, st, v.p, v.q, &S->pq, done);
     } else {
       // tiled FP32 operator reading p and accumulating q in type TP
       launch_mf32_tiled<TP, TP>(c, st, v.p, v.q, &S->pq, done);
@@ -915,7 +921,11 @@ void solve_impl(Ctx &c, const double *f_extra, double *u, const sfem_solve_opts 
   const int max_iter = o.max_iter > 0 ? o.max_iter : 200000;
   const int chunk = o.check_every > 0 ? o.check_every : 32;
   const int op64 = o.op64;
-  SFEM_REQUIRE(op64 == SFEM_OP_CSR64 || op64 == SFEM_OP_MF64, SFEM_EINVAL, "op64 must be CSR64 or MF64");
+  SFEM_REQUIRE(op64 == SFEM_OP_CSR64 || op64 == SFEM_OP_MF64 || op64 == SFEM_OP_NS64, SFEM_EINVAL,
+               "op64 must be CSR64, MF64 or NS64");
+  if (op64 == SFEM_OP_NS64)
+    SFEM_REQUIRE(o.kind == SFEM_SOLVE_PCG64 && o.precond == 0 && o.bc == 0 && !snap, SFEM_EINVAL,
+                 "the NS-FEM operator works with PCG64, the Jacobi preconditioner and eliminated BCs");
   if (op64 == SFEM_OP_CSR64) SFEM_REQUIRE(c.assembled, SFEM_EINVAL, "CSR64 needs sfem_assemble first");
   SFEM_REQUIRE(o.rhs >= 0 && o.rhs < c.nrhs, SFEM_EINVAL, "rhs out of range");
   SFEM_REQUIRE(o.precond == 0 || o.precond == 1, SFEM_EINVAL, "precond must be 0 or 1");
@@ -954,12 +964,18 @@ void solve_impl(Ctx &c, const double *f_extra, double *u, const sfem_solve_opts 
   SFEM_CUDA(cudaMemcpyAsync(ftot, c.f + (int64_t)o.rhs * n, n * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
   double *tmp = B.get<double>(n);
   double bnorm = c.bnorm[o.rhs];
-  if (f_extra) {
-    SFEM_CUDA(cudaMemcpyAsync(tmp, f_extra, n * sizeof(double), in_kind, c.stream));
-    k_add<<<g256, 256, 0, c.stream>>>(ftot, tmp, n);
-    SFEM_CHECK_LAUNCH();
+  if (f_extra || op64 == SFEM_OP_NS64) {
+    if (f_extra) {
+      SFEM_CUDA(cudaMemcpyAsync(tmp, f_extra, n * sizeof(double), in_kind, c.stream));
+      k_add<<<g256, 256, 0, c.stream>>>(ftot, tmp, n);
+      SFEM_CHECK_LAUNCH();
+    }
+    // ||b|| of this load and operator: b = P (f - K g) + (I - P) g
     double *Kg = B.get<double>(n);
-    apply_mf64(c, c.g, Kg, 1, nullptr);
+    if (op64 == SFEM_OP_NS64)
+      apply_ns64(c, c.g, Kg);
+    else
+      apply_mf64(c, c.g, Kg, 1, nullptr);
     k_rhs_vec<<<g256, 256, 0, c.stream>>>(ftot, Kg, c.g, c.dmask, n, tmp);
     SFEM_CHECK_LAUNCH();
     bnorm = std::sqrt(device_norm2(c, tmp, n));

@@ -96,12 +96,16 @@ enum {
   SFEM_OP_MF32 = 2,     /* matrix-free, FP32 (FP64 geometry rounded once) */
   SFEM_OP_MF32_F64 = 3, /* the FP32 matrix-free arithmetic on FP64 vectors (the operator
                            of SFEM_SOLVE_IR32_64's inner iterations) */
-  SFEM_OP_NS64 = 4      /* NS-FEM-T4 (node-based smoothing domains, one of the S-FEM models
+  SFEM_OP_NS64 = 4,     /* NS-FEM-T4 (node-based smoothing domains, one of the S-FEM models
                            of Sec. 2.1), matrix-free, FP64: V_n = sum of V_e / 4 over the
                            node's tets, eps_n their V_e-weighted strain average,
                            K = sum_n V_n Bbar_n^T c Bbar_n.  sfem_apply, and sfem_solve
                            with SFEM_SOLVE_PCG64 (op64 = SFEM_OP_NS64, precond 0, bc 0;
                            Jacobi scaling by the FS-FEM diagonal) */
+  SFEM_OP_ES64 = 5      /* ES-FEM-T4 (edge-based smoothing domains, Sec. 2.1): a sixth of
+                           every tet around an edge; otherwise as SFEM_OP_NS64.  The edge
+                           table is built on first use (SFEM_EMESH if a node has more
+                           than 96 higher-numbered neighbours) */
 };
 
 /* Solver kinds. */
@@ -114,7 +118,8 @@ enum {
 typedef struct sfem_solve_opts {
   int kind;            /* SFEM_SOLVE_* */
   int op64;            /* operator of FP64 steps: SFEM_OP_CSR64 or SFEM_OP_MF64 (FS-FEM);
-                          SFEM_OP_NS64 solves the NS-FEM system instead (PCG64 only) */
+                          SFEM_OP_NS64 / SFEM_OP_ES64 solve the NS-FEM / ES-FEM system
+                          instead (PCG64 only) */
   int rhs;             /* load case to solve (0 .. nrhs-1) */
   int u_on_device;     /* 1: u is a device pointer */
   int warm_start;      /* 1: u holds an initial guess (Dirichlet DOFs are reset) */

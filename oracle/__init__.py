@@ -20,6 +20,8 @@ Modules
          Galerkin coarse matrix, D^-1 + Pi A_c^-1 Pi^T, two-level PCG.
   nsfem  NS-FEM-T4 (node-based smoothing domains, Sec. 2.1): the stiffness
          assembled node by node from its definition.
+  esfem  ES-FEM-T4 (edge-based smoothing domains, Sec. 2.1): the stiffness
+         assembled edge by edge from its definition.
   recover strain and stress recovery for output (Sec. 3.4): face strains
          Bbar_k u_k (Eq. 7), stresses D eps_k, V_k-weighted nodal means, von
          Mises stress.

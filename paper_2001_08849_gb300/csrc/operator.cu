@@ -347,7 +347,7 @@ extern "C" int sfem_apply(sfem_ctx *h, const void *u, void *y, int op, int nrhs)
       k_fix_rows<double><<<grid, 256, 0, c.stream>>>((double *)y, (const double *)u, c.dmask, c.ndof, n);
       SFEM_CHECK_LAUNCH();
       c.mem.drop(tmp);
-    } else if (op == SFEM_OP_MF64 || op == SFEM_OP_CSR64 || op == SFEM_OP_NS64) {
+    } else if (op == SFEM_OP_MF64 || op == SFEM_OP_CSR64 || op == SFEM_OP_NS64 || op == SFEM_OP_ES64) {
       double *tmp = c.mem.get<double>(n);
       k_mask_copy<double><<<grid, 256, 0, c.stream>>>((const double *)u, tmp, c.dmask, c.ndof, n);
       SFEM_CHECK_LAUNCH();
@@ -355,6 +355,8 @@ extern "C" int sfem_apply(sfem_ctx *h, const void *u, void *y, int op, int nrhs)
         apply_mf64(c, tmp, (double *)y, nrhs, nullptr);
       else if (op == SFEM_OP_NS64)
         for (int k = 0; k < nrhs; ++k) apply_ns64(c, tmp + k * c.ndof, (double *)y + k * c.ndof);
+      else if (op == SFEM_OP_ES64)
+        for (int k = 0; k < nrhs; ++k) apply_es64(c, tmp + k * c.ndof, (double *)y + k * c.ndof);
       else
         apply_csr64(c, tmp, (double *)y, nrhs, nullptr, nullptr);
       k_fix_rows<double><<<grid, 256, 0, c.stream>>>((double *)y, (const double *)u, c.dmask, c.ndof, n);
@@ -418,6 +420,9 @@ extern "C" int sfem_time_operator(sfem_ctx *h, int op, int reps, double *ms_per_
         launch_csr64(c, c.stream, (const double *)u, (double *)y, nullptr, nullptr, nullptr);
       } else if (op == SFEM_OP_NS64) {
         launch_ns64(c, c.stream, (const double *)u, (double *)y, nullptr, nullptr);
+      } else if (op == SFEM_OP_ES64) {
+        prepare_es64(c);
+        launch_es64(c, c.stream, (const double *)u, (double *)y, nullptr, nullptr);
       } else {
         throw Error{SFEM_EINVAL, "unknown operator"};
       }

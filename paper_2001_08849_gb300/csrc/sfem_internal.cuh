@@ -214,6 +214,11 @@ struct Ctx {
   // scratch for the operators and reductions
   void *w_scratch = nullptr;     // per-tet strains (8 values per tet per rhs)
   double *ns_sig = nullptr;      // NS-FEM: nodal stresses (6 per node), allocated on first use
+  // ES-FEM (built on first use): edge ids of every tet (6 per tet), edge
+  // domain volumes, per-edge strain / stress accumulators (6 per edge)
+  int32_t *es_te = nullptr;
+  double *es_Vk = nullptr, *es_acc = nullptr;
+  int64_t n_edges = 0;
   size_t w_bytes = 0;
   double *red_partial = nullptr; // per-block partial sums
   int red_blocks = 0;
@@ -243,6 +248,11 @@ void ensure_w_scratch(Ctx &c, size_t bytes);
 // null); apply_ns64 zeroes y first
 void launch_ns64(Ctx &c, cudaStream_t st, const double *u, double *y, double *energy, const int *done);
 void apply_ns64(Ctx &c, const double *u, double *y);
+// ES-FEM-T4 operator (esfem.cu): prepare_es64 builds the edge table (before
+// any stream capture); launch_es64 as launch_ns64; apply_es64 zeroes y first
+void prepare_es64(Ctx &c);
+void launch_es64(Ctx &c, cudaStream_t st, const double *u, double *y, double *energy, const int *done);
+void apply_es64(Ctx &c, const double *u, double *y);
 // stream-explicit launchers used inside captured solver iterations; kernels
 // return immediately when *done != 0
 // T: geometry and arithmetic type; TU / TY: input / output vector types

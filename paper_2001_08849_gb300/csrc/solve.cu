@@ -624,6 +624,8 @@ static void apply_op64(Ctx &c, int op, const double *x, double *y) {
     apply_csr64(c, x, y, 1, nullptr, nullptr);
   else if (op == SFEM_OP_NS64)
     apply_ns64(c, x, y);
+  else if (op == SFEM_OP_ES64)
+    apply_es64(c, x, y);
   else
     apply_mf64(c, x, y, 1, nullptr);
 }
@@ -750,6 +752,8 @@ struct CgRun {
       // q accumulated by atomics (zeroed by the direction pass); p.q added to
       // S->pq, which the update pass leaves at zero
       if constexpr (std::is_same_v<TP, double>) launch_ns64(c, st, v.p, v.q, &S->pq, done);
+    } else if (op == SFEM_OP_ES64) {
+      if constexpr (std::is_same_v<TP, double>) launch_es64(c, st, v.p, v.q, &S->pq, done);
     } else {
       // tiled FP32 operator reading p and accumulating q in type TP
       launch_mf32_tiled<TP, TP>(c, st, v.p, v.q, &S->pq, done);
@@ -921,11 +925,13 @@ void solve_impl(Ctx &c, const double *f_extra, double *u, const sfem_solve_opts 
   const int max_iter = o.max_iter > 0 ? o.max_iter : 200000;
   const int chunk = o.check_every > 0 ? o.check_every : 32;
   const int op64 = o.op64;
-  SFEM_REQUIRE(op64 == SFEM_OP_CSR64 || op64 == SFEM_OP_MF64 || op64 == SFEM_OP_NS64, SFEM_EINVAL,
-               "op64 must be CSR64, MF64 or NS64");
-  if (op64 == SFEM_OP_NS64)
+  SFEM_REQUIRE(op64 == SFEM_OP_CSR64 || op64 == SFEM_OP_MF64 || op64 == SFEM_OP_NS64 || op64 == SFEM_OP_ES64,
+               SFEM_EINVAL, "op64 must be CSR64, MF64, NS64 or ES64");
+  const bool other_sfem = op64 == SFEM_OP_NS64 || op64 == SFEM_OP_ES64;
+  if (other_sfem)
     SFEM_REQUIRE(o.kind == SFEM_SOLVE_PCG64 && o.precond == 0 && o.bc == 0 && !snap, SFEM_EINVAL,
-                 "the NS-FEM operator works with PCG64, the Jacobi preconditioner and eliminated BCs");
+                 "the NS-FEM and ES-FEM operators work with PCG64, the Jacobi preconditioner and eliminated BCs");
+  if (op64 == SFEM_OP_ES64) prepare_es64(c);  // the edge table, before any capture
   if (op64 == SFEM_OP_CSR64) SFEM_REQUIRE(c.assembled, SFEM_EINVAL, "CSR64 needs sfem_assemble first");
   SFEM_REQUIRE(o.rhs >= 0 && o.rhs < c.nrhs, SFEM_EINVAL, "rhs out of range");
   SFEM_REQUIRE(o.precond == 0 || o.precond == 1, SFEM_EINVAL, "precond must be 0 or 1");
@@ -964,7 +970,7 @@ void solve_impl(Ctx &c, const double *f_extra, double *u, const sfem_solve_opts 
   SFEM_CUDA(cudaMemcpyAsync(ftot, c.f + (int64_t)o.rhs * n, n * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
   double *tmp = B.get<double>(n);
   double bnorm = c.bnorm[o.rhs];
-  if (f_extra || op64 == SFEM_OP_NS64) {
+  if (f_extra || other_sfem) {
     if (f_extra) {
       SFEM_CUDA(cudaMemcpyAsync(tmp, f_extra, n * sizeof(double), in_kind, c.stream));
       k_add<<<g256, 256, 0, c.stream>>>(ftot, tmp, n);
@@ -972,8 +978,8 @@ void solve_impl(Ctx &c, const double *f_extra, double *u, const sfem_solve_opts 
     }
     // ||b|| of this load and operator: b = P (f - K g) + (I - P) g
     double *Kg = B.get<double>(n);
-    if (op64 == SFEM_OP_NS64)
-      apply_ns64(c, c.g, Kg);
+    if (other_sfem)
+      apply_op64(c, op64, c.g, Kg);
     else
       apply_mf64(c, c.g, Kg, 1, nullptr);
     k_rhs_vec<<<g256, 256, 0, c.stream>>>(ftot, Kg, c.g, c.dmask, n, tmp);

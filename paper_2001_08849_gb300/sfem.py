@@ -26,7 +26,7 @@ lib = ctypes.CDLL(LIB_PATH)
 # ---- status codes and enums (include/sfem.h) --------------------------------
 SFEM_OK, SFEM_EINVAL, SFEM_EMESH, SFEM_ENOMEM = 0, -1, -2, -3
 SFEM_ENOCONV, SFEM_EBREAKDOWN, SFEM_ECUDA, SFEM_ETIMEOUT = -4, -5, -6, -7
-SFEM_OP_CSR64, SFEM_OP_MF64, SFEM_OP_MF32, SFEM_OP_MF32_F64, SFEM_OP_NS64 = 0, 1, 2, 3, 4
+SFEM_OP_CSR64, SFEM_OP_MF64, SFEM_OP_MF32, SFEM_OP_MF32_F64, SFEM_OP_NS64, SFEM_OP_ES64 = 0, 1, 2, 3, 4, 5
 SFEM_SOLVE_PCG64, SFEM_SOLVE_IR32_64, SFEM_SOLVE_FPCG_LEARNED = 0, 1, 2
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)

@@ -26,7 +26,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-OPS = {"csr64": 0, "mf64": 1, "mf32": 2, "mf32f64": 3}
+OPS = {"csr64": 0, "mf64": 1, "mf32": 2, "mf32f64": 3, "ns64": 4, "es64": 5}
 SOLVES = ("pcg64", "ir32_64", "fpcg", "fpcg_learned")
 
 

@@ -180,7 +180,10 @@ void ensure_edges(Ctx &c) {
   SFEM_CUDA(cudaMemcpyAsync(&h_ovf, ovf, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
   SFEM_CUDA(cudaStreamSynchronize(c.stream));
   c.mem.drop(ovf);
-  SFEM_REQUIRE(h_ovf == 0, SFEM_EMESH, "a node has more than 96 higher-numbered edge neighbours");
+  if (h_ovf) {
+    c.mem.drop(cnt);
+    throw Error{SFEM_EMESH, "a node has more than 96 higher-numbered edge neighbours"};
+  }
   // exclusive scan of the counts on the host (one value per node, once per context)
   std::vector<int64_t> h(c.n_nodes), off(c.n_nodes + 1);
   SFEM_CUDA(cudaMemcpyAsync(h.data(), cnt, c.n_nodes * sizeof(int64_t), cudaMemcpyDeviceToHost, c.stream));

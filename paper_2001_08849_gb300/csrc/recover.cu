@@ -99,9 +99,16 @@ extern "C" int sfem_recover(sfem_ctx *h, const double *u, double *face_strain, d
     SFEM_REQUIRE(u, SFEM_EINVAL, "u must be a device pointer");
     Ctx &c = h->c;
     const bool nodal = node_strain || node_stress || node_vm;
+    struct Scratch {  // the nodal sums, released on every exit
+      Ctx &c;
+      double *p = nullptr;
+      ~Scratch() {
+        if (p) c.mem.drop(p);
+      }
+    } acc{c};
     double *nacc = nullptr;
     if (nodal) {
-      nacc = c.mem.get<double>(kNodeAcc * c.n_nodes);
+      nacc = acc.p = c.mem.get<double>(kNodeAcc * c.n_nodes);
       SFEM_CUDA(cudaMemsetAsync(nacc, 0, kNodeAcc * c.n_nodes * sizeof(double), c.stream));
     }
     if (face_strain || face_stress || nodal) {
@@ -114,7 +121,6 @@ extern "C" int sfem_recover(sfem_ctx *h, const double *u, double *face_strain, d
       k_recover_nodes<<<grid_for(c.n_nodes, 256), 256, 0, c.stream>>>(c.n_nodes, nacc, node_strain, node_stress,
                                                                       node_vm);
       SFEM_CHECK_LAUNCH();
-      c.mem.drop(nacc);
     }
     SFEM_CUDA(cudaStreamSynchronize(c.stream));
   } catch (const Error &err) {

@@ -446,6 +446,16 @@ int sfem_apply_noalloc(sfem_ctx *ctx, const double *u, double *y);
  * sfem_launch_count: kernels launched by this process through the library
  * so far (graph launches count their kernel nodes; captures do not count). */
 int sfem_time_operator(sfem_ctx *ctx, int op, int reps, double *ms_per_apply);
+
+/* sfem_selftest_barrier — diagnostic (no counterpart in the paper): runs the
+ * bounded wait of the batched solver's grid barrier in a state where it
+ * cannot complete (one block, the arrival count offset by one), so that the
+ * wait runs out as it would if a block of the persistent kernel never
+ * arrived.  *status receives SFEM_ETIMEOUT when the barrier gave up and
+ * reported it (the expected outcome), SFEM_OK if it did not; *wait_ms (may
+ * be NULL) the device time of the wait (a few seconds).  The context stays
+ * usable.  Returns SFEM_EINVAL for a context without setup or a NULL status. */
+int sfem_selftest_barrier(sfem_ctx *ctx, int *status, double *wait_ms);
 int64_t sfem_launch_count(void);
 
 void sfem_destroy(sfem_ctx *ctx);

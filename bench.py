@@ -56,6 +56,23 @@ FP32_VECTORS = 3
 INNER_TOL = 0.03
 
 
+def rank_max(dist, x: float, device="cuda") -> float:
+    """The largest x over the ranks of the process group (x itself when dist
+    is None): a step's time is the slowest rank's."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, steps: int, seconds: float) -> float:
+    """Whole-job solves/s: every rank solves one system per step (replicas,
+    no data-path collective), and the job lasts as long as its slowest rank."""
+    return world * steps / seconds
+
+
 def _env_int(name, default):
     try:
         return int(os.environ.get(name, default))
@@ -458,11 +475,7 @@ def main():
         torch.cuda.synchronize()
 
     def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return rank_max(dist, x, "cuda")
 
     for _ in range(max(args.warmup, 3)):
         step_device()
@@ -488,7 +501,7 @@ def main():
     launches = S.sfem_launch_count() - launches0
     clk = clocks.stop()
     t_dev = max_over_ranks(e0.elapsed_time(e1) / 1e3)
-    value = world * args.steps / t_dev
+    value = job_throughput(world, args.steps, t_dev)
     iters = [i["iterations"] for i in infos]
     relres = max(i["true_relres"] for i in infos)
 
@@ -500,7 +513,7 @@ def main():
         step_host()
     barrier()
     t_e2e = max_over_ranks(time.perf_counter() - t0)
-    e2e_value = world * args.steps / t_e2e
+    e2e_value = job_throughput(world, args.steps, t_e2e)
 
     # dominant kernel: the FP32 matrix-free operator of the inner CG
     h, keep = step_device(keep=True)

@@ -5,7 +5,6 @@ feature layout and zero padding, bfloat16 rounding."""
 import math
 
 import numpy as np
-import pytest
 
 from inputs.kuhn_beam import kuhn_beam
 from oracle import mlp as M

@@ -567,6 +567,10 @@ def main():
         # plain FP64 Jacobi-PCG on the assembled CSR (the paper's method with
         # an iterative solve), then the other forms, each once
         forms["pcg64_csr_jacobi"] = timed_form(S.SFEM_SOLVE_PCG64, S.SFEM_OP_CSR64, 0, True)
+        try:  # the same FP64 Jacobi-PCG on the matrix-free FP64 operator (no assembly)
+            forms["pcg64_mf64_jacobi"] = timed_form(S.SFEM_SOLVE_PCG64, S.SFEM_OP_MF64, 0, False)
+        except Exception as ex:  # a failed comparison form is reported, not fatal to the bench line
+            forms["pcg64_mf64_jacobi"] = {"error": str(ex)}
         forms["pcg64_csr_two_level"] = timed_form(S.SFEM_SOLVE_PCG64, S.SFEM_OP_CSR64, 1, True)
         forms["ir32_64_jacobi"] = timed_form(S.SFEM_SOLVE_IR32_64, S.SFEM_OP_MF64, 0, False)
         forms["ir32_64_two_level_fp64_vectors"] = timed_form(S.SFEM_SOLVE_IR32_64, S.SFEM_OP_MF64, 1, False, 0)

@@ -532,7 +532,6 @@ def main():
     traffic = None
     try:
         tr = json.load(open(os.path.join(ROOT, "profiles", "mf32_traffic.json")))
-        from paper_2001_08849_gb300.opbench import tiled_source_sha
         if (tr.get("source_sha256") == tiled_source_sha() and tr.get("ndof") == ndof
                 and tr.get("op") == "mf32"):
             traffic = tr["dram_bytes_per_apply"]

@@ -433,7 +433,10 @@ int sfem_get_diag(sfem_ctx *ctx, double *diag /* ndof, diagonal of A */);
  *          loads it until the process exits, shared by all calls: calls that
  *          overlap on the GPU (several streams or contexts) race on it.
  * The first call on a device looks up the scratch address (with the
- * context's device current); make that first call before any stream capture.
+ * context's device current) and keeps it for the life of the process; make
+ * that first call before any stream capture.  A device reset
+ * (cudaDeviceReset) ends every context of this library and also the
+ * validity of that kept address: the entry point is not usable after one.
  * Work runs on the context stream.  No cudaMalloc/cudaFree is called. */
 int sfem_apply_noalloc(sfem_ctx *ctx, const double *u, double *y);
 

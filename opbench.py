@@ -1,8 +1,8 @@
 """Operator and solver micro-benchmarks through the C ABI, for timing and
 for profiling single kernels in isolation (e.g. under ncu).
 
-  python -m paper_2001_08849_gb300.opbench --cells 200 40 42 --op mf32f64 --reps 20
-  python -m paper_2001_08849_gb300.opbench --cells 200 40 42 --solve fpcg_learned --tol 1e-8
+  python opbench.py --cells 200 40 42 --op mf32f64 --reps 20
+  python opbench.py --cells 200 40 42 --solve fpcg_learned --tol 1e-8
 
 --op: repeated raw operator applications (sfem_time_operator); prints the
 mean device ms per application, DOF/s and the algorithmic bytes of the FP32
@@ -22,7 +22,7 @@ import os
 import sys
 import time
 
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 

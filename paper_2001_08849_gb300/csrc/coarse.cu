@@ -17,11 +17,16 @@
 //     nodes two element layers apart, so centres farther apart than two
 //     cells are not coupled when patches span at least three elements, and
 //     within a stride-5 class the members are 5 apart;
-//   * A_c is symmetrised, factored by a blocked FP64 Cholesky (L), inverted
-//     to W = L^-1 and C = W^T W = A_c^-1 in FP32 (blocked, 64 x 64 tiles).
-// Per PCG iteration (coarse_correction): rc = Pi^T r (one block per cell,
-// fixed-order sums, then a fixed-order gather per centre), yc = C rc (FP32
-// GEMV over the L2-resident C), and the CG kernels add P Pi yc to D^-1 r.
+//   * A_c is symmetrised and factored by a blocked Cholesky (L) that skips
+//     the zero blocks outside its band, in FP32 by default (FP64 on a
+//     non-positive pivot or on request, sfem_coarse_opts.factor), inverted
+//     to W = L^-1 and C = W^T W = A_c^-1 in FP32 (blocked, 64 x 64 tiles;
+//     only the lower blocks of the symmetric C are stored).
+// Per PCG iteration (coarse_correction): rc = Pi^T r (FP32 atomics per run
+// of nodes of one interpolation cell in the solve's fused kernels;
+// fixed-order sums and a fixed-order gather per centre at initialisation,
+// reliable updates and sfem_coarse_apply), yc = C rc (FP32 product with
+// the L2-resident packed C), and the CG kernels add P Pi yc to D^-1 r.
 
 #include <cuda_runtime.h>
 

@@ -34,7 +34,9 @@ static double *g_noalloc_addr[kNoAllocMaxDevices] = {};
 
 // Device address of the scratch array on `dev` (the current device).  In
 // host code g_noalloc_w names a host-side shadow, not device memory, so the
-// address is looked up once per device and cached.
+// address is looked up once per device and cached for the process's life.
+// A cudaDeviceReset would make the cached address stale; it also ends every
+// context of the library, so the entry point is not usable after one.
 static double *noalloc_scratch(int dev) {
   SFEM_REQUIRE(dev >= 0 && dev < kNoAllocMaxDevices, SFEM_EINVAL, "device id out of range");
   std::lock_guard<std::mutex> lock(g_noalloc_mu);

@@ -12,10 +12,17 @@
 //            u += d, the FP64 true residual f - K u replaces the FP32 one and
 //            CG goes on in the same Krylov space (search direction kept),
 //            so the refinement costs no restart.
-// Iterations run as captured CUDA graphs of `check_every` iterations.  The
-// CG scalars live in device memory; once converged, a device flag turns the
-// remaining captured kernels into no-ops, so the host only polls the
-// scalars between graph launches (two launches kept in flight).
+// The CG scalars live in device memory.  By default each CG (re)start is one
+// graph launch: a conditional WHILE node whose body runs four iterations and
+// then a kernel that clears the loop flag when the device-side state says
+// stop (converged, reliable update due, breakdown, fallback, guard count);
+// the host wakes only between restarts.  Where conditional nodes are not
+// available, or with SFEM_GRAPH_LOOP=0 (kernels inside a conditional node
+// are invisible to ncu), the solve replays captured graphs of `check_every`
+// iterations instead: once converged, a device flag turns the remaining
+// captured kernels into no-ops, and the host polls the scalars between
+// graph launches (two launches kept in flight).  Both give the same
+// iterates.
 
 #include <cuda_runtime.h>
 

@@ -10,13 +10,18 @@ The oracle cannot solve at this size, so the checks are sampled:
   with those oracle rows and the oracle's traction load b: bounded by the
   solve's own stopping test, |r_i| <= ||r|| <= 1e-8 ||b||;
 - the mixed solution against the FP64 two-level PCG solution of the same
-  system at the same tolerance (relative L2 difference, printed).
+  system at the same tolerance (relative L2 difference, printed);
+- the FP32 tiled operator (the inner operator of the mixed solve: 16-bit
+  tile-local ids and halo tables at their full-size extent) on an FP32
+  input at the same sampled rows, with the row-wise FP32 bound of
+  tests/test_gpu_parity.py.
 """
 import numpy as np
 import pytest
 
 from inputs.kuhn_beam import cantilever
 from oracle import fsfem as F
+from tolerances import mf32_row_bound
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -68,6 +73,12 @@ def test_large_beam_mixed_solve(S, nu, max_diff):
         yv = torch.empty_like(v)
         S.sfem_apply(fe.h, v, yv, S.SFEM_OP_MF64)
         yv = yv.cpu().numpy()
+        v32 = v.float()
+        yv32 = torch.empty_like(v32)
+        S.sfem_apply(fe.h, v32, yv32, S.SFEM_OP_MF32)
+        yv32 = yv32.double().cpu().numpy()
+        vm32 = v32.double().cpu().numpy() * free
+        v32_inf = np.abs(vm32).max()
         x = u.cpu().numpy()
         f = F.traction_load(m.n_nodes, m.xyz, p.trac_tris, p.trac)[0]
         bnorm = np.linalg.norm(f * free)
@@ -81,6 +92,8 @@ def test_large_beam_mixed_solve(S, nu, max_diff):
                     continue
                 ref = vals[c] @ vm[cols]
                 assert abs(yv[r] - ref) <= 1e-11 * (np.abs(vals[c]) @ np.abs(vm[cols])), (node, c)
+                d32 = abs(yv32[r] - vals[c] @ vm32[cols])
+                assert d32 <= mf32_row_bound(vals[c], vm32[cols], v32_inf), (node, c, d32)
                 res = abs(f[r] - vals[c] @ x[cols])
                 worst = max(worst, res / bnorm)
         print(f"nu={nu}: sampled residual rows (oracle K) max |r_i| / ||b|| = {worst:.2e}")

@@ -7,6 +7,14 @@ Tolerances (stated once, used below):
   * FP32 operator: the operator data is FP64 rounded once to FP32 and the
     apply sums O(100) FP32 terms per entry, so
     |dy|_inf <= 2e-5 || |K||u| ||_inf and ||dy||_2 <= 1e-5 ||y||_2;
+  * FP32 operator, row by row (sampled rows at full size, FP32 input u):
+    |dy_i| <= 64 * 2^-24 * (|K| (|u| + ||u||_inf))_i.  Each output entry
+    passes through fewer than 32 FP32 roundings along its longest chain
+    (operator data rounded from FP64, the tile's reference displacement
+    subtracted, 4-term strain sums, the face average of two strains, the
+    6-term stress, the 3-term nodal force, the compensated nodal sum); the
+    subtracted reference is at most ||u||_inf in size; c = 64 doubles the
+    rounding count;
   * displacements of reduced-precision solves: relative L2 <= 1e-6 against
     the oracle's exact (Cholesky) solution;
   * FP64 Jacobi-PCG iteration counts within 10% of the oracle's: finite-
@@ -20,6 +28,7 @@ import pytest
 from inputs.kuhn_beam import cantilever, clamp_dofs, face_nodes, kuhn_beam
 from oracle import fsfem as F
 from oracle import solve as OS
+from tolerances import MF32_ROW_C, mf32_row_bound
 
 pytestmark = pytest.mark.gpu
 
@@ -334,6 +343,15 @@ def test_full_size_sampled_rows_and_solve(S, cfg2):
         y64 = torch.empty_like(u)
         S.sfem_apply(ctx.h, u, y64, S.SFEM_OP_MF64)
         y64 = y64.cpu().numpy()
+        # the FP32 tiled operator (4928 tiles of <= 512 tets, 16-bit local
+        # ids, halo tets) on the FP32-rounded input, as the mixed solve runs it
+        u32 = u.float()
+        y32 = torch.empty_like(u32)
+        S.sfem_apply(ctx.h, u32, y32, S.SFEM_OP_MF32)
+        y32 = y32.double().cpu().numpy()
+        um32 = u32.double().cpu().numpy() * free
+        u32_inf = np.abs(um32).max()
+        worst32 = 0.0
         nodes = np.concatenate([[0, m.n_nodes - 1], rng.integers(0, m.n_nodes, 24)])
         for node in nodes:
             cols, vals = F.K_rows_submesh(m.xyz, m.tets, p.E, p.nu, int(node))
@@ -350,6 +368,11 @@ def test_full_size_sampled_rows_and_solve(S, cfg2):
                 if free[r]:
                     yr = ref @ um[cols]
                     assert abs(y64[r] - yr) <= 1e-11 * (np.abs(ref) @ np.abs(um[cols]))
+                    bound = mf32_row_bound(ref, um32[cols], u32_inf)
+                    d32 = abs(y32[r] - ref @ um32[cols])
+                    worst32 = max(worst32, d32 / bound * MF32_ROW_C)
+                    assert d32 <= bound, (node, c, d32, bound)
+        print(f"\nMF32 sampled rows: max |dy_i| / (2^-24 (|K|(|u|+|u|_inf))_i) = {worst32:.2f} (bound {MF32_ROW_C:.0f})")
         # mixed-precision solve to 1e-8; global equilibrium: reactions balance the load
         x = torch.zeros(ctx.ndof, dtype=torch.float64, device="cuda")
         si = S.sfem_solve(ctx.h, x, S.solve_opts(kind=S.SFEM_SOLVE_IR32_64, tol=1e-8, u_on_device=True))

@@ -18,6 +18,8 @@ def S():
 def test_exports_every_header_function(S):
     names = S.header_functions()
     assert "sfem_mesh_setup" in names and "sfem_solve" in names
+    # the allocation-free apply is declared and exported like the others
+    assert "sfem_apply_noalloc" in names and hasattr(S.lib, "sfem_apply_noalloc")
     for n in names:
         assert hasattr(S.lib, n), n
 
@@ -44,6 +46,7 @@ def test_argument_checks_without_gpu(S):
         assert h.value is None
     # null handles
     assert S.lib.sfem_apply(None, None, None, 0, 1) == S.SFEM_EINVAL
+    assert S.lib.sfem_apply_noalloc(None, None, None) == S.SFEM_EINVAL
     assert S.lib.sfem_assemble(None, None) == S.SFEM_EINVAL
     assert S.lib.sfem_solve(None, None, None, None, None) == S.SFEM_EINVAL
     S.lib.sfem_destroy(None)

@@ -56,6 +56,17 @@ FP32_VECTORS = 3
 INNER_TOL = 0.03
 
 
+def tiled_source_sha() -> str:
+    """SHA-256 of the sources of the tiled FP32 operator kernel: a stored
+    DRAM-traffic figure is valid only for the kernel it was measured on."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("tiles.cu", "tile_apply.cuh"):
+        with open(os.path.join(ROOT, "paper_2001_08849_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
 def rank_max(dist, x: float, device="cuda") -> float:
     """The largest x over the ranks of the process group (x itself when dist
     is None): a step's time is the slowest rank's."""

@@ -581,8 +581,8 @@ extern "C" int sfem_batch_solve(sfem_ctx *const *ctxs, int n, double *const *u, 
       k_set_bc_all<<<grid_for(nd * nr, 256), 256, 0, st>>>(X, c.g, c.dmask, nd, nr, !opts->warm_start);
       SFEM_CHECK_LAUNCH();
       for (double *v : {D, P, Q}) SFEM_CUDA(cudaMemsetAsync(v, 0, nd * nr * sizeof(double), st));
-      hb[b].A = TileArgs{c.tl.tile_start, c.tl.hoff,       c.tl.noff, c.tl.halo_tet, c.tl.halo_lconn,
-                         c.tl.tile_nodes, c.tl.node_inc,   c.tl.rec,  c.n_tets};
+      hb[b].A = TileArgs{c.tl.tile_start, c.tl.hoff,     c.tl.noff, c.tl.halo_tet, c.tl.halo_lconn,
+                         c.tl.tile_nodes, c.tl.node_inc, c.tl.rec,  c.n_tets,       c.tl.slot_stride};
       hb[b].first_sys = s;
       hb[b].nrhs = nr;
       hb[b].lam = (float)c.lam;

@@ -443,8 +443,6 @@ __global__ void __launch_bounds__(kTileThreads, 3) k_cs_galerkin(TileArgs A, Coa
             for (int q = 0; q < 3; ++q) g[q] = fmaf(w, G.g[a][q], g[q]);
           }
           T.swa[j] = make_float4(g[0], g[1], g[2], G.V);
-          reinterpret_cast<uint2 *>(T.sinc)[j] =
-              make_uint2(__float_as_uint(R.rr[r][3].z), __float_as_uint(R.rr[r][3].w));
         }
       }
       for (int h = threadIdx.x; h < T.H; h += kTileThreads) {
@@ -478,13 +476,13 @@ __global__ void __launch_bounds__(kTileThreads, 3) k_cs_galerkin(TileArgs A, Coa
         for (int a = 0; a < 4; ++a) {
           if (nb[a] != kNoNbr) {
             const float4 wn = T.swa[nb[a]];
-            const float k = 0.25f / (we.w + wn.w);
+            const float k = __fdividef(0.25f, we.w + wn.w);
             ks += k;
             Sg[r][0] = fmaf(k, wn.x, Sg[r][0]);
             Sg[r][1] = fmaf(k, wn.y, Sg[r][1]);
             Sg[r][2] = fmaf(k, wn.z, Sg[r][2]);
           } else {
-            ks += 0.25f / we.w;
+            ks += __fdividef(0.25f, we.w);
           }
         }
         Sg[r][0] = fmaf(ks, we.x, Sg[r][0]);
@@ -508,17 +506,8 @@ __global__ void __launch_bounds__(kTileThreads, 3) k_cs_galerkin(TileArgs A, Coa
           const float tr = S[0] + S[1] + S[2];
           const float st[6] = {lam * tr + 2.f * mu * S[0], lam * tr + 2.f * mu * S[1], lam * tr + 2.f * mu * S[2],
                                mu * S[3], mu * S[4], mu * S[5]};
-          float f[12];
 #pragma unroll
-          for (int a = 0; a < 4; ++a) {
-            f[3 * a] = G.g[a][0] * st[0] + G.g[a][1] * st[5] + G.g[a][2] * st[4];
-            f[3 * a + 1] = G.g[a][0] * st[5] + G.g[a][1] * st[1] + G.g[a][2] * st[3];
-            f[3 * a + 2] = G.g[a][0] * st[4] + G.g[a][1] * st[3] + G.g[a][2] * st[2];
-          }
-          float4 *fo = reinterpret_cast<float4 *>(T.sfe + 12 * j);
-          fo[0] = make_float4(f[0], f[1], f[2], f[3]);
-          fo[1] = make_float4(f[4], f[5], f[6], f[7]);
-          fo[2] = make_float4(f[8], f[9], f[10], f[11]);
+          for (int a = 0; a < 4; ++a) store_slot_force(T, R.rr[r][3], a, G.g[a], st);
         }
         __syncthreads();
         node_forces();
@@ -1050,7 +1039,7 @@ static void setup_coarse(Ctx &c, const sfem_coarse_opts *opts) {
     SFEM_REQUIRE(smem <= 227 * 1024, SFEM_EINVAL, "tile too large for the Galerkin assembly");
     SFEM_CUDA(cudaFuncSetAttribute(k_cs_galerkin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     TileArgs TA{c.tl.tile_start, c.tl.hoff, c.tl.noff, c.tl.halo_tet, c.tl.halo_lconn, c.tl.tile_nodes,
-                c.tl.node_inc, c.tl.rec, c.n_tets};
+                c.tl.node_inc, c.tl.rec, c.n_tets, c.tl.slot_stride};
     k_cs_galerkin<<<(unsigned)c.tl.n_tiles, kTileThreads, smem, c.stream>>>(TA, cs, c.dmask, (float)c.lam,
                                                                               (float)c.mu, stage_off, Ac, ovf,
                                                                               ovf + 1);

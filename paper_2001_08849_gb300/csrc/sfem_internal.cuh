@@ -132,11 +132,12 @@ struct TileData {
   int64_t *noff = nullptr;       // n_tiles + 1 node-list offsets
   int32_t *halo_tet = nullptr;   // halo tets (tile order)
   uint2 *halo_lconn = nullptr;   // their local connectivity (4 x 16 bit)
-  int32_t *tile_nodes = nullptr; // sorted node ids per tile
-  uint16_t *node_inc = nullptr;  // per tile node: first slot of its incidence list
+  int32_t *tile_nodes = nullptr; // node ids per tile, in the order of the slot layout
+  uint32_t *node_inc = nullptr;  // per tile node: slot-0 position | own-slot count << 16
   float4 *rec = nullptr;         // 64-byte per-tet records (tile order): V_e grad N_1..3,
-                                 // V_e, local connectivity, local neighbours
+                                 // V_e, local connectivity, local neighbours, slot positions
   int max_halo = 0, max_nodes = 0;
+  int slot_stride = 0;           // floats per component array of a tile's force slots
   size_t smem = 0;               // dynamic shared memory of the operator kernel
 };
 

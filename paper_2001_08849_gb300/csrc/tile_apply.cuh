@@ -15,16 +15,25 @@ constexpr int kTileThreads = 256;        // threads per tile CTA
 constexpr int kTilePer = kTileMax / kTileThreads;
 constexpr unsigned short kNoNbr = 0xFFFF;
 
+// Nodal force slots of a tile.  Tile nodes are ordered by their number of
+// own slots (slots 4j+a of the tile's tets j whose vertex a is the node),
+// largest first, and taken in groups of 32 (one warp of the nodal-sum
+// phase).  Slot k of node q lies at position base(q / 32) + 32 k + q % 32 of
+// three float arrays (x, y, z components, stride slot_stride), so the warp
+// summing 32 nodes reads 32 consecutive floats per step, and each tet writes
+// its four slot forces straight to their positions (stored in its record).
+// Per tile node, node_inc holds (position of its slot 0) | (count << 16).
 struct TileArgs {
   const int32_t *tile_start;
   const int64_t *hoff, *noff;
   const int32_t *halo_tet;
   const uint2 *halo_lconn;
   const int32_t *tile_nodes;
-  const uint16_t *node_inc;  // per tile node: first slot in its incidence list
+  const uint32_t *node_inc;  // per tile node: slot-0 position | own-slot count << 16
   const float4 *rec;   // 64-byte per-tet records, tile order, as 4 planes of float4 (word 4q..4q+3 of
                        // tet t at rec[q * rs + t]): a warp's loads of one plane are contiguous
   int64_t rs;          // plane stride (the tet count)
+  int slot_stride;     // floats per component array of the force slots (a multiple of 32)
 };
 
 struct TetGeo {
@@ -97,17 +106,23 @@ __device__ __forceinline__ void tile_load(const TileArgs &A, int tile, TileRegs 
 }
 
 // Shared-memory layout of one tile: displacements (L float4) sharing their
-// space with the nodal forces of the tile tets (4 slots x xyz = 12 floats
-// per tet; written only after the strains have been formed), strains split
-// in two float4 arrays (w0..w3 | w4, w5, V, 0) over tile + halo tets,
-// incidence list and node starts.
+// space with the force slots (three arrays of slot_stride floats; written
+// only after the strains have been formed), strains split in two float4
+// arrays (w0..w3 | w4, w5, V, 0) over tile + halo tets, and the per-node
+// slot position and count.
 struct TileView {
-  int n_own, H, L, nt;
+  int n_own, H, L, nt, ns;
   int64_t h0, n0;
   float4 *su, *swa, *swb;
-  float *sfe;
-  uint16_t *sinc, *snode;
+  float *sfx;       // x components of the slots; y at sfx + ns, z at sfx + 2 ns
+  uint32_t *snode;
 };
+
+// float4 words taken by the displacement / force-slot region
+__host__ __device__ __forceinline__ int tile_slot_words(int L, int slot_stride) {
+  const int fw = (3 * slot_stride + 3) / 4;
+  return L > fw ? L : fw;
+}
 
 __device__ __forceinline__ TileView tile_view(const TileArgs &A, int tile, float4 *smem) {
   TileView T;
@@ -118,17 +133,33 @@ __device__ __forceinline__ TileView tile_view(const TileArgs &A, int tile, float
   T.H = (int)(A.hoff[tile + 1] - T.h0);
   T.L = (int)(A.noff[tile + 1] - T.n0);
   T.nt = T.n_own + T.H;
+  T.ns = A.slot_stride;
   T.su = smem;
-  T.sfe = reinterpret_cast<float *>(smem);                              // 12 * n_own, over su
-  T.swa = T.su + max(T.L, 3 * T.n_own);
+  T.sfx = reinterpret_cast<float *>(smem);                              // 3 * ns, over su
+  T.swa = T.su + tile_slot_words(T.L, T.ns);
   T.swb = T.swa + T.nt;
-  T.sinc = reinterpret_cast<uint16_t *>(T.swb + T.nt);                  // 4 * n_own
-  T.snode = T.sinc + 4 * T.n_own;                                       // L
+  T.snode = reinterpret_cast<uint32_t *>(T.swb + T.nt);                 // L
   return T;
 }
 
-// strains of the tile's own and halo tets from the displacements in su;
-// also stores the own slots' incidence entries
+// position of the slot of vertex a of a tile tet; q3 is the tet record's
+// fourth float4 (words 14, 15: four 16-bit positions)
+__device__ __forceinline__ int slot_pos(const float4 &q3, int a) {
+  const uint32_t w = __float_as_uint(a < 2 ? q3.z : q3.w);
+  return (int)((a & 1) ? (w >> 16) : (w & 0xFFFF));
+}
+
+// nodal force (V_e grad N_a)^T sigma of vertex a into its slot
+// (sigma in Voigt order xx yy zz yz zx xy)
+__device__ __forceinline__ void store_slot_force(const TileView &T, const float4 &q3, int a, const float (&g)[3],
+                                                 const float (&st)[6]) {
+  const int p = slot_pos(q3, a);
+  T.sfx[p] = g[0] * st[0] + g[1] * st[5] + g[2] * st[4];
+  T.sfx[T.ns + p] = g[0] * st[5] + g[1] * st[1] + g[2] * st[3];
+  T.sfx[2 * T.ns + p] = g[0] * st[4] + g[1] * st[3] + g[2] * st[2];
+}
+
+// strains of the tile's own and halo tets from the displacements in su
 __device__ __forceinline__ void tile_strains(const TileArgs &A, const TileRegs &R, const TileView &T) {
 #pragma unroll
   for (int r = 0; r < kTilePer; ++r) {
@@ -141,8 +172,6 @@ __device__ __forceinline__ void tile_strains(const TileArgs &A, const TileRegs &
       strain_to(T.su, lc, G, w2);
       T.swa[j] = w2[0];
       T.swb[j] = w2[1];
-      reinterpret_cast<uint2 *>(T.sinc)[j] =
-          make_uint2(__float_as_uint(R.rr[r][3].z), __float_as_uint(R.rr[r][3].w));
     }
   }
   for (int h = threadIdx.x; h < T.H; h += kTileThreads) {
@@ -174,13 +203,15 @@ __device__ __forceinline__ float tile_forces(const TileRegs &R, const TileView &
     const float W[6] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y};
     const float Ve = w1.z;
     // face weights kap_a = 1/(4 (V_e + V_nbr)), 1/(4 V_e) on exterior faces
+    // (the hardware reciprocal: both tets of a face form the same sum and so
+    // the same weight)
     float S[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     float ks = 0.f;
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
       if (nb[a] != kNoNbr) {
         const float4 n0v = T.swa[nb[a]], n1v = T.swb[nb[a]];
-        const float k = 0.25f / (Ve + n1v.z);
+        const float k = __fdividef(0.25f, Ve + n1v.z);
         ks += k;
         S[0] = fmaf(k, n0v.x, S[0]);
         S[1] = fmaf(k, n0v.y, S[1]);
@@ -189,7 +220,7 @@ __device__ __forceinline__ float tile_forces(const TileRegs &R, const TileView &
         S[4] = fmaf(k, n1v.x, S[4]);
         S[5] = fmaf(k, n1v.y, S[5]);
       } else {
-        ks += 0.25f / Ve;
+        ks += __fdividef(0.25f, Ve);
       }
     }
 #pragma unroll
@@ -201,34 +232,25 @@ __device__ __forceinline__ float tile_forces(const TileRegs &R, const TileView &
 #pragma unroll
     for (int i = 0; i < 6; ++i) el = fmaf(W[i], st[i], el);
     en += el;
-    float f[12];
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      f[3 * a] = G.g[a][0] * st[0] + G.g[a][1] * st[5] + G.g[a][2] * st[4];
-      f[3 * a + 1] = G.g[a][0] * st[5] + G.g[a][1] * st[1] + G.g[a][2] * st[3];
-      f[3 * a + 2] = G.g[a][0] * st[4] + G.g[a][1] * st[3] + G.g[a][2] * st[2];
-    }
-    float4 *fo = reinterpret_cast<float4 *>(T.sfe + 12 * j);
-    fo[0] = make_float4(f[0], f[1], f[2], f[3]);
-    fo[1] = make_float4(f[4], f[5], f[6], f[7]);
-    fo[2] = make_float4(f[8], f[9], f[10], f[11]);
+    for (int a = 0; a < 4; ++a) store_slot_force(T, R.rr[r][3], a, G.g[a], st);
   }
   return en;
 }
 
-// the force at tile node i: its own slots summed in a fixed order with
-// compensation (the element forces at a node nearly cancel); false when the
-// node has no slot in this tile
+// the force at tile node i: its own slots summed in a fixed order (the
+// tets' order in the tile) with compensation (the element forces at a node
+// nearly cancel); false when the node has no slot in this tile.  Called by
+// the 32 threads of a node group together, it reads consecutive floats.
 __device__ __forceinline__ bool tile_node_force(const TileView &T, int i, float &fx, float &fy, float &fz) {
-  const int nslots = 4 * T.n_own;
-  const int b = T.snode[i], e = (i + 1 < T.L) ? T.snode[i + 1] : nslots;
+  const uint32_t info = T.snode[i];
+  const int b = (int)(info & 0xFFFF), n = (int)(info >> 16);
   fx = fy = fz = 0.f;
-  if (b == e) return false;
+  if (n == 0) return false;
   float cx = 0.f, cy = 0.f, cz = 0.f;
-  for (int k = b; k < e; ++k) {
-    const int slot = T.sinc[k];
-    const float *fp = T.sfe + 12 * (slot >> 2) + 3 * (slot & 3);
-    const float yx = fp[0] - cx, yy = fp[1] - cy, yz = fp[2] - cz;
+  const float *px = T.sfx + b, *py = px + T.ns, *pz = py + T.ns;
+  for (int k = 0; k < n; ++k) {
+    const float yx = px[32 * k] - cx, yy = py[32 * k] - cy, yz = pz[32 * k] - cz;
     const float tx = fx + yx, ty = fy + yy, tz = fz + yz;
     cx = __fsub_rn(__fsub_rn(tx, fx), yx);
     cy = __fsub_rn(__fsub_rn(ty, fy), yy);
@@ -283,10 +305,19 @@ __device__ __forceinline__ float tile_compute(const TileArgs &A, int tile, const
   tile_strains(A, R, T);
   __syncthreads();
   const float en = tile_forces(R, T, lam, mu);
-  __syncthreads();
+  __shared__ float s_en[kTileThreads / 32];
   if (energy_out) {  // FP32 within the tile (512 terms), FP64 across tiles
-    const float e = block_sum_f<kTileThreads>(en);
-    if (threadIdx.x == 0) atomicAdd(energy_out, (double)e);
+    float e = en;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(0xffffffffu, e, o);
+    if ((threadIdx.x & 31) == 0) s_en[threadIdx.x >> 5] = e;
+  }
+  __syncthreads();
+  if (energy_out && threadIdx.x == 0) {  // warp partials in a fixed order
+    float e = 0.f;
+#pragma unroll
+    for (int w = 0; w < kTileThreads / 32; ++w) e += s_en[w];
+    atomicAdd(energy_out, (double)e);
   }
   for (int i = threadIdx.x; i < T.L; i += kTileThreads) {
     float fx, fy, fz;

@@ -10,16 +10,19 @@
 //   2. strains of the tile's tets and of its halo (the neighbours across
 //      the tile's outer faces, recomputed here) -> smem;
 //   3. face-averaged stress per tile tet and its four nodal forces -> smem;
-//   4. each tile node sums its slots in a fixed order (tile-local
-//      incidence list built at setup; no shared-memory atomics) and adds
-//      the sum to y with one global atomic per component.
+//   4. each tile node sums its slots in a fixed order and adds the sum to y
+//      with one global atomic per component.  The slots are laid out at
+//      setup so that this phase reads shared memory without bank conflicts
+//      and without an index: nodes ordered by slot count and taken 32 at a
+//      time, slot k of a node at (group base) + 32 k + (lane); each tet
+//      writes its four slot forces to positions stored in its record.
 // Setup reorders tets by a coarse spatial binning of their centroids
 // (counting sort on a Morton-free lexicographic bin grid), cuts bins into
-// tiles of at most kTileMax tets, and builds per tile: the sorted node
-// list, 16-bit local connectivity, 16-bit local neighbour indices (into
-// tile tets, then halo tets) and the halo list.  Per-tet data streamed by
+// tiles of at most kTileMax tets, and builds per tile: the node list (in
+// the order of the slot layout), 16-bit local connectivity, 16-bit local
+// neighbour indices (into tile tets, then halo tets) and the halo list.  Per-tet data streamed by
 // the kernel: one 64-byte record in four 16-byte planes (V_e-scaled
-// gradients, V_e, local connectivity, local neighbours, incidence entries);
+// gradients, V_e, local connectivity, local neighbours, slot positions);
 // the face weights 1/(4 (V_e + V_nbr))
 // are formed from the volumes staged in shared memory.
 
@@ -132,10 +135,8 @@ __global__ void k_tile_ranges(const int64_t *__restrict__ bin_ptr, const int64_t
 //   [9]     V_e in FP32
 //   [10,11] local connectivity (4 x 16 bit), written by k_tile_build
 //   [12,13] local neighbours (4 x 16 bit, 0xFFFF exterior), k_tile_build
-//   [14,15] four entries (16 bit) of the tile's node-incidence list: the
-//           list holds, for each tile node in turn, the slots 4j+a of the
-//           tile tets j whose vertex a is that node; record j stores
-//           entries 4j..4j+3
+//   [14,15] positions (4 x 16 bit) of the tet's four nodal force slots in
+//           the tile's slot arrays (see TileArgs), k_tile_build
 __global__ void k_reorder(const int32_t *__restrict__ perm, int64_t n, const float *__restrict__ Gs32,
                           const double *__restrict__ vol, float4 *__restrict__ rec, int32_t *__restrict__ iperm) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -271,23 +272,28 @@ struct TileBuild {
   int32_t *halo_tet;
   uint2 *halo_lconn;
   int32_t *tile_nodes;
-  float4 *rec;   // per-tet records (tile order, 4 planes): lconn -> words 10,11; lnbr -> 12,13; inc -> 14,15
+  float4 *rec;   // per-tet records (tile order, 4 planes): lconn -> words 10,11; lnbr -> 12,13; slots -> 14,15
   int64_t rs;    // plane stride
-  uint16_t *node_inc;  // per tile node: start of its slots in the incidence list
+  uint32_t *node_inc;  // per tile node: slot-0 position | own-slot count << 16
+  int *max_slots;      // largest slot-array length over the tiles
   unsigned long long *overflow;
 };
 
 // one CTA per tile; dynamic smem: halo candidates (kHaloCand padded) +
-// node candidates (4*(kTileMax + kHaloCand) padded)
+// node candidates (4*(kTileMax + kHaloCand) padded), and in pass 2 the slot
+// layout tables (2 * kNodeP)
 constexpr int kHaloP = 2048;                        // >= kHaloCand, power of two
 constexpr int kNodeP = 16384;                       // >= 4*(kTileMax + kHaloCand)
+constexpr int kMaxTileNodes = 8000;                 // 2 L + L/32 + 3 <= kNodeP (pass-2 tables)
 static_assert(kHaloP >= kHaloCand && kNodeP >= 4 * (kTileMax + kHaloCand), "tile build buffers too small");
+static_assert(2 * kMaxTileNodes + kMaxTileNodes / 32 + 3 <= kNodeP, "slot layout tables too small");
 constexpr int kBuildThreads = 1024;
 
 __global__ void __launch_bounds__(kBuildThreads) k_tile_build(TileBuild B, int pass) {
   extern __shared__ int sm[];
   int *halo = sm;                 // kHaloP
   int *nodes = sm + kHaloP;       // kNodeP
+  int *aux = nodes + kNodeP;      // 2 * kNodeP (pass 2)
   const int tile = blockIdx.x;
   const int s = B.tile_start[tile], e = B.tile_start[tile + 1];
   const int n_own = e - s;
@@ -323,16 +329,14 @@ __global__ void __launch_bounds__(kBuildThreads) k_tile_build(TileBuild B, int p
     if (threadIdx.x == 0) {
       B.n_halo[tile] = H;
       B.n_nodes[tile] = L;
-      if (L > 65535 || n_own + H > 65535) atomicAdd(B.overflow, 1ull);
+      if (L > kMaxTileNodes || n_own + H > 65535) atomicAdd(B.overflow, 1ull);
     }
     return;
   }
   const int64_t h0 = B.hoff[tile], n0 = B.noff[tile];
-  for (int i = threadIdx.x; i < L; i += blockDim.x) B.tile_nodes[n0 + i] = nodes[i];
-  // node-incidence list of the tile's own slots, sorted by (local node, slot):
-  // keys live in the halo buffer region beyond H (the halo list itself is
-  // still needed below), so use a separate scratch: the tail of `nodes`
-  // past L is free.
+  // the tile's own slots sorted by (node, slot): the slots of each node in
+  // the fixed order of the tets in the tile.  The keys live in the tail of
+  // `nodes` past L (the halo list is still needed below).
   int *keys = nodes + ((L + 31) & ~31);
   const int KP = pow2_at_least(4 * n_own);  // >= 4 n_own slots, power of two
   for (int i = threadIdx.x; i < KP; i += blockDim.x) {
@@ -346,16 +350,17 @@ __global__ void __launch_bounds__(kBuildThreads) k_tile_build(TileBuild B, int p
   }
   __syncthreads();
   block_bitonic_sort(keys, KP, KP);
-  uint16_t *rinc = reinterpret_cast<uint16_t *>(B.rec + 3 * B.rs + s);
-  for (int i = threadIdx.x; i < 4 * n_own; i += blockDim.x) {
-    // entry i goes to record (s + i/4), 16-bit word 28 + i%4 (words 14,15:
-    // the last two of plane 3)
-    rinc[(i / 4) * 8 + 4 + (i % 4)] = (uint16_t)(keys[i] & 2047);
-  }
-  // start of each tile node's slots: number of keys below (l << 11)
-  for (int l = threadIdx.x; l < L; l += blockDim.x) {
+  // slot layout (see TileArgs): nodes ordered by own-slot count, largest
+  // first (ties by node id), in groups of 32; group g starts at gbase[g] and
+  // holds 32 x (count of its first node) positions
+  int *key2 = aux;                  // pow2(L): (2047 - count) << 16 | ascending index
+  int *start = aux + kNodeP;        // L + 1: first key of each node (ascending index)
+  int *jds = start + L + 1;         // L: position of each node in the count order
+  int *gbase = jds + L;             // groups + 1
+  const int ngroups = (L + 31) / 32;
+  for (int l = threadIdx.x; l <= L; l += blockDim.x) {
     int lo = 0, hi = 4 * n_own;
-    const int key = l << 11;
+    const int key = l << 11;        // number of keys below (l << 11)
     while (lo < hi) {
       const int mid = (lo + hi) >> 1;
       if (keys[mid] < key)
@@ -363,13 +368,40 @@ __global__ void __launch_bounds__(kBuildThreads) k_tile_build(TileBuild B, int p
       else
         hi = mid;
     }
-    B.node_inc[n0 + l] = (uint16_t)lo;
+    start[l] = lo;
+  }
+  __syncthreads();
+  for (int l = threadIdx.x; l < L; l += blockDim.x) key2[l] = ((2047 - (start[l + 1] - start[l])) << 16) | l;
+  block_bitonic_sort(key2, pow2_at_least(L), L);
+  for (int q = threadIdx.x; q < L; q += blockDim.x) jds[key2[q] & 0xFFFF] = q;
+  if (threadIdx.x == 0) {
+    int b = 0;
+    for (int g = 0; g < ngroups; ++g) {
+      gbase[g] = b;
+      b += 32 * (2047 - (key2[32 * g] >> 16));
+    }
+    gbase[ngroups] = b;
+    atomicMax(B.max_slots, b);
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < L; q += blockDim.x) {
+    const int l = key2[q] & 0xFFFF, cnt = 2047 - (key2[q] >> 16);
+    B.tile_nodes[n0 + q] = nodes[l];
+    B.node_inc[n0 + q] = (uint32_t)(gbase[q >> 5] + (q & 31)) | ((uint32_t)cnt << 16);
+  }
+  uint16_t *rpos = reinterpret_cast<uint16_t *>(B.rec + 3 * B.rs + s);
+  for (int p = threadIdx.x; p < 4 * n_own; p += blockDim.x) {
+    // slot i = 4j + a (tet j, vertex a) is the k-th slot of its node; its
+    // position goes to record (s + j), 16-bit word 28 + a (words 14, 15)
+    const int key = keys[p], l = key >> 11, i = key & 2047;
+    const int k = p - start[l], q = jds[l];
+    rpos[(i / 4) * 8 + 4 + (i % 4)] = (uint16_t)(gbase[q >> 5] + 32 * k + (q & 31));
   }
   for (int j = threadIdx.x; j < n_own + H; j += blockDim.x) {
     const int tnew = j < n_own ? s + j : halo[j - n_own];
     const int64_t to = B.perm[tnew];
     unsigned int l[4];
-    for (int a = 0; a < 4; ++a) l[a] = (unsigned int)bsearch_int(nodes, L, B.tets[4 * to + a]);
+    for (int a = 0; a < 4; ++a) l[a] = (unsigned int)jds[bsearch_int(nodes, L, B.tets[4 * to + a])];
     const uint2 lc = make_uint2(l[0] | (l[1] << 16), l[2] | (l[3] << 16));
     if (j < n_own) {
       unsigned int *rw2 = reinterpret_cast<unsigned int *>(B.rec + 2 * B.rs + tnew);  // words 8-11
@@ -501,16 +533,17 @@ void build_tiles(Ctx &c) {
   B.n_halo = nh;
   B.n_nodes = nn;
   B.overflow = ovf;
-  const size_t build_smem = (kHaloP + kNodeP) * sizeof(int);
-  SFEM_CUDA(cudaFuncSetAttribute(k_tile_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)build_smem));
+  const size_t build_smem = (kHaloP + kNodeP) * sizeof(int);       // pass 1
+  const size_t build_smem2 = (kHaloP + 3 * kNodeP) * sizeof(int);  // pass 2: slot layout tables
+  SFEM_CUDA(cudaFuncSetAttribute(k_tile_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)build_smem2));
   k_tile_build<<<(unsigned)nt, kBuildThreads, build_smem, c.stream>>>(B, 1);
   SFEM_CHECK_LAUNCH();
   c.tl.hoff = c.mem.get<int64_t>(nt + 1);
   c.tl.noff = c.mem.get<int64_t>(nt + 1);
   const int64_t total_h = scan_counts(c, nh, nt, c.tl.hoff);
   const int64_t total_n = scan_counts(c, nn, nt, c.tl.noff);
-  int *mx = c.mem.get<int>(2);
-  SFEM_CUDA(cudaMemsetAsync(mx, 0, 2 * sizeof(int), c.stream));
+  int *mx = c.mem.get<int>(3);  // largest halo, node list, slot array (pass 2)
+  SFEM_CUDA(cudaMemsetAsync(mx, 0, 3 * sizeof(int), c.stream));
   k_max_i32<<<grid_for(nt, 256), 256, 0, c.stream>>>(nh, nn, nt, mx);
   SFEM_CHECK_LAUNCH();
   int hm[2];
@@ -518,13 +551,13 @@ void build_tiles(Ctx &c) {
   SFEM_CUDA(cudaMemcpyAsync(hm, mx, sizeof hm, cudaMemcpyDeviceToHost, c.stream));
   SFEM_CUDA(cudaMemcpyAsync(&hovf, ovf, 8, cudaMemcpyDeviceToHost, c.stream));
   SFEM_CUDA(cudaStreamSynchronize(c.stream));
-  SFEM_REQUIRE(hovf == 0, SFEM_EMESH, "tile tables exceed 16-bit local indices");
+  SFEM_REQUIRE(hovf == 0, SFEM_EMESH, "tile tables exceed their local index ranges");
   c.tl.max_halo = hm[0];
   c.tl.max_nodes = hm[1];
   c.tl.halo_tet = c.mem.get<int32_t>(std::max<int64_t>(total_h, 1));
   c.tl.halo_lconn = c.mem.get<uint2>(std::max<int64_t>(total_h, 1));
   c.tl.tile_nodes = c.mem.get<int32_t>(total_n);
-  c.tl.node_inc = c.mem.get<uint16_t>(total_n);
+  c.tl.node_inc = c.mem.get<uint32_t>(total_n);
   B.hoff = c.tl.hoff;
   B.noff = c.tl.noff;
   B.halo_tet = c.tl.halo_tet;
@@ -533,16 +566,20 @@ void build_tiles(Ctx &c) {
   B.node_inc = c.tl.node_inc;
   B.rec = c.tl.rec;
   B.rs = n;
-  k_tile_build<<<(unsigned)nt, kBuildThreads, build_smem, c.stream>>>(B, 2);
+  B.max_slots = mx + 2;
+  k_tile_build<<<(unsigned)nt, kBuildThreads, build_smem2, c.stream>>>(B, 2);
   SFEM_CHECK_LAUNCH();
+  int hslots = 0;
+  SFEM_CUDA(cudaMemcpyAsync(&hslots, mx + 2, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+  SFEM_CUDA(cudaStreamSynchronize(c.stream));
+  c.tl.slot_stride = std::max(hslots, 32);  // a multiple of 32 (groups of 32 positions)
   c.mem.drop(nh);
   c.mem.drop(nn);
   c.mem.drop(ovf);
   c.mem.drop(mx);
   c.mem.drop(hist);
-  c.tl.smem = (size_t)std::max<int64_t>(c.tl.max_nodes, 3 * kTileMax) * sizeof(float4) +
-              (size_t)c.tl.max_nodes * sizeof(uint16_t) + (size_t)(kTileMax + c.tl.max_halo) * 2 * sizeof(float4) +
-              (size_t)kTileMax * 8;
+  c.tl.smem = (size_t)tile_slot_words(c.tl.max_nodes, c.tl.slot_stride) * sizeof(float4) +
+              (size_t)(kTileMax + c.tl.max_halo) * 2 * sizeof(float4) + (size_t)c.tl.max_nodes * sizeof(uint32_t);
   c.tl.smem = (c.tl.smem + 15) & ~size_t(15);
   SFEM_REQUIRE(c.tl.smem <= 220 * 1024, SFEM_EMESH, "tile working set exceeds shared memory");
   c.tl.total_halo = total_h;
@@ -571,7 +608,7 @@ void build_tiles(Ctx &c) {
 template <class TU, class TY>
 void launch_mf32_tiled(Ctx &c, cudaStream_t st, const TU *u, TY *y, double *energy_out, const int *done) {
   TileArgs A{c.tl.tile_start, c.tl.hoff, c.tl.noff, c.tl.halo_tet, c.tl.halo_lconn, c.tl.tile_nodes,
-             c.tl.node_inc, c.tl.rec, c.n_tets};
+             c.tl.node_inc, c.tl.rec, c.n_tets, c.tl.slot_stride};
   k_mf32_tiled<TU, TY><<<(unsigned)c.tl.n_tiles, kTileThreads, c.tl.smem, st>>>(
       A, u, y, (float)c.lam, (float)c.mu, energy_out, done);
   SFEM_CHECK_LAUNCH();

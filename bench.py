@@ -101,6 +101,8 @@ def parse():
     ap.add_argument("--no-forms", action="store_true", help="skip the PCG64 comparison solve")
     ap.add_argument("--learned-train", type=int, default=8, help="training loads of the learned form")
     ap.add_argument("--learned-test", type=int, default=2, help="held-out loads of the learned form")
+    ap.add_argument("--oracle-sample", type=int, nargs=2, default=None, metavar=("SLAB_CELLS", "ITERS"),
+                    help="internal: print one oracle sample as JSON (run in a subprocess by cpu_baseline)")
     return ap.parse_args()
 
 
@@ -108,17 +110,23 @@ def parse():
 # CPU oracle sample (cpu_baseline and the reference arm)
 # ---------------------------------------------------------------------------
 
+_BEAM_CACHE = {}
+
+
 def oracle_sample(slab_cells=10, iters=40):
     """Time the FP64 oracle, as it stands, on a bounded sample of the
-    workload and scale to one full solve.
+    workload, and estimate one full solve from it.
 
-    Sample: the first `slab_cells` cell layers (x) of the same beam
-    (slab_cells x 40 x 42 cells, same jitter, clamp and material) -> oracle
-    assembly (faces, Eq. 7, Eq. 9, Eq. 12 -> CSR) and `iters` Jacobi-PCG
-    iterations on it.  Full solve = assembly time x (tets ratio) +
-    per-iteration time x (nnz ratio) x the oracle's own iteration count to
+    Sample (what is run and timed): the first `slab_cells` cell layers (x)
+    of the same beam (slab_cells x 40 x 42 cells, same jitter, clamp and
+    material) -> oracle assembly (faces, Eq. 7, Eq. 9, Eq. 12 -> CSR), then
+    `iters` Jacobi-PCG iterations on the slab's system.
+    Estimate (what is scaled): full solve = assembly time x (tets ratio) +
+    time per iteration x (nnz ratio) x the oracle's own iteration count to
     1e-8 on the full beam (tests/golden/beam_2m_reference.json, written by
-    a script that runs only the oracle)."""
+    a script that runs only the oracle).
+    cores_used = process CPU time / wall time over the sample (the threads
+    the oracle actually kept busy)."""
     import numpy as np
     from inputs.kuhn_beam import cantilever
     from oracle import fsfem as F
@@ -126,15 +134,17 @@ def oracle_sample(slab_cells=10, iters=40):
 
     ref = json.load(open(os.path.join(ROOT, "tests", "golden", "beam_2m_reference.json")))
     nx, ny, nz = CELLS
-    full = cantilever(nx, ny, nz, seed=SEED)
+    if "full" not in _BEAM_CACHE:          # the mesh generator is input preparation, not oracle work
+        _BEAM_CACHE["full"] = cantilever(nx, ny, nz, seed=SEED)
+    full = _BEAM_CACHE["full"]
     m = full.mesh
     nslab_nodes = (slab_cells + 1) * (ny + 1) * (nz + 1)
     ntet_slab = slab_cells * ny * nz * 6
     xyz = m.xyz[:nslab_nodes]
     tets = m.tets[:ntet_slab]
-    t0 = time.perf_counter()
+    c0, w0 = time.process_time(), time.perf_counter()
     asm = F.assemble(xyz, tets, full.E, full.nu)
-    t_asm = time.perf_counter() - t0
+    t_asm = time.perf_counter() - w0
     rng = np.random.default_rng(0)
     K = asm.matrix()
     dofs = full.dir_dofs[full.dir_dofs < 3 * nslab_nodes]
@@ -143,24 +153,62 @@ def oracle_sample(slab_cells=10, iters=40):
     t0 = time.perf_counter()
     OS.jacobi_pcg(A, b, tol=1e-300, max_iter=iters, max_restarts=0)
     t_it = (time.perf_counter() - t0) / iters
+    wall = time.perf_counter() - w0
+    cores_used = (time.process_time() - c0) / wall
     n_it = int(ref["iterations_1e-8"])
     t_full = t_asm * (m.n_tets / ntet_slab) + t_it * (ref["nnz"] / asm.indices.size) * n_it
     return {
-        "value": 1.0 / t_full, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
-        "sample": (f"oracle assembly of a {slab_cells}x{ny}x{nz}-cell slab of the beam ({ntet_slab} tets, "
-                   f"{t_asm:.2f} s) and {iters} Jacobi-PCG iterations on it ({t_it * 1e3:.1f} ms each); "
-                   f"scaled to {m.n_tets} tets, {ref['nnz']} nnz and the oracle's {n_it} iterations to 1e-8"),
-        "est_time_to_solve_s": t_full,
-        "threads_note": "numpy/BLAS default threading; scipy sparse products and Python loops single-threaded",
+        "value": 1.0 / t_full, "unit": "solves/s", "cores": round(cores_used, 2), "kind": "oracle",
+        "sample": (f"measured: oracle assembly of a {slab_cells}x{ny}x{nz}-cell slab of the beam ({ntet_slab} "
+                   f"tets, {t_asm:.2f} s) and {iters} Jacobi-PCG iterations on it ({t_it * 1e3:.1f} ms each), "
+                   f"{wall:.2f} s; estimated from it: the full solve, scaled to {m.n_tets} tets, "
+                   f"{ref['nnz']} nnz and the oracle's {n_it} iterations to 1e-8"),
+        "sample_wall_s": wall, "sample_assembly_s": t_asm, "sample_iteration_ms": 1e3 * t_it,
+        "sample_fraction_of_solve": wall / t_full, "est_time_to_solve_s": t_full,
+        "threads_limit": os.environ.get("OMP_NUM_THREADS", "default"),
     }
 
 
+THREAD_VARS = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS")
+
+
+def oracle_sample_subprocess(threads=None, slab_cells=10, iters=40):
+    """oracle_sample in a fresh interpreter (so that the BLAS thread limit
+    takes effect before numpy loads; also keeps the oracle out of a process
+    that holds a CUDA context).  threads=None: the library defaults."""
+    env = dict(os.environ)
+    for k in THREAD_VARS:
+        env.pop(k, None)
+        if threads is not None:
+            env[k] = str(threads)
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-sample", str(slab_cells), str(iters)]
+    r = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=600)
+    if r.returncode != 0:
+        raise RuntimeError(f"oracle sample failed: {r.stderr[-400:]}")
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline_entry():
+    """The oracle timed on the host cores with one thread and with the
+    library defaults (all cores available); the one-thread figure is the
+    reported value."""
+    one = oracle_sample_subprocess(threads=1)
+    allc = oracle_sample_subprocess(threads=None)
+    out = dict(one)
+    out["all_threads"] = {"value": allc["value"], "cores": allc["cores"], "sample_wall_s": allc["sample_wall_s"],
+                          "est_time_to_solve_s": allc["est_time_to_solve_s"], "host_cores": os.cpu_count()}
+    return out
+
+
 def run_reference(args, rank, world):
+    """Reference arm: each step is one oracle sample (oracle_sample), run on
+    the host cores; ms_per_step is the measured wall time of a sample step
+    and value the full-solve throughput estimated from the samples."""
     if rank != 0:
         return
-    res = []
     for _ in range(args.warmup):
         oracle_sample(slab_cells=4, iters=10)
+    res = []
     t0 = time.perf_counter()
     for _ in range(args.steps):
         res.append(oracle_sample())
@@ -170,10 +218,14 @@ def run_reference(args, rank, world):
     cb["value"] = v
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"Kuhn cantilever {CELLS[0]}x{CELLS[1]}x{CELLS[2]} cells x 6 = 2,016,000 tets",
-                   "solver": "oracle Jacobi-PCG (FP64, CPU)", "tol": TOL},
+                   "solver": "oracle Jacobi-PCG (FP64, CPU)", "tol": TOL,
+                   "step": "one oracle sample: slab assembly + 40 Jacobi-PCG iterations (see cpu_baseline)"},
+        "value_note": "value = full solves/s estimated from the timed samples; ms_per_step = measured wall "
+                      "time of one sample step, which does sample_fraction_of_solve of a solve",
+        "est_time_to_solve_s": 1.0 / v,
         "cpu_baseline": cb,
         "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "sample_wall_s": wall,
@@ -413,8 +465,40 @@ def learned_form(S, n_train=8, n_test=2, every=8, epochs=10):
 # our arm
 # ---------------------------------------------------------------------------
 
+COMPARE = ("pcg64_csr_jacobi", "pcg64_mf64_jacobi", "ir32_64_jacobi", "ir32_64_two_level", "fpcg_learned")
+
+
+def compare_keys(forms):
+    """Flat top-level keys for the time-to-solve comparison at rel res 1e-8
+    on the same GPU: tts_<form>_s, it_<form>, relres_<form> (fpcg_learned:
+    the mean over the held-out loads, learned side)."""
+    out = {}
+    for name in COMPARE:
+        f = forms.get(name)
+        if not f or "error" in f:
+            continue
+        if name == "fpcg_learned":
+            rows = f.get("learned") or []
+            if not rows:
+                continue
+            t = sum(r["time_to_solve_s"] for r in rows) / len(rows)
+            it = sum(r["iterations"] for r in rows) / len(rows)
+            rr = max(r["true_relres"] for r in rows)
+            out["fpcg_learned_iteration_gain"] = f.get("iteration_gain")
+            out["fpcg_learned_time_gain"] = f.get("time_gain")
+        else:
+            t, it, rr = f["time_to_solve_s"], f["iterations"], f["true_relres"]
+        out[f"tts_{name}_s"] = t
+        out[f"it_{name}"] = it
+        out[f"relres_{name}"] = rr
+    return out
+
+
 def main():
     args = parse()
+    if args.oracle_sample is not None:
+        print(json.dumps(oracle_sample(*args.oracle_sample)), flush=True)
+        return
     world = _env_int("WORLD_SIZE", 1)
     rank = _env_int("RANK", 0)
     local = _env_int("LOCAL_RANK", 0)
@@ -558,29 +642,38 @@ def main():
             ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             ea.record(stream)
             hh, kk = S.sfem_mesh_setup(*dev[:2], prob.E, prob.nu, *dev[2:], inputs_on_device=True)
-            if assemble:
-                S.sfem_assemble(hh)
-            if precond:
-                S.sfem_coarse_setup(hh, patch_dims=coarse_dims)
-            x = torch.zeros(ndof, dtype=torch.float64, device="cuda")
-            inf = S.sfem_solve(hh, x, S.solve_opts(kind=kind, op64=op64, tol=TOL, u_on_device=True,
-                                                    precond=precond, fp32_vectors=fp32_vectors), check=False)
-            eb.record(stream)
-            torch.cuda.synchronize()
-            out = {"time_to_solve_s": ea.elapsed_time(eb) / 1e3, "iterations": inf["iterations"],
-                   "true_relres": inf["true_relres"], "status": inf["status"], "solve_ms": inf["solve_ms"]}
-            if assemble:
-                out["csr64_apply_ms"] = S.sfem_time_operator(hh, S.SFEM_OP_CSR64, reps=10)
-            S.sfem_destroy(hh)
+            try:
+                if assemble:
+                    S.sfem_assemble(hh)
+                if precond:
+                    S.sfem_coarse_setup(hh, patch_dims=coarse_dims)
+                x = torch.zeros(ndof, dtype=torch.float64, device="cuda")
+                inf = S.sfem_solve(hh, x, S.solve_opts(kind=kind, op64=op64, tol=TOL, u_on_device=True,
+                                                        precond=precond, fp32_vectors=fp32_vectors), check=False)
+                eb.record(stream)
+                torch.cuda.synchronize()
+                out = {"time_to_solve_s": ea.elapsed_time(eb) / 1e3, "iterations": inf["iterations"],
+                       "true_relres": inf["true_relres"], "status": inf["status"], "solve_ms": inf["solve_ms"]}
+                if assemble:
+                    out["csr64_apply_ms"] = S.sfem_time_operator(hh, S.SFEM_OP_CSR64, reps=10)
+            finally:
+                S.sfem_destroy(hh)
             return out
+
+        def guarded(name, *a):
+            """A comparison form that fails with a library status is reported,
+            not fatal to the bench line; a CUDA context error is re-raised."""
+            try:
+                forms[name] = timed_form(*a)
+            except S.SfemError as ex:
+                torch.cuda.synchronize()           # raises if the context itself is broken
+                forms[name] = {"error": str(ex)}
 
         # plain FP64 Jacobi-PCG on the assembled CSR (the paper's method with
         # an iterative solve), then the other forms, each once
         forms["pcg64_csr_jacobi"] = timed_form(S.SFEM_SOLVE_PCG64, S.SFEM_OP_CSR64, 0, True)
-        try:  # the same FP64 Jacobi-PCG on the matrix-free FP64 operator (no assembly)
-            forms["pcg64_mf64_jacobi"] = timed_form(S.SFEM_SOLVE_PCG64, S.SFEM_OP_MF64, 0, False)
-        except Exception as ex:  # a failed comparison form is reported, not fatal to the bench line
-            forms["pcg64_mf64_jacobi"] = {"error": str(ex)}
+        # the same FP64 Jacobi-PCG on the matrix-free FP64 operator (no assembly)
+        guarded("pcg64_mf64_jacobi", S.SFEM_SOLVE_PCG64, S.SFEM_OP_MF64, 0, False)
         forms["pcg64_csr_two_level"] = timed_form(S.SFEM_SOLVE_PCG64, S.SFEM_OP_CSR64, 1, True)
         forms["ir32_64_jacobi"] = timed_form(S.SFEM_SOLVE_IR32_64, S.SFEM_OP_MF64, 0, False)
         forms["ir32_64_two_level_fp64_vectors"] = timed_form(S.SFEM_SOLVE_IR32_64, S.SFEM_OP_MF64, 1, False, 0)
@@ -597,9 +690,9 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
-            cpu = oracle_sample()
+            cpu = cpu_baseline_entry()
         except Exception as ex:  # the oracle is a baseline, not the product
-            cpu = {"value": None, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
+            cpu = {"value": None, "unit": "solves/s", "cores": None, "kind": "oracle",
                    "sample": f"failed: {ex}"}
 
     if rank == 0:
@@ -617,6 +710,7 @@ def main():
                        "l2": "no flush: operator data per step exceeds the 129 MB L2",
                        "parallelism": f"replicas x{world}"},
             "time_to_solve_s": t_dev / args.steps,
+            **compare_keys(forms),
             "iterations": iters, "true_relres_max": relres,
             "operator_gdof_per_s": ndof / (ms_mf32 * 1e-3) / 1e9,
             "operator_gdof_per_s_fp64_vectors": ndof / (ms_mf32_f64 * 1e-3) / 1e9,

@@ -133,7 +133,7 @@ struct TileData {
   int32_t *halo_tet = nullptr;   // halo tets (tile order)
   uint2 *halo_lconn = nullptr;   // their local connectivity (4 x 16 bit)
   int32_t *tile_nodes = nullptr; // node ids per tile, in the order of the slot layout
-  uint32_t *node_inc = nullptr;  // per tile node: slot-0 position | own-slot count << 16
+  uint32_t *node_inc = nullptr;  // per tile node: base of its slot group | own-slot count << 16
   float4 *rec = nullptr;         // 64-byte per-tet records (tile order): V_e grad N_1..3,
                                  // V_e, local connectivity, local neighbours, slot positions
   int max_halo = 0, max_nodes = 0;

@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "reduce.cuh"
 
 namespace sfem {
@@ -18,18 +20,21 @@ constexpr unsigned short kNoNbr = 0xFFFF;
 // Nodal force slots of a tile.  Tile nodes are ordered by their number of
 // own slots (slots 4j+a of the tile's tets j whose vertex a is the node),
 // largest first, and taken in groups of 32 (one warp of the nodal-sum
-// phase).  Slot k of node q lies at position base(q / 32) + 32 k + q % 32 of
-// three float arrays (x, y, z components, stride slot_stride), so the warp
-// summing 32 nodes reads 32 consecutive floats per step, and each tet writes
-// its four slot forces straight to their positions (stored in its record).
-// Per tile node, node_inc holds (position of its slot 0) | (count << 16).
+// phase).  Slot k of node q lies at position
+//   base(q / 32) + 32 k + ((q + k) mod 32)
+// of three float arrays (x, y, z components, stride slot_stride): the warp
+// summing 32 nodes reads one row of 32 banks per step, and the slots of one
+// node fall in different banks, so the tets sharing a node write them
+// without bank conflicts.  Each tet writes its four slot forces straight to
+// their positions (stored in its record).  Per tile node, node_inc holds
+// base(q / 32) | (count << 16).
 struct TileArgs {
   const int32_t *tile_start;
   const int64_t *hoff, *noff;
   const int32_t *halo_tet;
   const uint2 *halo_lconn;
   const int32_t *tile_nodes;
-  const uint32_t *node_inc;  // per tile node: slot-0 position | own-slot count << 16
+  const uint32_t *node_inc;  // per tile node: base of its group | own-slot count << 16
   const float4 *rec;   // 64-byte per-tet records, tile order, as 4 planes of float4 (word 4q..4q+3 of
                        // tet t at rec[q * rs + t]): a warp's loads of one plane are contiguous
   int64_t rs;          // plane stride (the tet count)
@@ -68,18 +73,23 @@ __device__ __forceinline__ void load_rec(const float4 *__restrict__ rec, int64_t
   for (int i = 0; i < 3; ++i) G.g[0][i] = -(G.g[1][i] + G.g[2][i] + G.g[3][i]);
 }
 
-// w = V_e eps_e (Voigt) from the tile's smem displacements; w[6] = V_e
+// w = V_e eps_e (Voigt) from the tile's smem displacements; w[6] = V_e.
+// The gradients of a tet sum to zero, so grad u = sum_{a>=1} (u_a - u_0)
+// (x) grad N_a: the FP32 arithmetic acts on differences of displacements
+// within the tet (no cancellation of a common rigid part).
 __device__ __forceinline__ void strain_to(const float4 *su, uint2 lc, const TetGeo &G, float4 *w2) {
   const int l[4] = {(int)(lc.x & 0xFFFF), (int)(lc.x >> 16), (int)(lc.y & 0xFFFF), (int)(lc.y >> 16)};
   float H[3][3] = {};
+  const float4 u0 = su[l[0]];
 #pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    const float4 u = su[l[a]];
+  for (int a = 1; a < 4; ++a) {
+    const float4 ua = su[l[a]];
+    const float dx = ua.x - u0.x, dy = ua.y - u0.y, dz = ua.z - u0.z;
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-      H[0][j] = fmaf(u.x, G.g[a][j], H[0][j]);
-      H[1][j] = fmaf(u.y, G.g[a][j], H[1][j]);
-      H[2][j] = fmaf(u.z, G.g[a][j], H[2][j]);
+      H[0][j] = fmaf(dx, G.g[a][j], H[0][j]);
+      H[1][j] = fmaf(dy, G.g[a][j], H[1][j]);
+      H[2][j] = fmaf(dz, G.g[a][j], H[2][j]);
     }
   }
   w2[0] = make_float4(H[0][0], H[1][1], H[2][2], H[1][2] + H[2][1]);
@@ -241,16 +251,17 @@ __device__ __forceinline__ float tile_forces(const TileRegs &R, const TileView &
 // the force at tile node i: its own slots summed in a fixed order (the
 // tets' order in the tile) with compensation (the element forces at a node
 // nearly cancel); false when the node has no slot in this tile.  Called by
-// the 32 threads of a node group together, it reads consecutive floats.
+// the 32 threads of a node group together, each step reads one bank row.
 __device__ __forceinline__ bool tile_node_force(const TileView &T, int i, float &fx, float &fy, float &fz) {
   const uint32_t info = T.snode[i];
-  const int b = (int)(info & 0xFFFF), n = (int)(info >> 16);
+  const int b = (int)(info & 0xFFFF), n = (int)(info >> 16), lane = i & 31;
   fx = fy = fz = 0.f;
   if (n == 0) return false;
   float cx = 0.f, cy = 0.f, cz = 0.f;
   const float *px = T.sfx + b, *py = px + T.ns, *pz = py + T.ns;
   for (int k = 0; k < n; ++k) {
-    const float yx = px[32 * k] - cx, yy = py[32 * k] - cy, yz = pz[32 * k] - cz;
+    const int o = 32 * k + ((lane + k) & 31);
+    const float yx = px[o] - cx, yy = py[o] - cy, yz = pz[o] - cz;
     const float tx = fx + yx, ty = fy + yy, tz = fz + yz;
     cx = __fsub_rn(__fsub_rn(tx, fx), yx);
     cy = __fsub_rn(__fsub_rn(ty, fy), yy);
@@ -283,8 +294,11 @@ __device__ __forceinline__ float tile_compute(const TileArgs &A, int tile, const
   // the small tile-local differences instead of the full displacements,
   // which removes most of the cancellation error of the FP32 strains.
   // (With FP32 input the differences of nearby values are exact.)
-  TU ref[3];
-  {
+  // (FP32 input needs no reference: the strains difference FP32 values
+  // within each tet, see strain_to.)
+  constexpr bool kRef = !std::is_same<TU, float>::value;
+  TU ref[3] = {TU(0), TU(0), TU(0)};
+  if (kRef) {
     const TU *rp = u + 3 * (int64_t)A.tile_nodes[T.n0];
 #pragma unroll
     for (int c = 0; c < 3; ++c) ref[c] = kCoherentU ? __ldcg(rp + c) : __ldg(rp + c);

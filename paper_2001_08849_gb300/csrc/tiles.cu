@@ -14,8 +14,9 @@
 //      with one global atomic per component.  The slots are laid out at
 //      setup so that this phase reads shared memory without bank conflicts
 //      and without an index: nodes ordered by slot count and taken 32 at a
-//      time, slot k of a node at (group base) + 32 k + (lane); each tet
-//      writes its four slot forces to positions stored in its record.
+//      time, slot k of a node in bank row k of its group, in a bank rotated
+//      by k; each tet writes its four slot forces to positions stored in
+//      its record.
 // Setup reorders tets by a coarse spatial binning of their centroids
 // (counting sort on a Morton-free lexicographic bin grid), cuts bins into
 // tiles of at most kTileMax tets, and builds per tile: the node list (in
@@ -274,7 +275,7 @@ struct TileBuild {
   int32_t *tile_nodes;
   float4 *rec;   // per-tet records (tile order, 4 planes): lconn -> words 10,11; lnbr -> 12,13; slots -> 14,15
   int64_t rs;    // plane stride
-  uint32_t *node_inc;  // per tile node: slot-0 position | own-slot count << 16
+  uint32_t *node_inc;  // per tile node: base of its slot group | own-slot count << 16
   int *max_slots;      // largest slot-array length over the tiles
   unsigned long long *overflow;
 };
@@ -387,7 +388,7 @@ __global__ void __launch_bounds__(kBuildThreads) k_tile_build(TileBuild B, int p
   for (int q = threadIdx.x; q < L; q += blockDim.x) {
     const int l = key2[q] & 0xFFFF, cnt = 2047 - (key2[q] >> 16);
     B.tile_nodes[n0 + q] = nodes[l];
-    B.node_inc[n0 + q] = (uint32_t)(gbase[q >> 5] + (q & 31)) | ((uint32_t)cnt << 16);
+    B.node_inc[n0 + q] = (uint32_t)gbase[q >> 5] | ((uint32_t)cnt << 16);
   }
   uint16_t *rpos = reinterpret_cast<uint16_t *>(B.rec + 3 * B.rs + s);
   for (int p = threadIdx.x; p < 4 * n_own; p += blockDim.x) {
@@ -395,7 +396,7 @@ __global__ void __launch_bounds__(kBuildThreads) k_tile_build(TileBuild B, int p
     // position goes to record (s + j), 16-bit word 28 + a (words 14, 15)
     const int key = keys[p], l = key >> 11, i = key & 2047;
     const int k = p - start[l], q = jds[l];
-    rpos[(i / 4) * 8 + 4 + (i % 4)] = (uint16_t)(gbase[q >> 5] + 32 * k + (q & 31));
+    rpos[(i / 4) * 8 + 4 + (i % 4)] = (uint16_t)(gbase[q >> 5] + 32 * k + (((q & 31) + k) & 31));
   }
   for (int j = threadIdx.x; j < n_own + H; j += blockDim.x) {
     const int tnew = j < n_own ? s + j : halo[j - n_own];

@@ -336,6 +336,7 @@ extern "C" int sfem_apply(sfem_ctx *h, const void *u, void *y, int op, int nrhs)
       k_fix_rows<float><<<grid, 256, 0, c.stream>>>((float *)y, (const float *)u, c.dmask, c.ndof, n);
       SFEM_CHECK_LAUNCH();
       c.mem.drop(tmp);
+      check_tile_error(c);
     } else if (op == SFEM_OP_MF32_F64) {
       // FP32 arithmetic on FP64 vectors (the operator of the mixed-precision solve)
       double *tmp = c.mem.get<double>(n);
@@ -347,6 +348,7 @@ extern "C" int sfem_apply(sfem_ctx *h, const void *u, void *y, int op, int nrhs)
       k_fix_rows<double><<<grid, 256, 0, c.stream>>>((double *)y, (const double *)u, c.dmask, c.ndof, n);
       SFEM_CHECK_LAUNCH();
       c.mem.drop(tmp);
+      check_tile_error(c);
     } else if (op == SFEM_OP_MF64 || op == SFEM_OP_CSR64 || op == SFEM_OP_NS64 || op == SFEM_OP_ES64) {
       double *tmp = c.mem.get<double>(n);
       k_mask_copy<double><<<grid, 256, 0, c.stream>>>((const double *)u, tmp, c.dmask, c.ndof, n);
@@ -437,6 +439,7 @@ extern "C" int sfem_time_operator(sfem_ctx *h, int op, int reps, double *ms_per_
     *ms_per_apply = (double)ms / reps;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    check_tile_error(c);
     c.mem.drop(u);
     c.mem.drop(y);
     c.mem.drop(energy);

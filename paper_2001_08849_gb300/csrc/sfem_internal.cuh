@@ -138,6 +138,12 @@ struct TileData {
                                  // V_e, local connectivity, local neighbours, slot positions
   int max_halo = 0, max_nodes = 0;
   int slot_stride = 0;           // floats per component array of a tile's force slots
+  // persistent prefetching form of the operator (tiles.cu): shared-memory
+  // layout, grid, and a device word set when one of its waits gave up
+  int pf_capN = 0, pf_capH = 0, pf_capH2 = 0, pf_ibytes = 0, pf_off_i = 0, pf_off_u = 0, pf_off_w = 0;
+  size_t pf_smem = 0;
+  int pf_grid = 0;               // 0: the one-CTA-per-tile form is used
+  int *err = nullptr;
   size_t smem = 0;               // dynamic shared memory of the operator kernel
 };
 
@@ -271,6 +277,8 @@ double device_norm2(Ctx &c, const double *x, int64_t n);
 // setup pieces used by other units
 void compute_diag(Ctx &c);
 void build_tiles(Ctx &c);
+// throws SFEM_ECUDA if a wait of the prefetching tiled operator gave up
+void check_tile_error(Ctx &c);
 // tiled FP32 operator y += K u (y must be zeroed by the caller); u, y of
 // type TU/TY (float or double); the energy u^T K u is added to *energy_out
 // (zeroed by the caller)

@@ -1249,6 +1249,7 @@ extern "C" int sfem_solve(sfem_ctx *h, const double *f_extra, double *u, const s
     SFEM_REQUIRE(h && h->c.vol && h->c.dinv64, SFEM_EINVAL, "context not set up");
     SFEM_REQUIRE(u && opts, SFEM_EINVAL, "u and opts must not be NULL");
     solve_impl(h->c, f_extra, u, *opts, local);
+    check_tile_error(h->c);
   } catch (const Error &err) {
     set_last_error(err.msg);
     local.status = err.status;

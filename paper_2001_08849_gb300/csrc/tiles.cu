@@ -33,9 +33,11 @@
 #include <climits>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 
 #include "reduce.cuh"
 #include "sfem_internal.cuh"
+#include "async.cuh"
 #include "tile_apply.cuh"
 
 namespace sfem {
@@ -451,8 +453,310 @@ __global__ void __launch_bounds__(kTileThreads, 4)
 }
 
 // ---------------------------------------------------------------------------
+// the fused operator, persistent form with prefetch
+// ---------------------------------------------------------------------------
+// Each CTA loops over tiles blockIdx.x, blockIdx.x + gridDim.x, ...  While it
+// computes tile n, the inputs of the next tiles are already on their way
+// into shared memory, so the tile's phases no longer wait on global loads:
+//   * the own-tet records of tile n+1 (four contiguous planes) by bulk
+//     copies, issued once the records of tile n are in registers;
+//   * the index arrays of tile n+2 (node list, node slot info, halo ids,
+//     halo connectivity; contiguous per tile) by bulk copies into one of two
+//     index buffers, issued once tile n has finished with that buffer;
+//   * the displacements of tile n+1 at its nodes, gathered by cp.async as
+//     soon as its index buffer has landed (before tile n's strains).
+// The halo tets' records are still read from global memory in the strain
+// phase (their ids come from shared memory).  The index arrays are
+// allocated with padding so that the copied ranges can start and end on
+// 16-byte boundaries; each buffer records where the tile's entries begin.
+struct PfLayout {
+  int n_tiles;
+  int capN, capH, capH2;  // entries per index-buffer array (nodes/info, halo ids, halo connectivity)
+  int ibytes;             // bytes of one index buffer
+  int off_i, off_u, off_w;  // byte offsets of the index buffers, the displacement buffer, the work area
+};
+
+// index buffer: 8 ints of tile data, then node ids, node slot info, halo
+// ids, halo connectivity
+struct PfTile {
+  int s, n_own, n0, L, h0, H, dn, dh;  // dn, dh: offsets of the tile's first node / halo entry
+};
+
+__device__ __forceinline__ int *pf_nodes(unsigned char *ib) { return reinterpret_cast<int *>(ib + 32); }
+__device__ __forceinline__ uint32_t *pf_info(unsigned char *ib, const PfLayout &P) {
+  return reinterpret_cast<uint32_t *>(ib + 32 + 4 * P.capN);
+}
+__device__ __forceinline__ int *pf_htet(unsigned char *ib, const PfLayout &P) {
+  return reinterpret_cast<int *>(ib + 32 + 8 * P.capN);
+}
+__device__ __forceinline__ uint2 *pf_hlc(unsigned char *ib, const PfLayout &P) {
+  return reinterpret_cast<uint2 *>(ib + 32 + 8 * P.capN + 4 * P.capH);
+}
+
+// thread 0: tile data into the buffer header, index arrays by bulk copies
+__device__ void pf_issue_index(const TileArgs &A, const PfLayout &P, int tile, unsigned char *ib, uint64_t *bar) {
+  PfTile *m = reinterpret_cast<PfTile *>(ib);
+  const int s = A.tile_start[tile];
+  const int64_t n0 = A.noff[tile], n1 = A.noff[tile + 1], h0 = A.hoff[tile], h1 = A.hoff[tile + 1];
+  const int64_t na = n0 & ~int64_t(3), ne = (n1 + 3) & ~int64_t(3);
+  const int64_t ha = h0 & ~int64_t(3), he = (h1 + 3) & ~int64_t(3);
+  const int64_t la = h0 & ~int64_t(1), le = (h1 + 1) & ~int64_t(1);
+  m->s = s;
+  m->n_own = A.tile_start[tile + 1] - s;
+  m->n0 = (int)n0;  // (only its low bits are used: dn)
+  m->L = (int)(n1 - n0);
+  m->h0 = (int)h0;
+  m->H = (int)(h1 - h0);
+  m->dn = (int)(n0 - na);
+  m->dh = (int)(h0 - ha);
+  const uint32_t bn = (uint32_t)(ne - na) * 4u;
+  const uint32_t bh = h1 > h0 ? (uint32_t)(he - ha) * 4u : 0u;
+  const uint32_t bl = h1 > h0 ? (uint32_t)(le - la) * 8u : 0u;
+  mbar_arrive_expect_tx(bar, 2u * bn + bh + bl);
+  bulk_load(pf_nodes(ib), A.tile_nodes + na, bn, bar);
+  bulk_load(pf_info(ib, P), A.node_inc + na, bn, bar);
+  if (bh) {
+    bulk_load(pf_htet(ib, P), A.halo_tet + ha, bh, bar);
+    bulk_load(pf_hlc(ib, P), A.halo_lconn + la, bl, bar);
+  }
+}
+
+// thread 0: the own-tet record planes of a tile by bulk copies
+__device__ void pf_issue_records(const TileArgs &A, int tile, float4 *rb, uint64_t *bar) {
+  const int s = A.tile_start[tile], n_own = A.tile_start[tile + 1] - s;
+  const uint32_t b = (uint32_t)n_own * 16u;
+  mbar_arrive_expect_tx(bar, 4u * b);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) bulk_load(rb + q * kTileMax, A.rec + q * A.rs + s, b, bar);
+}
+
+// all threads: gather u at the tile's nodes (its index buffer has landed)
+template <class TU>
+__device__ __forceinline__ void pf_issue_u(unsigned char *ib, const TU *u, TU *ub) {
+  const PfTile *m = reinterpret_cast<const PfTile *>(ib);
+  const int *nodes = pf_nodes(ib) + m->dn;
+  for (int i = threadIdx.x; i < m->L; i += kTileThreads) {
+    const TU *up = u + 3 * (int64_t)nodes[i];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) cp_async<sizeof(TU)>(ub + 3 * i + c, up + c);
+  }
+  cp_async_commit();
+}
+
+// after a wait that gave up: let this CTA's copies in flight land (bounded)
+__device__ void pf_drain() {
+  cp_async_wait_all();
+  const uint64_t t0 = global_ns();
+  while (global_ns() - t0 < 1000000ull) {
+  }
+}
+
+template <class TU, class TY>
+__global__ void __launch_bounds__(kTileThreads, 2)
+    k_mf32_tiled_pf(TileArgs A, PfLayout P, const TU *__restrict__ u, TY *__restrict__ y, float lam, float mu,
+                    double *energy_out, const int *done, int *err) {
+  if (done && *done) return;
+  extern __shared__ __align__(16) unsigned char sm_pf[];
+  uint64_t *bar = reinterpret_cast<uint64_t *>(sm_pf);  // [0] records, [1], [2] index buffers
+  float4 *rb = reinterpret_cast<float4 *>(sm_pf + 32);  // 4 record planes of kTileMax
+  unsigned char *ib0 = sm_pf + P.off_i;
+  TU *ub = reinterpret_cast<TU *>(sm_pf + P.off_u);
+  float4 *W = reinterpret_cast<float4 *>(sm_pf + P.off_w);
+  __shared__ float s_en[kTileThreads / 32];
+  constexpr bool kRef = !std::is_same<TU, float>::value;  // see tile_compute
+  int tile = blockIdx.x;
+  if (tile >= P.n_tiles) return;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) mbar_init(&bar[k], 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    pf_issue_index(A, P, tile, ib0, &bar[1]);
+    pf_issue_records(A, tile, rb, &bar[0]);
+  }
+  bool failed = __syncthreads_or(!mbar_wait(&bar[1], 0));
+  int next = tile + gridDim.x;
+  if (!failed) {
+    pf_issue_u<TU>(ib0, u, ub);
+    if (threadIdx.x == 0 && next < P.n_tiles) pf_issue_index(A, P, next, ib0 + P.ibytes, &bar[2]);
+  }
+  for (int n = 0; !failed && tile < P.n_tiles; ++n) {
+    const int b = n & 1;
+    unsigned char *ib = ib0 + b * P.ibytes;
+    const PfTile m = *reinterpret_cast<const PfTile *>(ib);
+    // this tile's records -> registers; its displacements have landed
+    const bool rec_ok = mbar_wait(&bar[0], n & 1);
+    TileRegs R;
+#pragma unroll
+    for (int r = 0; r < kTilePer; ++r) {
+      const int j = threadIdx.x + r * kTileThreads;
+      if (j < m.n_own) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) R.rr[r][q] = rb[q * kTileMax + j];
+      }
+    }
+    cp_async_wait_all();
+    if (__syncthreads_or(!rec_ok)) {
+      failed = true;
+      break;
+    }
+    if (threadIdx.x == 0 && next < P.n_tiles) {
+      fence_proxy_async_smem();
+      pf_issue_records(A, next, rb, &bar[0]);
+    }
+    TileView T;
+    T.n_own = m.n_own;
+    T.H = m.H;
+    T.L = m.L;
+    T.nt = m.n_own + m.H;
+    T.ns = A.slot_stride;
+    T.h0 = m.h0;
+    T.n0 = 0;
+    T.su = W;
+    T.sfx = reinterpret_cast<float *>(W);
+    T.swa = W + tile_slot_words(T.L, T.ns);
+    T.swb = T.swa + T.nt;
+    T.snode = pf_info(ib, P) + m.dn;
+    {
+      const TU r0 = kRef ? ub[0] : TU(0), r1 = kRef ? ub[1] : TU(0), r2 = kRef ? ub[2] : TU(0);
+      for (int i = threadIdx.x; i < T.L; i += kTileThreads)
+        T.su[i] = make_float4((float)(ub[3 * i] - r0), (float)(ub[3 * i + 1] - r1), (float)(ub[3 * i + 2] - r2),
+                              0.f);
+    }
+    __syncthreads();
+    // the next tile's displacements, once its index buffer has landed
+    if (next < P.n_tiles) {
+      if (__syncthreads_or(!mbar_wait(&bar[1 + (b ^ 1)], ((n + 1) >> 1) & 1))) {
+        failed = true;
+        break;
+      }
+      pf_issue_u<TU>(ib0 + (b ^ 1) * P.ibytes, u, ub);
+    }
+    // strains of the own tets (records in registers) and the halo tets
+#pragma unroll
+    for (int r = 0; r < kTilePer; ++r) {
+      const int j = threadIdx.x + r * kTileThreads;
+      if (j < T.n_own) {
+        TetGeo G;
+        uint2 lc;
+        rec_unpack(R.rr[r], G, lc);
+        float4 w2[2];
+        strain_to(T.su, lc, G, w2);
+        T.swa[j] = w2[0];
+        T.swb[j] = w2[1];
+      }
+    }
+    {
+      const int *htet = pf_htet(ib, P) + m.dh;
+      const uint2 *hlc = pf_hlc(ib, P) + (m.h0 & 1);
+      for (int h = threadIdx.x; h < T.H; h += kTileThreads) {
+        TetGeo G;
+        uint2 lc;
+        load_rec(A.rec, A.rs, htet[h], G, lc, nullptr);
+        lc = hlc[h];
+        float4 w2[2];
+        strain_to(T.su, lc, G, w2);
+        T.swa[T.n_own + h] = w2[0];
+        T.swb[T.n_own + h] = w2[1];
+      }
+    }
+    __syncthreads();
+    const float en = tile_forces(R, T, lam, mu);
+    if (energy_out) {  // FP32 within the tile, FP64 across tiles
+      float e = en;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(0xffffffffu, e, o);
+      if ((threadIdx.x & 31) == 0) s_en[threadIdx.x >> 5] = e;
+    }
+    __syncthreads();
+    if (energy_out && threadIdx.x == 0) {
+      float e = 0.f;
+#pragma unroll
+      for (int w = 0; w < kTileThreads / 32; ++w) e += s_en[w];
+      atomicAdd(energy_out, (double)e);
+    }
+    {
+      const int *nodes = pf_nodes(ib) + m.dn;
+      for (int i = threadIdx.x; i < T.L; i += kTileThreads) {
+        float fx, fy, fz;
+        if (!tile_node_force(T, i, fx, fy, fz)) continue;
+        TY *yp = y + 3 * (int64_t)nodes[i];
+        atomicAdd(yp, (TY)fx);
+        atomicAdd(yp + 1, (TY)fy);
+        atomicAdd(yp + 2, (TY)fz);
+      }
+    }
+    __syncthreads();
+    // index buffer b is free: the indices of the tile after next
+    const int next2 = next + gridDim.x;
+    if (threadIdx.x == 0 && next2 < P.n_tiles) {
+      fence_proxy_async_smem();
+      pf_issue_index(A, P, next2, ib, &bar[1 + b]);
+    }
+    tile = next;
+    next = next2;
+  }
+  if (failed) {
+    if (threadIdx.x == 0) atomicExch(err, 1);
+    pf_drain();
+  }
+}
+
+// ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
+static int align_up(int x, int a) { return (x + a - 1) / a * a; }
+
+// shared-memory layout and grid of the prefetching operator; it is used when
+// two CTAs fit on an SM, else the one-CTA-per-tile kernel stays in use
+static void setup_prefetch(Ctx &c) {
+  TileData &t = c.tl;
+  t.pf_capN = align_up(t.max_nodes + 6, 4);
+  t.pf_capH = align_up(t.max_halo + 6, 4);
+  t.pf_capH2 = align_up(t.max_halo + 2, 2);
+  t.pf_ibytes = align_up(32 + 8 * t.pf_capN + 4 * t.pf_capH + 8 * t.pf_capH2, 16);
+  t.pf_off_i = 32 + 4 * kTileMax * (int)sizeof(float4);
+  t.pf_off_u = t.pf_off_i + 2 * t.pf_ibytes;
+  t.pf_off_w = align_up(t.pf_off_u + 3 * t.max_nodes * (int)sizeof(double), 16);
+  t.pf_smem = (size_t)t.pf_off_w + (size_t)tile_slot_words(t.max_nodes, t.slot_stride) * sizeof(float4) +
+              (size_t)(kTileMax + t.max_halo) * 2 * sizeof(float4);
+  if (!t.err) {
+    t.err = c.mem.get<int>(1);
+    SFEM_CUDA(cudaMemsetAsync(t.err, 0, sizeof(int), c.stream));
+  }
+  t.pf_grid = 0;
+  if (t.pf_smem > 227 * 1024) return;
+  static size_t pf_smem_set = 0;
+  if (t.pf_smem > pf_smem_set) {
+    SFEM_CUDA(cudaFuncSetAttribute(k_mf32_tiled_pf<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)t.pf_smem));
+    SFEM_CUDA(cudaFuncSetAttribute(k_mf32_tiled_pf<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)t.pf_smem));
+    pf_smem_set = t.pf_smem;
+  }
+  int per_sm = 0, nsm = 0, dev = 0;
+  SFEM_CUDA(cudaGetDevice(&dev));
+  SFEM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  SFEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mf32_tiled_pf<float, float>, kTileThreads,
+                                                          t.pf_smem));
+  if (per_sm < 2) return;
+  t.pf_grid = (int)std::min<int64_t>(t.n_tiles, (int64_t)per_sm * nsm);
+}
+
+// a wait of the prefetching operator gave up (reported once, then cleared)
+void check_tile_error(Ctx &c) {
+  if (!c.tl.err) return;
+  int h = 0;
+  SFEM_CUDA(cudaMemcpyAsync(&h, c.tl.err, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+  SFEM_CUDA(cudaStreamSynchronize(c.stream));
+  if (h) {
+    SFEM_CUDA(cudaMemsetAsync(c.tl.err, 0, sizeof(int), c.stream));
+    throw Error{SFEM_ECUDA, "the tiled operator's asynchronous copies did not complete in time"};
+  }
+}
+
 void build_tiles(Ctx &c) {
   const int64_t n = c.n_tets;
   // bounding box and bin grid (mean bin holds about kTileTarget tets)
@@ -555,10 +859,11 @@ void build_tiles(Ctx &c) {
   SFEM_REQUIRE(hovf == 0, SFEM_EMESH, "tile tables exceed their local index ranges");
   c.tl.max_halo = hm[0];
   c.tl.max_nodes = hm[1];
-  c.tl.halo_tet = c.mem.get<int32_t>(std::max<int64_t>(total_h, 1));
-  c.tl.halo_lconn = c.mem.get<uint2>(std::max<int64_t>(total_h, 1));
-  c.tl.tile_nodes = c.mem.get<int32_t>(total_n);
-  c.tl.node_inc = c.mem.get<uint32_t>(total_n);
+  // (padded: the prefetching operator copies 16-byte aligned ranges)
+  c.tl.halo_tet = c.mem.get<int32_t>(std::max<int64_t>(total_h, 1) + 4);
+  c.tl.halo_lconn = c.mem.get<uint2>(std::max<int64_t>(total_h, 1) + 2);
+  c.tl.tile_nodes = c.mem.get<int32_t>(total_n + 4);
+  c.tl.node_inc = c.mem.get<uint32_t>(total_n + 4);
   B.hoff = c.tl.hoff;
   B.noff = c.tl.noff;
   B.halo_tet = c.tl.halo_tet;
@@ -585,6 +890,7 @@ void build_tiles(Ctx &c) {
   SFEM_REQUIRE(c.tl.smem <= 220 * 1024, SFEM_EMESH, "tile working set exceeds shared memory");
   c.tl.total_halo = total_h;
   c.tl.total_nodes = total_n;
+  setup_prefetch(c);
   // opt in to the dynamic shared memory this mesh needs (never lowered, so
   // contexts of smaller meshes keep working)
   static size_t smem_set = 48 * 1024;
@@ -610,8 +916,15 @@ template <class TU, class TY>
 void launch_mf32_tiled(Ctx &c, cudaStream_t st, const TU *u, TY *y, double *energy_out, const int *done) {
   TileArgs A{c.tl.tile_start, c.tl.hoff, c.tl.noff, c.tl.halo_tet, c.tl.halo_lconn, c.tl.tile_nodes,
              c.tl.node_inc, c.tl.rec, c.n_tets, c.tl.slot_stride};
-  k_mf32_tiled<TU, TY><<<(unsigned)c.tl.n_tiles, kTileThreads, c.tl.smem, st>>>(
-      A, u, y, (float)c.lam, (float)c.mu, energy_out, done);
+  if (c.tl.pf_grid > 0) {
+    const PfLayout P{(int)c.tl.n_tiles, c.tl.pf_capN,  c.tl.pf_capH,  c.tl.pf_capH2,
+                     c.tl.pf_ibytes,    c.tl.pf_off_i, c.tl.pf_off_u, c.tl.pf_off_w};
+    k_mf32_tiled_pf<TU, TY><<<(unsigned)c.tl.pf_grid, kTileThreads, c.tl.pf_smem, st>>>(
+        A, P, u, y, (float)c.lam, (float)c.mu, energy_out, done, c.tl.err);
+  } else {
+    k_mf32_tiled<TU, TY><<<(unsigned)c.tl.n_tiles, kTileThreads, c.tl.smem, st>>>(A, u, y, (float)c.lam,
+                                                                                 (float)c.mu, energy_out, done);
+  }
   SFEM_CHECK_LAUNCH();
 }
 

@@ -461,6 +461,16 @@ int sfem_time_operator(sfem_ctx *ctx, int op, int reps, double *ms_per_apply);
 int sfem_selftest_barrier(sfem_ctx *ctx, int *status, double *wait_ms);
 int64_t sfem_launch_count(void);
 
+/* sfem_tile_info — diagnostic (no counterpart in the paper): the layout of
+ * the FP32 tiled operator of a context.  Writes up to n of, in order:
+ *   [0] tiles, [1] largest halo (tets), [2] largest node list, [3] length of
+ *   a tile's force-slot arrays, [4] total halo tets, [5] total tile nodes,
+ *   [6] shared memory of the one-CTA-per-tile kernel (bytes), [7] shared
+ *   memory of the persistent prefetching kernel (bytes), [8] its grid (0:
+ *   the one-CTA-per-tile kernel runs instead).
+ * Returns SFEM_EINVAL for a context without setup, a NULL out or n < 1. */
+int sfem_tile_info(sfem_ctx *ctx, int64_t *out, int n);
+
 void sfem_destroy(sfem_ctx *ctx);
 const char *sfem_strerror(int status);
 const char *sfem_last_error(void);

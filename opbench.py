@@ -95,7 +95,7 @@ def main(argv=None):
             out = {"op": a.op, "cells": a.cells, "n_tets": n_tets, "ndof": ctx.ndof, "ms_per_apply": ms,
                    "gdof_per_s": ctx.ndof / ms / 1e6,
                    "alg_bytes_mf32": 72 * n_tets + (16 if a.op == "mf32f64" else 8) * ctx.ndof,
-                   "tiled_source_sha256": tiled_source_sha()}
+                   "tiled_source_sha256": tiled_source_sha(), "tiles": S.sfem_tile_info(ctx.h)}
         else:
             model = None
             coarse = None

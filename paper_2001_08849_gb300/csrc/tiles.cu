@@ -933,3 +933,19 @@ template void launch_mf32_tiled<double, double>(Ctx &, cudaStream_t, const doubl
                                                 const int *);
 
 }  // namespace sfem
+
+extern "C" int sfem_tile_info(sfem_ctx *h, int64_t *out, int n) {
+  using namespace sfem;
+  try {
+    SFEM_REQUIRE(h && h->c.vol && out && n >= 1, SFEM_EINVAL, "bad arguments");
+    const TileData &t = h->c.tl;
+    SFEM_REQUIRE(t.ready, SFEM_EINVAL, "the tiled operator is not set up");
+    const int64_t v[9] = {t.n_tiles,     t.max_halo,    t.max_nodes,        t.slot_stride, t.total_halo,
+                          t.total_nodes, (int64_t)t.smem, (int64_t)t.pf_smem, t.pf_grid};
+    for (int i = 0; i < n && i < 9; ++i) out[i] = v[i];
+  } catch (const Error &err) {
+    set_last_error(err.msg);
+    return err.status;
+  }
+  return SFEM_OK;
+}

@@ -112,6 +112,7 @@ _SIG = {
     "sfem_version": (ctypes.c_int, []),
     "sfem_time_operator": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "sfem_launch_count": (ctypes.c_int64, []),
+    "sfem_tile_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64), ctypes.c_int]),
     "sfem_apply_noalloc": (ctypes.c_int, [_P, _P, _P]),
     "sfem_batch_solve": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(_P),
                                         ctypes.POINTER(sfem_batch_opts), ctypes.POINTER(sfem_solve_info),
@@ -408,6 +409,18 @@ def sfem_time_operator(h, op=SFEM_OP_MF32, reps=20) -> float:
 
 def sfem_launch_count() -> int:
     return int(lib.sfem_launch_count())
+
+
+TILE_INFO_KEYS = ("n_tiles", "max_halo", "max_nodes", "slot_stride", "total_halo", "total_nodes",
+                  "smem_per_tile_cta", "smem_prefetch_cta", "prefetch_grid")
+
+
+def sfem_tile_info(h) -> dict:
+    """Layout of the FP32 tiled operator and which of its two kernels runs
+    (see include/sfem.h)."""
+    out = (ctypes.c_int64 * len(TILE_INFO_KEYS))()
+    _check(lib.sfem_tile_info(h, out, len(TILE_INFO_KEYS)), "sfem_tile_info")
+    return dict(zip(TILE_INFO_KEYS, (int(v) for v in out)))
 
 
 def sfem_strerror(status: int) -> str:

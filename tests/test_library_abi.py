@@ -47,6 +47,7 @@ def test_argument_checks_without_gpu(S):
     # null handles
     assert S.lib.sfem_apply(None, None, None, 0, 1) == S.SFEM_EINVAL
     assert S.lib.sfem_apply_noalloc(None, None, None) == S.SFEM_EINVAL
+    assert S.lib.sfem_tile_info(None, None, 1) == S.SFEM_EINVAL
     assert S.lib.sfem_assemble(None, None) == S.SFEM_EINVAL
     assert S.lib.sfem_solve(None, None, None, None, None) == S.SFEM_EINVAL
     S.lib.sfem_destroy(None)

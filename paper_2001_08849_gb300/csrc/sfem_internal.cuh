@@ -143,6 +143,7 @@ struct TileData {
   int pf_capN = 0, pf_capH = 0, pf_capH2 = 0, pf_ibytes = 0, pf_off_i = 0, pf_off_u = 0, pf_off_w = 0;
   size_t pf_smem = 0;
   int pf_grid = 0;               // 0: the one-CTA-per-tile form is used
+  int pf_threads = 0;            // threads per CTA of the persistent form (256 or 512)
   int *err = nullptr;
   size_t smem = 0;               // dynamic shared memory of the operator kernel
 };

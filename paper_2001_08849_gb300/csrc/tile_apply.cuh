@@ -97,10 +97,14 @@ __device__ __forceinline__ void strain_to(const float4 *su, uint2 lc, const TetG
 }
 
 // own-tet records of a tile, kept in registers for both phases (and for
-// every right-hand side of a batched apply)
-struct TileRegs {
-  float4 rr[kTilePer][4];
+// every right-hand side of a batched apply); NT threads per tile, tet
+// threadIdx.x + r NT in rr[r]
+template <int NT>
+struct TileRegsT {
+  static constexpr int kPer = kTileMax / NT;
+  float4 rr[kPer][4];
 };
+using TileRegs = TileRegsT<kTileThreads>;
 
 __device__ __forceinline__ void tile_load(const TileArgs &A, int tile, TileRegs &R) {
   const int s = A.tile_start[tile], n_own = A.tile_start[tile + 1] - s;
@@ -198,11 +202,12 @@ __device__ __forceinline__ void tile_strains(const TileArgs &A, const TileRegs &
 
 // face-averaged stress of every own tet and its four nodal force slots;
 // returns this thread's share of the energy sum w . t
-__device__ __forceinline__ float tile_forces(const TileRegs &R, const TileView &T, float lam, float mu) {
-  float en = 0.f;  // this thread's kTilePer tets
+template <int NT = kTileThreads>
+__device__ __forceinline__ float tile_forces(const TileRegsT<NT> &R, const TileView &T, float lam, float mu) {
+  float en = 0.f;  // this thread's tets
 #pragma unroll
-  for (int r = 0; r < kTilePer; ++r) {
-    const int j = threadIdx.x + r * kTileThreads;
+  for (int r = 0; r < TileRegsT<NT>::kPer; ++r) {
+    const int j = threadIdx.x + r * NT;
     if (j >= T.n_own) continue;
     TetGeo G;
     uint2 lc;

@@ -531,11 +531,11 @@ __device__ void pf_issue_records(const TileArgs &A, int tile, float4 *rb, uint64
 }
 
 // all threads: gather u at the tile's nodes (its index buffer has landed)
-template <class TU>
+template <class TU, int NT>
 __device__ __forceinline__ void pf_issue_u(unsigned char *ib, const TU *u, TU *ub) {
   const PfTile *m = reinterpret_cast<const PfTile *>(ib);
   const int *nodes = pf_nodes(ib) + m->dn;
-  for (int i = threadIdx.x; i < m->L; i += kTileThreads) {
+  for (int i = threadIdx.x; i < m->L; i += NT) {
     const TU *up = u + 3 * (int64_t)nodes[i];
 #pragma unroll
     for (int c = 0; c < 3; ++c) cp_async<sizeof(TU)>(ub + 3 * i + c, up + c);
@@ -551,10 +551,12 @@ __device__ void pf_drain() {
   }
 }
 
-template <class TU, class TY>
-__global__ void __launch_bounds__(kTileThreads, 2)
+// NT threads per CTA (256 or 512), two CTAs per SM
+template <class TU, class TY, int NT>
+__global__ void __launch_bounds__(NT, 2)
     k_mf32_tiled_pf(TileArgs A, PfLayout P, const TU *__restrict__ u, TY *__restrict__ y, float lam, float mu,
                     double *energy_out, const int *done, int *err) {
+  using Regs = TileRegsT<NT>;
   if (done && *done) return;
   extern __shared__ __align__(16) unsigned char sm_pf[];
   uint64_t *bar = reinterpret_cast<uint64_t *>(sm_pf);  // [0] records, [1], [2] index buffers
@@ -562,7 +564,7 @@ __global__ void __launch_bounds__(kTileThreads, 2)
   unsigned char *ib0 = sm_pf + P.off_i;
   TU *ub = reinterpret_cast<TU *>(sm_pf + P.off_u);
   float4 *W = reinterpret_cast<float4 *>(sm_pf + P.off_w);
-  __shared__ float s_en[kTileThreads / 32];
+  __shared__ float s_en[NT / 32];
   constexpr bool kRef = !std::is_same<TU, float>::value;  // see tile_compute
   int tile = blockIdx.x;
   if (tile >= P.n_tiles) return;
@@ -579,7 +581,7 @@ __global__ void __launch_bounds__(kTileThreads, 2)
   bool failed = __syncthreads_or(!mbar_wait(&bar[1], 0));
   int next = tile + gridDim.x;
   if (!failed) {
-    pf_issue_u<TU>(ib0, u, ub);
+    pf_issue_u<TU, NT>(ib0, u, ub);
     if (threadIdx.x == 0 && next < P.n_tiles) pf_issue_index(A, P, next, ib0 + P.ibytes, &bar[2]);
   }
   for (int n = 0; !failed && tile < P.n_tiles; ++n) {
@@ -588,10 +590,10 @@ __global__ void __launch_bounds__(kTileThreads, 2)
     const PfTile m = *reinterpret_cast<const PfTile *>(ib);
     // this tile's records -> registers; its displacements have landed
     const bool rec_ok = mbar_wait(&bar[0], n & 1);
-    TileRegs R;
+    Regs R;
 #pragma unroll
-    for (int r = 0; r < kTilePer; ++r) {
-      const int j = threadIdx.x + r * kTileThreads;
+    for (int r = 0; r < Regs::kPer; ++r) {
+      const int j = threadIdx.x + r * NT;
       if (j < m.n_own) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) R.rr[r][q] = rb[q * kTileMax + j];
@@ -621,7 +623,7 @@ __global__ void __launch_bounds__(kTileThreads, 2)
     T.snode = pf_info(ib, P) + m.dn;
     {
       const TU r0 = kRef ? ub[0] : TU(0), r1 = kRef ? ub[1] : TU(0), r2 = kRef ? ub[2] : TU(0);
-      for (int i = threadIdx.x; i < T.L; i += kTileThreads)
+      for (int i = threadIdx.x; i < T.L; i += NT)
         T.su[i] = make_float4((float)(ub[3 * i] - r0), (float)(ub[3 * i + 1] - r1), (float)(ub[3 * i + 2] - r2),
                               0.f);
     }
@@ -632,12 +634,12 @@ __global__ void __launch_bounds__(kTileThreads, 2)
         failed = true;
         break;
       }
-      pf_issue_u<TU>(ib0 + (b ^ 1) * P.ibytes, u, ub);
+      pf_issue_u<TU, NT>(ib0 + (b ^ 1) * P.ibytes, u, ub);
     }
     // strains of the own tets (records in registers) and the halo tets
 #pragma unroll
-    for (int r = 0; r < kTilePer; ++r) {
-      const int j = threadIdx.x + r * kTileThreads;
+    for (int r = 0; r < Regs::kPer; ++r) {
+      const int j = threadIdx.x + r * NT;
       if (j < T.n_own) {
         TetGeo G;
         uint2 lc;
@@ -651,7 +653,7 @@ __global__ void __launch_bounds__(kTileThreads, 2)
     {
       const int *htet = pf_htet(ib, P) + m.dh;
       const uint2 *hlc = pf_hlc(ib, P) + (m.h0 & 1);
-      for (int h = threadIdx.x; h < T.H; h += kTileThreads) {
+      for (int h = threadIdx.x; h < T.H; h += NT) {
         TetGeo G;
         uint2 lc;
         load_rec(A.rec, A.rs, htet[h], G, lc, nullptr);
@@ -663,7 +665,7 @@ __global__ void __launch_bounds__(kTileThreads, 2)
       }
     }
     __syncthreads();
-    const float en = tile_forces(R, T, lam, mu);
+    const float en = tile_forces<NT>(R, T, lam, mu);
     if (energy_out) {  // FP32 within the tile, FP64 across tiles
       float e = en;
 #pragma unroll
@@ -674,12 +676,12 @@ __global__ void __launch_bounds__(kTileThreads, 2)
     if (energy_out && threadIdx.x == 0) {
       float e = 0.f;
 #pragma unroll
-      for (int w = 0; w < kTileThreads / 32; ++w) e += s_en[w];
+      for (int w = 0; w < NT / 32; ++w) e += s_en[w];
       atomicAdd(energy_out, (double)e);
     }
     {
       const int *nodes = pf_nodes(ib) + m.dn;
-      for (int i = threadIdx.x; i < T.L; i += kTileThreads) {
+      for (int i = threadIdx.x; i < T.L; i += NT) {
         float fx, fy, fz;
         if (!tile_node_force(T, i, fx, fy, fz)) continue;
         TY *yp = y + 3 * (int64_t)nodes[i];
@@ -727,21 +729,39 @@ static void setup_prefetch(Ctx &c) {
     SFEM_CUDA(cudaMemsetAsync(t.err, 0, sizeof(int), c.stream));
   }
   t.pf_grid = 0;
+  t.pf_threads = 0;
   if (t.pf_smem > 227 * 1024) return;
   static size_t pf_smem_set = 0;
   if (t.pf_smem > pf_smem_set) {
-    SFEM_CUDA(cudaFuncSetAttribute(k_mf32_tiled_pf<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    SFEM_CUDA(cudaFuncSetAttribute(k_mf32_tiled_pf<float, float, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)t.pf_smem));
-    SFEM_CUDA(cudaFuncSetAttribute(k_mf32_tiled_pf<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    SFEM_CUDA(cudaFuncSetAttribute(k_mf32_tiled_pf<double, double, 512>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.pf_smem));
+    SFEM_CUDA(cudaFuncSetAttribute(k_mf32_tiled_pf<float, float, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)t.pf_smem));
+    SFEM_CUDA(cudaFuncSetAttribute(k_mf32_tiled_pf<double, double, 256>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.pf_smem));
     pf_smem_set = t.pf_smem;
   }
-  int per_sm = 0, nsm = 0, dev = 0;
+  int nsm = 0, dev = 0;
   SFEM_CUDA(cudaGetDevice(&dev));
   SFEM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  SFEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mf32_tiled_pf<float, float>, kTileThreads,
+  // 512 threads (one tet each) where two such CTAs fit on an SM, else 256
+  int per512 = 0, per256 = 0;
+  SFEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per512, k_mf32_tiled_pf<float, float, 512>, 512,
                                                           t.pf_smem));
-  if (per_sm < 2) return;
+  SFEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per256, k_mf32_tiled_pf<float, float, 256>, 256,
+                                                          t.pf_smem));
+  int per_sm = 0;
+  if (per512 >= 2) {
+    t.pf_threads = 512;
+    per_sm = per512;
+  } else if (per256 >= 2) {
+    t.pf_threads = 256;
+    per_sm = per256;
+  } else {
+    return;
+  }
   t.pf_grid = (int)std::min<int64_t>(t.n_tiles, (int64_t)per_sm * nsm);
 }
 
@@ -919,8 +939,12 @@ void launch_mf32_tiled(Ctx &c, cudaStream_t st, const TU *u, TY *y, double *ener
   if (c.tl.pf_grid > 0) {
     const PfLayout P{(int)c.tl.n_tiles, c.tl.pf_capN,  c.tl.pf_capH,  c.tl.pf_capH2,
                      c.tl.pf_ibytes,    c.tl.pf_off_i, c.tl.pf_off_u, c.tl.pf_off_w};
-    k_mf32_tiled_pf<TU, TY><<<(unsigned)c.tl.pf_grid, kTileThreads, c.tl.pf_smem, st>>>(
-        A, P, u, y, (float)c.lam, (float)c.mu, energy_out, done, c.tl.err);
+    if (c.tl.pf_threads == 512)
+      k_mf32_tiled_pf<TU, TY, 512><<<(unsigned)c.tl.pf_grid, 512, c.tl.pf_smem, st>>>(
+          A, P, u, y, (float)c.lam, (float)c.mu, energy_out, done, c.tl.err);
+    else
+      k_mf32_tiled_pf<TU, TY, 256><<<(unsigned)c.tl.pf_grid, 256, c.tl.pf_smem, st>>>(
+          A, P, u, y, (float)c.lam, (float)c.mu, energy_out, done, c.tl.err);
   } else {
     k_mf32_tiled<TU, TY><<<(unsigned)c.tl.n_tiles, kTileThreads, c.tl.smem, st>>>(A, u, y, (float)c.lam,
                                                                                  (float)c.mu, energy_out, done);
@@ -940,9 +964,9 @@ extern "C" int sfem_tile_info(sfem_ctx *h, int64_t *out, int n) {
     SFEM_REQUIRE(h && h->c.vol && out && n >= 1, SFEM_EINVAL, "bad arguments");
     const TileData &t = h->c.tl;
     SFEM_REQUIRE(t.ready, SFEM_EINVAL, "the tiled operator is not set up");
-    const int64_t v[9] = {t.n_tiles,     t.max_halo,    t.max_nodes,        t.slot_stride, t.total_halo,
-                          t.total_nodes, (int64_t)t.smem, (int64_t)t.pf_smem, t.pf_grid};
-    for (int i = 0; i < n && i < 9; ++i) out[i] = v[i];
+    const int64_t v[10] = {t.n_tiles,     t.max_halo,      t.max_nodes,        t.slot_stride, t.total_halo,
+                           t.total_nodes, (int64_t)t.smem, (int64_t)t.pf_smem, t.pf_grid,    t.pf_threads};
+    for (int i = 0; i < n && i < 10; ++i) out[i] = v[i];
   } catch (const Error &err) {
     set_last_error(err.msg);
     return err.status;

@@ -412,7 +412,7 @@ def sfem_launch_count() -> int:
 
 
 TILE_INFO_KEYS = ("n_tiles", "max_halo", "max_nodes", "slot_stride", "total_halo", "total_nodes",
-                  "smem_per_tile_cta", "smem_prefetch_cta", "prefetch_grid")
+                  "smem_per_tile_cta", "smem_prefetch_cta", "prefetch_grid", "prefetch_threads")
 
 
 def sfem_tile_info(h) -> dict:

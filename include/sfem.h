@@ -466,8 +466,9 @@ int64_t sfem_launch_count(void);
  *   [0] tiles, [1] largest halo (tets), [2] largest node list, [3] length of
  *   a tile's force-slot arrays, [4] total halo tets, [5] total tile nodes,
  *   [6] shared memory of the one-CTA-per-tile kernel (bytes), [7] shared
- *   memory of the persistent prefetching kernel (bytes), [8] its grid (0:
- *   the one-CTA-per-tile kernel runs instead), [9] its threads per CTA.
+ *   memory of the persistent prefetching kernel for FP32 vectors (bytes),
+ *   [8] its grid (0: the one-CTA-per-tile kernel runs instead), [9] its
+ *   threads per CTA.
  * Returns SFEM_EINVAL for a context without setup, a NULL out or n < 1. */
 int sfem_tile_info(sfem_ctx *ctx, int64_t *out, int n);
 

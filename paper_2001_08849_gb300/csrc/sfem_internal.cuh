@@ -140,10 +140,12 @@ struct TileData {
   int slot_stride = 0;           // floats per component array of a tile's force slots
   // persistent prefetching form of the operator (tiles.cu): shared-memory
   // layout, grid, and a device word set when one of its waits gave up
-  int pf_capN = 0, pf_capH = 0, pf_capH2 = 0, pf_ibytes = 0, pf_off_i = 0, pf_off_u = 0, pf_off_w = 0;
-  size_t pf_smem = 0;
-  int pf_grid = 0;               // 0: the one-CTA-per-tile form is used
-  int pf_threads = 0;            // threads per CTA of the persistent form (256 or 512)
+  int pf_capN = 0, pf_capH = 0, pf_capH2 = 0, pf_capR = 0, pf_ibytes = 0, pf_off_i = 0, pf_off_h = 0,
+      pf_off_u = 0;
+  int pf_off_w[2] = {0, 0};      // [0] FP32 input, [1] FP64 input
+  size_t pf_smem[2] = {0, 0};
+  int pf_grid[2] = {0, 0};       // 0: the one-CTA-per-tile form is used
+  int pf_threads[2] = {0, 0};    // threads per CTA of the persistent form (256 or 512)
   int *err = nullptr;
   size_t smem = 0;               // dynamic shared memory of the operator kernel
 };

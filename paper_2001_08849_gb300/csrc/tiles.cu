@@ -473,7 +473,8 @@ struct PfLayout {
   int n_tiles;
   int capN, capH, capH2;  // entries per index-buffer array (nodes/info, halo ids, halo connectivity)
   int ibytes;             // bytes of one index buffer
-  int off_i, off_u, off_w;  // byte offsets of the index buffers, the displacement buffer, the work area
+  int capR;               // halo records per halo buffer plane
+  int off_i, off_h, off_u, off_w;  // byte offsets: index buffers, halo records, displacements, work area
 };
 
 // index buffer: 8 ints of tile data, then node ids, node slot info, halo
@@ -481,6 +482,23 @@ struct PfLayout {
 struct PfTile {
   int s, n_own, n0, L, h0, H, dn, dh;  // dn, dh: offsets of the tile's first node / halo entry
 };
+
+// tile ranges of one tile, read by the issuing thread a whole tile ahead
+struct PfMeta {
+  int s, e;
+  int64_t n0, n1, h0, h1;
+};
+
+__device__ __forceinline__ PfMeta pf_meta(const TileArgs &A, int tile) {
+  PfMeta m;
+  m.s = A.tile_start[tile];
+  m.e = A.tile_start[tile + 1];
+  m.n0 = A.noff[tile];
+  m.n1 = A.noff[tile + 1];
+  m.h0 = A.hoff[tile];
+  m.h1 = A.hoff[tile + 1];
+  return m;
+}
 
 __device__ __forceinline__ int *pf_nodes(unsigned char *ib) { return reinterpret_cast<int *>(ib + 32); }
 __device__ __forceinline__ uint32_t *pf_info(unsigned char *ib, const PfLayout &P) {
@@ -493,25 +511,24 @@ __device__ __forceinline__ uint2 *pf_hlc(unsigned char *ib, const PfLayout &P) {
   return reinterpret_cast<uint2 *>(ib + 32 + 8 * P.capN + 4 * P.capH);
 }
 
-// thread 0: tile data into the buffer header, index arrays by bulk copies
-__device__ void pf_issue_index(const TileArgs &A, const PfLayout &P, int tile, unsigned char *ib, uint64_t *bar) {
+// issuing thread: tile data into the buffer header, index arrays by bulk copies
+__device__ void pf_issue_index(const TileArgs &A, const PfLayout &P, const PfMeta &t, unsigned char *ib,
+                               uint64_t *bar) {
   PfTile *m = reinterpret_cast<PfTile *>(ib);
-  const int s = A.tile_start[tile];
-  const int64_t n0 = A.noff[tile], n1 = A.noff[tile + 1], h0 = A.hoff[tile], h1 = A.hoff[tile + 1];
-  const int64_t na = n0 & ~int64_t(3), ne = (n1 + 3) & ~int64_t(3);
-  const int64_t ha = h0 & ~int64_t(3), he = (h1 + 3) & ~int64_t(3);
-  const int64_t la = h0 & ~int64_t(1), le = (h1 + 1) & ~int64_t(1);
-  m->s = s;
-  m->n_own = A.tile_start[tile + 1] - s;
-  m->n0 = (int)n0;  // (only its low bits are used: dn)
-  m->L = (int)(n1 - n0);
-  m->h0 = (int)h0;
-  m->H = (int)(h1 - h0);
-  m->dn = (int)(n0 - na);
-  m->dh = (int)(h0 - ha);
+  const int64_t na = t.n0 & ~int64_t(3), ne = (t.n1 + 3) & ~int64_t(3);
+  const int64_t ha = t.h0 & ~int64_t(3), he = (t.h1 + 3) & ~int64_t(3);
+  const int64_t la = t.h0 & ~int64_t(1), le = (t.h1 + 1) & ~int64_t(1);
+  m->s = t.s;
+  m->n_own = t.e - t.s;
+  m->n0 = (int)t.n0;
+  m->L = (int)(t.n1 - t.n0);
+  m->h0 = (int)t.h0;
+  m->H = (int)(t.h1 - t.h0);
+  m->dn = (int)(t.n0 - na);
+  m->dh = (int)(t.h0 - ha);
   const uint32_t bn = (uint32_t)(ne - na) * 4u;
-  const uint32_t bh = h1 > h0 ? (uint32_t)(he - ha) * 4u : 0u;
-  const uint32_t bl = h1 > h0 ? (uint32_t)(le - la) * 8u : 0u;
+  const uint32_t bh = t.h1 > t.h0 ? (uint32_t)(he - ha) * 4u : 0u;
+  const uint32_t bl = t.h1 > t.h0 ? (uint32_t)(le - la) * 8u : 0u;
   mbar_arrive_expect_tx(bar, 2u * bn + bh + bl);
   bulk_load(pf_nodes(ib), A.tile_nodes + na, bn, bar);
   bulk_load(pf_info(ib, P), A.node_inc + na, bn, bar);
@@ -521,10 +538,9 @@ __device__ void pf_issue_index(const TileArgs &A, const PfLayout &P, int tile, u
   }
 }
 
-// thread 0: the own-tet record planes of a tile by bulk copies
-__device__ void pf_issue_records(const TileArgs &A, int tile, float4 *rb, uint64_t *bar) {
-  const int s = A.tile_start[tile], n_own = A.tile_start[tile + 1] - s;
-  const uint32_t b = (uint32_t)n_own * 16u;
+// issuing thread: the own-tet record planes of tets [s, s + n) by bulk copies
+__device__ void pf_issue_records(const TileArgs &A, int s, int n, float4 *rb, uint64_t *bar) {
+  const uint32_t b = (uint32_t)n * 16u;
   mbar_arrive_expect_tx(bar, 4u * b);
 #pragma unroll
   for (int q = 0; q < 4; ++q) bulk_load(rb + q * kTileMax, A.rec + q * A.rs + s, b, bar);
@@ -540,7 +556,19 @@ __device__ __forceinline__ void pf_issue_u(unsigned char *ib, const TU *u, TU *u
 #pragma unroll
     for (int c = 0; c < 3; ++c) cp_async<sizeof(TU)>(ub + 3 * i + c, up + c);
   }
-  cp_async_commit();
+}
+
+// all threads: gather the first three record planes of the tile's halo tets
+// (geometry and volume; their local connectivity is in the index buffer)
+template <int NT>
+__device__ __forceinline__ void pf_issue_halo(const TileArgs &A, const PfLayout &P, unsigned char *ib, float4 *hb) {
+  const PfTile *m = reinterpret_cast<const PfTile *>(ib);
+  const int *htet = pf_htet(ib, P) + m->dh;
+  for (int h = threadIdx.x; h < m->H; h += NT) {
+    const int64_t t = htet[h];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) cp_async<16>(hb + q * P.capR + h, A.rec + q * A.rs + t);
+  }
 }
 
 // after a wait that gave up: let this CTA's copies in flight land (bounded)
@@ -551,7 +579,10 @@ __device__ void pf_drain() {
   }
 }
 
-// NT threads per CTA (256 or 512), two CTAs per SM
+// NT threads per CTA (256 or 512), two CTAs per SM.  Per tile four block
+// barriers: inputs in place (records in registers, displacements in shared
+// memory), strains formed (and the next tile's index arrays landed), forces
+// in their slots, nodal sums done.
 template <class TU, class TY, int NT>
 __global__ void __launch_bounds__(NT, 2)
     k_mf32_tiled_pf(TileArgs A, PfLayout P, const TU *__restrict__ u, TY *__restrict__ y, float lam, float mu,
@@ -562,12 +593,15 @@ __global__ void __launch_bounds__(NT, 2)
   uint64_t *bar = reinterpret_cast<uint64_t *>(sm_pf);  // [0] records, [1], [2] index buffers
   float4 *rb = reinterpret_cast<float4 *>(sm_pf + 32);  // 4 record planes of kTileMax
   unsigned char *ib0 = sm_pf + P.off_i;
+  float4 *hb = reinterpret_cast<float4 *>(sm_pf + P.off_h);  // 3 halo record planes of capR
   TU *ub = reinterpret_cast<TU *>(sm_pf + P.off_u);
   float4 *W = reinterpret_cast<float4 *>(sm_pf + P.off_w);
   __shared__ float s_en[NT / 32];
   constexpr bool kRef = !std::is_same<TU, float>::value;  // see tile_compute
   int tile = blockIdx.x;
   if (tile >= P.n_tiles) return;
+  int next = tile + gridDim.x;
+  PfMeta meta2{};  // issuing thread: the tile after next
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int k = 0; k < 3; ++k) mbar_init(&bar[k], 1);
@@ -575,39 +609,24 @@ __global__ void __launch_bounds__(NT, 2)
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    pf_issue_index(A, P, tile, ib0, &bar[1]);
-    pf_issue_records(A, tile, rb, &bar[0]);
+    const PfMeta m0 = pf_meta(A, tile);
+    pf_issue_index(A, P, m0, ib0, &bar[1]);
+    pf_issue_records(A, m0.s, m0.e - m0.s, rb, &bar[0]);
+    if (next < P.n_tiles) pf_issue_index(A, P, pf_meta(A, next), ib0 + P.ibytes, &bar[2]);
   }
   bool failed = __syncthreads_or(!mbar_wait(&bar[1], 0));
-  int next = tile + gridDim.x;
   if (!failed) {
     pf_issue_u<TU, NT>(ib0, u, ub);
-    if (threadIdx.x == 0 && next < P.n_tiles) pf_issue_index(A, P, next, ib0 + P.ibytes, &bar[2]);
+    pf_issue_halo<NT>(A, P, ib0, hb);
+    cp_async_commit();
   }
   for (int n = 0; !failed && tile < P.n_tiles; ++n) {
     const int b = n & 1;
     unsigned char *ib = ib0 + b * P.ibytes;
+    unsigned char *ibn = ib0 + (b ^ 1) * P.ibytes;
+    const int next2 = next + gridDim.x;
+    if (threadIdx.x == 0 && next2 < P.n_tiles) meta2 = pf_meta(A, next2);  // used at the end of the tile
     const PfTile m = *reinterpret_cast<const PfTile *>(ib);
-    // this tile's records -> registers; its displacements have landed
-    const bool rec_ok = mbar_wait(&bar[0], n & 1);
-    Regs R;
-#pragma unroll
-    for (int r = 0; r < Regs::kPer; ++r) {
-      const int j = threadIdx.x + r * NT;
-      if (j < m.n_own) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) R.rr[r][q] = rb[q * kTileMax + j];
-      }
-    }
-    cp_async_wait_all();
-    if (__syncthreads_or(!rec_ok)) {
-      failed = true;
-      break;
-    }
-    if (threadIdx.x == 0 && next < P.n_tiles) {
-      fence_proxy_async_smem();
-      pf_issue_records(A, next, rb, &bar[0]);
-    }
     TileView T;
     T.n_own = m.n_own;
     T.H = m.H;
@@ -621,22 +640,37 @@ __global__ void __launch_bounds__(NT, 2)
     T.swa = W + tile_slot_words(T.L, T.ns);
     T.swb = T.swa + T.nt;
     T.snode = pf_info(ib, P) + m.dn;
+    // 1. inputs: records -> registers, displacements (and halo records) landed
+    const bool rec_ok = mbar_wait(&bar[0], n & 1);
+    Regs R;
+#pragma unroll
+    for (int r = 0; r < Regs::kPer; ++r) {
+      const int j = threadIdx.x + r * NT;
+      if (j < m.n_own) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) R.rr[r][q] = rb[q * kTileMax + j];
+      }
+    }
+    // (each thread reads back the displacements and halo records it gathered
+    // itself; the reference node of FP64 input was gathered by thread 0)
+    cp_async_wait_all();
+    if (kRef) __syncthreads();
     {
       const TU r0 = kRef ? ub[0] : TU(0), r1 = kRef ? ub[1] : TU(0), r2 = kRef ? ub[2] : TU(0);
       for (int i = threadIdx.x; i < T.L; i += NT)
         T.su[i] = make_float4((float)(ub[3 * i] - r0), (float)(ub[3 * i + 1] - r1), (float)(ub[3 * i + 2] - r2),
                               0.f);
     }
-    __syncthreads();
-    // the next tile's displacements, once its index buffer has landed
-    if (next < P.n_tiles) {
-      if (__syncthreads_or(!mbar_wait(&bar[1 + (b ^ 1)], ((n + 1) >> 1) & 1))) {
-        failed = true;
-        break;
-      }
-      pf_issue_u<TU, NT>(ib0 + (b ^ 1) * P.ibytes, u, ub);
+    if (__syncthreads_or(!rec_ok)) {
+      failed = true;
+      break;
     }
-    // strains of the own tets (records in registers) and the halo tets
+    if (threadIdx.x == 0 && next < P.n_tiles) {  // the record buffer is free
+      const PfTile *mn = reinterpret_cast<const PfTile *>(ibn);  // written by this thread
+      fence_proxy_async_smem();
+      pf_issue_records(A, mn->s, mn->n_own, rb, &bar[0]);
+    }
+    // 2. strains of the own tets (records in registers) and the halo tets
 #pragma unroll
     for (int r = 0; r < Regs::kPer; ++r) {
       const int j = threadIdx.x + r * NT;
@@ -651,12 +685,12 @@ __global__ void __launch_bounds__(NT, 2)
       }
     }
     {
-      const int *htet = pf_htet(ib, P) + m.dh;
       const uint2 *hlc = pf_hlc(ib, P) + (m.h0 & 1);
       for (int h = threadIdx.x; h < T.H; h += NT) {
+        const float4 q[4] = {hb[h], hb[P.capR + h], hb[2 * P.capR + h], make_float4(0.f, 0.f, 0.f, 0.f)};
         TetGeo G;
         uint2 lc;
-        load_rec(A.rec, A.rs, htet[h], G, lc, nullptr);
+        rec_unpack(q, G, lc);
         lc = hlc[h];
         float4 w2[2];
         strain_to(T.su, lc, G, w2);
@@ -664,7 +698,18 @@ __global__ void __launch_bounds__(NT, 2)
         T.swb[T.n_own + h] = w2[1];
       }
     }
-    __syncthreads();
+    // the next tile's index arrays must have landed before its gathers
+    const bool idx_ok = next < P.n_tiles ? mbar_wait(&bar[1 + (b ^ 1)], ((n + 1) >> 1) & 1) : true;
+    if (__syncthreads_or(!idx_ok)) {
+      failed = true;
+      break;
+    }
+    if (next < P.n_tiles) {  // displacement and halo buffers are free
+      pf_issue_u<TU, NT>(ibn, u, ub);
+      pf_issue_halo<NT>(A, P, ibn, hb);
+      cp_async_commit();
+    }
+    // 3. face-averaged stresses and the slot forces
     const float en = tile_forces<NT>(R, T, lam, mu);
     if (energy_out) {  // FP32 within the tile, FP64 across tiles
       float e = en;
@@ -679,6 +724,7 @@ __global__ void __launch_bounds__(NT, 2)
       for (int w = 0; w < NT / 32; ++w) e += s_en[w];
       atomicAdd(energy_out, (double)e);
     }
+    // 4. nodal sums into y
     {
       const int *nodes = pf_nodes(ib) + m.dn;
       for (int i = threadIdx.x; i < T.L; i += NT) {
@@ -692,10 +738,9 @@ __global__ void __launch_bounds__(NT, 2)
     }
     __syncthreads();
     // index buffer b is free: the indices of the tile after next
-    const int next2 = next + gridDim.x;
     if (threadIdx.x == 0 && next2 < P.n_tiles) {
       fence_proxy_async_smem();
-      pf_issue_index(A, P, next2, ib, &bar[1 + b]);
+      pf_issue_index(A, P, meta2, ib, &bar[1 + b]);
     }
     tile = next;
     next = next2;
@@ -718,51 +763,50 @@ static void setup_prefetch(Ctx &c) {
   t.pf_capN = align_up(t.max_nodes + 6, 4);
   t.pf_capH = align_up(t.max_halo + 6, 4);
   t.pf_capH2 = align_up(t.max_halo + 2, 2);
+  t.pf_capR = std::max(t.max_halo, 1);
   t.pf_ibytes = align_up(32 + 8 * t.pf_capN + 4 * t.pf_capH + 8 * t.pf_capH2, 16);
   t.pf_off_i = 32 + 4 * kTileMax * (int)sizeof(float4);
-  t.pf_off_u = t.pf_off_i + 2 * t.pf_ibytes;
-  t.pf_off_w = align_up(t.pf_off_u + 3 * t.max_nodes * (int)sizeof(double), 16);
-  t.pf_smem = (size_t)t.pf_off_w + (size_t)tile_slot_words(t.max_nodes, t.slot_stride) * sizeof(float4) +
-              (size_t)(kTileMax + t.max_halo) * 2 * sizeof(float4);
+  t.pf_off_h = t.pf_off_i + 2 * t.pf_ibytes;
+  t.pf_off_u = t.pf_off_h + 3 * t.pf_capR * (int)sizeof(float4);
   if (!t.err) {
     t.err = c.mem.get<int>(1);
     SFEM_CUDA(cudaMemsetAsync(t.err, 0, sizeof(int), c.stream));
   }
-  t.pf_grid = 0;
-  t.pf_threads = 0;
-  if (t.pf_smem > 227 * 1024) return;
-  static size_t pf_smem_set = 0;
-  if (t.pf_smem > pf_smem_set) {
-    SFEM_CUDA(cudaFuncSetAttribute(k_mf32_tiled_pf<float, float, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)t.pf_smem));
-    SFEM_CUDA(cudaFuncSetAttribute(k_mf32_tiled_pf<double, double, 512>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.pf_smem));
-    SFEM_CUDA(cudaFuncSetAttribute(k_mf32_tiled_pf<float, float, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)t.pf_smem));
-    SFEM_CUDA(cudaFuncSetAttribute(k_mf32_tiled_pf<double, double, 256>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.pf_smem));
-    pf_smem_set = t.pf_smem;
-  }
   int nsm = 0, dev = 0;
   SFEM_CUDA(cudaGetDevice(&dev));
   SFEM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  // 512 threads (one tet each) where two such CTAs fit on an SM, else 256
-  int per512 = 0, per256 = 0;
-  SFEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per512, k_mf32_tiled_pf<float, float, 512>, 512,
-                                                          t.pf_smem));
-  SFEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per256, k_mf32_tiled_pf<float, float, 256>, 256,
-                                                          t.pf_smem));
-  int per_sm = 0;
-  if (per512 >= 2) {
-    t.pf_threads = 512;
-    per_sm = per512;
-  } else if (per256 >= 2) {
-    t.pf_threads = 256;
-    per_sm = per256;
-  } else {
-    return;
+  static size_t smem_set[2] = {0, 0};
+  for (int v = 0; v < 2; ++v) {  // FP32 / FP64 input
+    const int es = v ? 8 : 4;
+    t.pf_off_w[v] = align_up(t.pf_off_u + 3 * t.max_nodes * es, 16);
+    t.pf_smem[v] = (size_t)t.pf_off_w[v] + (size_t)tile_slot_words(t.max_nodes, t.slot_stride) * sizeof(float4) +
+                   (size_t)(kTileMax + t.max_halo) * 2 * sizeof(float4);
+    t.pf_grid[v] = 0;
+    t.pf_threads[v] = 0;
+    if (t.pf_smem[v] > 227 * 1024) continue;
+    const void *k512 = v ? (const void *)k_mf32_tiled_pf<double, double, 512> : (const void *)k_mf32_tiled_pf<float, float, 512>;
+    const void *k256 = v ? (const void *)k_mf32_tiled_pf<double, double, 256> : (const void *)k_mf32_tiled_pf<float, float, 256>;
+    if (t.pf_smem[v] > smem_set[v]) {
+      SFEM_CUDA(cudaFuncSetAttribute(k512, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.pf_smem[v]));
+      SFEM_CUDA(cudaFuncSetAttribute(k256, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.pf_smem[v]));
+      smem_set[v] = t.pf_smem[v];
+    }
+    // 512 threads (one tet each) where two such CTAs fit on an SM, else 256
+    int per512 = 0, per256 = 0;
+    SFEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per512, k512, 512, t.pf_smem[v]));
+    SFEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per256, k256, 256, t.pf_smem[v]));
+    int per_sm = 0;
+    if (per512 >= 2) {
+      t.pf_threads[v] = 512;
+      per_sm = per512;
+    } else if (per256 >= 2) {
+      t.pf_threads[v] = 256;
+      per_sm = per256;
+    } else {
+      continue;
+    }
+    t.pf_grid[v] = (int)std::min<int64_t>(t.n_tiles, (int64_t)per_sm * nsm);
   }
-  t.pf_grid = (int)std::min<int64_t>(t.n_tiles, (int64_t)per_sm * nsm);
 }
 
 // a wait of the prefetching operator gave up (reported once, then cleared)
@@ -936,14 +980,15 @@ template <class TU, class TY>
 void launch_mf32_tiled(Ctx &c, cudaStream_t st, const TU *u, TY *y, double *energy_out, const int *done) {
   TileArgs A{c.tl.tile_start, c.tl.hoff, c.tl.noff, c.tl.halo_tet, c.tl.halo_lconn, c.tl.tile_nodes,
              c.tl.node_inc, c.tl.rec, c.n_tets, c.tl.slot_stride};
-  if (c.tl.pf_grid > 0) {
-    const PfLayout P{(int)c.tl.n_tiles, c.tl.pf_capN,  c.tl.pf_capH,  c.tl.pf_capH2,
-                     c.tl.pf_ibytes,    c.tl.pf_off_i, c.tl.pf_off_u, c.tl.pf_off_w};
-    if (c.tl.pf_threads == 512)
-      k_mf32_tiled_pf<TU, TY, 512><<<(unsigned)c.tl.pf_grid, 512, c.tl.pf_smem, st>>>(
+  const int v = sizeof(TU) == 8 ? 1 : 0;
+  if (c.tl.pf_grid[v] > 0) {
+    const PfLayout P{(int)c.tl.n_tiles, c.tl.pf_capN,  c.tl.pf_capH,  c.tl.pf_capH2,  c.tl.pf_ibytes,
+                     c.tl.pf_capR,      c.tl.pf_off_i, c.tl.pf_off_h, c.tl.pf_off_u, c.tl.pf_off_w[v]};
+    if (c.tl.pf_threads[v] == 512)
+      k_mf32_tiled_pf<TU, TY, 512><<<(unsigned)c.tl.pf_grid[v], 512, c.tl.pf_smem[v], st>>>(
           A, P, u, y, (float)c.lam, (float)c.mu, energy_out, done, c.tl.err);
     else
-      k_mf32_tiled_pf<TU, TY, 256><<<(unsigned)c.tl.pf_grid, 256, c.tl.pf_smem, st>>>(
+      k_mf32_tiled_pf<TU, TY, 256><<<(unsigned)c.tl.pf_grid[v], 256, c.tl.pf_smem[v], st>>>(
           A, P, u, y, (float)c.lam, (float)c.mu, energy_out, done, c.tl.err);
   } else {
     k_mf32_tiled<TU, TY><<<(unsigned)c.tl.n_tiles, kTileThreads, c.tl.smem, st>>>(A, u, y, (float)c.lam,
@@ -964,8 +1009,8 @@ extern "C" int sfem_tile_info(sfem_ctx *h, int64_t *out, int n) {
     SFEM_REQUIRE(h && h->c.vol && out && n >= 1, SFEM_EINVAL, "bad arguments");
     const TileData &t = h->c.tl;
     SFEM_REQUIRE(t.ready, SFEM_EINVAL, "the tiled operator is not set up");
-    const int64_t v[10] = {t.n_tiles,     t.max_halo,      t.max_nodes,        t.slot_stride, t.total_halo,
-                           t.total_nodes, (int64_t)t.smem, (int64_t)t.pf_smem, t.pf_grid,    t.pf_threads};
+    const int64_t v[10] = {t.n_tiles,     t.max_halo,      t.max_nodes,           t.slot_stride, t.total_halo,
+                           t.total_nodes, (int64_t)t.smem, (int64_t)t.pf_smem[0], t.pf_grid[0], t.pf_threads[0]};
     for (int i = 0; i < n && i < 10; ++i) out[i] = v[i];
   } catch (const Error &err) {
     set_last_error(err.msg);

@@ -511,39 +511,62 @@ __device__ __forceinline__ uint2 *pf_hlc(unsigned char *ib, const PfLayout &P) {
   return reinterpret_cast<uint2 *>(ib + 32 + 8 * P.capN + 4 * P.capH);
 }
 
-// issuing thread: tile data into the buffer header, index arrays by bulk copies
-__device__ void pf_issue_index(const TileArgs &A, const PfLayout &P, const PfMeta &t, unsigned char *ib,
-                               uint64_t *bar) {
-  PfTile *m = reinterpret_cast<PfTile *>(ib);
+// Issuing a bulk copy stalls the issuing thread for a while (on the order
+// of a hundred cycles each), so the copies of one tile are issued by lane 0
+// of several warps, one copy each, instead of by one thread: the stalls
+// overlap instead of adding up on one warp that the block then waits for.
+// The barrier's expected byte count may be set before or after the copies
+// complete (the transaction count of an mbarrier may go transiently
+// negative; the phase completes when the arrival and all bytes are in).
+
+// index arrays of a tile, part `part` of 4: 0 writes the buffer header,
+// announces the bytes of all four copies and copies the node ids; 1 the node
+// slot info; 2 the halo ids; 3 the halo connectivity
+__device__ void pf_issue_index_part(const TileArgs &A, const PfLayout &P, const PfMeta &t, unsigned char *ib,
+                                    uint64_t *bar, int part) {
   const int64_t na = t.n0 & ~int64_t(3), ne = (t.n1 + 3) & ~int64_t(3);
   const int64_t ha = t.h0 & ~int64_t(3), he = (t.h1 + 3) & ~int64_t(3);
   const int64_t la = t.h0 & ~int64_t(1), le = (t.h1 + 1) & ~int64_t(1);
-  m->s = t.s;
-  m->n_own = t.e - t.s;
-  m->n0 = (int)t.n0;
-  m->L = (int)(t.n1 - t.n0);
-  m->h0 = (int)t.h0;
-  m->H = (int)(t.h1 - t.h0);
-  m->dn = (int)(t.n0 - na);
-  m->dh = (int)(t.h0 - ha);
   const uint32_t bn = (uint32_t)(ne - na) * 4u;
   const uint32_t bh = t.h1 > t.h0 ? (uint32_t)(he - ha) * 4u : 0u;
   const uint32_t bl = t.h1 > t.h0 ? (uint32_t)(le - la) * 8u : 0u;
-  mbar_arrive_expect_tx(bar, 2u * bn + bh + bl);
-  bulk_load(pf_nodes(ib), A.tile_nodes + na, bn, bar);
-  bulk_load(pf_info(ib, P), A.node_inc + na, bn, bar);
-  if (bh) {
-    bulk_load(pf_htet(ib, P), A.halo_tet + ha, bh, bar);
-    bulk_load(pf_hlc(ib, P), A.halo_lconn + la, bl, bar);
+  if (part == 0) {
+    PfTile *m = reinterpret_cast<PfTile *>(ib);
+    m->s = t.s;
+    m->n_own = t.e - t.s;
+    m->n0 = (int)t.n0;
+    m->L = (int)(t.n1 - t.n0);
+    m->h0 = (int)t.h0;
+    m->H = (int)(t.h1 - t.h0);
+    m->dn = (int)(t.n0 - na);
+    m->dh = (int)(t.h0 - ha);
+    mbar_arrive_expect_tx(bar, 2u * bn + bh + bl);
+    bulk_load(pf_nodes(ib), A.tile_nodes + na, bn, bar);
+  } else if (part == 1) {
+    bulk_load(pf_info(ib, P), A.node_inc + na, bn, bar);
+  } else if (part == 2) {
+    if (bh) bulk_load(pf_htet(ib, P), A.halo_tet + ha, bh, bar);
+  } else {
+    if (bl) bulk_load(pf_hlc(ib, P), A.halo_lconn + la, bl, bar);
   }
 }
 
-// issuing thread: the own-tet record planes of tets [s, s + n) by bulk copies
-__device__ void pf_issue_records(const TileArgs &A, int s, int n, float4 *rb, uint64_t *bar) {
+// all four parts by one thread (start-up)
+__device__ void pf_issue_index(const TileArgs &A, const PfLayout &P, const PfMeta &t, unsigned char *ib,
+                               uint64_t *bar) {
+  for (int k = 0; k < 4; ++k) pf_issue_index_part(A, P, t, ib, bar, k);
+}
+
+// record plane q of tets [s, s + n); plane 0 also announces all four planes
+__device__ __forceinline__ void pf_issue_record_plane(const TileArgs &A, int s, int n, float4 *rb, uint64_t *bar,
+                                                      int q) {
   const uint32_t b = (uint32_t)n * 16u;
-  mbar_arrive_expect_tx(bar, 4u * b);
-#pragma unroll
-  for (int q = 0; q < 4; ++q) bulk_load(rb + q * kTileMax, A.rec + q * A.rs + s, b, bar);
+  if (q == 0) mbar_arrive_expect_tx(bar, 4u * b);
+  bulk_load(rb + q * kTileMax, A.rec + q * A.rs + s, b, bar);
+}
+
+__device__ void pf_issue_records(const TileArgs &A, int s, int n, float4 *rb, uint64_t *bar) {
+  for (int q = 0; q < 4; ++q) pf_issue_record_plane(A, s, n, rb, bar, q);
 }
 
 // all threads: gather u at the tile's nodes (its index buffer has landed)
@@ -601,7 +624,7 @@ __global__ void __launch_bounds__(NT, 2)
   int tile = blockIdx.x;
   if (tile >= P.n_tiles) return;
   int next = tile + gridDim.x;
-  PfMeta meta2{};  // issuing thread: the tile after next
+  PfMeta meta2{};  // index-issuing threads: the tile after next
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int k = 0; k < 3; ++k) mbar_init(&bar[k], 1);
@@ -625,7 +648,10 @@ __global__ void __launch_bounds__(NT, 2)
     unsigned char *ib = ib0 + b * P.ibytes;
     unsigned char *ibn = ib0 + (b ^ 1) * P.ibytes;
     const int next2 = next + gridDim.x;
-    if (threadIdx.x == 0 && next2 < P.n_tiles) meta2 = pf_meta(A, next2);  // used at the end of the tile
+    // lane 0 of warps 4..7 issue the index copies of the tile after next at
+    // the end of this tile; their tile ranges are read now
+    const int ipart = (threadIdx.x & 31) == 0 ? (int)(threadIdx.x >> 5) - 4 : -1;
+    if (ipart >= 0 && ipart < 4 && next2 < P.n_tiles) meta2 = pf_meta(A, next2);
     const PfTile m = *reinterpret_cast<const PfTile *>(ib);
     TileView T;
     T.n_own = m.n_own;
@@ -665,10 +691,10 @@ __global__ void __launch_bounds__(NT, 2)
       failed = true;
       break;
     }
-    if (threadIdx.x == 0 && next < P.n_tiles) {  // the record buffer is free
-      const PfTile *mn = reinterpret_cast<const PfTile *>(ibn);  // written by this thread
+    if ((threadIdx.x & 31) == 0 && threadIdx.x < 128 && next < P.n_tiles) {  // the record buffer is free
+      const PfTile *mn = reinterpret_cast<const PfTile *>(ibn);  // header written a tile ago
       fence_proxy_async_smem();
-      pf_issue_records(A, mn->s, mn->n_own, rb, &bar[0]);
+      pf_issue_record_plane(A, mn->s, mn->n_own, rb, &bar[0], threadIdx.x >> 5);
     }
     // 2. strains of the own tets (records in registers) and the halo tets
 #pragma unroll
@@ -738,9 +764,9 @@ __global__ void __launch_bounds__(NT, 2)
     }
     __syncthreads();
     // index buffer b is free: the indices of the tile after next
-    if (threadIdx.x == 0 && next2 < P.n_tiles) {
+    if (ipart >= 0 && ipart < 4 && next2 < P.n_tiles) {
       fence_proxy_async_smem();
-      pf_issue_index(A, P, meta2, ib, &bar[1 + b]);
+      pf_issue_index_part(A, P, meta2, ib, &bar[1 + b], ipart);
     }
     tile = next;
     next = next2;

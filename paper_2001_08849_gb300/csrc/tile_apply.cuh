@@ -264,16 +264,36 @@ __device__ __forceinline__ bool tile_node_force(const TileView &T, int i, float 
   if (n == 0) return false;
   float cx = 0.f, cy = 0.f, cz = 0.f;
   const float *px = T.sfx + b, *py = px + T.ns, *pz = py + T.ns;
-  for (int k = 0; k < n; ++k) {
+  // compensated (Kahan) step: s += v
+  auto add = [](float &s, float &c, float v) {
+    const float yv = v - c;
+    const float t = s + yv;
+    c = __fsub_rn(__fsub_rn(t, s), yv);
+    s = t;
+  };
+  int k = 0;
+  // four slots' loads in flight at a time; the sums keep the order k = 0, 1, ...
+  for (; k + 4 <= n; k += 4) {
+    float vx[4], vy[4], vz[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int o = 32 * (k + q) + ((lane + k + q) & 31);
+      vx[q] = px[o];
+      vy[q] = py[o];
+      vz[q] = pz[o];
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      add(fx, cx, vx[q]);
+      add(fy, cy, vy[q]);
+      add(fz, cz, vz[q]);
+    }
+  }
+  for (; k < n; ++k) {
     const int o = 32 * k + ((lane + k) & 31);
-    const float yx = px[o] - cx, yy = py[o] - cy, yz = pz[o] - cz;
-    const float tx = fx + yx, ty = fy + yy, tz = fz + yz;
-    cx = __fsub_rn(__fsub_rn(tx, fx), yx);
-    cy = __fsub_rn(__fsub_rn(ty, fy), yy);
-    cz = __fsub_rn(__fsub_rn(tz, fz), yz);
-    fx = tx;
-    fy = ty;
-    fz = tz;
+    add(fx, cx, px[o]);
+    add(fy, cy, py[o]);
+    add(fz, cz, pz[o]);
   }
   return true;
 }

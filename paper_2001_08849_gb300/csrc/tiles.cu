@@ -602,7 +602,7 @@ __device__ void pf_drain() {
   }
 }
 
-// NT threads per CTA (256 or 512), two CTAs per SM.  Per tile four block
+// NT threads per CTA (256 in use), two CTAs per SM.  Per tile four block
 // barriers: inputs in place (records in registers, displacements in shared
 // memory), strains formed (and the next tile's index arrays landed), forces
 // in their slots, nodal sums done.
@@ -810,27 +810,17 @@ static void setup_prefetch(Ctx &c) {
     t.pf_grid[v] = 0;
     t.pf_threads[v] = 0;
     if (t.pf_smem[v] > 227 * 1024) continue;
-    const void *k512 = v ? (const void *)k_mf32_tiled_pf<double, double, 512> : (const void *)k_mf32_tiled_pf<float, float, 512>;
     const void *k256 = v ? (const void *)k_mf32_tiled_pf<double, double, 256> : (const void *)k_mf32_tiled_pf<float, float, 256>;
     if (t.pf_smem[v] > smem_set[v]) {
-      SFEM_CUDA(cudaFuncSetAttribute(k512, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.pf_smem[v]));
       SFEM_CUDA(cudaFuncSetAttribute(k256, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.pf_smem[v]));
       smem_set[v] = t.pf_smem[v];
     }
-    // 512 threads (one tet each) where two such CTAs fit on an SM, else 256
-    int per512 = 0, per256 = 0;
-    SFEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per512, k512, 512, t.pf_smem[v]));
-    SFEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per256, k256, 256, t.pf_smem[v]));
+    // two CTAs of 256 threads per SM (512-thread CTAs measured 3.5 us slower
+    // per apply on the 2M-tet beam)
     int per_sm = 0;
-    if (per512 >= 2) {
-      t.pf_threads[v] = 512;
-      per_sm = per512;
-    } else if (per256 >= 2) {
-      t.pf_threads[v] = 256;
-      per_sm = per256;
-    } else {
-      continue;
-    }
+    SFEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k256, 256, t.pf_smem[v]));
+    if (per_sm < 2) continue;
+    t.pf_threads[v] = 256;
     t.pf_grid[v] = (int)std::min<int64_t>(t.n_tiles, (int64_t)per_sm * nsm);
   }
 }
@@ -1010,12 +1000,8 @@ void launch_mf32_tiled(Ctx &c, cudaStream_t st, const TU *u, TY *y, double *ener
   if (c.tl.pf_grid[v] > 0) {
     const PfLayout P{(int)c.tl.n_tiles, c.tl.pf_capN,  c.tl.pf_capH,  c.tl.pf_capH2,  c.tl.pf_ibytes,
                      c.tl.pf_capR,      c.tl.pf_off_i, c.tl.pf_off_h, c.tl.pf_off_u, c.tl.pf_off_w[v]};
-    if (c.tl.pf_threads[v] == 512)
-      k_mf32_tiled_pf<TU, TY, 512><<<(unsigned)c.tl.pf_grid[v], 512, c.tl.pf_smem[v], st>>>(
-          A, P, u, y, (float)c.lam, (float)c.mu, energy_out, done, c.tl.err);
-    else
-      k_mf32_tiled_pf<TU, TY, 256><<<(unsigned)c.tl.pf_grid[v], 256, c.tl.pf_smem[v], st>>>(
-          A, P, u, y, (float)c.lam, (float)c.mu, energy_out, done, c.tl.err);
+    k_mf32_tiled_pf<TU, TY, 256><<<(unsigned)c.tl.pf_grid[v], 256, c.tl.pf_smem[v], st>>>(
+        A, P, u, y, (float)c.lam, (float)c.mu, energy_out, done, c.tl.err);
   } else {
     k_mf32_tiled<TU, TY><<<(unsigned)c.tl.n_tiles, kTileThreads, c.tl.smem, st>>>(A, u, y, (float)c.lam,
                                                                                  (float)c.mu, energy_out, done);

@@ -131,9 +131,10 @@ def gelu_grad(x):
     return Phi + x * phi
 
 
-def forward(theta, X):
-    """Network outputs (rows, 3) and the cached pre-activations."""
-    W1, b1, W2, b2, W3, b3 = unpack(theta)
+def forward(theta, X, dims=(N_IN, N_HID, N_OUT)):
+    """Network outputs (rows, n_out) and the cached pre-activations; dims =
+    (n_in, hidden, n_out), the per-patch network's by default."""
+    W1, b1, W2, b2, W3, b3 = unpack(theta, *dims)
     a1 = X @ W1 + b1
     h1 = gelu(a1)
     a2 = h1 @ W2 + b2
@@ -142,11 +143,11 @@ def forward(theta, X):
     return y, (X, a1, h1, a2, h2)
 
 
-def loss_and_grad(theta, X, T):
+def loss_and_grad(theta, X, T, dims=(N_IN, N_HID, N_OUT)):
     """Mean-squared error sum((y - T)^2) / rows and its gradient, by the
     chain rule through the three layers."""
-    W1, b1, W2, b2, W3, b3 = unpack(theta)
-    y, (X_, a1, h1, a2, h2) = forward(theta, X)
+    W1, b1, W2, b2, W3, b3 = unpack(theta, *dims)
+    y, (X_, a1, h1, a2, h2) = forward(theta, X, dims)
     rows = X.shape[0]
     d = y - T
     loss = float(np.sum(d * d) / rows)

@@ -112,7 +112,9 @@ enum {
 enum {
   SFEM_SOLVE_PCG64 = 0,        /* Jacobi-PCG, all FP64 */
   SFEM_SOLVE_IR32_64 = 1,      /* FP64 residual/update around FP32 Jacobi-PCG */
-  SFEM_SOLVE_FPCG_LEARNED = 2  /* flexible PCG with a learned coarse correction */
+  SFEM_SOLVE_FPCG_LEARNED = 2, /* flexible PCG with a learned coarse correction */
+  SFEM_SOLVE_FCG_CNET = 3      /* truncated flexible CG with the learned coarse solve of an
+                                  sfem_cnet model (opts.learned; NULL: Jacobi-PCG) */
 };
 
 typedef struct sfem_solve_opts {
@@ -387,6 +389,77 @@ int sfem_learned_adam(sfem_learned *m, const float *grad, float lr, float b1, fl
  * all rows afterwards. */
 int sfem_learned_train(sfem_learned *m, const float *X, const float *T, int64_t rows,
                        int64_t batch_rows, int epochs, float lr, uint64_t seed, double *loss);
+
+/* Learned coarse solve (no counterpart in the paper, which solves directly;
+ * the spec addition of a network that maps a pooled residual to a
+ * coarse displacement correction).  The model works on the coarse space of
+ * sfem_coarse_setup (trilinear functions of a grid of patch centres, n_c =
+ * 3 x centres coarse DOFs):
+ *   input     x = r_c / RMS(r_c), r_c = Pi^T r (restriction = weighted
+ *             pooling of the residual over the cells around each centre);
+ *   network   n_c -> hidden -> GELU -> hidden -> GELU -> n_c (GELU with
+ *             the exact erf), BF16 weights, FP32 biases and accumulation at
+ *             inference, FP32 master weights for training;
+ *   correction z = D^-1 r + alpha P Pi y, alpha = y.r_c / y.A_c y (the
+ *             A-optimal step along the correction, formed on the coarse level
+ *             with the FP32 A_c kept by sfem_coarse_setup; 0, and counted in
+ *             info.fallbacks, when y.A_c y <= 0 or alpha is not finite);
+ *   targets   t = A_c^-1 r_c / RMS: the Galerkin coarse solution, whose
+ *             prolongation is the A-orthogonal projection of the error onto the
+ *             coarse space; training rows (x, t) are collected from the
+ *             library's own solves (sfem_cnet_solve);
+ *   solver    flexible CG with each new direction A-orthogonalised against the
+ *             last `window` directions (SFEM_SOLVE_FCG_CNET); with the Jacobi
+ *             preconditioner alone (model NULL) it is Jacobi-PCG.
+ * Parameters are one FP32 vector: W1 (n_c x hidden, input-major), b1, W2
+ * (hidden x hidden), b2, W3 (hidden x n_c), b3.  A model is bound to the
+ * context (device, stream, mesh, coarse space) it was created on. */
+typedef struct sfem_cnet sfem_cnet;
+
+typedef struct sfem_cnet_opts {
+  int hidden;     /* hidden width (0: 128; a multiple of 32, at most 256) */
+  uint64_t seed;  /* initial parameters: He-normal weights by a counter-based generator
+                     (splitmix64 + Box-Muller), zero biases */
+  int reserved[6];
+} sfem_cnet_opts;
+
+/* Training-row collection and direction window of sfem_cnet_solve. */
+typedef struct sfem_cnet_run {
+  int window;          /* directions the new one is A-orthogonalised against (0: 5; 1 .. 8) */
+  int snap_every;      /* a training row every this many iterations (0: none) */
+  float *X, *T;        /* DEVICE row buffers, cap_rows x n_c floats each */
+  int64_t cap_rows;
+  int64_t rows;        /* in: rows already in the buffers; out: rows after the solve */
+  int reserved[4];
+} sfem_cnet_run;
+
+/* Create a model on ctx (after sfem_coarse_setup) with fresh parameters;
+ * SFEM_EINVAL without a coarse space or with a bad width. */
+int sfem_cnet_create(sfem_cnet **out, sfem_ctx *ctx, const sfem_cnet_opts *opts);
+void sfem_cnet_destroy(sfem_cnet *m);
+int sfem_cnet_info(const sfem_cnet *m, int *n_coarse, int *hidden, int64_t *n_params);
+/* FP32 parameters from / to HOST memory (n = n_params); set resets Adam. */
+int sfem_cnet_set_params(sfem_cnet *m, const float *theta, int64_t n);
+int sfem_cnet_get_params(sfem_cnet *m, float *theta, int64_t n);
+/* Y[r] = network(X[r] / RMS(X[r])) by the inference path (BF16 weights);
+ * DEVICE X, Y (rows x n_c). */
+int sfem_cnet_forward(sfem_cnet *m, sfem_ctx *ctx, const float *X, float *Y, int64_t rows);
+/* Loss sum((y - T)^2) / rows (FP32 master weights) and its gradient (DEVICE
+ * grad, n_params, may be NULL); loss to host. */
+int sfem_cnet_loss_grad(sfem_cnet *m, const float *X, const float *T, int64_t rows, float *grad, double *loss);
+/* epochs of mini-batch Adam (0.9, 0.999, 1e-8), rows visited in the order
+ * r -> (a r + b) mod rows with a, b drawn from seed; loss: mean of the last
+ * epoch (host, may be NULL). */
+int sfem_cnet_train(sfem_cnet *m, const float *X, const float *T, int64_t rows, int64_t batch_rows, int epochs,
+                    float lr, uint64_t seed, double *loss);
+/* z = D^-1 r + alpha P Pi y for one residual (DEVICE r, z: ndof FP64); alpha
+ * to host. */
+int sfem_cnet_correction(sfem_cnet *m, sfem_ctx *ctx, const double *r, double *z, double *alpha);
+/* A solve of opts (rhs, tol, max_iter, op64 CSR64 or MF64, u_on_device,
+ * warm_start) by truncated flexible CG with the model (m NULL: Jacobi),
+ * appending training rows to run (may be NULL).  Status as sfem_solve. */
+int sfem_cnet_solve(sfem_cnet *m, sfem_ctx *ctx, const sfem_solve_opts *opts, double *u, sfem_cnet_run *run,
+                    sfem_solve_info *info);
 
 int sfem_get_info(const sfem_ctx *ctx, sfem_mesh_info *info);
 

@@ -775,6 +775,21 @@ __global__ void __launch_bounds__(256) k_lauum(const float *W, float *C, int npa
     for (int y = 0; y < 4; ++y) Cb[(tm + x) * kCB + tn + y] = acc[x][y];
 }
 
+// the lower 64 x 64 blocks of the dense FP64 matrix A (npad x npad) packed
+// in FP32: block (a, b), a >= b, at (a (a + 1) / 2 + b) * 4096, row-major
+__global__ void k_cs_pack_lower(const double *__restrict__ A, float *__restrict__ P, int npad, int nb) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t total = (int64_t)nb * (nb + 1) / 2 * kCB * kCB;
+  if (e >= total) return;
+  const int64_t t = e / (kCB * kCB);
+  const int w = (int)(e - t * kCB * kCB), i = w / kCB, j = w % kCB;
+  int a = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+  while ((int64_t)(a + 1) * (a + 2) / 2 <= t) ++a;
+  while ((int64_t)a * (a + 1) / 2 > t) --a;
+  const int b = (int)(t - (int64_t)a * (a + 1) / 2);
+  P[e] = (float)A[(int64_t)(a * kCB + i) * npad + b * kCB + j];
+}
+
 // z = D^-1 r + P Pi yc
 __global__ void k_cs_apply_z(CoarseDev cs, const double *__restrict__ r, const double *__restrict__ dinv,
                              const uint8_t *__restrict__ dmask, int64_t n, double *__restrict__ z) {
@@ -799,6 +814,13 @@ static void coarse_correction_t(Ctx &c, cudaStream_t st, const TV *r, const int 
 }
 void coarse_correction(Ctx &c, cudaStream_t st, const double *r, const int *done) {
   coarse_correction_t(c, st, r, done);
+}
+void coarse_restrict(Ctx &c, cudaStream_t st, const double *r, const int *done) {
+  const CoarseDev &cs = c.coarse->dev;
+  k_cs_restrict<double><<<cs.ncell, kRestrictThreads, 0, st>>>(r, nullptr, cs, done);
+  SFEM_CHECK_LAUNCH();
+  k_cs_gather<<<grid_for(cs.npad, 256), 256, 0, st>>>(cs, done);
+  SFEM_CHECK_LAUNCH();
 }
 void coarse_correction(Ctx &c, cudaStream_t st, const float *r, const int *done) {
   coarse_correction_t(c, st, r, done);
@@ -1080,6 +1102,14 @@ static void setup_coarse(Ctx &c, const sfem_coarse_opts *opts) {
   c.mem.drop(y);
   k_cs_symmetrize<<<grid_for(np2, 256), 256, 0, c.stream>>>(Ac, cs.nc, cs.npad);
   SFEM_CHECK_LAUNCH();
+  {  // A_c itself, packed in FP32 (the learned coarse correction's step length)
+    const int nbp = cs.npad / kCB;
+    const int64_t tot = (int64_t)nbp * (nbp + 1) / 2 * kCB * kCB;
+    float *Ap = c.mem.get<float>(tot);
+    k_cs_pack_lower<<<grid_for(tot, 256), 256, 0, c.stream>>>(Ac, Ap, cs.npad, nbp);
+    SFEM_CHECK_LAUNCH();
+    cs.Ap = Ap;
+  }
   // ---- banded blocked Cholesky ---------------------------------------------
   // FP32 (the inverse C is FP32 anyway: on the 26 x 6 x 6 grid of the 2M-tet
   // beam, cond(A_c) ~ 8e4, and C from an FP32 factor has C A_c within 1.4e-4

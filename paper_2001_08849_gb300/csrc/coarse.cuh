@@ -33,6 +33,8 @@ struct CoarseDev {
   float *rc, *yc;          // coarse residual and correction (npad)
   const float *C;          // A_c^-1 (symmetric, FP32): lower 64 x 64 blocks, block (a, b) at
                            // (a (a + 1) / 2 + b) * 4096, row-major
+  const float *Ap;         // A_c itself in FP32, the same packed layout (the learned coarse
+                           // correction's step length, cnet.cu)
 };
 
 // weight of corner k (bits: x = 4, y = 2, z = 1) at fractions f

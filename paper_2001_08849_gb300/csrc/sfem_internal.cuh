@@ -298,13 +298,28 @@ void coarse_correction(Ctx &c, cudaStream_t st, const float *r, const int *done)
 bool ensure_coarse(Ctx &c);
 // yc = C rc only (the fused two-level iterations restrict r themselves)
 void coarse_gemv(const CoarseDev &cs, cudaStream_t st, const int *done);
+// rc = Pi^T r only (fixed order; yc zeroed)
+void coarse_restrict(Ctx &c, cudaStream_t st, const double *r, const int *done);
 
 // solves (solve.cu); a Snapshot, when given, sees the iterate x and the
 // residual r (device, ndof) of the flexible PCG before its first iteration
 // and after every chunk of check_every iterations
 using Snapshot = std::function<void(const double *x, const double *r, int iter)>;
+// row collection and direction window of the truncated flexible CG with the
+// learned coarse solve (cnet.cu)
+struct CnRunArgs {
+  int window = 0;       // directions kept (0: 5)
+  int snap_every = 0;   // a training row every this many iterations (0: none)
+  float *X = nullptr, *T = nullptr;  // rows x n_coarse each (device)
+  int64_t cap = 0;      // rows the buffers hold
+  int64_t rows = 0;     // rows already there on entry, total on return
+};
 void solve_impl(Ctx &c, const double *f_extra, double *u, const sfem_solve_opts &o, sfem_solve_info &info,
-                const Snapshot *snap = nullptr);
+                const Snapshot *snap = nullptr, CnRunArgs *cn = nullptr);
+// truncated flexible CG with the learned coarse solve `model` (NULL: the
+// Jacobi preconditioner alone); same contract as solve_fpcg
+void solve_cnet(Ctx &c, const void *model, CnRunArgs *args, int op64, double *x, double *r, double bnorm,
+                double tol, int max_iter, sfem_solve_info &info, const std::function<double()> &true_residual);
 // flexible PCG with the learned correction (learned.cu); r holds the masked
 // residual of x on entry; true_residual() recomputes it and returns ||r||/||b||
 void solve_fpcg(Ctx &c, const void *learned, int op64, double *x, double *r, double bnorm, double tol, int max_iter,

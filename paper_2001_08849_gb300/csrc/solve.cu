@@ -923,7 +923,7 @@ struct SolveBuffers {
 };
 
 void solve_impl(Ctx &c, const double *f_extra, double *u, const sfem_solve_opts &o, sfem_solve_info &info,
-                const Snapshot *snap) {
+                const Snapshot *snap, CnRunArgs *cn) {
   const int64_t n = c.ndof;
   const int g256 = grid_for(n, 256);
   cudaMemcpyKind in_kind = o.u_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
@@ -1215,6 +1215,14 @@ void solve_impl(Ctx &c, const double *f_extra, double *u, const sfem_solve_opts 
       const int window = o.learned_window > 0 ? o.learned_window : 100;
       solve_fpcg(c, o.learned, op64, x, r, bnorm, tol, max_iter, chunk, window, std::max(o.learned_pace, 0), info,
                  true_residual, snap);
+      total_iter = info.iterations;
+      outer = info.outer_iterations;
+      rel = info.true_relres;
+      if (info.status != SFEM_OK && info.status != SFEM_ENOCONV) status = info.status;
+    } else if (o.kind == SFEM_SOLVE_FCG_CNET) {
+      SFEM_REQUIRE(!coarse && !penalty && !snap, SFEM_EINVAL,
+                   "FCG_CNET takes its coarse space from the model, with eliminated BCs");
+      solve_cnet(c, o.learned, cn, op64, x, r, bnorm, tol, max_iter, info, true_residual);
       total_iter = info.iterations;
       outer = info.outer_iterations;
       rel = info.true_relres;

@@ -27,7 +27,7 @@ lib = ctypes.CDLL(LIB_PATH)
 SFEM_OK, SFEM_EINVAL, SFEM_EMESH, SFEM_ENOMEM = 0, -1, -2, -3
 SFEM_ENOCONV, SFEM_EBREAKDOWN, SFEM_ECUDA, SFEM_ETIMEOUT = -4, -5, -6, -7
 SFEM_OP_CSR64, SFEM_OP_MF64, SFEM_OP_MF32, SFEM_OP_MF32_F64, SFEM_OP_NS64, SFEM_OP_ES64 = 0, 1, 2, 3, 4, 5
-SFEM_SOLVE_PCG64, SFEM_SOLVE_IR32_64, SFEM_SOLVE_FPCG_LEARNED = 0, 1, 2
+SFEM_SOLVE_PCG64, SFEM_SOLVE_IR32_64, SFEM_SOLVE_FPCG_LEARNED, SFEM_SOLVE_FCG_CNET = 0, 1, 2, 3
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -89,10 +89,33 @@ class sfem_learned_opts(ctypes.Structure):
                 ("reserved", ctypes.c_int * 6)]
 
 
+class sfem_cnet_opts(ctypes.Structure):
+    _fields_ = [("hidden", ctypes.c_int), ("seed", ctypes.c_uint64), ("reserved", ctypes.c_int * 6)]
+
+
+class sfem_cnet_run(ctypes.Structure):
+    _fields_ = [("window", ctypes.c_int), ("snap_every", ctypes.c_int), ("X", ctypes.c_void_p),
+                ("T", ctypes.c_void_p), ("cap_rows", ctypes.c_int64), ("rows", ctypes.c_int64),
+                ("reserved", ctypes.c_int * 4)]
+
+
 _P = ctypes.c_void_p
 _I64 = ctypes.c_int64
 _F = ctypes.c_float
 _SIG = {
+    "sfem_cnet_create": (ctypes.c_int, [ctypes.POINTER(_P), _P, ctypes.POINTER(sfem_cnet_opts)]),
+    "sfem_cnet_destroy": (None, [_P]),
+    "sfem_cnet_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(_I64)]),
+    "sfem_cnet_set_params": (ctypes.c_int, [_P, _P, _I64]),
+    "sfem_cnet_get_params": (ctypes.c_int, [_P, _P, _I64]),
+    "sfem_cnet_forward": (ctypes.c_int, [_P, _P, _P, _P, _I64]),
+    "sfem_cnet_loss_grad": (ctypes.c_int, [_P, _P, _P, _I64, _P, ctypes.POINTER(ctypes.c_double)]),
+    "sfem_cnet_train": (ctypes.c_int, [_P, _P, _P, _I64, _I64, ctypes.c_int, _F, ctypes.c_uint64,
+                                       ctypes.POINTER(ctypes.c_double)]),
+    "sfem_cnet_correction": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(ctypes.c_double)]),
+    "sfem_cnet_solve": (ctypes.c_int, [_P, _P, ctypes.POINTER(sfem_solve_opts), _P, ctypes.POINTER(sfem_cnet_run),
+                                       ctypes.POINTER(sfem_solve_info)]),
     "sfem_mesh_setup": (ctypes.c_int, [ctypes.POINTER(_P), _P, _I64, _P, _I64, ctypes.c_double, ctypes.c_double,
                                        _P, _P, _I64, _P, _P, _I64, ctypes.POINTER(sfem_opts), _P]),
     "sfem_assemble": (ctypes.c_int, [_P, ctypes.POINTER(sfem_csr)]),
@@ -545,6 +568,83 @@ class Learned:
             self.close()
         except Exception:
             pass
+
+
+class CNet:
+    """An sfem_cnet model (learned coarse solve) on the coarse space of
+    context `h` (see include/sfem.h).  Device arrays are torch CUDA tensors
+    (float32 rows of n_coarse values, float64 vectors)."""
+
+    def __init__(self, h, hidden=0, seed=0, keepalive=None):
+        o = sfem_cnet_opts()
+        o.hidden, o.seed = int(hidden), int(seed)
+        m = _P()
+        _check(lib.sfem_cnet_create(ctypes.byref(m), h, ctypes.byref(o)), "sfem_cnet_create")
+        self.h = m.value
+        self._keep = keepalive
+        nc, hid, npar = ctypes.c_int(), ctypes.c_int(), _I64()
+        _check(lib.sfem_cnet_info(self.h, ctypes.byref(nc), ctypes.byref(hid), ctypes.byref(npar)), "sfem_cnet_info")
+        self.n_coarse, self.hidden, self.n_params = nc.value, hid.value, npar.value
+
+    def set_params(self, theta):
+        th = np.ascontiguousarray(theta, dtype=np.float32)
+        _check(lib.sfem_cnet_set_params(self.h, _ptr(th), th.size), "sfem_cnet_set_params")
+
+    def get_params(self):
+        th = np.zeros(self.n_params, np.float32)
+        _check(lib.sfem_cnet_get_params(self.h, _ptr(th), th.size), "sfem_cnet_get_params")
+        return th
+
+    def forward(self, ctx_h, X, Y):
+        _check(lib.sfem_cnet_forward(self.h, ctx_h, _ptr(X), _ptr(Y), int(X.shape[0])), "sfem_cnet_forward")
+
+    def loss_grad(self, X, T, grad=None) -> float:
+        loss = ctypes.c_double()
+        _check(lib.sfem_cnet_loss_grad(self.h, _ptr(X), _ptr(T), int(X.shape[0]), _ptr(grad), ctypes.byref(loss)),
+               "sfem_cnet_loss_grad")
+        return loss.value
+
+    def train(self, X, T, rows=None, batch_rows=1024, epochs=1, lr=1e-3, seed=0) -> float:
+        rows = int(X.shape[0]) if rows is None else int(rows)
+        loss = ctypes.c_double()
+        _check(lib.sfem_cnet_train(self.h, _ptr(X), _ptr(T), rows, int(batch_rows), int(epochs), float(lr),
+                                   int(seed), ctypes.byref(loss)), "sfem_cnet_train")
+        return loss.value
+
+    def correction(self, ctx_h, r, z) -> float:
+        a = ctypes.c_double()
+        _check(lib.sfem_cnet_correction(self.h, ctx_h, _ptr(r), _ptr(z), ctypes.byref(a)), "sfem_cnet_correction")
+        return a.value
+
+    def close(self):
+        if self.h:
+            lib.sfem_cnet_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def cnet_solve(model, ctx_h, u, opts, window=0, snap_every=0, X=None, T=None, rows=0, check=True):
+    """sfem_cnet_solve: u (float64 tensor, device when opts.u_on_device),
+    model a CNet or None (Jacobi); appends training rows to X, T (float32
+    CUDA tensors of cap x n_coarse) when snap_every > 0.  Returns (info
+    dict, rows)."""
+    run = sfem_cnet_run()
+    run.window, run.snap_every = int(window), int(snap_every)
+    run.X, run.T = _ptr(X), _ptr(T)
+    run.cap_rows = 0 if X is None else int(X.shape[0])
+    run.rows = int(rows)
+    info = sfem_solve_info()
+    st = lib.sfem_cnet_solve(model.h if model is not None else None, ctx_h, ctypes.byref(opts), _ptr(u),
+                             ctypes.byref(run), ctypes.byref(info))
+    out = {k: getattr(info, k) for k, _ in info._fields_ if k != "reserved"}
+    if check and st != SFEM_OK:
+        raise SfemError(st, "sfem_cnet_solve")
+    return out, int(run.rows)
 
 
 # ---- convenience wrapper ----------------------------------------------------

@@ -452,6 +452,13 @@ int sfem_cnet_loss_grad(sfem_cnet *m, const float *X, const float *T, int64_t ro
  * epoch (host, may be NULL). */
 int sfem_cnet_train(sfem_cnet *m, const float *X, const float *T, int64_t rows, int64_t batch_rows, int epochs,
                     float lr, uint64_t seed, double *loss);
+/* Rows first .. first + count - 1 of the DEVICE buffers X, T (n_c floats
+ * each): x standard normal (counter-based generator of (seed, entry)), t =
+ * A_c^-1 x by the coarse setup's FP32 inverse, both divided by their RMS.
+ * Rows that teach the network the coarse solve in every direction, beside
+ * the rows of the solver's own residuals. */
+int sfem_cnet_random_rows(sfem_cnet *m, sfem_ctx *ctx, float *X, float *T, int64_t first, int64_t count,
+                          uint64_t seed);
 /* z = D^-1 r + alpha P Pi y for one residual (DEVICE r, z: ndof FP64); alpha
  * to host. */
 int sfem_cnet_correction(sfem_cnet *m, sfem_ctx *ctx, const double *r, double *z, double *alpha);

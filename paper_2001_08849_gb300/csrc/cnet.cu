@@ -532,6 +532,74 @@ static double cn_train(CNet &L, const float *X, const float *T, int64_t rows, in
   return last;
 }
 
+// ---- random training rows -------------------------------------------------------
+// dense symmetric C (nc x nc) from its packed lower 64 x 64 blocks
+__global__ void k_cn_unpack(const float *__restrict__ Cp, int nc, float *__restrict__ Cd) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)nc * nc) return;
+  int i = (int)(e / nc), j = (int)(e % nc);
+  if (j > i) {
+    const int t = i;
+    i = j;
+    j = t;
+  }
+  const int a = i / 64, b = j / 64;
+  const int64_t t = (int64_t)a * (a + 1) / 2 + b;
+  Cd[e] = Cp[t * 4096 + (i % 64) * 64 + (j % 64)];
+}
+
+// standard normal entries by Box-Muller on splitmix64 uniforms of (seed, index)
+__global__ void k_cn_randn(float *__restrict__ X, int64_t n, uint64_t seed) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint64_t h = splitmix64(seed * 0x100000001b3ull + (uint64_t)i);
+  const double u1 = (double)((h >> 11) + 1) * (1.0 / 9007199254740992.0);
+  const double u2 = (double)(splitmix64(h) >> 11) * (1.0 / 9007199254740992.0);
+  X[i] = (float)(sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2));
+}
+
+// each row of A (rows x n) divided by its RMS (one block per row)
+__global__ void k_cn_rownorm(float *__restrict__ A, int n) {
+  float *row = A + (int64_t)blockIdx.x * n;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += (double)row[i] * row[i];
+  s = block_sum<256>(s);
+  __shared__ float inv;
+  if (threadIdx.x == 0) inv = s > 0.0 ? (float)(1.0 / sqrt(s / n)) : 0.f;
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) row[i] *= inv;
+}
+
+// rows [first, first + count) of (X, T): x Gaussian, t = C x, both
+// normalised to unit RMS (C = A_c^-1 of the coarse setup, FP32)
+static void cn_random_rows(CNet &L, const CoarseDev &cs, float *X, float *T, int64_t first, int64_t count,
+                           uint64_t seed) {
+  if (count <= 0) return;
+  cudaStream_t st = L.stream;
+  const int nc = L.nc;
+  float *Cd = L.mem.get<float>((size_t)nc * nc);
+  try {
+    k_cn_unpack<<<grid_for((int64_t)nc * nc, 256), 256, 0, st>>>(cs.C, nc, Cd);
+    SFEM_CHECK_LAUNCH();
+    float *Xr = X + first * nc, *Tr = T + first * nc;
+    k_cn_randn<<<grid_for(count * nc, 256), 256, 0, st>>>(Xr, count * nc, seed);
+    SFEM_CHECK_LAUNCH();
+    for (int64_t r0 = 0; r0 < count; r0 += 65536) {  // GEMM grids of at most 1024 row tiles
+      const int nr = (int)std::min<int64_t>(65536, count - r0);
+      cn_gemm(L, nr, nc, nc, Xr + r0 * nc, nc, false, Cd, nc, false, Tr + r0 * nc, nc);
+    }
+    k_cn_rownorm<<<(unsigned)count, 256, 0, st>>>(Xr, nc);
+    SFEM_CHECK_LAUNCH();
+    k_cn_rownorm<<<(unsigned)count, 256, 0, st>>>(Tr, nc);
+    SFEM_CHECK_LAUNCH();
+    SFEM_CUDA(cudaStreamSynchronize(st));
+  } catch (...) {
+    L.mem.drop(Cd);
+    throw;
+  }
+  L.mem.drop(Cd);
+}
+
 // ---- inference and the solver ---------------------------------------------------
 // y = MLP(rc / RMS(rc)) from the restricted residual in cs.rc, then alpha
 // (S->s, S->yr, S->yAy, S->alpha); every kernel returns at once while *stop
@@ -925,6 +993,15 @@ extern "C" int sfem_cnet_correction(sfem_cnet *m, sfem_ctx *h, const double *r, 
     throw;
   }
   L.mem.drop(S);
+  CN_END
+}
+
+extern "C" int sfem_cnet_random_rows(sfem_cnet *m, sfem_ctx *h, float *X, float *T, int64_t first, int64_t count,
+                                     uint64_t seed) {
+  CN_BEGIN
+  cn_check_ctx(m, h);
+  SFEM_REQUIRE(X && T && first >= 0 && count >= 0, SFEM_EINVAL, "X, T required, first and count >= 0");
+  cn_random_rows(m->L, h->c.coarse->dev, X, T, first, count, seed);
   CN_END
 }
 

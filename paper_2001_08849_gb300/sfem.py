@@ -114,6 +114,7 @@ _SIG = {
     "sfem_cnet_train": (ctypes.c_int, [_P, _P, _P, _I64, _I64, ctypes.c_int, _F, ctypes.c_uint64,
                                        ctypes.POINTER(ctypes.c_double)]),
     "sfem_cnet_correction": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(ctypes.c_double)]),
+    "sfem_cnet_random_rows": (ctypes.c_int, [_P, _P, _P, _P, _I64, _I64, ctypes.c_uint64]),
     "sfem_cnet_solve": (ctypes.c_int, [_P, _P, ctypes.POINTER(sfem_solve_opts), _P, ctypes.POINTER(sfem_cnet_run),
                                        ctypes.POINTER(sfem_solve_info)]),
     "sfem_mesh_setup": (ctypes.c_int, [ctypes.POINTER(_P), _P, _I64, _P, _I64, ctypes.c_double, ctypes.c_double,
@@ -610,6 +611,10 @@ class CNet:
         _check(lib.sfem_cnet_train(self.h, _ptr(X), _ptr(T), rows, int(batch_rows), int(epochs), float(lr),
                                    int(seed), ctypes.byref(loss)), "sfem_cnet_train")
         return loss.value
+
+    def random_rows(self, ctx_h, X, T, first, count, seed=0):
+        _check(lib.sfem_cnet_random_rows(self.h, ctx_h, _ptr(X), _ptr(T), int(first), int(count), int(seed)),
+               "sfem_cnet_random_rows")
 
     def correction(self, ctx_h, r, z) -> float:
         a = ctypes.c_double()

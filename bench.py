@@ -99,7 +99,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the PCG64 comparison solve")
-    ap.add_argument("--learned-train", type=int, default=8, help="training loads of the learned form")
+    ap.add_argument("--learned-train", type=int, default=4, help="training loads of the learned form")
     ap.add_argument("--learned-test", type=int, default=2, help="held-out loads of the learned form")
     ap.add_argument("--oracle-sample", type=int, nargs=2, default=None, metavar=("SLAB_CELLS", "ITERS"),
                     help="internal: print one oracle sample as JSON (run in a subprocess by cpu_baseline)")
@@ -390,11 +390,18 @@ def mixed_family_form(S):
     return out
 
 
-def learned_form(S, n_train=8, n_test=2, every=8, epochs=10):
-    """Train the coarse-correction network on snapshots of Jacobi-PCG runs of
-    the 2M-tet beam under random loads (seeds 100..), then time held-out
-    loads (seeds 200..) with flexible PCG + correction against flexible PCG
-    with the Jacobi preconditioner alone (FP64, CSR operator, tol 1e-8)."""
+def learned_coarse_form(S, n_train=4, n_test=2, n_random=20000, rounds=2, cap=100000, max_iter=12000, hidden=0,
+                        every=4, probe=False, coarse_dims=(0, 0, 0)):
+    """The learned coarse solve on the 2M-tet beam: a network on the
+    restricted residual trained toward the Galerkin coarse solution (the
+    library's default coarse grid), on rows of the solver's own solves of
+    random load cases (seeds 100..; round 0: Jacobi-PCG rows every 3
+    iterations and n_random random coarse rows; then `rounds` on-policy
+    rounds of the learned solver, rows every 2 iterations, solves capped at
+    max_iter), then held-out loads (seeds 200..): truncated flexible CG
+    (window 5) with the network against Jacobi-PCG and against the exact
+    two-level PCG, FP64, CSR operator, tol 1e-8, each timed with CUDA
+    events."""
     import numpy as np
     import torch
     from inputs.kuhn_beam import multi_load_cantilever
@@ -403,61 +410,84 @@ def learned_form(S, n_train=8, n_test=2, every=8, epochs=10):
     test = list(range(200, 200 + n_test))
     prob = multi_load_cantilever(nx, ny, nz, train + test, seed=SEED)
     fe = S.FsFem(prob, on_device=True)
-    model = None
+    net = None
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ea.record(stream)
+        out = fn()
+        eb.record(stream)
+        torch.cuda.synchronize()
+        return out, ea.elapsed_time(eb) / 1e3
+
     try:
         S.sfem_assemble(fe.h)
-        dims = tuple(-(-(c + 1) // 8) for c in CELLS)          # patches of 8 x 8 x 8 nodes
-        model = S.Learned(fe.h, patch_dims=dims, seed=1, keepalive=fe._keep)
-        n = fe.ndof
-        cap = int(1.2 * 6000 / every) * model.n_patches * n_train
-        X = torch.empty(cap, 84, dtype=torch.float32, device="cuda")
-        T = torch.empty(cap, 3, dtype=torch.float32, device="cuda")
-        rows, jac_iters = 0, []
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
+        ci = S.sfem_coarse_setup(fe.h, patch_dims=tuple(coarse_dims))
+        net = S.CNet(fe.h, hidden=hidden, seed=1, keepalive=fe._keep)
+        nc = net.n_coarse
+        trend = []
+
+        def held_out_probe():  # iterations of the first held-out load (diagnostic)
+            if probe:
+                o = S.solve_opts(kind=S.SFEM_SOLVE_PCG64, op64=S.SFEM_OP_CSR64, rhs=n_train, tol=TOL,
+                                 u_on_device=True, max_iter=30000)
+                u = torch.zeros(fe.ndof, dtype=torch.float64, device="cuda")
+                trend.append(S.cnet_solve(net, fe.h, u, o, window=5, check=False)[0]["iterations"])
+        X = torch.zeros((cap, nc), dtype=torch.float32, device="cuda")
+        T = torch.zeros_like(X)
+        rows = 0
+        data_s = train_s = 0.0
         for k in range(n_train):
-            us = torch.zeros(n, dtype=torch.float64, device="cuda")
-            S.sfem_solve(fe.h, us, S.solve_opts(kind=S.SFEM_SOLVE_PCG64, op64=S.SFEM_OP_CSR64, rhs=k, tol=1e-10,
-                                                u_on_device=True), check=False)
-            got, info = model.collect(fe.h, S.solve_opts(kind=S.SFEM_SOLVE_FPCG_LEARNED, op64=S.SFEM_OP_CSR64,
-                                                         rhs=k, tol=TOL, check_every=every), us, X, T, rows)
-            rows += got
-            jac_iters.append(info["iterations"])
-        torch.cuda.synchronize()
-        data_s = time.perf_counter() - t0
-        loss0 = model.loss_grad(X[:min(rows, 1 << 18)], T[:min(rows, 1 << 18)])  # a sample of the rows
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        loss1 = model.train(X, T, rows=rows, batch_rows=4096, epochs=epochs, lr=1e-3, seed=3)
-        torch.cuda.synchronize()
-        train_s = time.perf_counter() - t0
-        pace = int(np.mean(jac_iters))
-        res = {"jacobi": [], "learned": []}
+            o = S.solve_opts(kind=S.SFEM_SOLVE_PCG64, op64=S.SFEM_OP_CSR64, rhs=k, tol=TOL, u_on_device=True)
+            u = torch.zeros(fe.ndof, dtype=torch.float64, device="cuda")
+            (_, rows), t = timed(lambda: S.cnet_solve(None, fe.h, u, o, snap_every=3, X=X, T=T, rows=rows))
+            data_s += t
+        n_rand = min(n_random, cap - rows)
+        _, t = timed(lambda: net.random_rows(fe.h, X, T, rows, n_rand, seed=1))
+        data_s += t
+        rows += n_rand
+        loss0, t = timed(lambda: net.train(X, T, rows=rows, batch_rows=256, epochs=80, lr=1e-3, seed=1))
+        train_s += t
+        loss = loss0
+        held_out_probe()
+        for rnd in range(rounds):
+            for k in range(n_train):
+                o = S.solve_opts(kind=S.SFEM_SOLVE_PCG64, op64=S.SFEM_OP_CSR64, rhs=k, tol=TOL, u_on_device=True,
+                                 max_iter=max_iter)
+                u = torch.zeros(fe.ndof, dtype=torch.float64, device="cuda")
+                (_, rows), t = timed(lambda: S.cnet_solve(net, fe.h, u, o, window=5, snap_every=every, X=X, T=T,
+                                                          rows=rows, check=False))
+                data_s += t
+            loss, t = timed(lambda: net.train(X, T, rows=rows, batch_rows=256, epochs=30, lr=1e-3, seed=2 + rnd))
+            train_s += t
+            held_out_probe()
+        res = {"jacobi": [], "learned": [], "two_level": []}
         for k in range(n_train, n_train + n_test):
-            for name, learned in (("jacobi", None), ("learned", model)):
-                u = torch.zeros(n, dtype=torch.float64, device="cuda")
-                o = S.solve_opts(kind=S.SFEM_SOLVE_FPCG_LEARNED, op64=S.SFEM_OP_CSR64, rhs=k, tol=TOL,
-                                 u_on_device=True, learned=learned, learned_pace=pace)
-                torch.cuda.synchronize()
-                t0 = time.perf_counter()
-                inf = S.sfem_solve(fe.h, u, o, check=False)
-                torch.cuda.synchronize()
-                res[name].append({"time_to_solve_s": time.perf_counter() - t0, "iterations": inf["iterations"],
-                                  "learned_iterations": inf["learned_iterations"],
+            o = S.solve_opts(kind=S.SFEM_SOLVE_PCG64, op64=S.SFEM_OP_CSR64, rhs=k, tol=TOL, u_on_device=True)
+            o2 = S.solve_opts(kind=S.SFEM_SOLVE_PCG64, op64=S.SFEM_OP_CSR64, rhs=k, tol=TOL, u_on_device=True,
+                              precond=1)
+            for name, fn in (("jacobi", lambda u: S.sfem_solve(fe.h, u, o, check=False)),
+                             ("learned", lambda u: S.cnet_solve(net, fe.h, u, o, window=5, check=False)[0]),
+                             ("two_level", lambda u: S.sfem_solve(fe.h, u, o2, check=False))):
+                u = torch.zeros(fe.ndof, dtype=torch.float64, device="cuda")
+                inf, t = timed(lambda: fn(u))
+                res[name].append({"time_to_solve_s": t, "iterations": inf["iterations"],
                                   "fallbacks": inf["fallbacks"], "true_relres": inf["true_relres"],
                                   "status": inf["status"]})
-        it_j = float(np.mean([r["iterations"] for r in res["jacobi"]]))
-        it_l = float(np.mean([r["iterations"] for r in res["learned"]]))
-        t_j = float(np.mean([r["time_to_solve_s"] for r in res["jacobi"]]))
-        t_l = float(np.mean([r["time_to_solve_s"] for r in res["learned"]]))
-        return {"train_loads": n_train, "test_loads": n_test, "patch_dims": list(dims),
-                "snapshot_every": every, "rows": rows, "epochs": epochs, "loss_before": loss0,
-                "loss_after": loss1, "data_s": data_s, "train_s": train_s, "pace": pace,
-                "jacobi": res["jacobi"], "learned": res["learned"],
-                "iteration_gain": it_j / it_l, "time_gain": t_j / t_l}
+        mean = lambda name, key: float(np.mean([r[key] for r in res[name]]))
+        return {"train_loads": n_train, "test_loads": n_test, "coarse_dims": list(ci["patch_dims"]),
+                "n_coarse": nc, "hidden": net.hidden, "rows": rows, "random_rows": n_rand, "rounds": rounds,
+                "loss_round0": loss0, "loss_final": loss, "data_s": data_s, "train_s": train_s,
+                "jacobi": res["jacobi"], "learned": res["learned"], "two_level": res["two_level"],
+                "held_out_trend": trend,
+                "iteration_gain": mean("jacobi", "iterations") / mean("learned", "iterations"),
+                "time_gain": mean("jacobi", "time_to_solve_s") / mean("learned", "time_to_solve_s"),
+                "vs_exact_two_level_iterations": mean("two_level", "iterations") / mean("learned", "iterations")}
     finally:
-        if model is not None:
-            model.close()
+        if net is not None:
+            net.close()
         fe.close()
 
 
@@ -465,27 +495,27 @@ def learned_form(S, n_train=8, n_test=2, every=8, epochs=10):
 # our arm
 # ---------------------------------------------------------------------------
 
-COMPARE = ("pcg64_csr_jacobi", "pcg64_mf64_jacobi", "ir32_64_jacobi", "ir32_64_two_level", "fpcg_learned")
+COMPARE = ("pcg64_csr_jacobi", "pcg64_mf64_jacobi", "ir32_64_jacobi", "ir32_64_two_level", "learned_coarse")
 
 
 def compare_keys(forms):
     """Flat top-level keys for the time-to-solve comparison at rel res 1e-8
-    on the same GPU: tts_<form>_s, it_<form>, relres_<form> (fpcg_learned:
+    on the same GPU: tts_<form>_s, it_<form>, relres_<form> (learned_coarse:
     the mean over the held-out loads, learned side)."""
     out = {}
     for name in COMPARE:
         f = forms.get(name)
         if not f or "error" in f:
             continue
-        if name == "fpcg_learned":
+        if name == "learned_coarse":
             rows = f.get("learned") or []
             if not rows:
                 continue
             t = sum(r["time_to_solve_s"] for r in rows) / len(rows)
             it = sum(r["iterations"] for r in rows) / len(rows)
             rr = max(r["true_relres"] for r in rows)
-            out["fpcg_learned_iteration_gain"] = f.get("iteration_gain")
-            out["fpcg_learned_time_gain"] = f.get("time_gain")
+            out["learned_coarse_iteration_gain"] = f.get("iteration_gain")
+            out["learned_coarse_time_gain"] = f.get("time_gain")
         else:
             t, it, rr = f["time_to_solve_s"], f["iterations"], f["true_relres"]
         out[f"tts_{name}_s"] = t
@@ -685,7 +715,7 @@ def main():
     if not args.no_forms and rank == 0:
         forms.update(mixed_family_form(S))
         forms["batch_64x4"] = batch_form(S)
-        forms["fpcg_learned"] = learned_form(S, n_train=args.learned_train, n_test=args.learned_test)
+        forms["learned_coarse"] = learned_coarse_form(S, n_train=args.learned_train, n_test=args.learned_test)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

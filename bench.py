@@ -397,8 +397,8 @@ def learned_coarse_form(S, n_train=4, n_test=2, n_random=20000, rounds=2, cap=10
     library's default coarse grid), on rows of the solver's own solves of
     random load cases (seeds 100..; round 0: Jacobi-PCG rows every 3
     iterations and n_random random coarse rows; then `rounds` on-policy
-    rounds of the learned solver, rows every 2 iterations, solves capped at
-    max_iter), then held-out loads (seeds 200..): truncated flexible CG
+    rounds of the learned solver, rows every `every` iterations, solves
+    capped at max_iter), then held-out loads (seeds 200..): truncated flexible CG
     (window 5) with the network against Jacobi-PCG and against the exact
     two-level PCG, FP64, CSR operator, tol 1e-8, each timed with CUDA
     events."""

@@ -279,24 +279,28 @@ struct TileBuild {
   int64_t rs;    // plane stride
   uint32_t *node_inc;  // per tile node: base of its slot group | own-slot count << 16
   int *max_slots;      // largest slot-array length over the tiles
+  int key2_len;        // pass 2: power of two >= the largest node list (slot layout sort)
   unsigned long long *overflow;
 };
 
 // one CTA per tile; dynamic smem: halo candidates (kHaloCand padded) +
 // node candidates (4*(kTileMax + kHaloCand) padded), and in pass 2 the slot
-// layout tables (2 * kNodeP)
+// layout tables (sized by the largest node list of pass 1: key2_len + 2 L +
+// L / 32 + 4 ints)
 constexpr int kHaloP = 2048;                        // >= kHaloCand, power of two
 constexpr int kNodeP = 16384;                       // >= 4*(kTileMax + kHaloCand)
-constexpr int kMaxTileNodes = 8000;                 // 2 L + L/32 + 3 <= kNodeP (pass-2 tables)
+constexpr int kMaxTileNodes = 8000;                 // bounds the pass-2 tables (see below)
 static_assert(kHaloP >= kHaloCand && kNodeP >= 4 * (kTileMax + kHaloCand), "tile build buffers too small");
-static_assert(2 * kMaxTileNodes + kMaxTileNodes / 32 + 3 <= kNodeP, "slot layout tables too small");
+// pass 2 tables at their largest: pow2(kMaxTileNodes) + 2 kMaxTileNodes + kMaxTileNodes / 32 + 4
+static_assert(8192 >= kMaxTileNodes && 8192 + 2 * kMaxTileNodes + kMaxTileNodes / 32 + 4 <= 2 * kNodeP,
+              "slot layout tables exceed the largest pass-2 shared memory");
 constexpr int kBuildThreads = 1024;
 
 __global__ void __launch_bounds__(kBuildThreads) k_tile_build(TileBuild B, int pass) {
   extern __shared__ int sm[];
   int *halo = sm;                 // kHaloP
   int *nodes = sm + kHaloP;       // kNodeP
-  int *aux = nodes + kNodeP;      // 2 * kNodeP (pass 2)
+  int *aux = nodes + kNodeP;      // slot layout tables (pass 2)
   const int tile = blockIdx.x;
   const int s = B.tile_start[tile], e = B.tile_start[tile + 1];
   const int n_own = e - s;
@@ -357,7 +361,7 @@ __global__ void __launch_bounds__(kBuildThreads) k_tile_build(TileBuild B, int p
   // first (ties by node id), in groups of 32; group g starts at gbase[g] and
   // holds 32 x (count of its first node) positions
   int *key2 = aux;                  // pow2(L): (2047 - count) << 16 | ascending index
-  int *start = aux + kNodeP;        // L + 1: first key of each node (ascending index)
+  int *start = aux + B.key2_len;    // L + 1: first key of each node (ascending index)
   int *jds = start + L + 1;         // L: position of each node in the count order
   int *gbase = jds + L;             // groups + 1
   const int ngroups = (L + 31) / 32;
@@ -918,9 +922,9 @@ void build_tiles(Ctx &c) {
   B.n_halo = nh;
   B.n_nodes = nn;
   B.overflow = ovf;
-  const size_t build_smem = (kHaloP + kNodeP) * sizeof(int);       // pass 1
-  const size_t build_smem2 = (kHaloP + 3 * kNodeP) * sizeof(int);  // pass 2: slot layout tables
-  SFEM_CUDA(cudaFuncSetAttribute(k_tile_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)build_smem2));
+  const size_t build_smem = (kHaloP + kNodeP) * sizeof(int);  // pass 1
+  SFEM_CUDA(cudaFuncSetAttribute(k_tile_build, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)((kHaloP + 3 * kNodeP) * sizeof(int))));  // the largest pass 2 can ask
   k_tile_build<<<(unsigned)nt, kBuildThreads, build_smem, c.stream>>>(B, 1);
   SFEM_CHECK_LAUNCH();
   c.tl.hoff = c.mem.get<int64_t>(nt + 1);
@@ -953,6 +957,10 @@ void build_tiles(Ctx &c) {
   B.rec = c.tl.rec;
   B.rs = n;
   B.max_slots = mx + 2;
+  B.key2_len = 32;
+  while (B.key2_len < c.tl.max_nodes) B.key2_len <<= 1;
+  const size_t build_smem2 =
+      (size_t)(kHaloP + kNodeP + B.key2_len + 2 * c.tl.max_nodes + c.tl.max_nodes / 32 + 4) * sizeof(int);
   k_tile_build<<<(unsigned)nt, kBuildThreads, build_smem2, c.stream>>>(B, 2);
   SFEM_CHECK_LAUNCH();
   int hslots = 0;

@@ -35,7 +35,17 @@
 
 namespace sfem {
 
-constexpr long long kBarrierSpinLimit = 1ll << 24;  // bounded wait: 4.3 s measured (2^24 sleeps of ~256 ns)
+// bounded wait of the grid barrier: 4 s of global time (%globaltimer), and
+// 2^24 sleeps as a second bound (measured 4.3 s: __nanosleep's duration is
+// only approximate, so the count alone does not bound the time)
+constexpr long long kBarrierSpinLimit = 1ll << 24;
+constexpr unsigned long long kBarrierWaitNs = 4000000000ull;
+
+__device__ __forceinline__ unsigned long long barrier_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 struct BatchBeam {
   TileArgs A;
@@ -120,8 +130,9 @@ __device__ __forceinline__ bool grid_barrier(const BatchDev &a) {
       atomicAdd(a.bar_gen, 1u);
     } else {
       long long spins = 0;
+      const unsigned long long t0 = barrier_ns();
       while (*gen == g) {
-        if (++spins > kBarrierSpinLimit) {
+        if (++spins > kBarrierSpinLimit || ((spins & 255) == 0 && barrier_ns() - t0 > kBarrierWaitNs)) {
           atomicExch(a.err, 1);
           good = 0;
           break;
@@ -455,7 +466,7 @@ static std::map<long long, int> g_tune_cache;  // key: (device, total tiles buck
 // Self-test of the bounded wait in grid_barrier: one CTA enters the barrier
 // with the arrival counter offset by one, so it is never the last arrival
 // and no block advances the generation.  Its wait runs out after
-// kBarrierSpinLimit spins (a few seconds), sets the error word and returns
+// kBarrierWaitNs (a few seconds), sets the error word and returns
 // false; nothing else waits on it.
 __global__ void k_barrier_selftest(BatchDev a, int *passed) {
   const bool ok = grid_barrier(a);

@@ -252,7 +252,13 @@ typedef struct sfem_batch_opts {
   int use_graph;         /* 1: capture a round as a CUDA graph */
   int precond;           /* 0: the persistent Jacobi solve of all systems together; 1: each
                             system by the two-level mixed solve of its context (coarse space
-                            built with the default options where possible; inner_tol 0: 0.03) */
+                            built with the default options where possible; inner_tol 0: 0.03);
+                            2: the persistent solve of all systems together with the two-level
+                            preconditioner of each context inside the launch (restriction,
+                            coarse product and prolongation as phases of the persistent
+                            kernel; coarse spaces built with the default options on first
+                            use and kept by the contexts; a beam without one runs Jacobi;
+                            inner_tol 0: 0.03) */
   int reserved[4];
 } sfem_batch_opts;
 
@@ -267,7 +273,10 @@ typedef struct sfem_batch_stats {
                              refreshes in a row improving the true residual by
                              less than 10%) and were finished by FP64 PCG (with the
                              two-level preconditioner where a coarse space exists) */
-  int reserved[3];
+  int launch_iterations;  /* iterations of the persistent launches (each steps every
+                             active system once), summed over launches */
+  float fallback_ms;      /* device time of the FP64 PCG fallbacks (part of ms) */
+  int reserved[1];
 } sfem_batch_stats;
 
 int sfem_batch_solve(sfem_ctx *const *ctxs, int n, double *const *u, const sfem_batch_opts *opts,

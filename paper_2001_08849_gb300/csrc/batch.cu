@@ -18,6 +18,23 @@
 // Rounds repeat (as a captured CUDA graph) until no system is active.
 // Per-system scalars are double-buffered by iteration parity so that no
 // block reads a value another block is writing.
+//
+// precond = 2 runs the same rounds with the two-level preconditioner
+// z = D^-1 r + P Pi C Pi^T r of each beam's coarse space (coarse.cu) inside
+// the persistent launch:
+//        P2  walks each beam's nodes grouped by interpolation cell (the
+//            coarse space's chunks of <= kChunkNodes nodes), one warp per
+//            256 nodes: the x/r updates, D^-1 r.r and r.r, and the
+//            restriction rc += Pi^T r (24 warp sums per cell, FP32 atomics
+//            into the system's rc);
+//        P2c yc = C rc over (beam, 64 x 64 block of the packed C) items, the
+//            block read once for all load cases of the beam, and
+//            rc.C rc added to z.r (z.r = D^-1 r.r + (Pi^T r).yc);
+//        P3  p = D^-1 r + P Pi yc + beta p;
+// one grid barrier more per iteration (four).  The refresh computes the
+// same z for the recomputed residuals (restriction and coarse product
+// kernels over the same items).  Beams without a coarse space fall back to
+// Jacobi inside the same launch (their P2 items are plain node ranges).
 
 #include <cuda_runtime.h>
 
@@ -51,6 +68,9 @@ struct BatchBeam {
   TileArgs A;
   int first_sys, nrhs;
   float lam, mu;
+  int64_t n_nodes;
+  int has_cs;   // precond 2: the beam has a coarse space (else Jacobi)
+  CoarseDev cs; // its coarse space (rc / yc unused: every system has its own)
 };
 
 struct BatchSys {
@@ -60,6 +80,8 @@ struct BatchSys {
   const double *f;
   int64_t n;
   double bnorm;
+  float *rc, *yc;  // precond 2: restricted residual and coarse correction (npad each)
+  int beam;
 };
 
 struct SysState {
@@ -94,6 +116,15 @@ struct BatchDev {
   int *beam_skip;          // per beam: 1 if no system of it needs the FP64 refresh
   int *any_active;
   long long *iters_run;    // total CG iterations (summed over systems) of the last launch
+  long long *launch_iters; // iterations of the persistent launches, summed over launches
+  // precond 2 (two-level inside the launch)
+  int two_level;
+  const int *uwork_prefix; // n_beams + 1: node chunks per beam (P2 items)
+  int total_uwork;
+  const int *cwork_prefix; // n_beams + 1: packed C blocks per beam (P2c items)
+  int total_cwork;
+  float *cvec;             // every system's rc and yc, concatenated
+  int64_t cvec_len;
 };
 
 // state written by another block during the same launch: read through L2
@@ -209,6 +240,244 @@ __device__ __forceinline__ SysState decide(const BatchDev &a, const SysState *st
   return n2;
 }
 
+// ---- two-level phases (precond 2) ------------------------------------------
+
+constexpr int kBatchWarpNodes = kChunkNodes / (kTileThreads / 32);  // nodes per warp of a P2 item
+static_assert(kTileThreads == 256, "the coarse product maps 64 rows x 4 column groups onto 256 threads");
+
+// largest b with prefix[b] <= w
+__device__ __forceinline__ int find_item(const int *prefix, int n, int w) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (prefix[mid] <= w)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+// a system the current iteration steps (P2 / P2c): active with a valid step
+__device__ __forceinline__ bool stepping(const SysState *st, const double *pq, int s, double &alpha) {
+  if (!__ldcg(&st[s].active)) return false;
+  const double pqs = __ldcg(&pq[s]);
+  alpha = __ldcg(&st[s].rz) / pqs;
+  return pqs > 0.0 && isfinite(alpha);
+}
+
+// a system whose residual the refresh recomputes
+__device__ __forceinline__ bool refreshing(const SysState &ss) {
+  return ss.status == 0 && !ss.active && ss.reason != 0;
+}
+
+// butterfly sum over the warp (every lane gets the total)
+__device__ __forceinline__ float warp_allsum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_allsum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// P2 item w (beam, node chunk); this warp's kBatchWarpNodes nodes of it.
+// kUpdate: the CG update of the stepping systems (d += alpha p,
+// r = P (r - alpha q)) with D^-1 r.r and r.r into sums, then rc += Pi^T r;
+// else (refresh) rc += Pi^T r of the refreshing systems' new residuals.
+// No block barrier: warps past the chunk's end return at once.
+template <bool kUpdate>
+__device__ __forceinline__ void tl_update_item(const BatchDev &a, const SysState *st, const double *pq,
+                                               double *sums, int w) {
+  const int b = find_item(a.uwork_prefix, a.n_beams, w);
+  const BatchBeam &B = a.beams[b];
+  const int k = w - a.uwork_prefix[b];
+  const bool cs_on = B.has_cs != 0;
+  if (!kUpdate && !cs_on) return;  // nothing to restrict
+  int cell = 0, first, end;
+  if (cs_on) {
+    const int4 ch = B.cs.chunk[k];
+    cell = ch.x;
+    first = ch.y;
+    end = ch.z;
+  } else {
+    first = k * kChunkNodes;
+    end = (int)min((int64_t)first + kChunkNodes, B.n_nodes);
+  }
+  const int lane = threadIdx.x & 31;
+  const int wb = first + kBatchWarpNodes * (threadIdx.x >> 5);
+  if (wb >= end) return;
+  const int we = min(wb + kBatchWarpNodes, end);
+  for (int j = 0; j < B.nrhs; ++j) {
+    const int s = B.first_sys + j;
+    double alpha = 0.0;
+    if (kUpdate) {
+      if (!stepping(st, pq, s, alpha)) continue;
+    } else {
+      if (!refreshing(st[s])) continue;
+    }
+    const BatchSys &S = a.sys[s];
+    double *__restrict__ d = S.d;
+    double *__restrict__ r = S.r;
+    const double *__restrict__ p = S.p;
+    const double *__restrict__ q = S.q;
+    const double *__restrict__ dinv = S.dinv;
+    const uint8_t *__restrict__ dmask = S.dmask;
+    const int32_t *__restrict__ cnodes = B.cs.cnodes;
+    const float *__restrict__ frac = B.cs.frac;
+    double rz = 0.0, rr = 0.0;
+    float acc[24];
+#pragma unroll
+    for (int v = 0; v < 24; ++v) acc[v] = 0.f;
+    for (int i = wb + lane; i < we; i += 32) {
+      const int64_t node = cs_on ? (int64_t)cnodes[i] : (int64_t)i;
+      float rf[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const int64_t dof = 3 * node + c;
+        double ri;
+        if (kUpdate) {
+          d[dof] = __ldcg(&d[dof]) + alpha * __ldcg(&p[dof]);
+          ri = dmask[dof] ? __ldcg(&r[dof]) - alpha * __ldcg(&q[dof]) : 0.0;
+          r[dof] = ri;
+          rz += dinv[dof] * ri * ri;
+          rr += ri * ri;
+        } else {
+          ri = __ldcg(&r[dof]);
+        }
+        rf[c] = (float)ri;
+      }
+      if (cs_on) {
+        const float f[3] = {frac[3 * node], frac[3 * node + 1], frac[3 * node + 2]};
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) {
+          const float wk = cs_weight(f, kk);
+#pragma unroll
+          for (int c = 0; c < 3; ++c) acc[3 * kk + c] = fmaf(wk, rf[c], acc[3 * kk + c]);
+        }
+      }
+    }
+    if (kUpdate) {
+      rz = warp_allsum(rz);
+      rr = warp_allsum(rr);
+      if (lane == 0) {
+        atomicAdd(&sums[2 * s], rz);
+        atomicAdd(&sums[2 * s + 1], rr);
+      }
+    }
+    if (cs_on) {
+#pragma unroll
+      for (int v = 0; v < 24; ++v) {
+        const float t = warp_allsum(acc[v]);
+        if (lane == v) atomicAdd(&S.rc[3 * cs_corner(B.cs, cell, v / 3) + v % 3], t);
+      }
+    }
+  }
+}
+
+// P2c item w (beam, block t of the packed C): yc += C rc for every selected
+// system of the beam (kUpdate: stepping; else refreshing), the block read
+// once, and rc.C rc added to sums[2 s] (z.r).  Block-uniform; uses
+// 2 x 64 + 8 x 64 floats of sm.
+template <bool kUpdate>
+__device__ __forceinline__ void tl_coarse_item(const BatchDev &a, const SysState *st, const double *pq,
+                                               double *sums, int w, float *sm) {
+  const int b = find_item(a.cwork_prefix, a.n_beams, w);
+  const BatchBeam &B = a.beams[b];
+  const int t = w - a.cwork_prefix[b];
+  int ab = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+  while ((ab + 1) * (ab + 2) / 2 <= t) ++ab;
+  while (ab * (ab + 1) / 2 > t) --ab;
+  const int bb = t - ab * (ab + 1) / 2;
+  const int i = threadIdx.x >> 2, q = threadIdx.x & 3;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const float4 *blk = reinterpret_cast<const float4 *>(B.cs.C + (int64_t)t * 4096) + i * 16 + q * 4;
+  float4 v[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) v[u] = __ldg(blk + u);
+  float *ra = sm, *rb = sm + 64, *part = sm + 128;  // part: 8 warps x 64
+  for (int j = 0; j < B.nrhs; ++j) {
+    const int s = B.first_sys + j;
+    double alpha;
+    const bool sel = kUpdate ? stepping(st, pq, s, alpha) : refreshing(st[s]);
+    if (!sel) continue;  // uniform over the block
+    const BatchSys &S = a.sys[s];
+    __syncthreads();
+    if (threadIdx.x < 64) {
+      ra[threadIdx.x] = __ldcg(&S.rc[ab * 64 + threadIdx.x]);
+      rb[threadIdx.x] = __ldcg(&S.rc[bb * 64 + threadIdx.x]);
+    }
+    __syncthreads();
+    // row i of C_ab times rb
+    const float *rbq = rb + 16 * q;
+    float acc = 0.f;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      acc = fmaf(v[u].x, rbq[4 * u],
+                 fmaf(v[u].y, rbq[4 * u + 1], fmaf(v[u].z, rbq[4 * u + 2], fmaf(v[u].w, rbq[4 * u + 3], acc))));
+    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+    if (q == 0) atomicAdd(&S.yc[ab * 64 + i], acc);
+    // rc.C rc: ra_i (C_ab rb)_i, twice for an off-diagonal block (C_ba = C_ab^T)
+    float e = q == 0 ? ra[i] * acc * (ab == bb ? 1.f : 2.f) : 0.f;
+    e = warp_allsum(e);
+    if (lane == 0) atomicAdd(&sums[2 * s], (double)e);
+    if (ab == bb) continue;  // uniform
+    // C_ab^T ra: column 16 q + 4 u + w gets v[u].{x,y,z,w} ra_i, summed over i
+    const float ri = ra[i];
+    float cpart[16];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      cpart[4 * u] = v[u].x * ri;
+      cpart[4 * u + 1] = v[u].y * ri;
+      cpart[4 * u + 2] = v[u].z * ri;
+      cpart[4 * u + 3] = v[u].w * ri;
+    }
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk)
+#pragma unroll
+      for (int o = 4; o < 32; o <<= 1) cpart[kk] += __shfl_xor_sync(0xffffffffu, cpart[kk], o);
+    if (lane < 4)
+#pragma unroll
+      for (int kk = 0; kk < 16; ++kk) part[warp * 64 + 16 * lane + kk] = cpart[kk];
+    __syncthreads();
+    if (threadIdx.x < 64) {
+      float x = 0.f;
+#pragma unroll
+      for (int w2 = 0; w2 < 8; ++w2) x += part[w2 * 64 + threadIdx.x];
+      atomicAdd(&S.yc[bb * 64 + threadIdx.x], x);
+    }
+  }
+}
+
+// new search directions p = z + beta p, q = 0 over DOFs [lo, hi) of system
+// S, z = D^-1 r (+ P Pi yc with the two-level preconditioner)
+__device__ __forceinline__ void batch_directions(const BatchDev &a, const BatchSys &S, int64_t lo, int64_t hi,
+                                                 int64_t step, double beta) {
+  double *__restrict__ p = S.p;
+  double *__restrict__ q = S.q;
+  const double *__restrict__ r = S.r;
+  const double *__restrict__ dinv = S.dinv;
+  const uint8_t *__restrict__ dmask = S.dmask;
+  if (a.two_level && a.beams[S.beam].has_cs) {
+    const CoarseDev cs = a.beams[S.beam].cs;
+    const float *yc = S.yc;
+    for (int64_t i = lo; i < hi; i += step) {
+      double z = dinv[i] * __ldcg(&r[i]);
+      if (dmask[i]) z += (double)cs_prolong_y(cs, yc, i);
+      p[i] = z + beta * __ldcg(&p[i]);
+      q[i] = 0.0;
+    }
+  } else {
+    for (int64_t i = lo; i < hi; i += step) {
+      p[i] = dinv[i] * __ldcg(&r[i]) + beta * __ldcg(&p[i]);
+      q[i] = 0.0;
+    }
+  }
+}
+
 // MINB: CTAs per SM the register budget is compiled for (1, 2 or 3); the
 // autotuner times the variants
 template <int MINB>
@@ -216,22 +485,19 @@ __global__ void __launch_bounds__(kTileThreads, MINB) k_batch_cg(BatchDev a) {
   extern __shared__ float4 smem[];
   const int start = *a.slot;
   int k = 0;
-  long long iters = 0;
+  long long iters = 0;  // block 0: systems stepped, summed over iterations (per thread)
   for (; k < a.max_iter_launch; ++k) {
     const int par = (start + k) & 1;
     const SysState *st = a.state + par * a.n_sys;
     double *pq = a.pq + par * a.n_sys;
     double *sums = a.sums + 2 * par * a.n_sys;
     // P1: operator over (beam, tile) work items
+    if (a.two_level)  // rc and yc of every system start from zero (P3 of the last iteration is done with yc)
+      for (int64_t i = (int64_t)blockIdx.x * kTileThreads + threadIdx.x; i < a.cvec_len;
+           i += (int64_t)gridDim.x * kTileThreads)
+        a.cvec[i] = 0.f;
     for (int w = blockIdx.x; w < a.total_work; w += gridDim.x) {
-      int lo = 0, hi = a.n_beams - 1;
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (a.work_prefix[mid] <= w)
-          lo = mid;
-        else
-          hi = mid - 1;
-      }
+      const int lo = find_item(a.work_prefix, a.n_beams, w);
       const BatchBeam &B = a.beams[lo];
       bool any = false;
       for (int j = 0; j < B.nrhs; ++j) any = any || __ldcg(&st[B.first_sys + j].active);
@@ -249,41 +515,53 @@ __global__ void __launch_bounds__(kTileThreads, MINB) k_batch_cg(BatchDev a) {
       }
     }
     if (!grid_barrier(a)) return;
-    // P2: updates of the active systems over this block's chunk of the
-    // concatenated DOFs (a block meets one or two systems, not all of them)
-    const DofChunk ch = dof_chunk(a);
-    for (int s = ch.s0; s < a.n_sys && a.sys_off[s] < ch.g1; ++s) {
-      const SysState ss = load_state(st + s);
-      if (!ss.active) continue;
-      const double pqs = __ldcg(&pq[s]);
-      const double alpha = ss.rz / pqs;
-      if (!(pqs > 0.0) || !isfinite(alpha)) continue;
-      const BatchSys &S = a.sys[s];
-      const int64_t lo = max(ch.g0, a.sys_off[s]) - a.sys_off[s], hi = min(ch.g1, a.sys_off[s + 1]) - a.sys_off[s];
-      double rz = 0.0, rr = 0.0;
-      for (int64_t i = lo + threadIdx.x; i < hi; i += kTileThreads) {
-        S.d[i] = __ldcg(&S.d[i]) + alpha * __ldcg(&S.p[i]);
-        const double ri = S.dmask[i] ? __ldcg(&S.r[i]) - alpha * __ldcg(&S.q[i]) : 0.0;
-        S.r[i] = ri;
-        rz += S.dinv[i] * ri * ri;
-        rr += ri * ri;
+    if (a.two_level) {
+      // P2: updates and restriction over (beam, node chunk) items
+      for (int w = blockIdx.x; w < a.total_uwork; w += gridDim.x) tl_update_item<true>(a, st, pq, sums, w);
+      if (!grid_barrier(a)) return;
+      // P2c: coarse products over (beam, C block) items
+      float *sm = reinterpret_cast<float *>(smem);
+      for (int w = blockIdx.x; w < a.total_cwork; w += gridDim.x) {
+        tl_coarse_item<true>(a, st, pq, sums, w, sm);
+        __syncthreads();  // sm is reused by the next item
       }
-      rz = block_sum<kTileThreads>(rz);
-      rr = block_sum<kTileThreads>(rr);
-      if (threadIdx.x == 0) {
-        atomicAdd(&sums[2 * s], rz);
-        atomicAdd(&sums[2 * s + 1], rr);
+    } else {
+      // P2: updates of the active systems over this block's chunk of the
+      // concatenated DOFs (a block meets one or two systems, not all of them)
+      const DofChunk ch = dof_chunk(a);
+      for (int s = ch.s0; s < a.n_sys && a.sys_off[s] < ch.g1; ++s) {
+        const SysState ss = load_state(st + s);
+        if (!ss.active) continue;
+        const double pqs = __ldcg(&pq[s]);
+        const double alpha = ss.rz / pqs;
+        if (!(pqs > 0.0) || !isfinite(alpha)) continue;
+        const BatchSys &S = a.sys[s];
+        const int64_t lo = max(ch.g0, a.sys_off[s]) - a.sys_off[s], hi = min(ch.g1, a.sys_off[s + 1]) - a.sys_off[s];
+        double rz = 0.0, rr = 0.0;
+        for (int64_t i = lo + threadIdx.x; i < hi; i += kTileThreads) {
+          S.d[i] = __ldcg(&S.d[i]) + alpha * __ldcg(&S.p[i]);
+          const double ri = S.dmask[i] ? __ldcg(&S.r[i]) - alpha * __ldcg(&S.q[i]) : 0.0;
+          S.r[i] = ri;
+          rz += S.dinv[i] * ri * ri;
+          rr += ri * ri;
+        }
+        rz = block_sum<kTileThreads>(rz);
+        rr = block_sum<kTileThreads>(rr);
+        if (threadIdx.x == 0) {
+          atomicAdd(&sums[2 * s], rz);
+          atomicAdd(&sums[2 * s + 1], rr);
+        }
       }
     }
     if (!grid_barrier(a)) return;
-    // P3: decisions (identical in every block; block 0 stores them) and new
-    // directions over this block's chunk
-    bool any_active = false;
+    // P3: decisions, one system per thread (identical in every block; block
+    // 0 stores them), then new directions over this block's chunk
     SysState *nx = a.state + (par ^ 1) * a.n_sys;
-    for (int s = 0; s < a.n_sys; ++s) {
+    int act = 0;
+    for (int s = threadIdx.x; s < a.n_sys; s += kTileThreads) {
       const SysState n2 = decide(a, st, pq, sums, s);
-      any_active = any_active || n2.active;
-      if (blockIdx.x == 0 && threadIdx.x == 0) {
+      act |= n2.active;
+      if (blockIdx.x == 0) {
         nx[s] = n2;
         double *nsums = a.sums + 2 * (par ^ 1) * a.n_sys;
         nsums[2 * s] = 0.0;
@@ -292,16 +570,13 @@ __global__ void __launch_bounds__(kTileThreads, MINB) k_batch_cg(BatchDev a) {
         if (__ldcg(&st[s].active)) ++iters;
       }
     }
+    const bool any_active = __syncthreads_or(act) != 0;
+    const DofChunk ch = dof_chunk(a);
     for (int s = ch.s0; s < a.n_sys && a.sys_off[s] < ch.g1; ++s) {
       const SysState n2 = decide(a, st, pq, sums, s);
       if (!n2.active) continue;
-      const BatchSys &S = a.sys[s];
-      const double beta = n2.beta;
       const int64_t lo = max(ch.g0, a.sys_off[s]) - a.sys_off[s], hi = min(ch.g1, a.sys_off[s + 1]) - a.sys_off[s];
-      for (int64_t i = lo + threadIdx.x; i < hi; i += kTileThreads) {
-        S.p[i] = S.dinv[i] * __ldcg(&S.r[i]) + beta * __ldcg(&S.p[i]);
-        S.q[i] = 0.0;
-      }
+      batch_directions(a, a.sys[s], lo + threadIdx.x, hi, kTileThreads, n2.beta);
     }
     if (!any_active) {
       ++k;
@@ -309,9 +584,17 @@ __global__ void __launch_bounds__(kTileThreads, MINB) k_batch_cg(BatchDev a) {
     }
     if (!grid_barrier(a)) return;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    *a.slot = (start + k) & 1;
-    *a.iters_run = iters;
+  if (blockIdx.x == 0) {
+    __shared__ unsigned long long s_it;
+    if (threadIdx.x == 0) s_it = 0ull;
+    __syncthreads();
+    if (iters) atomicAdd(&s_it, (unsigned long long)iters);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      *a.slot = (start + k) & 1;
+      *a.iters_run = (long long)s_it;
+      *a.launch_iters += k;
+    }
   }
 }
 
@@ -331,6 +614,10 @@ __global__ void k_refresh_x(BatchDev a) {
       S.d[i] = 0.0;
     }
   }
+  if (a.two_level)  // rc and yc start from zero for the refresh's restriction
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.cvec_len;
+         i += (int64_t)gridDim.x * blockDim.x)
+      a.cvec[i] = 0.f;
   if (blockIdx.x == 0) {
     for (int b = threadIdx.x; b < a.n_beams; b += blockDim.x) {
       const BatchBeam &B = a.beams[b];
@@ -367,6 +654,23 @@ __global__ void __launch_bounds__(256) k_refresh_r(BatchDev a) {
       atomicAdd(&sums[2 * s], rz);
       atomicAdd(&sums[2 * s + 1], rr);
     }
+  }
+}
+
+// precond 2: rc = Pi^T r of the recomputed residuals (after k_refresh_r)
+__global__ void __launch_bounds__(kTileThreads) k_refresh_restrict(BatchDev a) {
+  const SysState *st = a.state + (*a.slot) * a.n_sys;
+  for (int w = blockIdx.x; w < a.total_uwork; w += gridDim.x) tl_update_item<false>(a, st, nullptr, nullptr, w);
+}
+
+// precond 2: yc = C rc and rc.C rc into z.r of the refreshed systems
+__global__ void __launch_bounds__(kTileThreads) k_refresh_coarse(BatchDev a) {
+  __shared__ float sm[2 * 64 + 8 * 64];
+  const SysState *st = a.state + (*a.slot) * a.n_sys;
+  double *sums = a.sums + 2 * (*a.slot) * a.n_sys;
+  for (int w = blockIdx.x; w < a.total_cwork; w += gridDim.x) {
+    tl_coarse_item<false>(a, st, nullptr, sums, w, sm);
+    __syncthreads();
   }
 }
 
@@ -423,17 +727,14 @@ __global__ void k_refresh_state(BatchDev a) {
 
 // new directions of the systems this refresh reactivated (systems still
 // active because the launch hit its iteration cap already have theirs):
-// p = D^-1 r + beta p, q = 0
+// p = z + beta p (z = D^-1 r, plus P Pi yc with precond 2), q = 0
 __global__ void k_refresh_p(BatchDev a) {
   const SysState *st = a.state + (*a.slot) * a.n_sys;
   for (int s = 0; s < a.n_sys; ++s) {
     const SysState &ss = st[s];
     if (!ss.active || !ss.fresh) continue;
-    const BatchSys &S = a.sys[s];
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < S.n; i += (int64_t)gridDim.x * blockDim.x) {
-      S.p[i] = S.dinv[i] * S.r[i] + ss.beta * S.p[i];
-      S.q[i] = 0.0;
-    }
+    batch_directions(a, a.sys[s], (int64_t)blockIdx.x * blockDim.x + threadIdx.x, a.sys[s].n,
+                     (int64_t)gridDim.x * blockDim.x, ss.beta);
   }
 }
 
@@ -461,7 +762,7 @@ __global__ void k_set_bc_all(double *x, const double *g, const uint8_t *dmask, i
 
 // ---- autotuner: persistent-kernel CTAs per SM, cached per shape class -----
 static std::mutex g_tune_mu;
-static std::map<long long, int> g_tune_cache;  // key: (device, total tiles bucket) -> CTAs per SM
+static std::map<long long, int> g_tune_cache;  // key: (device, total tiles, mode) -> CTAs per SM
 
 // Self-test of the bounded wait in grid_barrier: one CTA enters the barrier
 // with the arrival counter offset by one, so it is never the last arrival
@@ -551,10 +852,11 @@ extern "C" int sfem_batch_solve(sfem_ctx *const *ctxs, int n, double *const *u, 
       smem = std::max(smem, ctxs[b]->c.tl.smem);
     }
     const double tol = opts->tol > 0 ? opts->tol : 1e-8;
-    const double delta = opts->inner_tol > 0 ? opts->inner_tol : 0.1;
+    const bool two_level = opts->precond == 2;
+    const double delta = opts->inner_tol > 0 ? opts->inner_tol : two_level ? 0.03 : 0.1;
     const int max_iter = opts->max_iter > 0 ? opts->max_iter : 200000;
     const int max_rounds = opts->max_rounds > 0 ? opts->max_rounds : 400;
-    SFEM_REQUIRE(opts->precond == 0 || opts->precond == 1, SFEM_EINVAL, "precond must be 0 or 1");
+    SFEM_REQUIRE(opts->precond >= 0 && opts->precond <= 2, SFEM_EINVAL, "precond must be 0, 1 or 2");
     if (opts->precond == 1) return batch_two_level(ctxs, n, u, *opts, tol, max_iter, infos, stats);
     auto get = [&](size_t bytes) {
       void *p = c0->mem.raw(bytes);
@@ -570,8 +872,18 @@ extern "C" int sfem_batch_solve(sfem_ctx *const *ctxs, int n, double *const *u, 
     // per-beam vectors and host-side tables
     std::vector<BatchBeam> hb(n);
     std::vector<BatchSys> hs(n_sys);
-    std::vector<int> prefix(n + 1, 0);
+    std::vector<int> prefix(n + 1, 0), uprefix(n + 1, 0), cprefix(n + 1, 0);
     std::vector<double *> xbeam(n), kxbeam(n);
+    // precond 2: coarse spaces (built with the default options on first use,
+    // kept by the contexts) and every system's rc / yc
+    int64_t cvec_len = 0;
+    if (two_level)
+      for (int b = 0; b < n; ++b) {
+        Ctx &c = ctxs[b]->c;
+        if (ensure_coarse(c)) cvec_len += 2 * (int64_t)c.coarse->dev.npad * c.nrhs;
+      }
+    float *cvec = cvec_len ? (float *)get(cvec_len * sizeof(float)) : nullptr;
+    int64_t coff = 0;
     int s = 0;
     for (int b = 0; b < n; ++b) {
       Ctx &c = ctxs[b]->c;
@@ -598,7 +910,14 @@ extern "C" int sfem_batch_solve(sfem_ctx *const *ctxs, int n, double *const *u, 
       hb[b].nrhs = nr;
       hb[b].lam = (float)c.lam;
       hb[b].mu = (float)c.mu;
+      hb[b].n_nodes = c.n_nodes;
+      const bool cs_on = two_level && c.coarse;
+      hb[b].has_cs = cs_on ? 1 : 0;
+      if (cs_on) hb[b].cs = c.coarse->dev;
       prefix[b + 1] = prefix[b] + (int)c.tl.n_tiles;
+      const int npad = cs_on ? c.coarse->dev.npad : 0;
+      uprefix[b + 1] = uprefix[b] + (cs_on ? c.coarse->dev.nchunk : (int)((c.n_nodes + kChunkNodes - 1) / kChunkNodes));
+      cprefix[b + 1] = cprefix[b] + (cs_on ? (npad / 64) * (npad / 64 + 1) / 2 : 0);
       for (int j = 0; j < nr; ++j, ++s) {
         BatchSys &S = hs[s];
         S.x = X + j * nd;
@@ -612,6 +931,10 @@ extern "C" int sfem_batch_solve(sfem_ctx *const *ctxs, int n, double *const *u, 
         S.f = c.f + j * nd;
         S.n = nd;
         S.bnorm = c.bnorm[j];
+        S.beam = b;
+        S.rc = cs_on ? cvec + coff : nullptr;
+        S.yc = cs_on ? cvec + coff + npad : nullptr;
+        coff += 2 * (int64_t)npad;
       }
     }
     std::vector<int64_t> soff(n_sys + 1, 0);
@@ -624,6 +947,17 @@ extern "C" int sfem_batch_solve(sfem_ctx *const *ctxs, int n, double *const *u, 
     a.beams = (BatchBeam *)get(n * sizeof(BatchBeam));
     a.sys = (BatchSys *)get(n_sys * sizeof(BatchSys));
     a.work_prefix = (int *)get((n + 1) * sizeof(int));
+    a.uwork_prefix = (int *)get((n + 1) * sizeof(int));
+    a.cwork_prefix = (int *)get((n + 1) * sizeof(int));
+    SFEM_CUDA(cudaMemcpyAsync((void *)a.uwork_prefix, uprefix.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice,
+                              st));
+    SFEM_CUDA(cudaMemcpyAsync((void *)a.cwork_prefix, cprefix.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice,
+                              st));
+    a.total_uwork = uprefix[n];
+    a.total_cwork = cprefix[n];
+    a.two_level = two_level ? 1 : 0;
+    a.cvec = cvec;
+    a.cvec_len = cvec_len;
     SFEM_CUDA(cudaMemcpyAsync((void *)a.beams, hb.data(), n * sizeof(BatchBeam), cudaMemcpyHostToDevice, st));
     SFEM_CUDA(cudaMemcpyAsync((void *)a.sys, hs.data(), n_sys * sizeof(BatchSys), cudaMemcpyHostToDevice, st));
     SFEM_CUDA(cudaMemcpyAsync((void *)a.work_prefix, prefix.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice,
@@ -641,6 +975,8 @@ extern "C" int sfem_batch_solve(sfem_ctx *const *ctxs, int n, double *const *u, 
     a.beam_skip = (int *)get(n * sizeof(int));
     a.any_active = (int *)get(sizeof(int));
     a.iters_run = (long long *)get(sizeof(long long));
+    a.launch_iters = (long long *)get(sizeof(long long));
+    SFEM_CUDA(cudaMemsetAsync(a.launch_iters, 0, sizeof(long long), st));
     a.tol2 = tol * tol;
     a.delta2 = delta * delta;
     a.max_iter = max_iter;
@@ -694,6 +1030,12 @@ extern "C" int sfem_batch_solve(sfem_ctx *const *ctxs, int n, double *const *u, 
       }
       k_refresh_r<<<red_grid, 256, 0, s2>>>(a);
       SFEM_CHECK_LAUNCH();
+      if (two_level) {
+        k_refresh_restrict<<<red_grid, kTileThreads, 0, s2>>>(a);
+        SFEM_CHECK_LAUNCH();
+        k_refresh_coarse<<<red_grid, kTileThreads, 0, s2>>>(a);
+        SFEM_CHECK_LAUNCH();
+      }
       k_refresh_state<<<1, 256, 0, s2>>>(a);
       SFEM_CHECK_LAUNCH();
       k_refresh_p<<<red_grid, 256, 0, s2>>>(a);
@@ -712,7 +1054,7 @@ extern "C" int sfem_batch_solve(sfem_ctx *const *ctxs, int n, double *const *u, 
     check();
 
     // autotune CTAs per SM on the first rounds (cached per shape class)
-    const long long key = ((long long)dev << 40) | (long long)total_work;
+    const long long key = ((long long)dev << 40) | ((long long)total_work << 1) | (two_level ? 1 : 0);
     int bpsm = 0;
     {
       std::lock_guard<std::mutex> lock(g_tune_mu);
@@ -812,6 +1154,12 @@ extern "C" int sfem_batch_solve(sfem_ctx *const *ctxs, int n, double *const *u, 
     // else Jacobi
     std::vector<sfem_solve_info> fb(n_sys);
     int n_fallback = 0;
+    long long launch_iters = 0;
+    SFEM_CUDA(cudaMemcpyAsync(&launch_iters, a.launch_iters, sizeof launch_iters, cudaMemcpyDeviceToHost, st));
+    cudaEvent_t f0, f1;
+    SFEM_CUDA(cudaEventCreate(&f0));
+    SFEM_CUDA(cudaEventCreate(&f1));
+    SFEM_CUDA(cudaEventRecord(f0, st));
     for (int b = 0, k2 = 0; b < n; ++b) {
       Ctx &c = ctxs[b]->c;
       for (int j = 0; j < c.nrhs; ++j, ++k2) {
@@ -834,6 +1182,7 @@ extern "C" int sfem_batch_solve(sfem_ctx *const *ctxs, int n, double *const *u, 
         ++n_fallback;
       }
     }
+    SFEM_CUDA(cudaEventRecord(f1, st));
     for (int b = 0; b < n; ++b) {
       Ctx &c = ctxs[b]->c;
       SFEM_CUDA(cudaMemcpyAsync(u[b], xbeam[b], c.ndof * c.nrhs * sizeof(double),
@@ -841,10 +1190,13 @@ extern "C" int sfem_batch_solve(sfem_ctx *const *ctxs, int n, double *const *u, 
     }
     SFEM_CUDA(cudaEventRecord(e1, st));
     SFEM_CUDA(cudaEventSynchronize(e1));
-    float ms = 0.f;
+    float ms = 0.f, fb_ms = 0.f;
     SFEM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    SFEM_CUDA(cudaEventElapsedTime(&fb_ms, f0, f1));
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    cudaEventDestroy(f0);
+    cudaEventDestroy(f1);
     int worst = SFEM_OK;
     long long total_it = 0;
     for (int i = 0; i < n_sys; ++i) total_it += hst[slot * n_sys + i].iter;
@@ -856,6 +1208,8 @@ extern "C" int sfem_batch_solve(sfem_ctx *const *ctxs, int n, double *const *u, 
       stats->n_systems = n_sys;
       stats->total_iterations = total_it;
       stats->ms = ms;
+      stats->launch_iterations = (int)std::min<long long>(launch_iters, INT32_MAX);
+      stats->fallback_ms = fb_ms;
     }
     for (int i = 0; i < n_sys; ++i) {
       const SysState &ss = hst[slot * n_sys + i];

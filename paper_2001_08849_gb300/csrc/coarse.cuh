@@ -51,8 +51,8 @@ __device__ __forceinline__ int cs_corner(const CoarseDev &cs, int cell, int k) {
   return (jx * cs.d[1] + jy) * cs.d[2] + jz;
 }
 
-// (Pi y)_i for DOF i = 3 node + c (not masked)
-__device__ __forceinline__ float cs_prolong(const CoarseDev &cs, int64_t i) {
+// (Pi y)_i for DOF i = 3 node + c (not masked), y given by the caller
+__device__ __forceinline__ float cs_prolong_y(const CoarseDev &cs, const float *yc, int64_t i) {
   const int64_t node = i / 3;
   const int c = (int)(i - 3 * node);
   const int ci = cs.cinfo[node];
@@ -61,12 +61,15 @@ __device__ __forceinline__ float cs_prolong(const CoarseDev &cs, int64_t i) {
   const int oy = ((ci >> 25) & 1) ? 3 * cs.d[2] : 0;
   const int oz = ((ci >> 26) & 1) ? 3 : 0;
   const float f[3] = {cs.frac[3 * node], cs.frac[3 * node + 1], cs.frac[3 * node + 2]};
-  const float *y = cs.yc + 3 * base + c;
+  const float *y = yc + 3 * base + c;
   float s = 0.f;
 #pragma unroll
   for (int k = 0; k < 8; ++k)
     s = fmaf(cs_weight(f, k), y[((k & 4) ? ox : 0) + ((k & 2) ? oy : 0) + ((k & 1) ? oz : 0)], s);
   return s;
 }
+
+// (Pi yc)_i with the coarse space's own correction vector
+__device__ __forceinline__ float cs_prolong(const CoarseDev &cs, int64_t i) { return cs_prolong_y(cs, cs.yc, i); }
 
 }  // namespace sfem

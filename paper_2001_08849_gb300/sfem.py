@@ -76,7 +76,8 @@ class sfem_batch_opts(ctypes.Structure):
 class sfem_batch_stats(ctypes.Structure):
     _fields_ = [("rounds", ctypes.c_int), ("ctas_per_sm", ctypes.c_int), ("graph", ctypes.c_int),
                 ("n_systems", ctypes.c_int), ("total_iterations", ctypes.c_longlong), ("ms", ctypes.c_double),
-                ("fallback_systems", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
+                ("fallback_systems", ctypes.c_int), ("launch_iterations", ctypes.c_int),
+                ("fallback_ms", ctypes.c_float), ("reserved", ctypes.c_int * 1)]
 
 
 class sfem_coarse_opts(ctypes.Structure):

@@ -48,15 +48,19 @@ def _oracle_solutions(p):
     return np.stack(sols)
 
 
-@pytest.mark.parametrize("graph", [True, False])
-def test_batch_matches_oracle(S, graph):
+@pytest.mark.parametrize("graph,precond", [(True, 0), (False, 0), (True, 2), (False, 2)])
+def test_batch_matches_oracle(S, graph, precond):
+    """precond 0: Jacobi; precond 2: the two-level preconditioner inside the
+    persistent launch (these small beams get one or two patch centres per
+    axis, so the clamped interpolation cells of the coarse space are
+    exercised)."""
     probs = _small_batch()
     ctxs = [S.FsFem(p) for p in probs]
     try:
         us = [np.zeros((p.nrhs, c.ndof)) for p, c in zip(probs, ctxs)]
         n_sys = sum(p.nrhs for p in probs)
-        infos, stats = S.sfem_batch_solve([c.h for c in ctxs], us, S.batch_opts(tol=1e-10, use_graph=graph),
-                                          n_sys)
+        infos, stats = S.sfem_batch_solve([c.h for c in ctxs], us,
+                                          S.batch_opts(tol=1e-10, use_graph=graph, precond=precond), n_sys)
         assert stats["n_systems"] == n_sys == 20
         assert stats["rounds"] >= 2 and stats["ctas_per_sm"] >= 1
         k = 0
@@ -127,7 +131,45 @@ def test_batch_two_level_uneven_beams(S):
                 S.sfem_solve(c.h, x, S.solve_opts(kind=S.SFEM_SOLVE_PCG64, rhs=r, tol=1e-9), check=False)
                 assert np.linalg.norm(us[k][r].cpu().numpy() - x) <= 1e-5 * np.linalg.norm(x)
         with pytest.raises(S.SfemError):
-            S.sfem_batch_solve([c.h for c in ctxs], us, S.batch_opts(precond=2, u_on_device=True), n_sys)
+            S.sfem_batch_solve([c.h for c in ctxs], us, S.batch_opts(precond=3, u_on_device=True), n_sys)
+    finally:
+        for c in ctxs:
+            c.close()
+
+
+def test_batch_persistent_two_level_uneven_beams(S):
+    """precond = 2 (the two-level preconditioner as phases of the persistent
+    launch) on eight beams of the uneven batch family, one of them with a
+    user-chosen coarse grid kept by its context: every system reaches 1e-8,
+    agrees with FP64 PCG of its context, and the batch needs a fraction of
+    the persistent Jacobi solve's iterations."""
+    import torch
+    probs = [p for p in batch_beams(64, seed=5) if p.mesh.n_tets < 60000][:8]
+    ctxs = [S.FsFem(p) for p in probs]
+    try:
+        S.sfem_coarse_setup(ctxs[2].h, patch_dims=(3, 2, 2))
+        us = [torch.zeros((p.nrhs, c.ndof), dtype=torch.float64, device="cuda") for p, c in zip(probs, ctxs)]
+        n_sys = sum(p.nrhs for p in probs)
+        _, st0 = S.sfem_batch_solve([c.h for c in ctxs], us, S.batch_opts(tol=1e-8, u_on_device=True), n_sys)
+        for u in us:
+            u.zero_()
+        infos, st2 = S.sfem_batch_solve([c.h for c in ctxs], us,
+                                        S.batch_opts(tol=1e-8, u_on_device=True, precond=2), n_sys)
+        print(f"\npersistent batch, 8 beams x 4 loads: Jacobi {st0['total_iterations']} iterations "
+              f"({st0['launch_iterations']} launch iterations, {st0['fallback_systems']} fallbacks, "
+              f"{st0['ms']:.1f} ms); two-level {st2['total_iterations']} ({st2['launch_iterations']}, "
+              f"{st2['fallback_systems']}, {st2['ms']:.1f} ms)")
+        assert S.sfem_coarse_info(ctxs[2].h)["patch_dims"] == (3, 2, 2)
+        assert all(i["status"] == S.SFEM_OK and i["true_relres"] <= 1e-8 for i in infos), infos
+        assert st2["n_systems"] == n_sys and st2["launch_iterations"] > 0
+        assert st2["fallback_systems"] <= 1
+        assert 3 * st2["total_iterations"] < st0["total_iterations"]
+        for k in (0, 2, 5):
+            c = ctxs[k]
+            for r in range(probs[k].nrhs):
+                x = np.zeros(c.ndof)
+                S.sfem_solve(c.h, x, S.solve_opts(kind=S.SFEM_SOLVE_PCG64, rhs=r, tol=1e-9), check=False)
+                assert np.linalg.norm(us[k][r].cpu().numpy() - x) <= 1e-5 * np.linalg.norm(x)
     finally:
         for c in ctxs:
             c.close()

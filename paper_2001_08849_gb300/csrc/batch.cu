@@ -94,13 +94,53 @@ struct SysState {
   double best;                       // best true relative residual so far
 };
 
+__host__ __device__ inline size_t wl_align(size_t x) { return (x + 15) / 16 * 16; }
+
+// byte offsets of the lists from the start of the area
+struct WlLayout {
+  int bm, bm2, bt, bch, bcb, bfs, bnr, act_b, act_na, pt, pu, pc, act_s, scan_i, pd, scan_l, bytes;
+};
+
+__host__ __device__ inline WlLayout wl_layout(int n_sys, int nb) {
+  WlLayout L{};
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = o;
+    o = wl_align(o + bytes);
+    return (int)at;
+  };
+  const size_t nw = (size_t)(n_sys + 31) / 32;
+  L.bm = take(4 * nw);
+  L.bm2 = take(4 * nw);
+  L.bt = take(4 * (size_t)nb);
+  L.bch = take(4 * (size_t)nb);
+  L.bcb = take(4 * (size_t)nb);
+  L.bfs = take(4 * (size_t)nb);
+  L.bnr = take(4 * (size_t)nb);
+  L.act_b = take(4 * (size_t)nb);
+  L.act_na = take(4 * (size_t)nb);
+  L.pt = take(4 * ((size_t)nb + 1));
+  L.pu = take(4 * ((size_t)nb + 1));
+  L.pc = take(4 * ((size_t)nb + 1));
+  L.act_s = take(4 * (size_t)n_sys);
+  L.scan_i = take(4 * 9 * 4);
+  L.pd = take(8 * ((size_t)n_sys + 1));
+  L.scan_l = take(8 * 9 * 2);
+  L.bytes = (int)o;
+  return L;
+}
+
 struct BatchDev {
   const BatchBeam *beams;
   int n_beams;
   const BatchSys *sys;
   int n_sys;
-  const int *work_prefix;  // n_beams + 1
+  const int *work_prefix;  // n_beams + 1: tiles x load cases per beam (P1 items, few systems active)
   int total_work;
+  const int *tile_prefix;  // n_beams + 1: tiles per beam (P1 items, most systems active)
+  int total_tiles;
+  int act_off;             // byte offset of the work lists in dynamic shared memory
+  WlLayout wl;             // their layout
   const int64_t *sys_off;  // n_sys + 1: the systems' DOFs concatenated (update phases split this range)
   int64_t total_dof;
   SysState *state;         // 2 * n_sys, slot *slot is current
@@ -119,7 +159,7 @@ struct BatchDev {
   long long *launch_iters; // iterations of the persistent launches, summed over launches
   // precond 2 (two-level inside the launch)
   int two_level;
-  const int *uwork_prefix; // n_beams + 1: node chunks per beam (P2 items)
+  const int *uwork_prefix; // n_beams + 1: node chunks x load cases per beam (P2 items)
   int total_uwork;
   const int *cwork_prefix; // n_beams + 1: packed C blocks per beam (P2c items)
   int total_cwork;
@@ -283,17 +323,203 @@ __device__ __forceinline__ double warp_allsum(double v) {
   return v;
 }
 
-// P2 item w (beam, node chunk); this warp's kBatchWarpNodes nodes of it.
-// kUpdate: the CG update of the stepping systems (d += alpha p,
+// ---- work lists in shared memory ---------------------------------------------
+// Every block rebuilds, at the start of each phase that needs them, the same
+// lists of the work of the active systems (in a fixed order, from the same
+// flags), so that its loops visit active items only and the items split
+// evenly over the grid: per active beam e (ascending) the beam act_b[e], its
+// active load cases act_na[e] and the exclusive prefixes of its tiles (pt),
+// node chunks x active load cases (pu) and coarse blocks (pc); per active
+// system i the system act_s[i] and the prefix of their DOFs (pd).
+
+struct WorkLists {
+  unsigned *bm, *bm2;
+  int *bt, *bch, *bcb, *bfs, *bnr;
+  int *act_b, *act_na, *pt, *pu, *pc, *act_s, *scan_i;
+  long long *pd, *scan_l;
+};
+
+__device__ __forceinline__ WorkLists work_lists(const BatchDev &a, float4 *smem) {
+  char *base = reinterpret_cast<char *>(smem) + a.act_off;
+  const WlLayout &L = a.wl;
+  WorkLists W;
+  W.bm = reinterpret_cast<unsigned *>(base + L.bm);
+  W.bm2 = reinterpret_cast<unsigned *>(base + L.bm2);
+  W.bt = reinterpret_cast<int *>(base + L.bt);
+  W.bch = reinterpret_cast<int *>(base + L.bch);
+  W.bcb = reinterpret_cast<int *>(base + L.bcb);
+  W.bfs = reinterpret_cast<int *>(base + L.bfs);
+  W.bnr = reinterpret_cast<int *>(base + L.bnr);
+  W.act_b = reinterpret_cast<int *>(base + L.act_b);
+  W.act_na = reinterpret_cast<int *>(base + L.act_na);
+  W.pt = reinterpret_cast<int *>(base + L.pt);
+  W.pu = reinterpret_cast<int *>(base + L.pu);
+  W.pc = reinterpret_cast<int *>(base + L.pc);
+  W.act_s = reinterpret_cast<int *>(base + L.act_s);
+  W.scan_i = reinterpret_cast<int *>(base + L.scan_i);
+  W.pd = reinterpret_cast<long long *>(base + L.pd);
+  W.scan_l = reinterpret_cast<long long *>(base + L.scan_l);
+  return W;
+}
+
+// exclusive scan of K values per thread over the block (kTileThreads); the
+// totals in tot (every thread); scratch holds 9 K values
+template <class T, int K>
+__device__ __forceinline__ void block_scan(T (&v)[K], T (&tot)[K], T *scratch) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  T inc[K];
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    inc[q] = v[q];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const T t = __shfl_up_sync(0xffffffffu, inc[q], o);
+      if (lane >= o) inc[q] += t;
+    }
+  }
+  if (lane == 31)
+#pragma unroll
+    for (int q = 0; q < K; ++q) scratch[warp * K + q] = inc[q];
+  __syncthreads();
+  if (warp == 0) {
+    constexpr int NW = kTileThreads / 32;
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      const T x0 = lane < NW ? scratch[lane * K + q] : T(0);
+      T x = x0;
+#pragma unroll
+      for (int o = 1; o < NW; o <<= 1) {
+        const T t = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += t;
+      }
+      __syncwarp();
+      if (lane < NW) scratch[lane * K + q] = x - x0;
+      if (lane == NW - 1) scratch[NW * K + q] = x;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    v[q] = inc[q] - v[q] + scratch[warp * K + q];
+    tot[q] = scratch[(kTileThreads / 32) * K + q];
+  }
+  __syncthreads();  // scratch is reused
+}
+
+__device__ __forceinline__ bool is_active(const unsigned *bm, int s) { return (bm[s >> 5] >> (s & 31)) & 1u; }
+
+// flags of all systems into a bitmap (one load per system and block);
+// returns the number of active systems
+__device__ __forceinline__ int load_active(const BatchDev &a, const SysState *st, unsigned *bm) {
+  int count = 0;
+  for (int base = 0; base < a.n_sys; base += kTileThreads) {
+    const int s = base + threadIdx.x;
+    const bool f = s < a.n_sys && __ldcg(&st[s].active);
+    const unsigned m = __ballot_sync(0xffffffffu, f);
+    const int word = (base >> 5) + (threadIdx.x >> 5);
+    if ((threadIdx.x & 31) == 0 && 32 * word < a.n_sys) bm[word] = m;
+    count += __syncthreads_count(f);
+  }
+  return count;
+}
+
+// the beams' static counts (tiles, node chunks, coarse blocks, first
+// system, load cases), once per launch
+__device__ __forceinline__ void load_beam_info(const BatchDev &a, const WorkLists &W) {
+  for (int b = threadIdx.x; b < a.n_beams; b += kTileThreads) {
+    const int nr = a.beams[b].nrhs;
+    W.bt[b] = a.tile_prefix[b + 1] - a.tile_prefix[b];
+    W.bch[b] = (a.uwork_prefix[b + 1] - a.uwork_prefix[b]) / nr;
+    W.bcb[b] = a.cwork_prefix[b + 1] - a.cwork_prefix[b];
+    W.bfs[b] = a.beams[b].first_sys;
+    W.bnr[b] = nr;
+  }
+  __syncthreads();
+}
+
+// lists of the active beams from the flags in W.bm; returns the number of
+// active beams, the item counts in n_items (tiles, chunk items, coarse blocks)
+__device__ __forceinline__ int build_beam_lists(const BatchDev &a, const WorkLists &W, int (&n_items)[3]) {
+  int carry[4] = {0, 0, 0, 0};
+  for (int base = 0; base < a.n_beams; base += kTileThreads) {
+    const int b = base + threadIdx.x;
+    int na = 0;
+    if (b < a.n_beams)
+      for (int j = 0; j < W.bnr[b]; ++j) na += is_active(W.bm, W.bfs[b] + j) ? 1 : 0;
+    int v[4] = {na > 0 ? 1 : 0, na > 0 ? W.bt[b] : 0, na * (b < a.n_beams ? W.bch[b] : 0), na > 0 ? W.bcb[b] : 0};
+    int tot[4];
+    block_scan<int, 4>(v, tot, W.scan_i);
+    if (na > 0) {
+      const int e = carry[0] + v[0];
+      W.act_b[e] = b;
+      W.act_na[e] = na;
+      W.pt[e] = carry[1] + v[1];
+      W.pu[e] = carry[2] + v[2];
+      W.pc[e] = carry[3] + v[3];
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) carry[q] += tot[q];
+  }
+  if (threadIdx.x == 0) {
+    W.pt[carry[0]] = carry[1];
+    W.pu[carry[0]] = carry[2];
+    W.pc[carry[0]] = carry[3];
+  }
+  __syncthreads();
+  n_items[0] = carry[1];
+  n_items[1] = carry[2];
+  n_items[2] = carry[3];
+  return carry[0];
+}
+
+// list of the systems flagged in `flags` and the prefix of their DOFs;
+// returns the number of systems, their DOFs in n_dof
+__device__ __forceinline__ int build_sys_list(const BatchDev &a, const WorkLists &W, const unsigned *flags,
+                                              long long &n_dof) {
+  long long carry[2] = {0, 0};
+  for (int base = 0; base < a.n_sys; base += kTileThreads) {
+    const int s = base + threadIdx.x;
+    const bool f = s < a.n_sys && is_active(flags, s);
+    long long v[2] = {f ? 1 : 0, f ? (long long)a.sys[s].n : 0};
+    long long tot[2];
+    block_scan<long long, 2>(v, tot, W.scan_l);
+    if (f) {
+      W.act_s[carry[0] + v[0]] = s;
+      W.pd[carry[0] + v[0]] = carry[1] + v[1];
+    }
+    carry[0] += tot[0];
+    carry[1] += tot[1];
+  }
+  if (threadIdx.x == 0) W.pd[carry[0]] = carry[1];
+  __syncthreads();
+  n_dof = carry[1];
+  return (int)carry[0];
+}
+
+// entry of item w in a prefix list p[0..n] (sentinel p[n]), walking forward
+// from e (the items of a block ascend)
+__device__ __forceinline__ int walk_list(const int *p, int n, int e, int w) {
+  while (e + 1 < n && p[e + 1] <= w) ++e;
+  return e;
+}
+
+// j-th active load case of beam b (jj counts the active ones)
+__device__ __forceinline__ int active_rhs(const WorkLists &W, int b, int jj) {
+  int j = 0;
+  for (;; ++j)
+    if (is_active(W.bm, W.bfs[b] + j) && jj-- == 0) break;
+  return j;
+}
+
+// P2 item: node chunk k of beam b, load case j; this warp's kBatchWarpNodes
+// nodes of it.  kUpdate: the CG update of a stepping system (d += alpha p,
 // r = P (r - alpha q)) with D^-1 r.r and r.r into sums, then rc += Pi^T r;
-// else (refresh) rc += Pi^T r of the refreshing systems' new residuals.
+// else (refresh) rc += Pi^T r of a refreshing system's new residual.
 // No block barrier: warps past the chunk's end return at once.
 template <bool kUpdate>
 __device__ __forceinline__ void tl_update_item(const BatchDev &a, const SysState *st, const double *pq,
-                                               double *sums, int w) {
-  const int b = find_item(a.uwork_prefix, a.n_beams, w);
+                                               double *sums, int b, int k, int j) {
   const BatchBeam &B = a.beams[b];
-  const int k = w - a.uwork_prefix[b];
   const bool cs_on = B.has_cs != 0;
   if (!kUpdate && !cs_on) return;  // nothing to restrict
   int cell = 0, first, end;
@@ -310,13 +536,13 @@ __device__ __forceinline__ void tl_update_item(const BatchDev &a, const SysState
   const int wb = first + kBatchWarpNodes * (threadIdx.x >> 5);
   if (wb >= end) return;
   const int we = min(wb + kBatchWarpNodes, end);
-  for (int j = 0; j < B.nrhs; ++j) {
+  {
     const int s = B.first_sys + j;
     double alpha = 0.0;
     if (kUpdate) {
-      if (!stepping(st, pq, s, alpha)) continue;
+      if (!stepping(st, pq, s, alpha)) return;
     } else {
-      if (!refreshing(st[s])) continue;
+      if (!refreshing(st[s])) return;
     }
     const BatchSys &S = a.sys[s];
     double *__restrict__ d = S.d;
@@ -377,16 +603,14 @@ __device__ __forceinline__ void tl_update_item(const BatchDev &a, const SysState
   }
 }
 
-// P2c item w (beam, block t of the packed C): yc += C rc for every selected
+// P2c item (beam b, block t of the packed C): yc += C rc for every selected
 // system of the beam (kUpdate: stepping; else refreshing), the block read
 // once, and rc.C rc added to sums[2 s] (z.r).  Block-uniform; uses
 // 2 x 64 + 8 x 64 floats of sm.
 template <bool kUpdate>
 __device__ __forceinline__ void tl_coarse_item(const BatchDev &a, const SysState *st, const double *pq,
-                                               double *sums, int w, float *sm) {
-  const int b = find_item(a.cwork_prefix, a.n_beams, w);
+                                               double *sums, int b, int t, float *sm) {
   const BatchBeam &B = a.beams[b];
-  const int t = w - a.cwork_prefix[b];
   int ab = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
   while ((ab + 1) * (ab + 2) / 2 <= t) ++ab;
   while (ab * (ab + 1) / 2 > t) --ab;
@@ -484,6 +708,8 @@ template <int MINB>
 __global__ void __launch_bounds__(kTileThreads, MINB) k_batch_cg(BatchDev a) {
   extern __shared__ float4 smem[];
   const int start = *a.slot;
+  const WorkLists W = work_lists(a, smem);
+  load_beam_info(a, W);
   int k = 0;
   long long iters = 0;  // block 0: systems stepped, summed over iterations (per thread)
   for (; k < a.max_iter_launch; ++k) {
@@ -491,23 +717,25 @@ __global__ void __launch_bounds__(kTileThreads, MINB) k_batch_cg(BatchDev a) {
     const SysState *st = a.state + par * a.n_sys;
     double *pq = a.pq + par * a.n_sys;
     double *sums = a.sums + 2 * par * a.n_sys;
-    // P1: operator over (beam, tile) work items
+    // work lists of the systems active in this iteration
+    load_active(a, st, W.bm);
+    int n_items[3];
+    const int n_e = build_beam_lists(a, W, n_items);
+    // P1: operator over (active beam, tile) items, the tile's records loaded
+    // once for all its active load cases
     if (a.two_level)  // rc and yc of every system start from zero (P3 of the last iteration is done with yc)
       for (int64_t i = (int64_t)blockIdx.x * kTileThreads + threadIdx.x; i < a.cvec_len;
            i += (int64_t)gridDim.x * kTileThreads)
         a.cvec[i] = 0.f;
-    for (int w = blockIdx.x; w < a.total_work; w += gridDim.x) {
-      const int lo = find_item(a.work_prefix, a.n_beams, w);
-      const BatchBeam &B = a.beams[lo];
-      bool any = false;
-      for (int j = 0; j < B.nrhs; ++j) any = any || __ldcg(&st[B.first_sys + j].active);
-      if (!any) continue;
-      const int tile = w - a.work_prefix[lo];
+    for (int w = blockIdx.x, e = 0; w < n_items[0]; w += gridDim.x) {
+      e = walk_list(W.pt, n_e, e, w);
+      const int b = W.act_b[e], tile = w - W.pt[e];
+      const BatchBeam &B = a.beams[b];
       TileRegs R;
       tile_load(B.A, tile, R);
-      for (int j = 0; j < B.nrhs; ++j) {
-        const int s = B.first_sys + j;
-        if (!__ldcg(&st[s].active)) continue;
+      for (int j = 0; j < W.bnr[b]; ++j) {
+        const int s = W.bfs[b] + j;
+        if (!is_active(W.bm, s)) continue;
         const BatchSys &S = a.sys[s];
         double en = (double)tile_compute<double, double, true>(B.A, tile, R, S.p, S.q, B.lam, B.mu, smem);
         en = block_sum<kTileThreads>(en);
@@ -516,33 +744,43 @@ __global__ void __launch_bounds__(kTileThreads, MINB) k_batch_cg(BatchDev a) {
     }
     if (!grid_barrier(a)) return;
     if (a.two_level) {
-      // P2: updates and restriction over (beam, node chunk) items
-      for (int w = blockIdx.x; w < a.total_uwork; w += gridDim.x) tl_update_item<true>(a, st, pq, sums, w);
+      // P2: updates and restriction over (active beam, node chunk, active
+      // load case) items
+      for (int w = blockIdx.x, e = 0; w < n_items[1]; w += gridDim.x) {
+        e = walk_list(W.pu, n_e, e, w);
+        const int b = W.act_b[e], local = w - W.pu[e], na = W.act_na[e];
+        const int chunk = local / na;
+        tl_update_item<true>(a, st, pq, sums, b, chunk, active_rhs(W, b, local - chunk * na));
+      }
       if (!grid_barrier(a)) return;
-      // P2c: coarse products over (beam, C block) items
+      // P2c: coarse products over (active beam, C block) items
       float *sm = reinterpret_cast<float *>(smem);
-      for (int w = blockIdx.x; w < a.total_cwork; w += gridDim.x) {
-        tl_coarse_item<true>(a, st, pq, sums, w, sm);
+      for (int w = blockIdx.x, e = 0; w < n_items[2]; w += gridDim.x) {
+        e = walk_list(W.pc, n_e, e, w);
+        tl_coarse_item<true>(a, st, pq, sums, W.act_b[e], w - W.pc[e], sm);
         __syncthreads();  // sm is reused by the next item
       }
     } else {
-      // P2: updates of the active systems over this block's chunk of the
-      // concatenated DOFs (a block meets one or two systems, not all of them)
-      const DofChunk ch = dof_chunk(a);
-      for (int s = ch.s0; s < a.n_sys && a.sys_off[s] < ch.g1; ++s) {
-        const SysState ss = load_state(st + s);
-        if (!ss.active) continue;
-        const double pqs = __ldcg(&pq[s]);
-        const double alpha = ss.rz / pqs;
-        if (!(pqs > 0.0) || !isfinite(alpha)) continue;
+      // P2: updates of the active systems over this block's share of their
+      // DOFs (a block meets one or two systems)
+      long long n_dof = 0;
+      const int n_s = build_sys_list(a, W, W.bm, n_dof);
+      const long long per = (n_dof + gridDim.x - 1) / gridDim.x;
+      const long long g0 = min(n_dof, (long long)blockIdx.x * per), g1 = min(n_dof, g0 + per);
+      int i = 0;
+      while (i + 1 < n_s && W.pd[i + 1] <= g0) ++i;
+      for (; g0 < g1 && i < n_s && W.pd[i] < g1; ++i) {
+        const int s = W.act_s[i];
+        double alpha;
+        if (!stepping(st, pq, s, alpha)) continue;
         const BatchSys &S = a.sys[s];
-        const int64_t lo = max(ch.g0, a.sys_off[s]) - a.sys_off[s], hi = min(ch.g1, a.sys_off[s + 1]) - a.sys_off[s];
+        const int64_t lo = max(g0, W.pd[i]) - W.pd[i], hi = min(g1, W.pd[i + 1]) - W.pd[i];
         double rz = 0.0, rr = 0.0;
-        for (int64_t i = lo + threadIdx.x; i < hi; i += kTileThreads) {
-          S.d[i] = __ldcg(&S.d[i]) + alpha * __ldcg(&S.p[i]);
-          const double ri = S.dmask[i] ? __ldcg(&S.r[i]) - alpha * __ldcg(&S.q[i]) : 0.0;
-          S.r[i] = ri;
-          rz += S.dinv[i] * ri * ri;
+        for (int64_t t = lo + threadIdx.x; t < hi; t += kTileThreads) {
+          S.d[t] = __ldcg(&S.d[t]) + alpha * __ldcg(&S.p[t]);
+          const double ri = S.dmask[t] ? __ldcg(&S.r[t]) - alpha * __ldcg(&S.q[t]) : 0.0;
+          S.r[t] = ri;
+          rz += S.dinv[t] * ri * ri;
           rr += ri * ri;
         }
         rz = block_sum<kTileThreads>(rz);
@@ -555,30 +793,44 @@ __global__ void __launch_bounds__(kTileThreads, MINB) k_batch_cg(BatchDev a) {
     }
     if (!grid_barrier(a)) return;
     // P3: decisions, one system per thread (identical in every block; block
-    // 0 stores them), then new directions over this block's chunk
+    // 0 stores them), then new directions over this block's share of the
+    // DOFs of the systems that go on
     SysState *nx = a.state + (par ^ 1) * a.n_sys;
-    int act = 0;
-    for (int s = threadIdx.x; s < a.n_sys; s += kTileThreads) {
-      const SysState n2 = decide(a, st, pq, sums, s);
-      act |= n2.active;
-      if (blockIdx.x == 0) {
-        nx[s] = n2;
-        double *nsums = a.sums + 2 * (par ^ 1) * a.n_sys;
-        nsums[2 * s] = 0.0;
-        nsums[2 * s + 1] = 0.0;
-        a.pq[(par ^ 1) * a.n_sys + s] = 0.0;
-        if (__ldcg(&st[s].active)) ++iters;
+    for (int base = 0; base < a.n_sys; base += kTileThreads) {
+      const int s = base + threadIdx.x;
+      bool act = false;
+      if (s < a.n_sys) {
+        const SysState n2 = decide(a, st, pq, sums, s);
+        act = n2.active != 0;
+        if (blockIdx.x == 0) {
+          nx[s] = n2;
+          double *nsums = a.sums + 2 * (par ^ 1) * a.n_sys;
+          nsums[2 * s] = 0.0;
+          nsums[2 * s + 1] = 0.0;
+          a.pq[(par ^ 1) * a.n_sys + s] = 0.0;
+          if (is_active(W.bm, s)) ++iters;
+        }
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, act);
+      const int word = (base >> 5) + (threadIdx.x >> 5);
+      if ((threadIdx.x & 31) == 0 && 32 * word < a.n_sys) W.bm2[word] = m;
+    }
+    __syncthreads();
+    long long n_dof = 0;
+    const int n_s = build_sys_list(a, W, W.bm2, n_dof);
+    {
+      const long long per = (n_dof + gridDim.x - 1) / gridDim.x;
+      const long long g0 = min(n_dof, (long long)blockIdx.x * per), g1 = min(n_dof, g0 + per);
+      int i = 0;
+      while (i + 1 < n_s && W.pd[i + 1] <= g0) ++i;
+      for (; g0 < g1 && i < n_s && W.pd[i] < g1; ++i) {
+        const int s = W.act_s[i];
+        const SysState n2 = decide(a, st, pq, sums, s);
+        const int64_t lo = max(g0, W.pd[i]) - W.pd[i], hi = min(g1, W.pd[i + 1]) - W.pd[i];
+        batch_directions(a, a.sys[s], lo + threadIdx.x, hi, kTileThreads, n2.beta);
       }
     }
-    const bool any_active = __syncthreads_or(act) != 0;
-    const DofChunk ch = dof_chunk(a);
-    for (int s = ch.s0; s < a.n_sys && a.sys_off[s] < ch.g1; ++s) {
-      const SysState n2 = decide(a, st, pq, sums, s);
-      if (!n2.active) continue;
-      const int64_t lo = max(ch.g0, a.sys_off[s]) - a.sys_off[s], hi = min(ch.g1, a.sys_off[s + 1]) - a.sys_off[s];
-      batch_directions(a, a.sys[s], lo + threadIdx.x, hi, kTileThreads, n2.beta);
-    }
-    if (!any_active) {
+    if (n_s == 0) {
       ++k;
       break;
     }
@@ -660,7 +912,11 @@ __global__ void __launch_bounds__(256) k_refresh_r(BatchDev a) {
 // precond 2: rc = Pi^T r of the recomputed residuals (after k_refresh_r)
 __global__ void __launch_bounds__(kTileThreads) k_refresh_restrict(BatchDev a) {
   const SysState *st = a.state + (*a.slot) * a.n_sys;
-  for (int w = blockIdx.x; w < a.total_uwork; w += gridDim.x) tl_update_item<false>(a, st, nullptr, nullptr, w);
+  for (int w = blockIdx.x; w < a.total_uwork; w += gridDim.x) {
+    const int b = find_item(a.uwork_prefix, a.n_beams, w);
+    const int nr = a.beams[b].nrhs, local = w - a.uwork_prefix[b];
+    tl_update_item<false>(a, st, nullptr, nullptr, b, local / nr, local % nr);
+  }
 }
 
 // precond 2: yc = C rc and rc.C rc into z.r of the refreshed systems
@@ -669,7 +925,8 @@ __global__ void __launch_bounds__(kTileThreads) k_refresh_coarse(BatchDev a) {
   const SysState *st = a.state + (*a.slot) * a.n_sys;
   double *sums = a.sums + 2 * (*a.slot) * a.n_sys;
   for (int w = blockIdx.x; w < a.total_cwork; w += gridDim.x) {
-    tl_coarse_item<false>(a, st, nullptr, sums, w, sm);
+    const int b = find_item(a.cwork_prefix, a.n_beams, w);
+    tl_coarse_item<false>(a, st, nullptr, sums, b, w - a.cwork_prefix[b], sm);
     __syncthreads();
   }
 }
@@ -872,7 +1129,7 @@ extern "C" int sfem_batch_solve(sfem_ctx *const *ctxs, int n, double *const *u, 
     // per-beam vectors and host-side tables
     std::vector<BatchBeam> hb(n);
     std::vector<BatchSys> hs(n_sys);
-    std::vector<int> prefix(n + 1, 0), uprefix(n + 1, 0), cprefix(n + 1, 0);
+    std::vector<int> prefix(n + 1, 0), tprefix(n + 1, 0), uprefix(n + 1, 0), cprefix(n + 1, 0);
     std::vector<double *> xbeam(n), kxbeam(n);
     // precond 2: coarse spaces (built with the default options on first use,
     // kept by the contexts) and every system's rc / yc
@@ -914,9 +1171,11 @@ extern "C" int sfem_batch_solve(sfem_ctx *const *ctxs, int n, double *const *u, 
       const bool cs_on = two_level && c.coarse;
       hb[b].has_cs = cs_on ? 1 : 0;
       if (cs_on) hb[b].cs = c.coarse->dev;
-      prefix[b + 1] = prefix[b] + (int)c.tl.n_tiles;
+      prefix[b + 1] = prefix[b] + (int)c.tl.n_tiles * nr;
+      tprefix[b + 1] = tprefix[b] + (int)c.tl.n_tiles;
       const int npad = cs_on ? c.coarse->dev.npad : 0;
-      uprefix[b + 1] = uprefix[b] + (cs_on ? c.coarse->dev.nchunk : (int)((c.n_nodes + kChunkNodes - 1) / kChunkNodes));
+      uprefix[b + 1] =
+          uprefix[b] + nr * (cs_on ? c.coarse->dev.nchunk : (int)((c.n_nodes + kChunkNodes - 1) / kChunkNodes));
       cprefix[b + 1] = cprefix[b] + (cs_on ? (npad / 64) * (npad / 64 + 1) / 2 : 0);
       for (int j = 0; j < nr; ++j, ++s) {
         BatchSys &S = hs[s];
@@ -947,6 +1206,10 @@ extern "C" int sfem_batch_solve(sfem_ctx *const *ctxs, int n, double *const *u, 
     a.beams = (BatchBeam *)get(n * sizeof(BatchBeam));
     a.sys = (BatchSys *)get(n_sys * sizeof(BatchSys));
     a.work_prefix = (int *)get((n + 1) * sizeof(int));
+    a.tile_prefix = (int *)get((n + 1) * sizeof(int));
+    SFEM_CUDA(cudaMemcpyAsync((void *)a.tile_prefix, tprefix.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice,
+                              st));
+    a.total_tiles = tprefix[n];
     a.uwork_prefix = (int *)get((n + 1) * sizeof(int));
     a.cwork_prefix = (int *)get((n + 1) * sizeof(int));
     SFEM_CUDA(cudaMemcpyAsync((void *)a.uwork_prefix, uprefix.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice,
@@ -964,7 +1227,12 @@ extern "C" int sfem_batch_solve(sfem_ctx *const *ctxs, int n, double *const *u, 
                               st));
     a.n_beams = n;
     a.n_sys = n_sys;
-    a.total_work = total_work;
+    a.total_work = prefix[n];
+    // the work lists follow the tile view in dynamic shared memory
+    a.act_off = (int)std::max<size_t>(wl_align(smem), 640 * sizeof(float));  // P2c uses 640 floats
+    a.wl = wl_layout(n_sys, n);
+    smem = (size_t)a.act_off + (size_t)a.wl.bytes;
+    SFEM_REQUIRE(smem <= 227 * 1024, SFEM_EINVAL, "too many systems or beams for the batched kernel's shared memory");
     a.state = (SysState *)get(2 * n_sys * sizeof(SysState));
     a.slot = (int *)get(sizeof(int));
     a.sums = (double *)get(4 * n_sys * sizeof(double));

@@ -3,8 +3,9 @@
 //
 // One "system" is one (context, load case).  A round is
 //   1. one persistent cooperative launch running FP32-operator CG
-//      iterations (FP64 vectors and reductions) for every active system:
-//        P1  operator over a global work list of (beam, tile); a tile's
+//      iterations (FP64 solution, residual and reductions; FP32 search
+//      direction p and operator output q) for every active system:
+//        P1  operator over the (active beam, tile) items; a tile's
 //            geometry is loaded once for all active load cases of its beam
 //        P2  x/r updates and the two dot products per system
 //        P3  per-system decisions (converged / reliable update due /
@@ -22,11 +23,11 @@
 // precond = 2 runs the same rounds with the two-level preconditioner
 // z = D^-1 r + P Pi C Pi^T r of each beam's coarse space (coarse.cu) inside
 // the persistent launch:
-//        P2  walks each beam's nodes grouped by interpolation cell (the
-//            coarse space's chunks of <= kChunkNodes nodes), one warp per
-//            256 nodes: the x/r updates, D^-1 r.r and r.r, and the
-//            restriction rc += Pi^T r (24 warp sums per cell, FP32 atomics
-//            into the system's rc);
+//        P2  walks each beam's nodes grouped by interpolation cell (runs
+//            of <= kSubNodes nodes of one cell, one item per run and load
+//            case), one warp per 64 nodes: the x/r updates, D^-1 r.r and
+//            r.r, and the restriction rc += Pi^T r (24 warp sums, FP32
+//            atomics into the system's rc);
 //        P2c yc = C rc over (beam, 64 x 64 block of the packed C) items, the
 //            block read once for all load cases of the beam, and
 //            rc.C rc added to z.r (z.r = D^-1 r.r + (Pi^T r).yc);
@@ -74,7 +75,8 @@ struct BatchBeam {
 };
 
 struct BatchSys {
-  double *x, *r, *p, *q, *d, *Kx;
+  double *x, *r, *d, *Kx;  // FP64: solution, residual, correction since the last refresh, K x
+  float *p, *q;             // FP32: search direction and its FP32-operator image
   const double *dinv;
   const uint8_t *dmask;
   const double *f;
@@ -98,7 +100,7 @@ __host__ __device__ inline size_t wl_align(size_t x) { return (x + 15) / 16 * 16
 
 // byte offsets of the lists from the start of the area
 struct WlLayout {
-  int bm, bm2, bt, bch, bcb, bfs, bnr, act_b, act_na, pt, pu, pc, act_s, scan_i, pd, scan_l, bytes;
+  int bm, bm2, bt, bch, bcb, bfs, bnr, act_b, act_na, pt, pu, pc, act_s, scan_i, pd, scan_l, sn, beta, bytes;
 };
 
 __host__ __device__ inline WlLayout wl_layout(int n_sys, int nb) {
@@ -126,6 +128,8 @@ __host__ __device__ inline WlLayout wl_layout(int n_sys, int nb) {
   L.scan_i = take(4 * 9 * 4);
   L.pd = take(8 * ((size_t)n_sys + 1));
   L.scan_l = take(8 * 9 * 2);
+  L.sn = take(8 * (size_t)n_sys);
+  L.beta = take(8 * (size_t)n_sys);
   L.bytes = (int)o;
   return L;
 }
@@ -159,7 +163,7 @@ struct BatchDev {
   long long *launch_iters; // iterations of the persistent launches, summed over launches
   // precond 2 (two-level inside the launch)
   int two_level;
-  const int *uwork_prefix; // n_beams + 1: node chunks x load cases per beam (P2 items)
+  const int *uwork_prefix; // n_beams + 1: node runs x load cases per beam (P2 items)
   int total_uwork;
   const int *cwork_prefix; // n_beams + 1: packed C blocks per beam (P2c items)
   int total_cwork;
@@ -282,7 +286,7 @@ __device__ __forceinline__ SysState decide(const BatchDev &a, const SysState *st
 
 // ---- two-level phases (precond 2) ------------------------------------------
 
-constexpr int kBatchWarpNodes = kChunkNodes / (kTileThreads / 32);  // nodes per warp of a P2 item
+constexpr int kBatchWarpNodes = kSubNodes / (kTileThreads / 32);  // nodes per warp of a P2 item (2 per lane)
 static_assert(kTileThreads == 256, "the coarse product maps 64 rows x 4 column groups onto 256 threads");
 
 // largest b with prefix[b] <= w
@@ -329,14 +333,15 @@ __device__ __forceinline__ double warp_allsum(double v) {
 // flags), so that its loops visit active items only and the items split
 // evenly over the grid: per active beam e (ascending) the beam act_b[e], its
 // active load cases act_na[e] and the exclusive prefixes of its tiles (pt),
-// node chunks x active load cases (pu) and coarse blocks (pc); per active
+// node runs x active load cases (pu) and coarse blocks (pc); per active
 // system i the system act_s[i] and the prefix of their DOFs (pd).
 
 struct WorkLists {
   unsigned *bm, *bm2;
   int *bt, *bch, *bcb, *bfs, *bnr;
   int *act_b, *act_na, *pt, *pu, *pc, *act_s, *scan_i;
-  long long *pd, *scan_l;
+  long long *pd, *scan_l, *sn;  // sn: DOFs of each system
+  double *beta;                 // each system's new beta (P3)
 };
 
 __device__ __forceinline__ WorkLists work_lists(const BatchDev &a, float4 *smem) {
@@ -359,6 +364,8 @@ __device__ __forceinline__ WorkLists work_lists(const BatchDev &a, float4 *smem)
   W.scan_i = reinterpret_cast<int *>(base + L.scan_i);
   W.pd = reinterpret_cast<long long *>(base + L.pd);
   W.scan_l = reinterpret_cast<long long *>(base + L.scan_l);
+  W.sn = reinterpret_cast<long long *>(base + L.sn);
+  W.beta = reinterpret_cast<double *>(base + L.beta);
   return W;
 }
 
@@ -423,8 +430,8 @@ __device__ __forceinline__ int load_active(const BatchDev &a, const SysState *st
   return count;
 }
 
-// the beams' static counts (tiles, node chunks, coarse blocks, first
-// system, load cases), once per launch
+// the beams' static counts (tiles, node runs, coarse blocks, first
+// system, load cases) and the systems' DOFs, once per launch
 __device__ __forceinline__ void load_beam_info(const BatchDev &a, const WorkLists &W) {
   for (int b = threadIdx.x; b < a.n_beams; b += kTileThreads) {
     const int nr = a.beams[b].nrhs;
@@ -434,11 +441,12 @@ __device__ __forceinline__ void load_beam_info(const BatchDev &a, const WorkList
     W.bfs[b] = a.beams[b].first_sys;
     W.bnr[b] = nr;
   }
+  for (int s = threadIdx.x; s < a.n_sys; s += kTileThreads) W.sn[s] = a.sys[s].n;
   __syncthreads();
 }
 
 // lists of the active beams from the flags in W.bm; returns the number of
-// active beams, the item counts in n_items (tiles, chunk items, coarse blocks)
+// active beams, the item counts in n_items (tiles, node-run items, coarse blocks)
 __device__ __forceinline__ int build_beam_lists(const BatchDev &a, const WorkLists &W, int (&n_items)[3]) {
   int carry[4] = {0, 0, 0, 0};
   for (int base = 0; base < a.n_beams; base += kTileThreads) {
@@ -480,7 +488,7 @@ __device__ __forceinline__ int build_sys_list(const BatchDev &a, const WorkLists
   for (int base = 0; base < a.n_sys; base += kTileThreads) {
     const int s = base + threadIdx.x;
     const bool f = s < a.n_sys && is_active(flags, s);
-    long long v[2] = {f ? 1 : 0, f ? (long long)a.sys[s].n : 0};
+    long long v[2] = {f ? 1 : 0, f ? W.sn[s] : 0};
     long long tot[2];
     block_scan<long long, 2>(v, tot, W.scan_l);
     if (f) {
@@ -511,7 +519,26 @@ __device__ __forceinline__ int active_rhs(const WorkLists &W, int b, int jj) {
   return j;
 }
 
-// P2 item: node chunk k of beam b, load case j; this warp's kBatchWarpNodes
+// reduce-scatter of 32 values over the warp by recursive halving (31
+// shuffles instead of 5 per value): returns, in lane l, the warp total of
+// value l
+__device__ __forceinline__ float warp_reduce_scatter32(float (&v)[32]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    const bool upper = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < o; ++i) {
+      const float send = upper ? v[i] : v[i + o];
+      const float keep = upper ? v[i + o] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  return v[0];
+}
+
+// P2 item: node run k (<= kSubNodes nodes of one interpolation cell) of
+// beam b, load case j; this warp's kBatchWarpNodes
 // nodes of it.  kUpdate: the CG update of a stepping system (d += alpha p,
 // r = P (r - alpha q)) with D^-1 r.r and r.r into sums, then rc += Pi^T r;
 // else (refresh) rc += Pi^T r of a refreshing system's new residual.
@@ -524,13 +551,13 @@ __device__ __forceinline__ void tl_update_item(const BatchDev &a, const SysState
   if (!kUpdate && !cs_on) return;  // nothing to restrict
   int cell = 0, first, end;
   if (cs_on) {
-    const int4 ch = B.cs.chunk[k];
+    const int4 ch = B.cs.sub[k];
     cell = ch.x;
     first = ch.y;
     end = ch.z;
   } else {
-    first = k * kChunkNodes;
-    end = (int)min((int64_t)first + kChunkNodes, B.n_nodes);
+    first = k * kSubNodes;
+    end = (int)min((int64_t)first + kSubNodes, B.n_nodes);
   }
   const int lane = threadIdx.x & 31;
   const int wb = first + kBatchWarpNodes * (threadIdx.x >> 5);
@@ -547,8 +574,8 @@ __device__ __forceinline__ void tl_update_item(const BatchDev &a, const SysState
     const BatchSys &S = a.sys[s];
     double *__restrict__ d = S.d;
     double *__restrict__ r = S.r;
-    const double *__restrict__ p = S.p;
-    const double *__restrict__ q = S.q;
+    const float *__restrict__ p = S.p;
+    const float *__restrict__ q = S.q;
     const double *__restrict__ dinv = S.dinv;
     const uint8_t *__restrict__ dmask = S.dmask;
     const int32_t *__restrict__ cnodes = B.cs.cnodes;
@@ -594,11 +621,11 @@ __device__ __forceinline__ void tl_update_item(const BatchDev &a, const SysState
       }
     }
     if (cs_on) {
+      float v[32];
 #pragma unroll
-      for (int v = 0; v < 24; ++v) {
-        const float t = warp_allsum(acc[v]);
-        if (lane == v) atomicAdd(&S.rc[3 * cs_corner(B.cs, cell, v / 3) + v % 3], t);
-      }
+      for (int q = 0; q < 32; ++q) v[q] = q < 24 ? acc[q] : 0.f;
+      const float t = warp_reduce_scatter32(v);  // lane l: the warp total of value l
+      if (lane < 24) atomicAdd(&S.rc[3 * cs_corner(B.cs, cell, lane / 3) + lane % 3], t);
     }
   }
 }
@@ -680,8 +707,8 @@ __device__ __forceinline__ void tl_coarse_item(const BatchDev &a, const SysState
 // S, z = D^-1 r (+ P Pi yc with the two-level preconditioner)
 __device__ __forceinline__ void batch_directions(const BatchDev &a, const BatchSys &S, int64_t lo, int64_t hi,
                                                  int64_t step, double beta) {
-  double *__restrict__ p = S.p;
-  double *__restrict__ q = S.q;
+  float *__restrict__ p = S.p;
+  float *__restrict__ q = S.q;
   const double *__restrict__ r = S.r;
   const double *__restrict__ dinv = S.dinv;
   const uint8_t *__restrict__ dmask = S.dmask;
@@ -691,13 +718,13 @@ __device__ __forceinline__ void batch_directions(const BatchDev &a, const BatchS
     for (int64_t i = lo; i < hi; i += step) {
       double z = dinv[i] * __ldcg(&r[i]);
       if (dmask[i]) z += (double)cs_prolong_y(cs, yc, i);
-      p[i] = z + beta * __ldcg(&p[i]);
-      q[i] = 0.0;
+      p[i] = (float)(z + beta * (double)__ldcg(&p[i]));
+      q[i] = 0.f;
     }
   } else {
     for (int64_t i = lo; i < hi; i += step) {
-      p[i] = dinv[i] * __ldcg(&r[i]) + beta * __ldcg(&p[i]);
-      q[i] = 0.0;
+      p[i] = (float)(dinv[i] * __ldcg(&r[i]) + beta * (double)__ldcg(&p[i]));
+      q[i] = 0.f;
     }
   }
 }
@@ -737,7 +764,7 @@ __global__ void __launch_bounds__(kTileThreads, MINB) k_batch_cg(BatchDev a) {
         const int s = W.bfs[b] + j;
         if (!is_active(W.bm, s)) continue;
         const BatchSys &S = a.sys[s];
-        double en = (double)tile_compute<double, double, true>(B.A, tile, R, S.p, S.q, B.lam, B.mu, smem);
+        double en = (double)tile_compute<float, float, true>(B.A, tile, R, S.p, S.q, B.lam, B.mu, smem);
         en = block_sum<kTileThreads>(en);
         if (threadIdx.x == 0) atomicAdd(&pq[s], en);
       }
@@ -777,8 +804,8 @@ __global__ void __launch_bounds__(kTileThreads, MINB) k_batch_cg(BatchDev a) {
         const int64_t lo = max(g0, W.pd[i]) - W.pd[i], hi = min(g1, W.pd[i + 1]) - W.pd[i];
         double rz = 0.0, rr = 0.0;
         for (int64_t t = lo + threadIdx.x; t < hi; t += kTileThreads) {
-          S.d[t] = __ldcg(&S.d[t]) + alpha * __ldcg(&S.p[t]);
-          const double ri = S.dmask[t] ? __ldcg(&S.r[t]) - alpha * __ldcg(&S.q[t]) : 0.0;
+          S.d[t] = __ldcg(&S.d[t]) + alpha * (double)__ldcg(&S.p[t]);
+          const double ri = S.dmask[t] ? __ldcg(&S.r[t]) - alpha * (double)__ldcg(&S.q[t]) : 0.0;
           S.r[t] = ri;
           rz += S.dinv[t] * ri * ri;
           rr += ri * ri;
@@ -802,6 +829,7 @@ __global__ void __launch_bounds__(kTileThreads, MINB) k_batch_cg(BatchDev a) {
       if (s < a.n_sys) {
         const SysState n2 = decide(a, st, pq, sums, s);
         act = n2.active != 0;
+        W.beta[s] = n2.beta;
         if (blockIdx.x == 0) {
           nx[s] = n2;
           double *nsums = a.sums + 2 * (par ^ 1) * a.n_sys;
@@ -825,9 +853,8 @@ __global__ void __launch_bounds__(kTileThreads, MINB) k_batch_cg(BatchDev a) {
       while (i + 1 < n_s && W.pd[i + 1] <= g0) ++i;
       for (; g0 < g1 && i < n_s && W.pd[i] < g1; ++i) {
         const int s = W.act_s[i];
-        const SysState n2 = decide(a, st, pq, sums, s);
         const int64_t lo = max(g0, W.pd[i]) - W.pd[i], hi = min(g1, W.pd[i + 1]) - W.pd[i];
-        batch_directions(a, a.sys[s], lo + threadIdx.x, hi, kTileThreads, n2.beta);
+        batch_directions(a, a.sys[s], lo + threadIdx.x, hi, kTileThreads, W.beta[s]);
       }
     }
     if (n_s == 0) {
@@ -1148,8 +1175,8 @@ extern "C" int sfem_batch_solve(sfem_ctx *const *ctxs, int n, double *const *u, 
       const int nr = c.nrhs;
       double *X = (double *)get(nd * nr * sizeof(double));
       double *R = (double *)get(nd * nr * sizeof(double));
-      double *P = (double *)get(nd * nr * sizeof(double));
-      double *Q = (double *)get(nd * nr * sizeof(double));
+      float *P = (float *)get(nd * nr * sizeof(float));
+      float *Q = (float *)get(nd * nr * sizeof(float));
       double *D = (double *)get(nd * nr * sizeof(double));
       double *KX = (double *)get(nd * nr * sizeof(double));
       xbeam[b] = X;
@@ -1160,7 +1187,8 @@ extern "C" int sfem_batch_solve(sfem_ctx *const *ctxs, int n, double *const *u, 
                                   opts->u_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
       k_set_bc_all<<<grid_for(nd * nr, 256), 256, 0, st>>>(X, c.g, c.dmask, nd, nr, !opts->warm_start);
       SFEM_CHECK_LAUNCH();
-      for (double *v : {D, P, Q}) SFEM_CUDA(cudaMemsetAsync(v, 0, nd * nr * sizeof(double), st));
+      SFEM_CUDA(cudaMemsetAsync(D, 0, nd * nr * sizeof(double), st));
+      for (float *v : {P, Q}) SFEM_CUDA(cudaMemsetAsync(v, 0, nd * nr * sizeof(float), st));
       hb[b].A = TileArgs{c.tl.tile_start, c.tl.hoff,     c.tl.noff, c.tl.halo_tet, c.tl.halo_lconn,
                          c.tl.tile_nodes, c.tl.node_inc, c.tl.rec,  c.n_tets,       c.tl.slot_stride};
       hb[b].first_sys = s;
@@ -1175,7 +1203,7 @@ extern "C" int sfem_batch_solve(sfem_ctx *const *ctxs, int n, double *const *u, 
       tprefix[b + 1] = tprefix[b] + (int)c.tl.n_tiles;
       const int npad = cs_on ? c.coarse->dev.npad : 0;
       uprefix[b + 1] =
-          uprefix[b] + nr * (cs_on ? c.coarse->dev.nchunk : (int)((c.n_nodes + kChunkNodes - 1) / kChunkNodes));
+          uprefix[b] + nr * (cs_on ? c.coarse->dev.nsub : (int)((c.n_nodes + kSubNodes - 1) / kSubNodes));
       cprefix[b + 1] = cprefix[b] + (cs_on ? (npad / 64) * (npad / 64 + 1) / 2 : 0);
       for (int j = 0; j < nr; ++j, ++s) {
         BatchSys &S = hs[s];

@@ -1032,6 +1032,15 @@ static void setup_coarse(Ctx &c, const sfem_coarse_opts *opts) {
   int4 *d_chunk = c.mem.get<int4>(chunks.size());
   SFEM_CUDA(cudaMemcpyAsync(d_chunk, chunks.data(), chunks.size() * sizeof(int4), cudaMemcpyHostToDevice, c.stream));
   cs.chunk = d_chunk;
+  // the same runs split to at most kSubNodes nodes (update items of the
+  // batched solver)
+  std::vector<int4> subs;
+  for (const int4 &ch : chunks)
+    for (int b = ch.y; b < ch.z; b += kSubNodes) subs.push_back(make_int4(ch.x, b, std::min(b + kSubNodes, ch.z), 0));
+  cs.nsub = (int)subs.size();
+  int4 *d_sub = c.mem.get<int4>(subs.size());
+  SFEM_CUDA(cudaMemcpyAsync(d_sub, subs.data(), subs.size() * sizeof(int4), cudaMemcpyHostToDevice, c.stream));
+  cs.sub = d_sub;
   int32_t *d_glist = c.mem.get<int32_t>(glist.size());
   SFEM_CUDA(cudaMemcpyAsync(d_glist, glist.data(), glist.size() * 4, cudaMemcpyHostToDevice, c.stream));
   cs.cinfo = d_cinfo;

@@ -14,6 +14,7 @@
 namespace sfem {
 
 constexpr int kChunkNodes = 2048;  // nodes per block of the restriction in the two-level iterations
+constexpr int kSubNodes = 512;     // nodes per update item of the batched solver (batch.cu)
 
 struct CoarseDev {
   int d[3];                // centres per axis
@@ -29,6 +30,8 @@ struct CoarseDev {
   const int32_t *coff;     // ncell + 1
   const int4 *chunk;       // nchunk: (cell, first, end) ranges of cnodes, <= kChunkNodes nodes each
   int nchunk;
+  const int4 *sub;         // nsub: the same ranges split to <= kSubNodes nodes
+  int nsub;
   float *cellsum;          // ncell x 24 partial restrictions (8 corners x 3)
   float *rc, *yc;          // coarse residual and correction (npad)
   const float *C;          // A_c^-1 (symmetric, FP32): lower 64 x 64 blocks, block (a, b) at

@@ -252,14 +252,18 @@ typedef struct sfem_batch_opts {
   int use_graph;         /* 1: capture a round as a CUDA graph */
   int precond;           /* 0: the persistent Jacobi solve of all systems together; 1: each
                             system by the two-level mixed solve of its context (coarse space
-                            built with the default options where possible; inner_tol 0: 0.03);
+                            built on first use where possible, see patch_nodes; inner_tol 0:
+                            0.03);
                             2: the persistent solve of all systems together with the two-level
                             preconditioner of each context inside the launch (restriction,
                             coarse product and prolongation as phases of the persistent
-                            kernel; coarse spaces built with the default options on first
-                            use and kept by the contexts; a beam without one runs Jacobi;
+                            kernel; coarse spaces built on first use, see patch_nodes,
+                            and kept by the contexts; a beam without one runs Jacobi;
                             inner_tol 0: 0.03) */
-  int reserved[4];
+  int patch_nodes;       /* precond 1 and 2: patch width (node spacings) of the coarse spaces
+                            the batch builds for contexts that have none (0: 6; the library's
+                            default grid if that setup fails) */
+  int reserved[3];
 } sfem_batch_opts;
 
 typedef struct sfem_batch_stats {

@@ -1172,11 +1172,22 @@ static void setup_coarse(Ctx &c, const sfem_coarse_opts *opts) {
   c.coarse = co;
 }
 
-bool ensure_coarse(Ctx &c) {
+bool ensure_coarse(Ctx &c, int patch_nodes) {
   if (c.coarse) return true;
+  if (patch_nodes > 0) {
+    sfem_coarse_opts o{};
+    o.patch_nodes = patch_nodes;
+    try {
+      setup_coarse(c, &o);
+      return true;
+    } catch (const Error &) {
+      c.coarse.reset();  // e.g. A_c not positive definite with narrow patches: the default grid next
+    }
+  }
   try {
     setup_coarse(c, nullptr);
   } catch (const Error &) {
+    c.coarse.reset();
     return false;  // no coarse space for this mesh (e.g. patches too narrow)
   }
   return true;

@@ -293,9 +293,10 @@ void launch_mf32_tiled(Ctx &c, cudaStream_t st, const TU *u, TY *y, double *ener
 // rc = Pi^T r (r masked), then yc = C rc
 void coarse_correction(Ctx &c, cudaStream_t st, const double *r, const int *done);
 void coarse_correction(Ctx &c, cudaStream_t st, const float *r, const int *done);
-// the context's coarse space, built with the default options if missing;
-// false when none can be built
-bool ensure_coarse(Ctx &c);
+// the context's coarse space, built if missing: patches of patch_nodes node
+// spacings (0: the default options; the default options again if that
+// setup fails); false when none can be built
+bool ensure_coarse(Ctx &c, int patch_nodes = 0);
 // yc = C rc only (the fused two-level iterations restrict r themselves)
 void coarse_gemv(const CoarseDev &cs, cudaStream_t st, const int *done);
 // rc = Pi^T r only (fixed order; yc zeroed)

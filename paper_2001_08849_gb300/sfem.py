@@ -70,7 +70,7 @@ class sfem_batch_opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("inner_tol", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("max_rounds", ctypes.c_int), ("iters_per_launch", ctypes.c_int), ("u_on_device", ctypes.c_int),
                 ("warm_start", ctypes.c_int), ("autotune", ctypes.c_int), ("use_graph", ctypes.c_int),
-                ("precond", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
+                ("precond", ctypes.c_int), ("patch_nodes", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
 
 
 class sfem_batch_stats(ctypes.Structure):
@@ -329,9 +329,9 @@ def sfem_solve(h, u, opts: sfem_solve_opts, f_extra=None, check=True) -> dict:
 
 
 def batch_opts(tol=1e-8, inner_tol=0.0, max_iter=0, max_rounds=0, iters_per_launch=0, u_on_device=False,
-               warm_start=False, autotune=True, use_graph=True, precond=0):
+               warm_start=False, autotune=True, use_graph=True, precond=0, patch_nodes=0):
     o = sfem_batch_opts()
-    o.precond = int(precond)
+    o.precond, o.patch_nodes = int(precond), int(patch_nodes)
     o.tol, o.inner_tol = float(tol), float(inner_tol)
     o.max_iter, o.max_rounds, o.iters_per_launch = int(max_iter), int(max_rounds), int(iters_per_launch)
     o.u_on_device, o.warm_start = int(bool(u_on_device)), int(bool(warm_start))

@@ -519,24 +519,6 @@ __device__ __forceinline__ int active_rhs(const WorkLists &W, int b, int jj) {
   return j;
 }
 
-// reduce-scatter of 32 values over the warp by recursive halving (31
-// shuffles instead of 5 per value): returns, in lane l, the warp total of
-// value l
-__device__ __forceinline__ float warp_reduce_scatter32(float (&v)[32]) {
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int o = 16; o >= 1; o >>= 1) {
-    const bool upper = (lane & o) != 0;
-#pragma unroll
-    for (int i = 0; i < o; ++i) {
-      const float send = upper ? v[i] : v[i + o];
-      const float keep = upper ? v[i + o] : v[i];
-      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
-    }
-  }
-  return v[0];
-}
-
 // P2 item: node run k (<= kSubNodes nodes of one interpolation cell) of
 // beam b, load case j; this warp's kBatchWarpNodes
 // nodes of it.  kUpdate: the CG update of a stepping system (d += alpha p,

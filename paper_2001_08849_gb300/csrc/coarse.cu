@@ -111,10 +111,14 @@ __global__ void k_cs_gather(CoarseDev cs, const int *done) {
 // yc += C rc with C = A_c^-1 symmetric, stored as its lower 64 x 64 blocks
 // (block (a, b), a >= b, at (a (a + 1) / 2 + b) * 4096, row-major): half the
 // bytes of the full matrix, which streams from DRAM every iteration (the
-// operator's records evict it from L2).  One CTA per block: the block is read
-// once with evict-first loads and applied twice, C_ab rc_b to yc_a and
-// C_ab^T rc_a to yc_b (a > b), by FP32 atomics; yc must be zero before.
-__global__ void __launch_bounds__(256) k_cs_symv(CoarseDev cs, const int *done) {
+// operator's records evict it from L2; keeping it there with an evict-last
+// policy, or marking the records evict-first, measured no faster).  One CTA
+// per block: the block is read once with evict-first loads and applied
+// twice, C_ab rc_b to yc_a and C_ab^T rc_a to yc_b (a > b), by FP32
+// atomics; yc must be zero before.
+// With rzc, rc.C rc is added to *rzc as well (rc_a.C_ab rc_b, twice for
+// a > b; one FP64 atomic per block).
+__global__ void __launch_bounds__(256) k_cs_symv(CoarseDev cs, const int *done, double *rzc) {
   if (done && *done) return;
   const int t = blockIdx.x;
   int a = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
@@ -141,6 +145,11 @@ __global__ void __launch_bounds__(256) k_cs_symv(CoarseDev cs, const int *done) 
   s += __shfl_xor_sync(0xffffffffu, s, 1);
   s += __shfl_xor_sync(0xffffffffu, s, 2);
   if (q == 0) atomicAdd(&cs.yc[a * kCB + i], s);
+  if (rzc) {  // whole block (rzc is uniform)
+    float e = q == 0 ? ra[i] * s * (a == b ? 1.f : 2.f) : 0.f;
+    e = block_sum_f<256>(e);
+    if (threadIdx.x == 0) atomicAdd(rzc, (double)e);
+  }
   if (a == b) return;  // a whole block: uniform
   // C_ab^T ra: column j = 16 q + 4 u + w gets v[u].{x,y,z,w} * ra[i]; sum over i
   // within the warp (8 rows), then over the 8 warps in shared memory
@@ -797,9 +806,9 @@ __global__ void k_cs_apply_z(CoarseDev cs, const double *__restrict__ r, const d
   if (i < n) z[i] = dinv[i] * r[i] + (dmask[i] ? (double)cs_prolong(cs, i) : 0.0);
 }
 
-void coarse_gemv(const CoarseDev &cs, cudaStream_t st, const int *done) {
+void coarse_gemv(const CoarseDev &cs, cudaStream_t st, const int *done, double *rzc) {
   const int nb = cs.npad / kCB;
-  k_cs_symv<<<nb * (nb + 1) / 2, 256, 0, st>>>(cs, done);
+  k_cs_symv<<<nb * (nb + 1) / 2, 256, 0, st>>>(cs, done, rzc);
   SFEM_CHECK_LAUNCH();
 }
 

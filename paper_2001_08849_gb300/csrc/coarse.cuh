@@ -54,6 +54,24 @@ __device__ __forceinline__ int cs_corner(const CoarseDev &cs, int cell, int k) {
   return (jx * cs.d[1] + jy) * cs.d[2] + jz;
 }
 
+// reduce-scatter of 32 values over the warp by recursive halving (31
+// shuffles instead of 5 per value): returns, in lane l, the warp total of
+// value l (the restrictions' 24 corner sums)
+__device__ __forceinline__ float warp_reduce_scatter32(float (&v)[32]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    const bool upper = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < o; ++i) {
+      const float send = upper ? v[i] : v[i + o];
+      const float keep = upper ? v[i + o] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  return v[0];
+}
+
 // (Pi y)_i for DOF i = 3 node + c (not masked), y given by the caller
 __device__ __forceinline__ float cs_prolong_y(const CoarseDev &cs, const float *yc, int64_t i) {
   const int64_t node = i / 3;

@@ -83,6 +83,7 @@ struct SolveScalars {
   int max_iter;
   int reason;       // why done: 1 converged, 2 reliable update due, 3 iteration cap
   int pad[3];
+  double rzj, rzc;  // two-level iterations: z.r = r.D^-1 r (update pass) + rc.C rc (coarse product)
 };
 
 // ---------------------------------------------------------------------------
@@ -298,7 +299,8 @@ void coarse_correction(Ctx &c, cudaStream_t st, const float *r, const int *done)
 // setup fails); false when none can be built
 bool ensure_coarse(Ctx &c, int patch_nodes = 0);
 // yc = C rc only (the fused two-level iterations restrict r themselves)
-void coarse_gemv(const CoarseDev &cs, cudaStream_t st, const int *done);
+// (with rzc: rc.C rc added to *rzc)
+void coarse_gemv(const CoarseDev &cs, cudaStream_t st, const int *done, double *rzc = nullptr);
 // rc = Pi^T r only (fixed order; yc zeroed)
 void coarse_restrict(Ctx &c, cudaStream_t st, const double *r, const int *done);
 

@@ -58,7 +58,6 @@ struct PcgVecs {
   int64_t n;
   bool coarse = false;  // two-level preconditioner: z = D^-1 r + P Pi yc
   CoarseDev cs{};
-  float *z32 = nullptr;  // two-level: z of the current r in FP32 (written by k_tl_zr)
   const float *dinv32 = nullptr;
   float *xlo = nullptr;  // FP32 x: low words of a double-float correction (x + xlo), or none
   // penalty method: the operator is followed by q += alpha S p (S: the DOFs
@@ -271,18 +270,20 @@ __global__ void __launch_bounds__(kVecBlock) k_pcg_direction(PcgVecs<TX, TR, TP>
 
 // ---- two-level iteration ------------------------------------------------------
 // With the coarse correction an iteration runs, after the operator:
-//   k_tl_update    x += alpha p, r = P (r - alpha q), q = 0, ||r||^2: a
-//                  streaming pass over the DOFs (4 per thread, vector
-//                  loads when the vectors are FP32 and 16-byte aligned);
-//   k_tl_restrict  rc += Pi^T r: one warp per run of 256 nodes of one
+//   k_tl_update    x += alpha p, r = P (r - alpha q), q = 0, ||r||^2 and
+//                  r.D^-1 r: a streaming pass over the DOFs (4 per thread,
+//                  vector loads when the vectors are FP32 and 16-byte
+//                  aligned);
+//   k_tl_restrict  rc += Pi^T r: one warp per run of 64 nodes of one
 //                  interpolation cell (nodes grouped by cell), its 24
-//                  sums (8 corners x 3 components) added to the cell's
-//                  centres by FP32 atomics;
-//   k_cs_symv      yc = C rc (packed symmetric C; yc cleared by the restriction);
-//   k_tl_zr        z = D^-1 r + P Pi yc in FP32 (stored), z.r and beta;
-//                  rc = 0 for the next restriction;
-//   k_tl_dir       p = z + beta p.
-// z, the restriction and the dot products' per-thread sums are FP32 (the
+//                  sums (8 corners x 3 components, reduce-scattered over the
+//                  warp) added to the cell's centres by FP32 atomics;
+//   k_cs_symv      yc = C rc (packed symmetric C; yc cleared by the
+//                  restriction) and rc.C rc;
+//   k_tl_dir       z.r = r.D^-1 r + rc.C rc (since P Pi yc . r = yc . rc),
+//                  beta, and p = D^-1 r + P Pi yc + beta p in one pass: z is
+//                  never stored; rc = 0 for the next restriction.
+// The restriction and the dot products' per-thread sums are FP32 (the
 // preconditioner and the step lengths tolerate 1e-7 relative rounding).
 // FP64 arithmetic runs at about one FMA per SM and clock on this GPU, so
 // the per-DOF FP64 work is kept to x += alpha p.
@@ -305,7 +306,8 @@ __global__ void __launch_bounds__(kVecBlock) k_tl_update(PcgVecs<TX, TR, TP> v, 
   TP *__restrict__ q = v.q;
   const TP *__restrict__ p = v.p;
   const uint8_t *__restrict__ msk = v.dmask;
-  float rr = 0.f;
+  const float *__restrict__ dinv = v.dinv32;
+  float rr = 0.f, rzj = 0.f;
   const int64_t nq = v.n / 4, stride = (int64_t)gridDim.x * kVecBlock;
   for (int64_t t = (int64_t)blockIdx.x * kVecBlock + threadIdx.x; t < nq; t += stride) {
     const int64_t i = 4 * t;
@@ -313,12 +315,15 @@ __global__ void __launch_bounds__(kVecBlock) k_tl_update(PcgVecs<TX, TR, TP> v, 
     float xlv[4] = {0.f, 0.f, 0.f, 0.f};
     TP pv[4], qv[4];
     TR rv[4];
+    float dv[4];
     uint8_t mv[4];
     if constexpr (kVec) {
       const float4 x4 = *reinterpret_cast<const float4 *>(x + i), xl4 = *reinterpret_cast<const float4 *>(xl + i);
       const float4 p4 = *reinterpret_cast<const float4 *>(p + i), q4 = *reinterpret_cast<const float4 *>(q + i);
       const float4 r4 = *reinterpret_cast<const float4 *>(r + i);
       const uchar4 m4 = *reinterpret_cast<const uchar4 *>(msk + i);
+      const float4 d4 = *reinterpret_cast<const float4 *>(dinv + i);
+      dv[0] = d4.x, dv[1] = d4.y, dv[2] = d4.z, dv[3] = d4.w;
       xv[0] = x4.x, xv[1] = x4.y, xv[2] = x4.z, xv[3] = x4.w;
       xlv[0] = xl4.x, xlv[1] = xl4.y, xlv[2] = xl4.z, xlv[3] = xl4.w;
       pv[0] = p4.x, pv[1] = p4.y, pv[2] = p4.z, pv[3] = p4.w;
@@ -333,6 +338,7 @@ __global__ void __launch_bounds__(kVecBlock) k_tl_update(PcgVecs<TX, TR, TP> v, 
         pv[c] = p[i + c];
         qv[c] = q[i + c];
         rv[c] = r[i + c];
+        dv[c] = dinv[i + c];
         mv[c] = msk[i + c];
       }
     }
@@ -346,6 +352,7 @@ __global__ void __launch_bounds__(kVecBlock) k_tl_update(PcgVecs<TX, TR, TP> v, 
       rn[c] = mv[c] ? fma(-ar, (TR)qv[c], rv[c]) : TR(0);
       const float rf = (float)rn[c];
       rr = fmaf(rf, rf, rr);
+      rzj = fmaf(dv[c] * rf, rf, rzj);
     }
     if constexpr (kVec) {
       *reinterpret_cast<float4 *>(x + i) = make_float4(xv[0], xv[1], xv[2], xv[3]);
@@ -372,20 +379,26 @@ __global__ void __launch_bounds__(kVecBlock) k_tl_update(PcgVecs<TX, TR, TP> v, 
     if (zero_q) q[i] = TP(0);
     const float rf = (float)rn;
     rr = fmaf(rf, rf, rr);
+    rzj = fmaf(dinv[i] * rf, rf, rzj);
   }
-  double vv[1] = {(double)rr};
-  if (grid_sum<kVecBlock, 1>(vv, partials, ticket, nullptr) && threadIdx.x == 0) finish_update(S, alpha, rz_old, vv[0]);
+  double vv[2] = {(double)rr, (double)rzj};
+  if (grid_sum<kVecBlock, 2>(vv, partials, ticket, nullptr) && threadIdx.x == 0) {
+    finish_update(S, alpha, rz_old, vv[0]);
+    S->rzj = vv[1];
+    S->rzc = 0.0;  // the coarse product adds rc.C rc
+  }
 }
 
-// nodes per warp of the restriction: 8 per lane, loads issued together
-constexpr int kRestrictWarpNodes = 256;
+// nodes per warp of the restriction (2 per lane) and per block
+constexpr int kRestrictWarpNodes = kSubNodes / (kVecBlock / 32);
+static_assert(kRestrictWarpNodes == 64, "two nodes per lane");
 
 template <class TR>
 __global__ void __launch_bounds__(kVecBlock) k_tl_restrict(const TR *__restrict__ r, CoarseDev cs, const int *done) {
   if (done && *done) return;
   if (blockIdx.x == 0)  // the coarse product accumulates into yc
     for (int i = threadIdx.x; i < cs.npad; i += kVecBlock) cs.yc[i] = 0.f;
-  const int4 ch = cs.chunk[blockIdx.x];
+  const int4 ch = cs.sub[blockIdx.x];
   const int lane = threadIdx.x & 31;
   const int b = ch.y + kRestrictWarpNodes * (threadIdx.x >> 5);
   if (b >= ch.z) return;  // whole warps; no block barrier follows
@@ -405,9 +418,9 @@ __global__ void __launch_bounds__(kVecBlock) k_tl_restrict(const TR *__restrict_
       f[u][c] = i0[u] >= 0 ? cs.frac[i0[u] + c] : 0.f;
       rf[u][c] = i0[u] >= 0 ? (float)r[i0[u] + c] : 0.f;
     }
-  float acc[24];
+  float acc[32];
 #pragma unroll
-  for (int j = 0; j < 24; ++j) acc[j] = 0.f;
+  for (int j = 0; j < 32; ++j) acc[j] = 0.f;
 #pragma unroll
   for (int u = 0; u < U; ++u)
 #pragma unroll
@@ -416,45 +429,52 @@ __global__ void __launch_bounds__(kVecBlock) k_tl_restrict(const TR *__restrict_
 #pragma unroll
       for (int c = 0; c < 3; ++c) acc[3 * kk + c] = fmaf(w, rf[u][c], acc[3 * kk + c]);
     }
-#pragma unroll
-  for (int j = 0; j < 24; ++j)
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc[j] += __shfl_down_sync(0xffffffffu, acc[j], o);
-  if (lane == 0) {
-#pragma unroll
-    for (int kk = 0; kk < 8; ++kk) {
-      float *rc = cs.rc + 3 * cs_corner(cs, ch.x, kk);
-#pragma unroll
-      for (int c = 0; c < 3; ++c) atomicAdd(rc + c, acc[3 * kk + c]);
-    }
-  }
+  const float t = warp_reduce_scatter32(acc);  // lane l: the warp total of value l
+  if (lane < 24) atomicAdd(cs.rc + 3 * cs_corner(cs, ch.x, lane / 3) + lane % 3, t);
 }
 
+// z.r and beta from the two partial sums, then p = D^-1 r + P Pi yc + beta p
+// (every block forms the same beta; block 0 stores it).  A non-positive or
+// non-finite z.r is a breakdown: p is left as it is.
 template <class TX, class TR, class TP>
-__global__ void __launch_bounds__(kVecBlock) k_tl_zr(PcgVecs<TX, TR, TP> v, SolveScalars *S, double *partials,
-                                                     unsigned int *ticket) {
+__global__ void __launch_bounds__(kVecBlock) k_tl_dir(PcgVecs<TX, TR, TP> v, SolveScalars *S) {
   if (S->done) return;
+  const double rz = S->rzj + S->rzc;
+  const double beta = rz / S->rz_prev;
+  const bool ok = isfinite(rz) && rz > 0.0 && isfinite(beta);
   const CoarseDev &cs = v.cs;
-  if (blockIdx.x == 0)  // k_cs_symv has consumed rc
-    for (int i = threadIdx.x; i < cs.npad; i += kVecBlock) cs.rc[i] = 0.f;
+  if (blockIdx.x == 0) {
+    for (int i = threadIdx.x; i < cs.npad; i += kVecBlock) cs.rc[i] = 0.f;  // k_cs_symv has consumed rc
+    if (threadIdx.x == 0) {
+      S->beta = beta;
+      S->rz = rz;
+      if (!ok) {
+        S->status = 1;
+        S->done = 1;
+      }
+    }
+  }
+  if (!ok) return;
   const TR *__restrict__ r = v.r;
   const float *__restrict__ dinv = v.dinv32;
   const uint8_t *__restrict__ msk = v.dmask;
-  float *__restrict__ z = v.z32;
+  TP *__restrict__ p = v.p;
   const float *__restrict__ yc = cs.yc;
+  const TP b = (TP)beta;
   const int64_t nn = v.n / 3;
   const int sx = 3 * cs.d[1] * cs.d[2], sy = 3 * cs.d[2];
-  float rz = 0.f;
 #pragma unroll 2
   for (int64_t node = (int64_t)blockIdx.x * kVecBlock + threadIdx.x; node < nn;
        node += (int64_t)gridDim.x * kVecBlock) {
     const int64_t i0 = 3 * node;
     TR rv[3];
+    TP pv[3];
     float dv[3];
     uint8_t mv[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       rv[c] = r[i0 + c];
+      pv[c] = p[i0 + c];
       dv[c] = dinv[i0 + c];
       mv[c] = msk[i0 + c];
     }
@@ -472,47 +492,10 @@ __global__ void __launch_bounds__(kVecBlock) k_tl_zr(PcgVecs<TX, TR, TP> v, Solv
     }
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      const float rf = (float)rv[c];
-      const float zc = fmaf(dv[c], rf, mv[c] ? y[c] : 0.f);
-      z[i0 + c] = zc;
-      rz = fmaf(zc, rf, rz);
+      const float zc = fmaf(dv[c], (float)rv[c], mv[c] ? y[c] : 0.f);
+      p[i0 + c] = fma(b, pv[c], (TP)zc);
     }
   }
-  double vv[1] = {(double)rz};
-  if (grid_sum<kVecBlock, 1>(vv, partials, ticket, nullptr) && threadIdx.x == 0) {
-    S->beta = vv[0] / S->rz_prev;
-    S->rz = vv[0];
-    if (!isfinite(vv[0]) || !(vv[0] > 0.0)) {
-      S->status = 1;
-      S->done = 1;
-    }
-  }
-}
-
-template <class TP, bool kVec>
-__global__ void __launch_bounds__(kVecBlock) k_tl_dir(TP *__restrict__ p, const float *__restrict__ z, int64_t n,
-                                                      const SolveScalars *S) {
-  static_assert(!kVec || std::is_same_v<TP, float>, "vector path is FP32");
-  if (S->done) return;
-  const TP b = (TP)S->beta;
-  const int64_t stride = (int64_t)gridDim.x * kVecBlock;
-  int64_t i0 = 0;
-  if constexpr (kVec) {  // FP32 p, 16-byte aligned
-    const int64_t nq = n / 4;
-    for (int64_t t = (int64_t)blockIdx.x * kVecBlock + threadIdx.x; t < nq; t += stride) {
-      const float4 z4 = reinterpret_cast<const float4 *>(z)[t];
-      float4 p4 = reinterpret_cast<float4 *>(p)[t];
-      p4.x = fmaf(b, p4.x, z4.x);
-      p4.y = fmaf(b, p4.y, z4.y);
-      p4.z = fmaf(b, p4.z, z4.z);
-      p4.w = fmaf(b, p4.w, z4.w);
-      reinterpret_cast<float4 *>(p)[t] = p4;
-    }
-    i0 = 4 * nq;
-  }
-#pragma unroll 4
-  for (int64_t i = i0 + (int64_t)blockIdx.x * kVecBlock + threadIdx.x; i < n; i += stride)
-    p[i] = fma(b, p[i], (TP)z[i]);
 }
 
 // ---- FP64 residual and refinement helpers ----------------------------------
@@ -781,7 +764,7 @@ struct CgRun {
         constexpr bool f32 = std::is_same_v<TX, float> && std::is_same_v<TR, float> && std::is_same_v<TP, float>;
         bool vec = false;
         if constexpr (f32)
-          vec = v.xlo && aligned16(v.x, v.xlo, v.r, v.p, v.q, v.z32) &&
+          vec = v.xlo && aligned16(v.x, v.xlo, v.r, v.p, v.q, v.dinv32) &&
                 (reinterpret_cast<uintptr_t>(v.dmask) & 3) == 0;
         if constexpr (f32) {
           if (vec)
@@ -791,16 +774,10 @@ struct CgRun {
         if (!vec)
           k_tl_update<TX, TR, TP, false><<<vb, kVecBlock, 0, st>>>(v, S, mf, c.red_partial, c.tickets + 3);
         SFEM_CHECK_LAUNCH();
-        static_assert(kChunkNodes <= (kVecBlock / 32) * kRestrictWarpNodes, "restriction chunk too large");
-        k_tl_restrict<TR><<<cs.nchunk, kVecBlock, 0, st>>>(v.r, cs, done);
+        k_tl_restrict<TR><<<cs.nsub, kVecBlock, 0, st>>>(v.r, cs, done);
         SFEM_CHECK_LAUNCH();
-        coarse_gemv(cs, st, done);
-        k_tl_zr<TX, TR, TP><<<vb, kVecBlock, 0, st>>>(v, S, c.red_partial, c.tickets + 10);
-        SFEM_CHECK_LAUNCH();
-        if constexpr (f32) {
-          if (vec) k_tl_dir<TP, true><<<vb, kVecBlock, 0, st>>>(v.p, v.z32, v.n, S);
-        }
-        if (!vec) k_tl_dir<TP, false><<<vb, kVecBlock, 0, st>>>(v.p, v.z32, v.n, S);
+        coarse_gemv(cs, st, done, &S->rzc);
+        k_tl_dir<TX, TR, TP><<<vb, kVecBlock, 0, st>>>(v, S);
         SFEM_CHECK_LAUNCH();
         return;
       }
@@ -963,12 +940,10 @@ void solve_impl(Ctx &c, const double *f_extra, double *u, const sfem_solve_opts 
   SFEM_CUDA(cudaEventRecord(e0, c.stream));
 
   SolveBuffers B(c);
-  float *zbuf = coarse ? B.get<float>(n) : nullptr;
   auto with_coarse = [&](auto &vv) {
     if (coarse) {
       vv.coarse = true;
       vv.cs = c.coarse->dev;
-      vv.z32 = zbuf;
       vv.dinv32 = c.dinv32;
     }
   };

@@ -530,9 +530,10 @@ __global__ void __launch_bounds__(kTileThreads, 3) k_cs_galerkin(TileArgs A, Coa
           T.su[i] = make_float4(comp == 0 ? v : 0.f, comp == 1 ? v : 0.f, comp == 2 ? v : 0.f, 0.f);
         }
         __syncthreads();
-        tile_strains(A, R, T);
+        TileOwnW Wn;
+        tile_strains(A, R, T, Wn);
         __syncthreads();
-        tile_forces(R, T, lam, mu);
+        tile_forces(R, T, Wn, lam, mu);
         __syncthreads();
         node_forces();
         restrict_add(3 * J + comp);

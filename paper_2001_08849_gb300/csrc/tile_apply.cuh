@@ -106,6 +106,16 @@ struct TileRegsT {
 };
 using TileRegs = TileRegsT<kTileThreads>;
 
+// the strains (w0..w3 | w4, w5, V, 0) of a thread's own tets, kept in
+// registers from the strain phase to the force phase (the shared-memory
+// copies are for the neighbours; re-reading them cost 2 of the 10 float4
+// loads per tet of the force phase)
+template <int NT>
+struct TileOwnWT {
+  float4 w[TileRegsT<NT>::kPer][2];
+};
+using TileOwnW = TileOwnWT<kTileThreads>;
+
 __device__ __forceinline__ void tile_load(const TileArgs &A, int tile, TileRegs &R) {
   const int s = A.tile_start[tile], n_own = A.tile_start[tile + 1] - s;
 #pragma unroll
@@ -174,7 +184,9 @@ __device__ __forceinline__ void store_slot_force(const TileView &T, const float4
 }
 
 // strains of the tile's own and halo tets from the displacements in su
-__device__ __forceinline__ void tile_strains(const TileArgs &A, const TileRegs &R, const TileView &T) {
+// (with kKeep the own tets' also into W)
+template <bool kKeep = false>
+__device__ __forceinline__ void tile_strains(const TileArgs &A, const TileRegs &R, const TileView &T, TileOwnW &W) {
 #pragma unroll
   for (int r = 0; r < kTilePer; ++r) {
     const int j = threadIdx.x + r * kTileThreads;
@@ -186,6 +198,10 @@ __device__ __forceinline__ void tile_strains(const TileArgs &A, const TileRegs &
       strain_to(T.su, lc, G, w2);
       T.swa[j] = w2[0];
       T.swb[j] = w2[1];
+      if (kKeep) {
+        W.w[r][0] = w2[0];
+        W.w[r][1] = w2[1];
+      }
     }
   }
   for (int h = threadIdx.x; h < T.H; h += kTileThreads) {
@@ -200,10 +216,13 @@ __device__ __forceinline__ void tile_strains(const TileArgs &A, const TileRegs &
   }
 }
 
-// face-averaged stress of every own tet and its four nodal force slots;
-// returns this thread's share of the energy sum w . t
-template <int NT = kTileThreads>
-__device__ __forceinline__ float tile_forces(const TileRegsT<NT> &R, const TileView &T, float lam, float mu) {
+// face-averaged stress of every own tet and its four nodal force slots
+// (the neighbours' strains from shared memory, the own ones from Wn with
+// kKeep, else from shared memory too; the kernels that keep them have the
+// registers to spare); returns this thread's share of the energy sum w . t
+template <int NT = kTileThreads, bool kKeep = false>
+__device__ __forceinline__ float tile_forces(const TileRegsT<NT> &R, const TileView &T, const TileOwnWT<NT> &Wn,
+                                             float lam, float mu) {
   float en = 0.f;  // this thread's tets
 #pragma unroll
   for (int r = 0; r < TileRegsT<NT>::kPer; ++r) {
@@ -214,7 +233,7 @@ __device__ __forceinline__ float tile_forces(const TileRegsT<NT> &R, const TileV
     rec_unpack(R.rr[r], G, lc);
     const uint2 nb2 = make_uint2(__float_as_uint(R.rr[r][3].x), __float_as_uint(R.rr[r][3].y));
     const int nb[4] = {(int)(nb2.x & 0xFFFF), (int)(nb2.x >> 16), (int)(nb2.y & 0xFFFF), (int)(nb2.y >> 16)};
-    const float4 w0 = T.swa[j], w1 = T.swb[j];
+    const float4 w0 = kKeep ? Wn.w[r][0] : T.swa[j], w1 = kKeep ? Wn.w[r][1] : T.swb[j];
     const float W[6] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y};
     const float Ve = w1.z;
     // face weights kap_a = 1/(4 (V_e + V_nbr)), 1/(4 V_e) on exterior faces
@@ -341,9 +360,10 @@ __device__ __forceinline__ float tile_compute(const TileArgs &A, int tile, const
     T.snode[i] = A.node_inc[T.n0 + i];
   }
   __syncthreads();
-  tile_strains(A, R, T);
+  TileOwnW Wn;
+  tile_strains(A, R, T, Wn);
   __syncthreads();
-  const float en = tile_forces(R, T, lam, mu);
+  const float en = tile_forces(R, T, Wn, lam, mu);
   __shared__ float s_en[kTileThreads / 32];
   if (energy_out) {  // FP32 within the tile (512 terms), FP64 across tiles
     float e = en;

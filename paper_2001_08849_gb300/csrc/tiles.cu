@@ -702,7 +702,9 @@ __global__ void __launch_bounds__(NT, 2)
       fence_proxy_async_smem();
       pf_issue_record_plane(A, mn->s, mn->n_own, rb, &bar[0], threadIdx.x >> 5);
     }
-    // 2. strains of the own tets (records in registers) and the halo tets
+    // 2. strains of the own tets (records in registers; the strains kept in
+    // registers for the force phase) and the halo tets
+    TileOwnWT<NT> Wn;
 #pragma unroll
     for (int r = 0; r < Regs::kPer; ++r) {
       const int j = threadIdx.x + r * NT;
@@ -710,10 +712,9 @@ __global__ void __launch_bounds__(NT, 2)
         TetGeo G;
         uint2 lc;
         rec_unpack(R.rr[r], G, lc);
-        float4 w2[2];
-        strain_to(T.su, lc, G, w2);
-        T.swa[j] = w2[0];
-        T.swb[j] = w2[1];
+        strain_to(T.su, lc, G, Wn.w[r]);
+        T.swa[j] = Wn.w[r][0];
+        T.swb[j] = Wn.w[r][1];
       }
     }
     {
@@ -742,7 +743,7 @@ __global__ void __launch_bounds__(NT, 2)
       cp_async_commit();
     }
     // 3. face-averaged stresses and the slot forces
-    const float en = tile_forces<NT>(R, T, lam, mu);
+    const float en = tile_forces<NT, true>(R, T, Wn, lam, mu);
     if (energy_out) {  // FP32 within the tile, FP64 across tiles
       float e = en;
 #pragma unroll

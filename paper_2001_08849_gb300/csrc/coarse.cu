@@ -760,6 +760,48 @@ __global__ void __launch_bounds__(256) k_trtri_cols(const float *L, const float 
   }
 }
 
+// The same column recurrence with the column's last bwb blocks W_lj kept in
+// a shared-memory ring (slot l mod bwb), so that a step loads only its L
+// blocks and W_ii, all issued together.  Shared memory: 2 bwb + 2 tiles.
+__global__ void __launch_bounds__(256) k_trtri_ring(const float *L, const float *Wd, float *W, int npad, int nb,
+                                                    int bwb) {
+  extern __shared__ __align__(16) unsigned char dyn_raw[];
+  Tile64<float> *ring = reinterpret_cast<Tile64<float> *>(dyn_raw);
+  Tile64<float> *Lt = ring + bwb;
+  Tile64<float> &D = Lt[bwb];
+  Tile64<float> &S = Lt[bwb + 1];
+  const int bj = blockIdx.x;
+  const int tm = (threadIdx.x >> 4) * 4, tn = (threadIdx.x & 15) * 4;
+  for (int e = threadIdx.x; e < kCB * kCB; e += blockDim.x) {
+    const float v = Wd[(int64_t)bj * kCB * kCB + e];
+    ring[bj % bwb].v[e / kCB][e % kCB] = v;
+    W[(int64_t)(bj * kCB + e / kCB) * npad + bj * kCB + e % kCB] = v;
+  }
+  for (int bi = bj + 1; bi < nb; ++bi) {
+    const int l0 = max(bj, bi - bwb);
+    __syncthreads();  // the previous step's ring write and tile reads are done
+    for (int l = l0; l < bi; ++l) load64(Lt[l - l0], L, npad, bi, l);
+    load64(D, Wd + (int64_t)bi * kCB * kCB, kCB, 0, 0);
+    __syncthreads();
+    float acc[4][4] = {};
+    for (int l = l0; l < bi; ++l) mm64<float, false, false>(acc, Lt[l - l0], ring[l % bwb], tm, tn);
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) S.v[tm + x][tn + y] = acc[x][y];
+    __syncthreads();  // S complete; ring slot bi mod bwb (block bi - bwb) no longer read
+    float out[4][4] = {};
+    mm64<float, false, false>(out, D, S, tm, tn);
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) {
+        ring[bi % bwb].v[tm + x][tn + y] = -out[x][y];
+        W[(int64_t)(bi * kCB + tm + x) * npad + bj * kCB + tn + y] = -out[x][y];
+      }
+  }
+}
+
 // C[a][b] = sum_{l >= a} W[l][a]^T W[l][b] for a >= b (packed lower blocks)
 __global__ void __launch_bounds__(256) k_lauum(const float *W, float *C, int npad, int nb) {
   __shared__ Tile64<float> As, Bs;
@@ -906,7 +948,10 @@ __global__ void k_cs_to_f32(const double *a, float *b, int64_t n) {
 
 // blocked Cholesky of the band of A (lower blocks within bwb of the
 // diagonal) in place, with the inverses of the diagonal blocks in Wd;
-// false on a non-positive pivot
+// false on a non-positive pivot.  (The whole band in one CTA, diagonal
+// block, panel and trailing blocks per step in shared memory, took 3.7
+// instead of 2.8 ms on the 2M-tet beam's 50 block steps: one SM's GEMM
+// throughput; the diagonal factor with its j loops not unrolled, 3.2 ms.)
 template <class T>
 static bool banded_cholesky(Ctx &c, T *A, T *Wd, int npad, int nb, int bwb, int *dev_info) {
   const size_t sm2 = 2 * sizeof(Tile64<T>);
@@ -1162,7 +1207,13 @@ static void setup_coarse(Ctx &c, const sfem_coarse_opts *opts) {
   float *W = c.mem.get<float>(np2);
   float *C = c.mem.get<float>((size_t)nb * (nb + 1) / 2 * kCB * kCB);
   SFEM_CUDA(cudaMemsetAsync(W, 0, np2 * sizeof(float), c.stream));
-  k_trtri_cols<<<nb, 256, 0, c.stream>>>(L32, Wd, W, cs.npad, nb, bwb);
+  const size_t smr = (2 * (size_t)bwb + 2) * sizeof(Tile64<float>);
+  if (smr <= 200 * 1024) {  // 1.27 -> 0.91 ms on the 2M-tet beam's 3150 coarse DOFs
+    SFEM_CUDA(cudaFuncSetAttribute(k_trtri_ring, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr));
+    k_trtri_ring<<<nb, 256, smr, c.stream>>>(L32, Wd, W, cs.npad, nb, bwb);
+  } else {
+    k_trtri_cols<<<nb, 256, 0, c.stream>>>(L32, Wd, W, cs.npad, nb, bwb);
+  }
   SFEM_CHECK_LAUNCH();
   k_lauum<<<nb * (nb + 1) / 2, 256, 0, c.stream>>>(W, C, cs.npad, nb);
   SFEM_CHECK_LAUNCH();

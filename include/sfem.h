@@ -262,7 +262,8 @@ typedef struct sfem_batch_opts {
                             inner_tol 0: 0.03) */
   int patch_nodes;       /* precond 1 and 2: patch width (node spacings) of the coarse spaces
                             the batch builds for contexts that have none (0: 6; the library's
-                            default grid if that setup fails) */
+                            default grid if that setup fails); -1: no coarse space is built,
+                            contexts without one run Jacobi (inside the launch with precond 2) */
   int reserved[3];
 } sfem_batch_opts;
 

@@ -1063,7 +1063,8 @@ static int batch_two_level(sfem_ctx *const *ctxs, int n, double *const *u, const
   long long total_it = 0;
   for (int b = 0; b < n; ++b) {
     Ctx &c = ctxs[b]->c;
-    const bool coarse = ensure_coarse(c, o.patch_nodes > 0 ? o.patch_nodes : kBatchPatchNodes);
+    const bool coarse = o.patch_nodes < 0 ? c.coarse != nullptr
+                                          : ensure_coarse(c, o.patch_nodes > 0 ? o.patch_nodes : kBatchPatchNodes);
     for (int j = 0; j < c.nrhs; ++j, ++k2) {
       sfem_solve_opts so{};
       so.kind = SFEM_SOLVE_IR32_64;
@@ -1128,7 +1129,7 @@ extern "C" int sfem_batch_solve(sfem_ctx *const *ctxs, int n, double *const *u, 
     const int max_iter = opts->max_iter > 0 ? opts->max_iter : 200000;
     const int max_rounds = opts->max_rounds > 0 ? opts->max_rounds : 400;
     SFEM_REQUIRE(opts->precond >= 0 && opts->precond <= 2, SFEM_EINVAL, "precond must be 0, 1 or 2");
-    SFEM_REQUIRE(opts->patch_nodes >= 0 && opts->patch_nodes <= 4096, SFEM_EINVAL, "patch_nodes out of range");
+    SFEM_REQUIRE(opts->patch_nodes >= -1 && opts->patch_nodes <= 4096, SFEM_EINVAL, "patch_nodes out of range");
     if (opts->precond == 1) return batch_two_level(ctxs, n, u, *opts, tol, max_iter, infos, stats);
     auto get = [&](size_t bytes) {
       void *p = c0->mem.raw(bytes);
@@ -1152,8 +1153,10 @@ extern "C" int sfem_batch_solve(sfem_ctx *const *ctxs, int n, double *const *u, 
     if (two_level)
       for (int b = 0; b < n; ++b) {
         Ctx &c = ctxs[b]->c;
-        if (ensure_coarse(c, opts->patch_nodes > 0 ? opts->patch_nodes : kBatchPatchNodes))
-          cvec_len += 2 * (int64_t)c.coarse->dev.npad * c.nrhs;
+        const bool cs_on = opts->patch_nodes < 0 ? c.coarse != nullptr
+                                                  : ensure_coarse(c, opts->patch_nodes > 0 ? opts->patch_nodes
+                                                                                           : kBatchPatchNodes);
+        if (cs_on) cvec_len += 2 * (int64_t)c.coarse->dev.npad * c.nrhs;
       }
     float *cvec = cvec_len ? (float *)get(cvec_len * sizeof(float)) : nullptr;
     int64_t coff = 0;
@@ -1453,7 +1456,7 @@ extern "C" int sfem_batch_solve(sfem_ctx *const *ctxs, int n, double *const *u, 
         sfem_solve_opts so{};
         so.kind = SFEM_SOLVE_PCG64;
         so.op64 = SFEM_OP_MF64;
-        so.precond = ensure_coarse(c) ? 1 : 0;
+        so.precond = (opts->patch_nodes < 0 ? c.coarse != nullptr : ensure_coarse(c)) ? 1 : 0;
         so.rhs = j;
         so.u_on_device = 1;
         so.warm_start = 1;

@@ -173,3 +173,39 @@ def test_batch_persistent_two_level_uneven_beams(S):
     finally:
         for c in ctxs:
             c.close()
+
+
+def test_batch_in_launch_two_level_with_jacobi_beams(S):
+    """precond = 2 with patch_nodes = -1: only the contexts that have a coarse
+    space (three of six here) use the two-level preconditioner, the others
+    run Jacobi inside the same persistent launch; every system reaches 1e-8
+    and agrees with FP64 PCG of its context, and no coarse space is built."""
+    import torch
+    probs = [p for p in batch_beams(64, seed=5) if p.mesh.n_tets < 60000][:6]
+    ctxs = [S.FsFem(p) for p in probs]
+    try:
+        for k in (0, 2, 4):
+            S.sfem_coarse_setup(ctxs[k].h)
+        us = [torch.zeros((p.nrhs, c.ndof), dtype=torch.float64, device="cuda") for p, c in zip(probs, ctxs)]
+        n_sys = sum(p.nrhs for p in probs)
+        infos, st = S.sfem_batch_solve([c.h for c in ctxs], us,
+                                       S.batch_opts(tol=1e-8, u_on_device=True, precond=2, patch_nodes=-1), n_sys)
+        assert all(i["status"] == S.SFEM_OK and i["true_relres"] <= 1e-8 for i in infos), infos
+        for k in (1, 3, 5):  # still without a coarse space
+            with pytest.raises(S.SfemError):
+                S.sfem_coarse_info(ctxs[k].h)
+        # two-level beams need far fewer iterations than the Jacobi beams of similar size
+        its = [sum(i["iterations"] for i in infos[4 * k:4 * k + 4]) for k in range(len(probs))]
+        print("\nper-beam iterations (two-level on beams 0, 2, 4):", its)
+        for k in (0, 1):
+            c = ctxs[k]
+            for r in range(probs[k].nrhs):
+                x = np.zeros(c.ndof)
+                S.sfem_solve(c.h, x, S.solve_opts(kind=S.SFEM_SOLVE_PCG64, rhs=r, tol=1e-9), check=False)
+                assert np.linalg.norm(us[k][r].cpu().numpy() - x) <= 1e-5 * np.linalg.norm(x)
+        with pytest.raises(S.SfemError):
+            S.sfem_batch_solve([c.h for c in ctxs], us, S.batch_opts(precond=2, patch_nodes=-2, u_on_device=True),
+                               n_sys)
+    finally:
+        for c in ctxs:
+            c.close()

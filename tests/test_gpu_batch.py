@@ -209,3 +209,39 @@ def test_batch_in_launch_two_level_with_jacobi_beams(S):
     finally:
         for c in ctxs:
             c.close()
+
+
+@pytest.mark.parametrize("precond", [0, 2])
+def test_batch_many_systems_mixed_load_cases(S, precond):
+    """110 small beams with 1 to 4 load cases each (273 systems: more than one
+    block-wide pass of the kernel's per-system loops and work lists): every
+    system reaches 1e-8, and a sample agrees with single-system FP64 PCG."""
+    import torch
+    rng = np.random.default_rng(11)
+    probs = []
+    for b in range(110):
+        cells = (int(rng.integers(4, 9)), int(rng.integers(2, 4)), int(rng.integers(2, 4)))
+        mesh = kuhn_beam(*cells, dims=(float(rng.uniform(2, 5)), 1.0, 1.0), jitter=0.1, seed=500 + b)
+        dofs, vals = clamp_dofs(mesh, 0, 0)
+        tris, trac = four_load_cases(mesh)
+        k = 1 + b % 4
+        probs.append(Problem(mesh, float(rng.uniform(50e9, 300e9)), float(rng.uniform(0.2, 0.45)), dofs, vals,
+                             tris, trac[:k]))
+    ctxs = [S.FsFem(p) for p in probs]
+    try:
+        us = [torch.zeros((p.nrhs, c.ndof), dtype=torch.float64, device="cuda") for p, c in zip(probs, ctxs)]
+        n_sys = sum(p.nrhs for p in probs)
+        assert n_sys == 273
+        infos, st = S.sfem_batch_solve([c.h for c in ctxs], us,
+                                       S.batch_opts(tol=1e-8, u_on_device=True, precond=precond), n_sys)
+        assert st["n_systems"] == n_sys
+        assert all(i["status"] == S.SFEM_OK and i["true_relres"] <= 1e-8 for i in infos)
+        for k in (0, 37, 74, 109):
+            c = ctxs[k]
+            for r in range(probs[k].nrhs):
+                x = np.zeros(c.ndof)
+                S.sfem_solve(c.h, x, S.solve_opts(kind=S.SFEM_SOLVE_PCG64, rhs=r, tol=1e-9), check=False)
+                assert np.linalg.norm(us[k][r].cpu().numpy() - x) <= 1e-5 * np.linalg.norm(x)
+    finally:
+        for c in ctxs:
+            c.close()

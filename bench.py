@@ -323,19 +323,28 @@ def batch_form(S):
                            "fallback_systems": stats["fallback_systems"],
                            "fallback_s": round(stats["fallback_ms"] / 1e3, 4)}
 
-        _, tl = run(S.batch_opts(tol=TOL, u_on_device=True, autotune=True, use_graph=True, precond=2), True)
+        i_tl, tl = run(S.batch_opts(tol=TOL, u_on_device=True, autotune=True, use_graph=True, precond=2), True)
         cinfo = [S.sfem_coarse_info(c.h) for c in ctxs]  # built by the first call, kept by the contexts
-        _, seq = run(S.batch_opts(tol=TOL, u_on_device=True, precond=1), True)
-        infos, jac = run(S.batch_opts(tol=TOL, u_on_device=True, autotune=True, use_graph=True), False)
+        i_seq, seq = run(S.batch_opts(tol=TOL, u_on_device=True, precond=1), True)
+        i_jac, jac = run(S.batch_opts(tol=TOL, u_on_device=True, autotune=True, use_graph=True), False)
         seq["note"] = "precond=1: each system by the two-level mixed solve of its context"
         jac["note"] = "precond=0: first call (its autotune rounds included)"
         tets = sum(p.mesh.n_tets for p in probs)
-        # effective operator bytes of the Jacobi launch: every CG iteration of
-        # every system reads its beam's operator data (72 B/tet) and two FP64
-        # vectors (16 B/DOF)
-        eff = sum(inf["iterations"] * (72 * p.mesh.n_tets + 16 * 3 * p.mesh.n_nodes)
-                  for p, k in zip(probs, range(len(probs))) for inf in infos[4 * k:4 * k + 4])
-        jac["effective_operator_GBps"] = eff / jac["time_s"] / 1e9
+
+        # effective operator bandwidth of a mode: every CG iteration of every
+        # system counts its beam's operator data (72 B/tet) and the operator's
+        # input and output vectors (8 B/DOF in FP32) once, over the mode's time
+        def eff_gbps(infos, t):
+            sys_it = [i["iterations"] for i in infos]
+            b, k = 0, 0
+            for p in probs:
+                for _ in range(p.nrhs):
+                    b += sys_it[k] * (72 * p.mesh.n_tets + 8 * 3 * p.mesh.n_nodes)
+                    k += 1
+            return b / t / 1e9
+
+        for d, inf in ((tl, i_tl), (seq, i_seq), (jac, i_jac)):
+            d["effective_operator_GBps"] = eff_gbps(inf, d["time_s"])
         out = {"beams": len(probs), "systems": n_sys, "total_tets": tets,
                "mode": "precond=2: the two-level preconditioner inside the persistent launch",
                "coarse": {"patch_nodes": 6, "n_coarse_mean": sum(i["n_coarse"] for i in cinfo) / len(cinfo),

@@ -18,7 +18,12 @@
 //      residual replacement with the search direction kept.
 // Rounds repeat (as a captured CUDA graph) until no system is active.
 // Per-system scalars are double-buffered by iteration parity so that no
-// block reads a value another block is writing.
+// block reads a value another block is writing.  At the start of every
+// iteration each block rebuilds, in shared memory, the lists of the active
+// beams and systems (every block from the same flags, so the lists agree),
+// and every phase walks those lists: inactive systems cost nothing, and the
+// active work splits evenly over the grid (the P2 and P3 of the Jacobi mode
+// split the active systems' DOFs; the decisions run one system per thread).
 //
 // precond = 2 runs the same rounds with the two-level preconditioner
 // z = D^-1 r + P Pi C Pi^T r of each beam's coarse space (coarse.cu) inside

@@ -555,6 +555,22 @@ int sfem_time_operator(sfem_ctx *ctx, int op, int reps, double *ms_per_apply);
 int sfem_selftest_barrier(sfem_ctx *ctx, int *status, double *wait_ms);
 int64_t sfem_launch_count(void);
 
+/* sfem_gemm_f32 — diagnostic (no counterpart in the paper): the FP32 GEMM
+ * that trains both learned corrections, alone.  C = op(A) op(B), row-major,
+ * M x N with inner dimension K; op(A) = A^T when ta != 0 (A stored K x M,
+ * leading dimension lda), else A (M x K); op(B) = B^T when tb != 0 (B stored
+ * N x K), else B (K x N).  All three are DEVICE pointers of the current
+ * device (not overlapping C); the call runs on its legacy default stream,
+ * synchronises, and writes the GEMM's device time to *ms (may be NULL).
+ * K = 0 writes zeros (A and B may then be NULL).
+ * Tensor cores (tcgen05, TF32 operands split in three products for FP32
+ * accuracy, FP32 accumulation), split over K when the output has fewer
+ * 128 x 128 tiles than the device has SMs.  Returns SFEM_EINVAL for bad
+ * sizes, leading dimensions or NULL pointers, SFEM_ETIMEOUT if a CTA gave up waiting for its
+ * MMAs (C is then incomplete), SFEM_ECUDA on a CUDA error. */
+int sfem_gemm_f32(int M, int N, int K, const float *A, int lda, int ta, const float *B, int ldb, int tb, float *C,
+                  int ldc, double *ms);
+
 /* sfem_tile_info — diagnostic (no counterpart in the paper): the layout of
  * the FP32 tiled operator of a context.  Writes up to n of, in order:
  *   [0] tiles, [1] largest halo (tets), [2] largest node list, [3] length of

@@ -69,6 +69,7 @@ struct CNet {
         *dy = nullptr, *d2 = nullptr, *d1 = nullptr;
   float *split = nullptr;
   size_t split_floats = 0;
+  int *gemm_err = nullptr;  // set by a tensor-core GEMM whose wait ran out
 };
 
 // device scalars of one solve (and of one correction)
@@ -426,7 +427,7 @@ __global__ void k_cn_gather_rows(const float *__restrict__ X, const float *__res
 
 static void cn_gemm(CNet &L, int M, int N, int K, const float *A, int lda, bool tA, const float *B, int ldb, bool tB,
                     float *C, int ldc) {
-  mlp_gemm(L.mem, L.split, L.split_floats, L.stream, M, N, K, A, lda, tA, B, ldb, tB, C, ldc);
+  mlp_gemm(L.mem, L.split, L.split_floats, L.stream, M, N, K, A, lda, tA, B, ldb, tB, C, ldc, L.gemm_err);
 }
 
 static void cn_ensure_cap(CNet &L, int64_t rows) {
@@ -529,6 +530,7 @@ static double cn_train(CNet &L, const float *X, const float *T, int64_t rows, in
     SFEM_CUDA(cudaStreamSynchronize(L.stream));
     last = s / (double)rows;
   }
+  check_gemm_err(L.gemm_err, L.stream);
   return last;
 }
 
@@ -592,7 +594,7 @@ static void cn_random_rows(CNet &L, const CoarseDev &cs, float *X, float *T, int
     SFEM_CHECK_LAUNCH();
     k_cn_rownorm<<<(unsigned)count, 256, 0, st>>>(Tr, nc);
     SFEM_CHECK_LAUNCH();
-    SFEM_CUDA(cudaStreamSynchronize(st));
+    check_gemm_err(L.gemm_err, st);
   } catch (...) {
     L.mem.drop(Cd);
     throw;
@@ -863,6 +865,8 @@ extern "C" int sfem_cnet_create(sfem_cnet **out, sfem_ctx *h, const sfem_cnet_op
     SFEM_CUDA(cudaMemsetAsync(L.tickets, 0, 8 * sizeof(unsigned int), L.stream));
     L.loss = L.mem.get<double>(2);
     SFEM_CUDA(cudaMemsetAsync(L.loss, 0, 2 * sizeof(double), L.stream));
+    L.gemm_err = L.mem.get<int>(1);
+    SFEM_CUDA(cudaMemsetAsync(L.gemm_err, 0, sizeof(int), L.stream));
     k_cn_init<<<grid_for(L.np, 256), 256, 0, L.stream>>>(L.theta, L.wbf, L.np, L.oB1, L.oW2, L.oB2, L.oW3, L.oB3,
                                                          (int)n, hid, opts ? opts->seed : 0ull);
     SFEM_CHECK_LAUNCH();
@@ -955,7 +959,7 @@ extern "C" int sfem_cnet_loss_grad(sfem_cnet *m, const float *X, const float *T,
     SFEM_CUDA(cudaMemcpyAsync(grad, L.grad, L.np * sizeof(float), cudaMemcpyDeviceToDevice, L.stream));
   double lh[2];
   SFEM_CUDA(cudaMemcpyAsync(lh, L.loss, sizeof lh, cudaMemcpyDeviceToHost, L.stream));
-  SFEM_CUDA(cudaStreamSynchronize(L.stream));
+  check_gemm_err(L.gemm_err, L.stream);
   if (loss) *loss = lh[0];
   CN_END
 }
@@ -1038,4 +1042,44 @@ extern "C" int sfem_cnet_solve(sfem_cnet *m, sfem_ctx *h, const sfem_solve_opts 
   if (info) *info = local;
   if (local.status != SFEM_OK) set_last_error(sfem_strerror(local.status));
   return local.status;
+}
+
+// the training GEMM of both learned corrections, alone (device pointers,
+// the legacy default stream of the current device)
+extern "C" int sfem_gemm_f32(int M, int N, int K, const float *A, int lda, int ta, const float *B, int ldb, int tb,
+                             float *C, int ldc, double *ms) {
+  if (!(M >= 1 && N >= 1 && K >= 0 && C && (K == 0 || (A && B)))) {
+    set_last_error("M, N >= 1, K >= 0, C and (for K > 0) A, B required");
+    return SFEM_EINVAL;
+  }
+  if (!(lda >= (ta ? M : std::max(K, 1)) && ldb >= (tb ? std::max(K, 1) : N) && ldc >= N)) {
+    set_last_error("leading dimensions too small");
+    return SFEM_EINVAL;
+  }
+  Allocator mem;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int status = SFEM_OK;
+  try {
+    float *split = nullptr;
+    size_t split_floats = 0;
+    int *err = mem.get<int>(1);
+    SFEM_CUDA(cudaMemsetAsync(err, 0, sizeof(int), nullptr));
+    SFEM_CUDA(cudaEventCreate(&e0));
+    SFEM_CUDA(cudaEventCreate(&e1));
+    SFEM_CUDA(cudaEventRecord(e0, nullptr));
+    mlp_gemm(mem, split, split_floats, nullptr, M, N, K, A, lda, ta != 0, B, ldb, tb != 0, C, ldc, err);
+    SFEM_CUDA(cudaEventRecord(e1, nullptr));
+    check_gemm_err(err, nullptr);
+    float t = 0.f;
+    SFEM_CUDA(cudaEventElapsedTime(&t, e0, e1));
+    if (ms) *ms = t;
+  } catch (const Error &err) {
+    set_last_error(err.msg);
+    status = err.status;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaStreamSynchronize(nullptr);
+  mem.release_all();
+  return status;
 }

@@ -81,6 +81,7 @@ struct Learned {
         *dy = nullptr, *d2 = nullptr, *d1 = nullptr;
   float *split = nullptr;     // split-K partial products
   size_t split_floats = 0;
+  int *gemm_err = nullptr;    // set by a tensor-core GEMM whose wait ran out
 };
 
 // ---- patches, pooling, features, prolongation ------------------------------
@@ -290,7 +291,7 @@ __global__ void k_sub(const double *a, const double *b, int64_t n, double *out) 
 
 static void gemm(Learned &L, int M, int N, int K, const float *A, int lda, bool tA, const float *B, int ldb, bool tB,
                  float *C, int ldc) {
-  mlp_gemm(L.mem, L.split, L.split_floats, L.stream, M, N, K, A, lda, tA, B, ldb, tB, C, ldc);
+  mlp_gemm(L.mem, L.split, L.split_floats, L.stream, M, N, K, A, lda, tA, B, ldb, tB, C, ldc, L.gemm_err);
 }
 
 static void ensure_cap(Learned &L, int64_t rows) {
@@ -474,6 +475,8 @@ extern "C" int sfem_learned_create(sfem_learned **out, sfem_ctx *h, const sfem_l
     L.partials = L.mem.get<double>(std::max(L.P, 4096));
     L.tickets = L.mem.get<unsigned int>(8);
     L.loss = L.mem.get<double>(2);
+    L.gemm_err = L.mem.get<int>(1);
+    SFEM_CUDA(cudaMemsetAsync(L.gemm_err, 0, sizeof(int), L.stream));
     SFEM_CUDA(cudaMemsetAsync(L.tickets, 0, 8 * sizeof(unsigned int), L.stream));
     SFEM_CUDA(cudaMemsetAsync(L.mom, 0, kNParams * sizeof(float), L.stream));
     SFEM_CUDA(cudaMemsetAsync(L.vel, 0, kNParams * sizeof(float), L.stream));
@@ -596,7 +599,7 @@ extern "C" int sfem_learned_loss_grad(sfem_learned *m, const float *X, const flo
   if (grad)
     SFEM_CUDA(cudaMemcpyAsync(grad, L.grad, kNParams * sizeof(float), cudaMemcpyDeviceToDevice, L.stream));
   if (loss) SFEM_CUDA(cudaMemcpyAsync(loss, L.loss, sizeof(double), cudaMemcpyDeviceToHost, L.stream));
-  SFEM_CUDA(cudaStreamSynchronize(L.stream));
+  check_gemm_err(L.gemm_err, L.stream);
   LRN_END
 }
 
@@ -646,7 +649,7 @@ extern "C" int sfem_learned_train(sfem_learned *m, const float *X, const float *
     SFEM_CUDA(cudaStreamSynchronize(L.stream));
     *loss = acc / (double)rows;
   }
-  SFEM_CUDA(cudaStreamSynchronize(L.stream));
+  check_gemm_err(L.gemm_err, L.stream);
   LRN_END
 }
 

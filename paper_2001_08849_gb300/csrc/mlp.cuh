@@ -1,5 +1,6 @@
 // Generic kernels of the small MLPs of the learned corrections (learned.cu:
-// per-patch network; cnet.cu: coarse network): FP32 GEMM, bias + GELU,
+// per-patch network; cnet.cu: coarse network): FP32 GEMM on the tensor
+// cores (tc_gemm.cuh), bias + GELU,
 // squared-error loss, GELU backward, column sums, Adam, BF16 rounding, the
 // counter-based generator of the initial weights.  Internal linkage: each
 // translation unit that includes this header has its own copy.
@@ -12,71 +13,9 @@
 
 #include "reduce.cuh"
 #include "sfem_internal.cuh"
+#include "tc_gemm.cuh"
 
 namespace sfem {
-
-// out[z] = op(A)[M x K-range z] op(B); row-major; op(A) = A^T when TA (A is
-// stored K x M), op(B) = B^T when TB (B stored N x K).  64x64 tiles, 4x4
-// outputs per thread, K split over gridDim.z ranges of k_split.
-template <bool TA, bool TB>
-static __global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, const float *__restrict__ A, int lda,
-                                              const float *__restrict__ B, int ldb, float *__restrict__ out,
-                                              int ldo, int64_t out_stride, int k_split) {
-  __shared__ float As[16][68];
-  __shared__ float Bs[16][68];
-  const int tid = threadIdx.x;
-  const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
-  const int kb = blockIdx.z * k_split, ke = min(K, kb + k_split);
-  const int tm = (tid >> 4) * 4, tn = (tid & 15) * 4;
-  float acc[4][4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-  for (int k0 = kb; k0 < ke; k0 += 16) {
-#pragma unroll
-    for (int l = 0; l < 4; ++l) {
-      const int e = tid + l * 256;
-      const int mm = TA ? (e & 63) : (e >> 4), kk = TA ? (e >> 6) : (e & 15);
-      const int gm = m0 + mm, gk = k0 + kk;
-      float v = 0.f;
-      if (gm < M && gk < ke) v = TA ? A[(int64_t)gk * lda + gm] : A[(int64_t)gm * lda + gk];
-      As[kk][mm] = v;
-    }
-#pragma unroll
-    for (int l = 0; l < 4; ++l) {
-      const int e = tid + l * 256;
-      const int nn = TB ? (e >> 4) : (e & 63), kk = TB ? (e & 15) : (e >> 6);
-      const int gn = n0 + nn, gk = k0 + kk;
-      float v = 0.f;
-      if (gn < N && gk < ke) v = TB ? B[(int64_t)gn * ldb + gk] : B[(int64_t)gk * ldb + gn];
-      Bs[kk][nn] = v;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < 16; ++kk) {
-      float a[4], b[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        a[i] = As[kk][tm + i];
-        b[i] = Bs[kk][tn + i];
-      }
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
-    }
-    __syncthreads();
-  }
-  float *o = out + (int64_t)blockIdx.z * out_stride;
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int gm = m0 + tm + i, gn = n0 + tn + j;
-      if (gm < M && gn < N) o[(int64_t)gm * ldo + gn] = acc[i][j];
-    }
-}
 
 // C[M x N] = sum over z of part[z] (fixed order)
 static __global__ void k_sum_splits(const float *__restrict__ part, int splits, int M, int N, float *__restrict__ C, int ldc) {
@@ -159,16 +98,34 @@ static __host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
   return x ^ (x >> 31);
 }
 
-// C = op(A) op(B) (row-major, FP32) by k_gemm, split over K for small grids
-// (partial products in `split`, grown as needed, summed in a fixed order)
+template <bool TA, bool TB>
+static void launch_gemm_tc(dim3 grid, cudaStream_t st, int M, int N, int K, const float *A, int lda, const float *B,
+                           int ldb, float *out, int ldo, int64_t stride, int k_split, int *err) {
+  static bool attr[64] = {};  // the shared-memory attribute, set once per device
+  int dev = 0;
+  SFEM_CUDA(cudaGetDevice(&dev));
+  if (dev >= 64 || !attr[dev]) {
+    SFEM_CUDA(cudaFuncSetAttribute(k_gemm_tc<TA, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem));
+    if (dev < 64) attr[dev] = true;
+  }
+  k_gemm_tc<TA, TB><<<grid, kTcThreads, kTcSmem, st>>>(M, N, K, A, lda, B, ldb, out, ldo, stride, k_split, err);
+}
+
+// C = op(A) op(B) (row-major, FP32) by k_gemm_tc, split over K when the
+// output tiles alone would leave SMs idle (partial products in `split`,
+// grown as needed, summed in a fixed order).  *err (device) is set when a
+// CTA's wait for its MMAs ran out.
 static void mlp_gemm(Allocator &mem, float *&split, size_t &split_floats, cudaStream_t st, int M, int N, int K,
-                     const float *A, int lda, bool tA, const float *B, int ldb, bool tB, float *C, int ldc) {
-  const int tiles = ((M + 63) / 64) * ((N + 63) / 64);
+                     const float *A, int lda, bool tA, const float *B, int ldb, bool tB, float *C, int ldc, int *err) {
+  int dev = 0, sms = 0;
+  SFEM_CUDA(cudaGetDevice(&dev));
+  SFEM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int tiles = ((M + kTcBM - 1) / kTcBM) * ((N + kTcBN - 1) / kTcBN);
   int splits = 1;
-  if (tiles < 64 && K >= 512) splits = std::min(64, std::max(1, K / 256));
-  const int k_split = ((K + splits - 1) / splits + 15) / 16 * 16;
-  splits = (K + k_split - 1) / k_split;
-  dim3 grid((N + 63) / 64, (M + 63) / 64, splits);
+  if (tiles < sms && K >= 4 * kTcBK) splits = std::min((sms + tiles - 1) / tiles, K / (2 * kTcBK));
+  const int k_split = ((K + splits - 1) / splits + kTcBK - 1) / kTcBK * kTcBK;
+  splits = k_split > 0 ? (K + k_split - 1) / k_split : 1;
+  dim3 grid((N + kTcBN - 1) / kTcBN, (M + kTcBM - 1) / kTcBM, splits);
   float *out = C;
   int ldo = ldc;
   int64_t stride = 0;
@@ -184,17 +141,29 @@ static void mlp_gemm(Allocator &mem, float *&split, size_t &split_floats, cudaSt
     stride = (int64_t)M * N;
   }
   if (tA && tB)
-    k_gemm<true, true><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, out, ldo, stride, k_split);
+    launch_gemm_tc<true, true>(grid, st, M, N, K, A, lda, B, ldb, out, ldo, stride, k_split, err);
   else if (tA)
-    k_gemm<true, false><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, out, ldo, stride, k_split);
+    launch_gemm_tc<true, false>(grid, st, M, N, K, A, lda, B, ldb, out, ldo, stride, k_split, err);
   else if (tB)
-    k_gemm<false, true><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, out, ldo, stride, k_split);
+    launch_gemm_tc<false, true>(grid, st, M, N, K, A, lda, B, ldb, out, ldo, stride, k_split, err);
   else
-    k_gemm<false, false><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, out, ldo, stride, k_split);
+    launch_gemm_tc<false, false>(grid, st, M, N, K, A, lda, B, ldb, out, ldo, stride, k_split, err);
   SFEM_CHECK_LAUNCH();
   if (splits > 1) {
     k_sum_splits<<<grid_for((int64_t)M * N, 256), 256, 0, st>>>(split, splits, M, N, C, ldc);
     SFEM_CHECK_LAUNCH();
+  }
+}
+
+// throws SFEM_ETIMEOUT when a tensor-core GEMM since the last check reported
+// a wait that ran out (the word is cleared)
+static void check_gemm_err(int *err, cudaStream_t st) {
+  int h = 0;
+  SFEM_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  SFEM_CUDA(cudaStreamSynchronize(st));
+  if (h) {
+    SFEM_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+    throw Error{SFEM_ETIMEOUT, "a tensor-core GEMM gave up waiting for its MMAs"};
   }
 }
 

@@ -137,6 +137,8 @@ _SIG = {
     "sfem_version": (ctypes.c_int, []),
     "sfem_time_operator": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "sfem_launch_count": (ctypes.c_int64, []),
+    "sfem_gemm_f32": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, ctypes.c_int, _P,
+                                     ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "sfem_tile_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64), ctypes.c_int]),
     "sfem_apply_noalloc": (ctypes.c_int, [_P, _P, _P]),
     "sfem_batch_solve": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(_P),
@@ -434,6 +436,25 @@ def sfem_time_operator(h, op=SFEM_OP_MF32, reps=20) -> float:
 
 def sfem_launch_count() -> int:
     return int(lib.sfem_launch_count())
+
+
+def sfem_gemm_f32(A, B, ta=False, tb=False, C=None) -> tuple:
+    """(C, ms): C = op(A) op(B) for contiguous FP32 CUDA tensors (op(X) = X^T
+    when its flag is set) by the tensor-core training GEMM; ms is its device
+    time."""
+    M = A.shape[1] if ta else A.shape[0]
+    K = A.shape[0] if ta else A.shape[1]
+    N = B.shape[0] if tb else B.shape[1]
+    if (B.shape[1] if tb else B.shape[0]) != K:
+        raise ValueError("inner dimensions differ")
+    if C is None:
+        import torch
+        C = torch.empty((M, N), dtype=torch.float32, device=A.device)
+    ms = ctypes.c_double()
+    lda, ldb = max(A.shape[1], 1), max(B.shape[1], 1)  # an empty operand (K = 0) is never read
+    _check(lib.sfem_gemm_f32(M, N, K, _ptr(A), lda, int(bool(ta)), _ptr(B), ldb, int(bool(tb)),
+                             _ptr(C), C.shape[1], ctypes.byref(ms)), "sfem_gemm_f32")
+    return C, ms.value
 
 
 TILE_INFO_KEYS = ("n_tiles", "max_halo", "max_nodes", "slot_stride", "total_halo", "total_nodes",

@@ -50,6 +50,11 @@ def test_argument_checks_without_gpu(S):
     assert S.lib.sfem_tile_info(None, None, 1) == S.SFEM_EINVAL
     assert S.lib.sfem_assemble(None, None) == S.SFEM_EINVAL
     assert S.lib.sfem_solve(None, None, None, None, None) == S.SFEM_EINVAL
+    # the tensor-core GEMM checks sizes, pointers and leading dimensions first
+    assert S.lib.sfem_gemm_f32(0, 1, 1, None, 1, 0, None, 1, 0, None, 1, None) == S.SFEM_EINVAL
+    buf = ctypes.c_void_p(16)  # never dereferenced: the checks fail first
+    assert S.lib.sfem_gemm_f32(4, 4, 8, buf, 4, 0, buf, 4, 0, buf, 4, None) == S.SFEM_EINVAL  # lda < K
+    assert S.lib.sfem_gemm_f32(4, 4, 8, buf, 8, 0, buf, 4, 0, buf, 3, None) == S.SFEM_EINVAL  # ldc < N
     S.lib.sfem_destroy(None)
     assert re.search(r"\w", S.lib.sfem_last_error().decode())
 

@@ -41,6 +41,7 @@
 namespace sfem {
 
 constexpr int kCB = 64;           // dense block order
+static_assert(kCB == 64, "k_cs_symv maps 128 threads to 64 x 64 blocks");
 constexpr int64_t kMaxCoarse = 8192;  // coarse DOFs (3 per centre)
 constexpr int kRestrictThreads = 256;
 
@@ -114,11 +115,14 @@ __global__ void k_cs_gather(CoarseDev cs, const int *done) {
 // operator's records evict it from L2; keeping it there with an evict-last
 // policy, or marking the records evict-first, measured no faster).  One CTA
 // per block: the block is read once with evict-first loads and applied
-// twice, C_ab rc_b to yc_a and C_ab^T rc_a to yc_b (a > b), by FP32
+// twice, C_ab rc_b to yc_a (row sums from registers) and C_ab^T rc_a to yc_b
+// (a > b; column sums from a shared-memory copy of the block), by FP32
 // atomics; yc must be zero before.
 // With rzc, rc.C rc is added to *rzc as well (rc_a.C_ab rc_b, twice for
 // a > b; one FP64 atomic per block).
-__global__ void __launch_bounds__(256) k_cs_symv(CoarseDev cs, const int *done, double *rzc) {
+constexpr int kSymvThreads = 128;  // two rows per thread; 9 CTAs per SM: the 1275 blocks of 3150 DOFs in one wave
+
+__global__ void __launch_bounds__(kSymvThreads, 9) k_cs_symv(CoarseDev cs, const int *done, double *rzc) {
   if (done && *done) return;
   const int t = blockIdx.x;
   int a = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
@@ -130,54 +134,59 @@ __global__ void __launch_bounds__(256) k_cs_symv(CoarseDev cs, const int *done, 
     ra[threadIdx.x] = cs.rc[a * kCB + threadIdx.x];
     rb[threadIdx.x] = cs.rc[b * kCB + threadIdx.x];
   }
-  // thread: row i = tid / 4, columns 16 q .. 16 q + 15 (q = tid % 4)
+  // thread: rows i and i + 32 (i = tid / 4), columns 16 q .. 16 q + 15 (q = tid % 4);
+  // off-diagonal blocks are also copied to shared memory (rows padded to 65
+  // floats) for the transposed product
+  __shared__ float bs[kCB][kCB + 1];
+  __shared__ float part[2][kCB];
   const int i = threadIdx.x >> 2, q = threadIdx.x & 3;
   const float4 *blk = reinterpret_cast<const float4 *>(cs.C + (int64_t)t * kCB * kCB) + i * (kCB / 4) + q * 4;
-  float4 v[4];
+  float4 v[2][4];
 #pragma unroll
-  for (int u = 0; u < 4; ++u) v[u] = __ldcs(blk + u);
+  for (int h = 0; h < 2; ++h)
+#pragma unroll
+    for (int u = 0; u < 4; ++u) v[h][u] = __ldcs(blk + h * 32 * (kCB / 4) + u);
+  if (a != b)
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        float *dst = &bs[i + 32 * h][16 * q + 4 * u];
+        dst[0] = v[h][u].x;
+        dst[1] = v[h][u].y;
+        dst[2] = v[h][u].z;
+        dst[3] = v[h][u].w;
+      }
   __syncthreads();
   const float *rbq = rb + 16 * q;
-  float s = 0.f;
+  float s[2];
 #pragma unroll
-  for (int u = 0; u < 4; ++u)
-    s = fmaf(v[u].x, rbq[4 * u], fmaf(v[u].y, rbq[4 * u + 1], fmaf(v[u].z, rbq[4 * u + 2], fmaf(v[u].w, rbq[4 * u + 3], s))));
-  s += __shfl_xor_sync(0xffffffffu, s, 1);
-  s += __shfl_xor_sync(0xffffffffu, s, 2);
-  if (q == 0) atomicAdd(&cs.yc[a * kCB + i], s);
+  for (int h = 0; h < 2; ++h) {
+    float x = 0.f;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      x = fmaf(v[h][u].x, rbq[4 * u],
+               fmaf(v[h][u].y, rbq[4 * u + 1], fmaf(v[h][u].z, rbq[4 * u + 2], fmaf(v[h][u].w, rbq[4 * u + 3], x))));
+    x += __shfl_xor_sync(0xffffffffu, x, 1);
+    x += __shfl_xor_sync(0xffffffffu, x, 2);
+    s[h] = x;
+    if (q == 0) atomicAdd(&cs.yc[a * kCB + i + 32 * h], x);
+  }
   if (rzc) {  // whole block (rzc is uniform)
-    float e = q == 0 ? ra[i] * s * (a == b ? 1.f : 2.f) : 0.f;
-    e = block_sum_f<256>(e);
+    float e = q == 0 ? (ra[i] * s[0] + ra[i + 32] * s[1]) * (a == b ? 1.f : 2.f) : 0.f;
+    e = block_sum_f<kSymvThreads>(e);
     if (threadIdx.x == 0) atomicAdd(rzc, (double)e);
   }
   if (a == b) return;  // a whole block: uniform
-  // C_ab^T ra: column j = 16 q + 4 u + w gets v[u].{x,y,z,w} * ra[i]; sum over i
-  // within the warp (8 rows), then over the 8 warps in shared memory
-  const float ri = ra[i];
-  float c[16];
+  // C_ab^T ra: thread (column j = tid % 64, rows 32 p .. 32 p + 31 with
+  // p = tid / 64) sums C_ab[i][j] ra[i]; then the two halves are added
+  const int j = threadIdx.x & (kCB - 1), p = threadIdx.x / kCB;
+  float x = 0.f;
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    c[4 * u] = v[u].x * ri;
-    c[4 * u + 1] = v[u].y * ri;
-    c[4 * u + 2] = v[u].z * ri;
-    c[4 * u + 3] = v[u].w * ri;
-  }
-#pragma unroll
-  for (int k = 0; k < 16; ++k)
-#pragma unroll
-    for (int o = 4; o < 32; o <<= 1) c[k] += __shfl_xor_sync(0xffffffffu, c[k], o);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  __shared__ float part[kCB / 8][kCB];  // per warp, per column
-  if (lane < 4)
-#pragma unroll
-    for (int k = 0; k < 16; ++k) part[warp][16 * lane + k] = c[k];
+  for (int r = 0; r < 32; ++r) x = fmaf(bs[32 * p + r][j], ra[32 * p + r], x);
+  part[p][j] = x;
   __syncthreads();
-  if (threadIdx.x < kCB) {
-    float x = 0.f;
-#pragma unroll
-    for (int w = 0; w < kCB / 8; ++w) x += part[w][threadIdx.x];
-    atomicAdd(&cs.yc[b * kCB + threadIdx.x], x);
-  }
+  if (threadIdx.x < kCB) atomicAdd(&cs.yc[b * kCB + threadIdx.x], part[0][threadIdx.x] + part[1][threadIdx.x]);
 }
 
 // ---- probing -----------------------------------------------------------------
@@ -851,7 +860,7 @@ __global__ void k_cs_apply_z(CoarseDev cs, const double *__restrict__ r, const d
 
 void coarse_gemv(const CoarseDev &cs, cudaStream_t st, const int *done, double *rzc) {
   const int nb = cs.npad / kCB;
-  k_cs_symv<<<nb * (nb + 1) / 2, 256, 0, st>>>(cs, done, rzc);
+  k_cs_symv<<<nb * (nb + 1) / 2, kSymvThreads, 0, st>>>(cs, done, rzc);
   SFEM_CHECK_LAUNCH();
 }
 

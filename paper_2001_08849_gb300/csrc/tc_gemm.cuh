@@ -113,20 +113,36 @@ __device__ __forceinline__ void tf32_split(float x, float &hi, float &lo) {
 // byte offset of element (row r, K index k) of an operand tile
 __device__ __forceinline__ int tc_off(int r, int k) { return r * 128 + ((((k >> 2) ^ r) & 7) << 4) + ((k & 3) << 2); }
 
+// Element (row, k) of this thread's i-th slot (i = 0..31) of an operand
+// tile.  KMajor (K contiguous in global memory, X[row * ld + k]): warp w
+// takes rows 4i + w, lane = k: one load reads a 128-byte row and the 32
+// stores hit 32 banks.  Otherwise (X[k * ld + row]): slot i of warp w is the
+// group of 8 rows x 4 k with index P = 4i + w (rows 8 (P % 16) .., k
+// 4 (P / 16) ..), lane l = row % 8 + 8 (k % 4): one load reads four 32-byte
+// runs of rows, and the swizzle sends the 32 stores to 32 banks.
+template <bool KMajor>
+__device__ __forceinline__ void tc_slot(int i, int &row, int &k) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (KMajor) {
+    row = 4 * i + warp;
+    k = lane;
+  } else {
+    const int P = 4 * i + warp;
+    row = 8 * (P & 15) + (lane & 7);
+    k = 4 * (P >> 4) + (lane >> 3);
+  }
+}
+
 // This thread's 32 elements of one operand tile for the K chunk at k0:
 // element (r0 + row, k) of op(X) for A (rows = M) or of op(B)^T for B (rows
-// = N).  KMajor: K is contiguous in global memory (X[row * ld + k]); warp w
-// takes rows 4i + w (i = 0..31), lane = k.  Otherwise X[k * ld + row]: warp
-// w takes k = 8w + j (j = 0..7) for the rows 32q + lane (q = 0..3).  Either
-// way one load instruction reads 32 consecutive floats.
+// = N), slots as tc_slot.
 template <bool KMajor>
 __device__ __forceinline__ void tc_fetch(const float *__restrict__ X, int ld, int r0, int rows, int k0, int kend,
                                          float (&v)[32]) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
   for (int i = 0; i < 32; ++i) {
-    const int row = KMajor ? 4 * i + warp : 32 * (i & 3) + lane;
-    const int k = KMajor ? lane : 8 * warp + (i >> 2);
+    int row, k;
+    tc_slot<KMajor>(i, row, k);
     const int r = r0 + row, kk = k0 + k;
     v[i] = 0.f;
     if (r < rows && kk < kend) v[i] = KMajor ? __ldg(X + (int64_t)r * ld + kk) : __ldg(X + (int64_t)kk * ld + r);
@@ -137,11 +153,10 @@ __device__ __forceinline__ void tc_fetch(const float *__restrict__ X, int ld, in
 // positions (the same element order as tc_fetch)
 template <bool KMajor>
 __device__ __forceinline__ void tc_stage(const float (&v)[32], uint8_t *hi, uint8_t *lo) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
   for (int i = 0; i < 32; ++i) {
-    const int row = KMajor ? 4 * i + warp : 32 * (i & 3) + lane;
-    const int k = KMajor ? lane : 8 * warp + (i >> 2);
+    int row, k;
+    tc_slot<KMajor>(i, row, k);
     const int off = tc_off(row, k);
     float h, l;
     tf32_split(v[i], h, l);

@@ -92,3 +92,56 @@ def test_two_level_pcg_reaches_the_direct_solution_faster_than_jacobi():
     assert np.linalg.norm(x - x_ref) <= 1e-7 * np.linalg.norm(x_ref)
     itj = OS.jacobi_pcg(A, b, tol=1e-10).iterations
     assert it2 < itj / 2, (it2, itj)
+
+
+def test_galerkin_matrix_equals_the_per_tet_gradient_form():
+    """A second derivation of A_c = Pi^T P K P Pi, from the definition of K
+    rather than from the assembled matrix: K = sum_k V_k Bbar_k^T D Bbar_k with
+    V_k Bbar_k = sum over the tets e of face k of (V_e / 4) B_e (Eq. 2-3, Eq. 9),
+    hence K = sum_e (V_e / 4) B_e^T D sum_{faces k of e} Bbar_k.  For the coarse
+    functions w_I e_a (hat weights w_I masked by the clamp) the tet gradient is
+    x_I = sum_nodes w_I grad N and the face-smoothed one of face k is
+    (V_e x_I^e + V_n x_I^n) / (V_e + V_n) (x_I^e on the exterior).  With
+    isotropic D (Lame lambda, mu) the 3x3 block of centres I, J is then
+    sum_e (V_e / 4) [lambda x_I y_J^T + mu y_J x_I^T + mu (x_I . y_J) I]
+    with y_J the sum of tet e's four face-smoothed gradients.  A wrong shear
+    factor, a transposed block or a dropped face fails this."""
+    p, K, A, b, free = _system((10, 3, 3))
+    m = p.mesh
+    xyz, tets = m.xyz, m.tets.astype(np.int64)
+    dims = (4, 2, 2)
+    Pi = C.prolongation(xyz, dims, free)
+    Ac_ref = C.galerkin(A, Pi)
+    P = int(np.prod(dims))
+    # hat weights per node and centre; the clamp prescribes whole nodes, so
+    # the three components carry the same masked weight
+    Pd = Pi.toarray()
+    W = Pd[0::3, 0::3]
+    assert np.array_equal(W, Pd[1::3, 1::3]) and np.array_equal(W, Pd[2::3, 2::3])
+    # tet volumes and shape-function gradients from the vertex coordinates
+    X4 = xyz[tets]                                     # (ne, 4, 3)
+    J = (X4[:, 1:] - X4[:, :1])                        # rows: edge vectors
+    V = np.abs(np.linalg.det(J)) / 6.0
+    Ginv = np.linalg.inv(J)                            # columns: grad N_1..3
+    grad = np.concatenate([-Ginv.sum(axis=2, keepdims=True), Ginv], axis=2).transpose(0, 2, 1)  # (ne, 4, 3)
+    X = np.einsum("eaj,eai->eji", W[tets], grad)       # (ne, P, 3): x_I of every tet
+    faces = F.build_faces(m.tets)
+    Y = np.zeros_like(X)
+    e0, e1 = faces.tet[:, 0], faces.tet[:, 1]
+    inner = e1 >= 0
+    gbar = X[e0].copy()
+    ve, vn = V[e0[inner]], V[e1[inner]]
+    gbar[inner] = (ve[:, None, None] * X[e0[inner]] + vn[:, None, None] * X[e1[inner]]) / (ve + vn)[:, None, None]
+    np.add.at(Y, e0, gbar)
+    np.add.at(Y, e1[inner], gbar[inner])
+    E, nu = p.E, p.nu
+    lam, mu = E * nu / ((1 + nu) * (1 - 2 * nu)), E / (2 * (1 + nu))
+    w = V / 4.0
+    T1 = np.einsum("e,eia,ejc->iajc", w, X, Y)
+    T2 = np.einsum("e,eic,eja->iajc", w, X, Y)
+    T3 = np.einsum("e,eib,ejb->ij", w, X, Y)
+    Ac = lam * T1 + mu * T2 + mu * np.einsum("ij,ac->iajc", T3, np.eye(3))
+    Ac = Ac.reshape(3 * P, 3 * P)
+    scale = np.abs(Ac_ref).max()
+    assert scale > 0
+    assert np.abs(Ac - Ac_ref).max() <= 1e-10 * scale, np.abs(Ac - Ac_ref).max() / scale

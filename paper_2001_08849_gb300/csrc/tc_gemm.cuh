@@ -1,7 +1,8 @@
 // FP32 GEMM of the learned corrections' training on the fifth-generation
 // tensor cores: tcgen05.mma of kind tf32 issued by one thread per CTA,
 // operands in shared memory, the 128 x 128 FP32 accumulator tile in tensor
-// memory (TMEM), read back by tcgen05.ld for the epilogue.
+// memory (TMEM), read back by tcgen05.ld and stored through shared memory
+// as coalesced rows.
 //
 // Accuracy: the 3xTF32 split of Ootomo and Yokota (2022, "Recovering single
 // precision accuracy from Tensor Cores while surpassing the FP32 theoretical
@@ -14,8 +15,10 @@
 // Shared-memory operand layout (K-major, 128-byte swizzle): an operand tile
 // of 128 rows x 32 K elements stores row r in the 128 bytes at r * 128, its
 // 16-byte chunk c (elements 4c .. 4c + 3) at chunk position c ^ (r % 8);
-// groups of 8 rows are 1024 bytes apart.  A warp stages one row per step:
-// a coalesced 128-byte load and 32 stores to 32 distinct banks.  One MMA
+// groups of 8 rows are 1024 bytes apart.  A warp stages one row per step
+// when K is contiguous in global memory (a coalesced 128-byte load), else 8
+// rows x 4 K values (four 32-byte loads); either way its 32 stores hit 32
+// distinct banks.  One MMA
 // consumes K = 8 (32 bytes of every row): its descriptor starts 32 bytes
 // further per step, the hardware applying the same swizzle.
 //

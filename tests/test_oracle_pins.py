@@ -417,3 +417,30 @@ def test_penalty_converges_to_elimination():
         errs.append(np.linalg.norm(up - u0) / np.linalg.norm(u0))
         assert np.abs(up[dofs] - vals).max() <= 1e3 / a * np.abs(u0).max()
     assert 30 < errs[0] / errs[1] < 300, errs
+
+
+def test_sliver_quality_and_mesh_validation():
+    """Sliver quality: 1 for the regular tet, invariant under scaling,
+    rotation and node order, 0 for a flat tet, 6 sqrt(2) V / l_rms^3 on the
+    unit right tet (V = 1/6, three unit edges and three sqrt(2) edges).  Mesh
+    validation rejects out-of-range ids, non-finite coordinates and a
+    malformed connectivity."""
+    reg = np.array([[1.0, 1.0, 1.0], [1.0, -1.0, -1.0], [-1.0, 1.0, -1.0], [-1.0, -1.0, 1.0]])
+    t = np.array([[0, 1, 2, 3]])
+    assert abs(F.sliver_quality(reg, t)[0] - 1.0) < 1e-14
+    c, s = np.cos(0.7), np.sin(0.7)
+    R = np.array([[c, -s, 0.0], [s, c, 0.0], [0.0, 0.0, 1.0]])
+    moved = 3.5 * reg @ R.T + np.array([2.0, -1.0, 0.5])
+    assert abs(F.sliver_quality(moved, np.array([[2, 0, 3, 1]]))[0] - 1.0) < 1e-13
+    flat = np.array([[0.0, 0.0, 0.0], [1.0, 0.0, 0.0], [0.0, 1.0, 0.0], [1.0, 1.0, 0.0]])
+    assert F.sliver_quality(flat, t)[0] == 0.0
+    right = np.array([[0.0, 0.0, 0.0], [1.0, 0.0, 0.0], [0.0, 1.0, 0.0], [0.0, 0.0, 1.0]])
+    l_rms = np.sqrt((3 * 1.0 + 3 * 2.0) / 6.0)
+    assert abs(F.sliver_quality(right, t)[0] - 6 * np.sqrt(2) / 6 / l_rms ** 3) < 1e-14
+    F.validate(right, t)
+    with pytest.raises(ValueError):
+        F.validate(right, np.array([[0, 1, 2, 4]]))
+    with pytest.raises(ValueError):
+        F.validate(np.where(np.arange(12).reshape(4, 3) == 5, np.nan, right), t)
+    with pytest.raises(ValueError):
+        F.validate(right, np.array([[0, 1, 2]]))

@@ -59,3 +59,33 @@ def test_reference_arm_other_ranks_do_no_work():
         warmup, steps, gpus = 1, 1, 2
 
     assert bench.run_reference(A(), 1, 2) is None  # returns at once: no oracle run on rank 1
+
+
+def test_compare_keys_flatten_the_forms():
+    """The comparison forms become flat top-level keys of the bench line:
+    time, iterations and residual per form (learned: the mean over held-out
+    loads and its gains), the batched modes' throughputs; a form that failed
+    or is missing adds nothing."""
+    import bench
+
+    one = {"time_to_solve_s": 1.5, "iterations": 100, "true_relres": 9e-9}
+    forms = {
+        "pcg64_csr_jacobi": dict(one),
+        "pcg64_mf64_jacobi": {"error": "out of memory"},
+        "ir32_64_two_level": dict(one, iterations=345),
+        "learned_coarse": {"learned": [dict(one, time_to_solve_s=2.0), dict(one, time_to_solve_s=4.0, iterations=300,
+                                                                             true_relres=8e-9)],
+                           "iteration_gain": 0.5, "time_gain": 0.25},
+        "batch_64x4": {"solves_per_s": 248.0, "fallback_systems": 2, "jacobi": {"solves_per_s": 26.0},
+                       "two_level_per_system": {"solves_per_s": 55.0}},
+    }
+    k = bench.compare_keys(forms)
+    assert k["tts_pcg64_csr_jacobi_s"] == 1.5 and k["it_pcg64_csr_jacobi"] == 100
+    assert "tts_pcg64_mf64_jacobi_s" not in k and "tts_ir32_64_jacobi_s" not in k
+    assert k["it_ir32_64_two_level"] == 345
+    assert k["tts_learned_coarse_s"] == 3.0 and k["it_learned_coarse"] == 200
+    assert k["relres_learned_coarse"] == 9e-9
+    assert k["learned_coarse_iteration_gain"] == 0.5 and k["learned_coarse_time_gain"] == 0.25
+    assert k["batch_64x4_solves_per_s"] == 248.0 and k["batch_64x4_fallbacks"] == 2
+    assert k["batch_64x4_jacobi_solves_per_s"] == 26.0 and k["batch_64x4_per_system_solves_per_s"] == 55.0
+    assert bench.job_throughput(1, 10, 0.5) == 20.0

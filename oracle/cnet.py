@@ -36,10 +36,13 @@ HIDDEN = 128
 
 
 def dims(n_c: int, hidden: int = HIDDEN):
+    """Layer widths of the coarse network: n_c -> hidden -> hidden -> n_c
+    (returned as input, hidden and output width)."""
     return (n_c, hidden, n_c)
 
 
 def n_params(n_c: int, hidden: int = HIDDEN) -> int:
+    """Parameter count of the coarse network (oracle/mlp.py layout)."""
     return mlp.n_params(n_c, hidden, n_c)
 
 

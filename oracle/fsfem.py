@@ -49,6 +49,7 @@ def tet_volume_eq10(xyz: np.ndarray, tets: np.ndarray) -> np.ndarray:
 
 
 def tet_volumes(xyz, tets) -> np.ndarray:
+    """|V_e| of every tet (Eq. 10 without the orientation sign)."""
     return np.abs(tet_volume_eq10(xyz, tets))
 
 
@@ -274,6 +275,8 @@ def smoothing_domains_average(xyz, tets, faces: Faces) -> SmoothingDomains:
 # ---------------------------------------------------------------------------
 
 def lame(E: float, nu: float):
+    """Lame parameters (lambda, mu) of Young's modulus E and Poisson ratio nu
+    (isotropic linear elasticity, the material of Sec. 4)."""
     lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu))
     mu = E / (2.0 * (1.0 + nu))
     return lam, mu
@@ -375,6 +378,7 @@ class Assembly:
     n_triplets: int
 
     def matrix(self) -> sp.csr_matrix:
+        """The assembled stiffness as a scipy CSR matrix (3 n_nodes square)."""
         return sp.csr_matrix((self.data, self.indices, self.indptr), shape=(self.ndof, self.ndof))
 
 

@@ -32,10 +32,13 @@ N_IN, N_HID, N_OUT = 84, 128, 3
 
 
 def n_params(n_in=N_IN, hid=N_HID, n_out=N_OUT) -> int:
+    """Parameter count of the three-layer network: W1, b1, W2, b2, W3, b3."""
     return n_in * hid + hid + hid * hid + hid + hid * n_out + n_out
 
 
 def unpack(theta, n_in=N_IN, hid=N_HID, n_out=N_OUT):
+    """Split the flat parameter vector into (W1, b1, W2, b2, W3, b3), W row-major
+    (fan_in x fan_out)."""
     sizes = [(n_in, hid), (hid,), (hid, hid), (hid,), (hid, n_out), (n_out,)]
     out, k = [], 0
     for s in sizes:
@@ -46,6 +49,7 @@ def unpack(theta, n_in=N_IN, hid=N_HID, n_out=N_OUT):
 
 
 def pack(parts) -> np.ndarray:
+    """Inverse of unpack: the parts concatenated in order, FP64."""
     return np.concatenate([np.asarray(p, dtype=np.float64).ravel() for p in parts])
 
 
@@ -122,10 +126,12 @@ def prolong(c_patch: np.ndarray, dims, xyz, lo, ext) -> np.ndarray:
 # ---- network ------------------------------------------------------------------
 
 def gelu(x):
+    """GELU(x) = x Phi(x), Phi the standard normal CDF (Hendrycks and Gimpel 2016)."""
     return 0.5 * x * (1.0 + np.vectorize(math.erf)(x / math.sqrt(2.0)))
 
 
 def gelu_grad(x):
+    """d GELU / dx = Phi(x) + x phi(x), phi the standard normal density."""
     phi = np.exp(-0.5 * x * x) / math.sqrt(2.0 * math.pi)
     Phi = 0.5 * (1.0 + np.vectorize(math.erf)(x / math.sqrt(2.0)))
     return Phi + x * phi
